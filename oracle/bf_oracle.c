@@ -1,0 +1,674 @@
+/*
+ * bf_oracle.c -- FP64 CPU oracle for the joint-acceleration bilateral filter
+ * (Dai, Yuan, Zhang, "Speeding up the Bilateral Filter: A Joint Acceleration Way").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, includes or
+ * calls this file; only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark load it (through oracle/oracle.py).  It shares no code, header,
+ * table or constant generator with the CUDA path.
+ *
+ * Everything is plain double precision, written to be checked against the paper
+ * by eye:
+ *   - range coefficients: Eqs. (13)-(15) on [-P, P], integrals by composite
+ *     Romberg quadrature;
+ *   - 1-D Haar dictionary and coefficients: Eqs. (17)-(20), Gaussian integrals by
+ *     erf differences;
+ *   - 2-D separable Haar coefficients: Eq. (22) (product of 1-D factors);
+ *   - best N-term selection by largest |coefficient|: Sec. III-A, Eq. (11);
+ *     candidates limited to the first 20N range coefficients, App. B;
+ *   - O1 exact bilateral filter, Eq. (1);
+ *   - O2 direct evaluation of Eq. (1) with the approximated kernels of
+ *     Eqs. (30) and (33) (the definition of the approximation);
+ *   - O3 the paper's fast algorithm, Eqs. (34)-(36): basis images, signed
+ *     2-D boxes from App. A / Eq. (37), box sums by 2-D summed-area tables
+ *     (Eqs. (24)-(26)), weighting by cos/sin at I(x), divide.
+ *
+ * Readings of points the paper leaves open (all listed in the design doc):
+ *   - square spatial window |y-x|_inf <= R, R = round(3 sigma_s) by default,
+ *     Haar interval T_s = R + 1/2;
+ *   - Haar functions take the mean of their one-sided limits at a jump
+ *     (only the offset 0 can fall on a jump because T_s is a half-integer);
+ *   - the Haar dictionary is {phi, psi_00} plus levels j = 1..J with
+ *     J = ceil(log2(2 T_s));
+ *   - ranking by raw |c|; values within relative 1e-12 form a tie group ordered
+ *     by (max(j1,j2), j1, j2, k1, k2) with phi as level -1; range ties by k;
+ *     coefficients below 1e-14 of the largest are never selected;
+ *   - the kernel weight of neighbour y for centre x is K~_s(x - y) (Eq. (32));
+ *   - collapsed range policy: cosine half-period P >= (dI + T_r)/2 so the
+ *     range box of Eq. (33) is identically 1 on the data (Case 1 of Sec. V-C,
+ *     "extend the truncated region"); k = 0 is a candidate;
+ *   - pixels outside the image are excluded (zero padding, num and den);
+ *   - den <= 1e-6 * (sum |K~_s|)(sum |a_k|) -> output I(x) and count it.
+ *
+ * Parity pinned by tests/test_oracle_*.py; see the design doc for the pin list.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_OK 0
+#define ORC_EINVAL 1
+#define ORC_ECAP 2
+
+/* kernel kinds */
+#define ORC_GAUSSIAN 0
+#define ORC_EXPONENTIAL 1
+#define ORC_BOX 2
+
+/* range policies */
+#define ORC_TRUNCATED_MIN_PERIOD 0
+#define ORC_UNTRUNCATED_FULL 1
+#define ORC_PAPER_TRUNCATED 3 /* P = T_r exactly (the paper's own series, used for Table VII) */
+
+static const double ORC_PI = 3.14159265358979323846;
+
+/* ------------------------------------------------------------------ */
+/* Kernel profiles                                                      */
+/* ------------------------------------------------------------------ */
+
+/* Range kernel K_r(t) (Sec. I: symmetric, decreasing on R+). */
+static double range_kernel(int kind, double sigma, double t)
+{
+    double a = fabs(t);
+    switch (kind) {
+    case ORC_GAUSSIAN: return exp(-(t * t) / (2.0 * sigma * sigma));
+    case ORC_EXPONENTIAL: return exp(-a / sigma);
+    case ORC_BOX: return a <= sigma ? 1.0 : 0.0;
+    }
+    return 0.0;
+}
+
+/* Default truncation point T_r = K_r^{-1}(eps) (Sec. IV-A), with 3 sigma for the
+ * Gaussian as used in Sec. V-C, eps = 0.01 for the exponential, sigma for the box. */
+double orc_default_tr(int kind, double sigma_r)
+{
+    switch (kind) {
+    case ORC_GAUSSIAN: return 3.0 * sigma_r;
+    case ORC_EXPONENTIAL: return sigma_r * log(100.0);
+    case ORC_BOX: return sigma_r;
+    }
+    return 3.0 * sigma_r;
+}
+
+/* Cosine half-period for a policy; t_r already resolved. */
+double orc_period(int policy, double t_r, double data_range)
+{
+    if (policy == ORC_UNTRUNCATED_FULL) return data_range;
+    if (policy == ORC_PAPER_TRUNCATED) return t_r;
+    double p = 0.5 * (data_range + t_r);
+    return p > t_r ? p : t_r;
+}
+
+/* ------------------------------------------------------------------ */
+/* Range coefficients, Eqs. (13)-(15) on [-P, P]                        */
+/* ------------------------------------------------------------------ */
+
+typedef struct { int kind; double sigma; double omega; } rng_integrand;
+
+/* Integrand on [0, L], where L never exceeds the kernel's support: the box kernel is
+ * therefore 1 on the whole interval (its cut-off is applied through L). */
+static double rng_f(const rng_integrand *q, double t)
+{
+    double kv = q->kind == ORC_BOX ? 1.0 : range_kernel(q->kind, q->sigma, t);
+    return kv * cos(q->omega * t);
+}
+
+/* Romberg integration of q over [a, b] to an absolute tolerance. */
+static double romberg(const rng_integrand *q, double a, double b, double tol)
+{
+    double R[22][22];
+    double h = b - a;
+    R[0][0] = 0.5 * h * (rng_f(q, a) + rng_f(q, b));
+    for (int n = 1; n < 22; n++) {
+        h *= 0.5;
+        double s = 0.0;
+        long m = 1L << (n - 1);
+        for (long i = 1; i <= m; i++) s += rng_f(q, a + (2 * i - 1) * h);
+        R[n][0] = 0.5 * R[n - 1][0] + h * s;
+        double f4 = 1.0;
+        for (int j = 1; j <= n; j++) {
+            f4 *= 4.0;
+            R[n][j] = R[n][j - 1] + (R[n][j - 1] - R[n - 1][j - 1]) / (f4 - 1.0);
+        }
+        if (n >= 4 && fabs(R[n][n] - R[n - 1][n - 1]) <= tol + 1e-15 * fabs(R[n][n])) return R[n][n];
+    }
+    return R[21][21];
+}
+
+/* a[k], k = 0..ncand-1, of the kernel truncated at t_r, expanded on [-P, P]:
+ *   a_0 = (1/2P) int_{-P}^{P} K^T_r,  a_k = (1/P) int_{-P}^{P} K^T_r cos(pi k t / P).
+ * The integrand is even, so both reduce to int_0^{min(t_r,P)}. */
+int orc_range_coeffs(int kind, double sigma_r, double t_r, double P, int ncand, double *a)
+{
+    if (!(sigma_r > 0) || !(t_r > 0) || !(P > 0) || ncand < 1 || !a) return ORC_EINVAL;
+    double L = t_r < P ? t_r : P;
+    if (kind == ORC_BOX && sigma_r < L) L = sigma_r;
+    for (int k = 0; k < ncand; k++) {
+        rng_integrand q = { kind, sigma_r, ORC_PI * k / P };
+        /* composite rule: at least 8 pieces and 4 pieces per half-oscillation */
+        int pieces = 8 + (int)ceil(4.0 * k * L / P);
+        double h = L / pieces, s = 0.0;
+        for (int i = 0; i < pieces; i++) s += romberg(&q, i * h, i == pieces - 1 ? L : (i + 1) * h, 1e-16 * h);
+        a[k] = (k == 0 ? 1.0 : 2.0) * s / P;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* 1-D Haar dictionary on [-T, T], Eqs. (17)-(20)                      */
+/* ------------------------------------------------------------------ */
+
+/* Dictionary order: index 0 = phi (level -1), 1 = psi_{0,0} (level 0),
+ * then level j = 1..J with k = -2^{j-1}..-1, 1..2^{j-1}.  Size 2^{J+1}. */
+static void haar_index(int idx, int *lev, int *k)
+{
+    if (idx == 0) { *lev = -1; *k = 0; return; }
+    if (idx == 1) { *lev = 0; *k = 0; return; }
+    int j = 1;
+    while (idx >= (1 << (j + 1))) j++;
+    int off = idx - (1 << j); /* 0 .. 2^j - 1 */
+    int half = 1 << (j - 1);
+    *lev = j;
+    *k = off < half ? off - half : off - half + 1;
+}
+
+/* Support pieces of a 1-D Haar function: +1 on [lo, mid], -1 on [mid, hi]
+ * (phi: +1 on [-T, T], encoded with mid = hi). */
+static void haar_support(int lev, int k, double T, double *lo, double *mid, double *hi)
+{
+    if (lev < 0) { *lo = -T; *mid = T; *hi = T; return; }
+    double Z = (lev == 0) ? 0.0 : (k > 0 ? 1.0 : -1.0) * (2.0 * abs(k) - 1.0) * T; /* Z_k of App. A */
+    double s = ldexp(1.0, -lev);
+    *lo = s * (Z - T);
+    *mid = s * Z;
+    *hi = s * (Z + T);
+}
+
+/* Value of the Haar function at x; at a jump, the mean of the one-sided limits. */
+double orc_haar_eval(int lev, int k, double T, double x)
+{
+    double lo, mid, hi;
+    haar_support(lev, k, T, &lo, &mid, &hi);
+    if (lev < 0) {
+        if (x > lo && x < hi) return 1.0;
+        if (x == lo || x == hi) return 0.5;
+        return 0.0;
+    }
+    if (x > lo && x < mid) return 1.0;
+    if (x > mid && x < hi) return -1.0;
+    if (x == lo) return 0.5;
+    if (x == hi) return -0.5;
+    if (x == mid) return 0.0; /* (+1 + -1) / 2 */
+    return 0.0;
+}
+
+/* int_a^b K_s(x) dx for the 1-D spatial profile. */
+static double spatial_profile_int(int kind, double sigma, double a, double b)
+{
+    if (kind == ORC_GAUSSIAN) {
+        double s2 = sigma * sqrt(2.0);
+        return sigma * sqrt(ORC_PI / 2.0) * (erf(b / s2) - erf(a / s2));
+    }
+    /* box spatial kernel: constant 1 on the window */
+    return b - a;
+}
+
+int orc_haar_levels(double T) { return (int)ceil(log2(2.0 * T)); }
+
+/* 1-D coefficients (Eq. (20)): c_0 = int f phi / 2T, c_jk = 2^j int f psi_jk / 2T.
+ * Fills c[0 .. 2^{J+1}-1], and lev/kk with the (j, k) of each entry. */
+int orc_haar1d(int kind, double sigma_s, double T, int J, double *c, int *lev, int *kk)
+{
+    if (!(T > 0) || J < 0 || J > 20 || (kind != ORC_GAUSSIAN && kind != ORC_BOX)) return ORC_EINVAL;
+    int n = 1 << (J + 1);
+    for (int idx = 0; idx < n; idx++) {
+        int j, k;
+        double lo, mid, hi;
+        haar_index(idx, &j, &k);
+        haar_support(j, k, T, &lo, &mid, &hi);
+        double v;
+        if (j < 0) v = spatial_profile_int(kind, sigma_s, lo, hi) / (2.0 * T);
+        else v = ldexp(1.0, j) * (spatial_profile_int(kind, sigma_s, lo, mid) - spatial_profile_int(kind, sigma_s, mid, hi)) / (2.0 * T);
+        c[idx] = v;
+        if (lev) lev[idx] = j;
+        if (kk) kk[idx] = k;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Best N-term selection, Sec. III-A                                    */
+/* ------------------------------------------------------------------ */
+
+typedef struct { double mag; double c; int t1, t2; int key[5]; } cand2d;
+
+static int key_cmp(const int *a, const int *b)
+{
+    for (int i = 0; i < 5; i++) if (a[i] != b[i]) return a[i] < b[i] ? -1 : 1;
+    return 0;
+}
+
+static int cmp_mag_desc(const void *pa, const void *pb)
+{
+    const cand2d *a = pa, *b = pb;
+    if (a->mag > b->mag) return -1;
+    if (a->mag < b->mag) return 1;
+    return key_cmp(a->key, b->key);
+}
+
+static int cmp_key(const void *pa, const void *pb)
+{
+    const cand2d *a = pa, *b = pb;
+    return key_cmp(a->key, b->key);
+}
+
+/* Orders the candidates: |c| descending; a run of values within relative 1e-12 of
+ * the run's first value is one tie group, ordered by key. Returns count kept. */
+static int rank_candidates(cand2d *v, int n)
+{
+    double mx = 0;
+    for (int i = 0; i < n; i++) if (v[i].mag > mx) mx = v[i].mag;
+    int m = 0;
+    for (int i = 0; i < n; i++) if (v[i].mag >= 1e-14 * mx && v[i].mag > 0) v[m++] = v[i];
+    qsort(v, m, sizeof(cand2d), cmp_mag_desc);
+    int i = 0;
+    while (i < m) {
+        int j = i + 1;
+        while (j < m && v[j].mag >= v[i].mag * (1.0 - 1e-12)) j++;
+        qsort(v + i, j - i, sizeof(cand2d), cmp_key);
+        i = j;
+    }
+    return m;
+}
+
+/* Range selection: top nr of |a_k|, ties (relative 1e-12) by smaller k. */
+int orc_select_range(const double *a, int ncand, int nr, int *ks, double *aks)
+{
+    cand2d *v = malloc(sizeof(cand2d) * ncand);
+    if (!v) return -1;
+    for (int k = 0; k < ncand; k++) {
+        v[k].mag = fabs(a[k]);
+        v[k].c = a[k];
+        v[k].t1 = k; v[k].t2 = 0;
+        v[k].key[0] = k; v[k].key[1] = v[k].key[2] = v[k].key[3] = v[k].key[4] = 0;
+    }
+    int m = rank_candidates(v, ncand);
+    int n = nr < m ? nr : m;
+    for (int i = 0; i < n; i++) { ks[i] = v[i].t1; aks[i] = v[i].c; }
+    free(v);
+    return n;
+}
+
+/* ------------------------------------------------------------------ */
+/* Plan: everything the evaluators need                                */
+/* ------------------------------------------------------------------ */
+
+#define ORC_MAX_NR 256
+#define ORC_MAX_NS 4096
+
+typedef struct {
+    int R; double Ts; int J; int n1d;
+    double Tr, P;
+    int nr; int ks[ORC_MAX_NR]; double ak[ORC_MAX_NR];
+    int ns; int sl1[ORC_MAX_NS], sk1[ORC_MAX_NS], sl2[ORC_MAX_NS], sk2[ORC_MAX_NS]; double sc[ORC_MAX_NS];
+    int tie_split;
+    double *Ks; /* (2R+1)^2, Ks[(dy+R)(2R+1) + dx+R] = K~_s(dx, dy) by direct Haar evaluation */
+    double den_eps;
+} orc_plan;
+
+static void plan_free(orc_plan *p) { free(p->Ks); p->Ks = NULL; }
+
+static int plan_build(orc_plan *p, int skind, double sigma_s, int radius, int ns_terms,
+                      int rkind, double sigma_r, double t_r, int nr_terms, int policy, double data_range)
+{
+    memset(p, 0, sizeof(*p));
+    if (!(sigma_s > 0) || !(sigma_r > 0) || ns_terms < 1 || nr_terms < 1 || nr_terms > ORC_MAX_NR) return ORC_EINVAL;
+    if (ns_terms > ORC_MAX_NS) return ORC_ECAP;
+    if (skind != ORC_GAUSSIAN && skind != ORC_BOX) return ORC_EINVAL;
+    p->R = radius > 0 ? radius : (int)lround(3.0 * sigma_s);
+    if (radius < 0) return ORC_EINVAL;
+    p->Ts = p->R + 0.5;
+    p->J = orc_haar_levels(p->Ts);
+    p->n1d = 1 << (p->J + 1);
+    p->Tr = t_r > 0 ? t_r : orc_default_tr(rkind, sigma_r);
+    p->P = orc_period(policy, p->Tr, data_range);
+    double trq = (policy == ORC_UNTRUNCATED_FULL) ? p->P : p->Tr;
+    p->Tr = trq;
+
+    /* range: first 20 N coefficients (App. B), top N by |a_k| */
+    int ncand = 20 * nr_terms;
+    double *a = malloc(sizeof(double) * ncand);
+    if (!a) return ORC_ECAP;
+    orc_range_coeffs(rkind, sigma_r, trq, p->P, ncand, a);
+    p->nr = orc_select_range(a, ncand, nr_terms, p->ks, p->ak);
+    free(a);
+
+    /* spatial: separable 2-D Haar coefficients c(t1,t2) = c1(t1) c1(t2) (Eq. (22)) */
+    int n = p->n1d;
+    double *c1 = malloc(sizeof(double) * n);
+    int *lv = malloc(sizeof(int) * n), *kv = malloc(sizeof(int) * n);
+    cand2d *v = malloc(sizeof(cand2d) * (size_t)n * n);
+    if (!c1 || !lv || !kv || !v) { free(c1); free(lv); free(kv); free(v); return ORC_ECAP; }
+    orc_haar1d(skind, sigma_s, p->Ts, p->J, c1, lv, kv);
+    size_t m = 0;
+    for (int i1 = 0; i1 < n; i1++)
+        for (int i2 = 0; i2 < n; i2++) {
+            cand2d *e = &v[m++];
+            e->c = c1[i1] * c1[i2];
+            e->mag = fabs(e->c);
+            e->t1 = i1; e->t2 = i2;
+            int j1 = lv[i1], j2 = lv[i2];
+            e->key[0] = j1 > j2 ? j1 : j2;
+            e->key[1] = j1; e->key[2] = j2; e->key[3] = kv[i1]; e->key[4] = kv[i2];
+        }
+    int kept = rank_candidates(v, (int)m);
+    p->ns = ns_terms < kept ? ns_terms : kept;
+    for (int i = 0; i < p->ns; i++) {
+        p->sl1[i] = lv[v[i].t1]; p->sk1[i] = kv[v[i].t1];
+        p->sl2[i] = lv[v[i].t2]; p->sk2[i] = kv[v[i].t2];
+        p->sc[i] = v[i].c;
+    }
+    p->tie_split = (p->ns < kept && v[p->ns].mag >= v[p->ns - 1].mag * (1.0 - 1e-12)) ? 1 : 0;
+    free(c1); free(lv); free(kv); free(v);
+
+    /* K~_s(dx, dy) at integer offsets, Eq. (30) evaluated directly */
+    int w = 2 * p->R + 1;
+    p->Ks = calloc((size_t)w * w, sizeof(double));
+    if (!p->Ks) return ORC_ECAP;
+    for (int dy = -p->R; dy <= p->R; dy++)
+        for (int dx = -p->R; dx <= p->R; dx++) {
+            double s = 0.0;
+            for (int i = 0; i < p->ns; i++)
+                s += p->sc[i] * orc_haar_eval(p->sl1[i], p->sk1[i], p->Ts, dx) * orc_haar_eval(p->sl2[i], p->sk2[i], p->Ts, dy);
+            p->Ks[(dy + p->R) * w + (dx + p->R)] = s;
+        }
+    double sk = 0, sa = 0;
+    for (int i = 0; i < w * w; i++) sk += fabs(p->Ks[i]);
+    for (int i = 0; i < p->nr; i++) sa += fabs(p->ak[i]);
+    p->den_eps = 1e-6 * sk * sa;
+    return ORC_OK;
+}
+
+/* Plan summary for the tests.  Arrays sized by the caller: ks/ak >= nr_terms,
+ * terms (5 ints + 1 double each) >= ns_terms, Ks >= (2R+1)^2 (pass NULL to skip).
+ * ints_out: R, J, nr, ns, tie_split.  dbl_out: Ts, Tr, P, den_eps. */
+int orc_plan_info(int skind, double sigma_s, int radius, int ns_terms,
+                  int rkind, double sigma_r, double t_r, int nr_terms, int policy, double data_range,
+                  int *ints_out, double *dbl_out, int *ks, double *ak,
+                  int *term_idx, double *term_c, double *Ks, int Ks_cap)
+{
+    orc_plan p;
+    int st = plan_build(&p, skind, sigma_s, radius, ns_terms, rkind, sigma_r, t_r, nr_terms, policy, data_range);
+    if (st) { plan_free(&p); return st; }
+    ints_out[0] = p.R; ints_out[1] = p.J; ints_out[2] = p.nr; ints_out[3] = p.ns; ints_out[4] = p.tie_split;
+    dbl_out[0] = p.Ts; dbl_out[1] = p.Tr; dbl_out[2] = p.P; dbl_out[3] = p.den_eps;
+    for (int i = 0; i < p.nr; i++) { ks[i] = p.ks[i]; ak[i] = p.ak[i]; }
+    for (int i = 0; i < p.ns; i++) {
+        term_idx[4 * i + 0] = p.sl1[i]; term_idx[4 * i + 1] = p.sk1[i];
+        term_idx[4 * i + 2] = p.sl2[i]; term_idx[4 * i + 3] = p.sk2[i];
+        term_c[i] = p.sc[i];
+    }
+    int w = 2 * p.R + 1;
+    if (Ks) {
+        if (Ks_cap < w * w) { plan_free(&p); return ORC_ECAP; }
+        memcpy(Ks, p.Ks, sizeof(double) * w * w);
+    }
+    plan_free(&p);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* O1: exact bilateral filter, Eq. (1)                                  */
+/* ------------------------------------------------------------------ */
+
+static double spatial_kernel2d(int kind, double sigma, int dx, int dy)
+{
+    if (kind == ORC_BOX) return 1.0;
+    return exp(-(double)(dx * dx + dy * dy) / (2.0 * sigma * sigma));
+}
+
+/* out[y*W+x] for every pixel; window |y-x|_inf <= R (R = round(3 sigma_s) if radius == 0),
+ * range kernel not truncated.  rows/nrows restrict the output to a subset of rows
+ * (rows == NULL: all rows). */
+int orc_exact_bf(const double *I, int H, int W, int skind, double sigma_s, int radius,
+                 int rkind, double sigma_r, double *out, const int *rows, int nrows, int nthreads)
+{
+    if (!I || !out || H < 0 || W < 0 || !(sigma_s > 0) || !(sigma_r > 0) || radius < 0) return ORC_EINVAL;
+    int R = radius > 0 ? radius : (int)lround(3.0 * sigma_s);
+    int w = 2 * R + 1;
+    double *Ks = malloc(sizeof(double) * w * w);
+    if (!Ks) return ORC_ECAP;
+    for (int dy = -R; dy <= R; dy++)
+        for (int dx = -R; dx <= R; dx++) Ks[(dy + R) * w + dx + R] = spatial_kernel2d(skind, sigma_s, dx, dy);
+    int nr = rows ? nrows : H;
+    (void)nthreads;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+    for (int ri = 0; ri < nr; ri++) {
+        int y = rows ? rows[ri] : ri;
+        for (int x = 0; x < W; x++) {
+            double ix = I[(size_t)y * W + x], num = 0.0, den = 0.0;
+            for (int dy = -R; dy <= R; dy++) {
+                int yy = y + dy;
+                if (yy < 0 || yy >= H) continue;
+                for (int dx = -R; dx <= R; dx++) {
+                    int xx = x + dx;
+                    if (xx < 0 || xx >= W) continue;
+                    double iy = I[(size_t)yy * W + xx];
+                    double wgt = Ks[(dy + R) * w + dx + R] * range_kernel(rkind, sigma_r, ix - iy);
+                    num += wgt * iy;
+                    den += wgt;
+                }
+            }
+            out[(size_t)ri * W + x] = num / den;
+        }
+    }
+    free(Ks);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* O2: Eq. (1) with the approximated kernels (definition)               */
+/* ------------------------------------------------------------------ */
+
+int orc_approx_direct(const double *I, int H, int W,
+                      int skind, double sigma_s, int radius, int ns_terms,
+                      int rkind, double sigma_r, double t_r, int nr_terms, int policy, double data_range,
+                      double *out, int *ndegen, int nthreads)
+{
+    if (!I || !out || H < 0 || W < 0) return ORC_EINVAL;
+    orc_plan p;
+    int st = plan_build(&p, skind, sigma_s, radius, ns_terms, rkind, sigma_r, t_r, nr_terms, policy, data_range);
+    if (st) { plan_free(&p); return st; }
+    int R = p.R, w = 2 * R + 1;
+    int degen = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+:degen) num_threads(nthreads > 0 ? nthreads : 1)
+    for (int y = 0; y < H; y++) {
+        for (int x = 0; x < W; x++) {
+            double ix = I[(size_t)y * W + x], num = 0.0, den = 0.0;
+            for (int dy = -R; dy <= R; dy++) {
+                int yy = y + dy;
+                if (yy < 0 || yy >= H) continue;
+                for (int dx = -R; dx <= R; dx++) {
+                    int xx = x + dx;
+                    if (xx < 0 || xx >= W) continue;
+                    double iy = I[(size_t)yy * W + xx];
+                    /* spatial weight K~_s(x - y) = K~_s(-dx, -dy) */
+                    double ks = p.Ks[(-dy + R) * w + (-dx + R)];
+                    if (ks == 0.0) continue;
+                    double kr = 0.0, t = ix - iy;
+                    for (int i = 0; i < p.nr; i++) kr += p.ak[i] * cos(ORC_PI * p.ks[i] * t / p.P);
+                    num += ks * kr * iy;
+                    den += ks * kr;
+                }
+            }
+            if (den <= p.den_eps) { out[(size_t)y * W + x] = ix; degen++; }
+            else out[(size_t)y * W + x] = num / den;
+        }
+    }
+    if (ndegen) *ndegen = degen;
+    plan_free(&p);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* O3: the paper's algorithm, Eqs. (34)-(36) with App. A boxes          */
+/* ------------------------------------------------------------------ */
+
+/* A discrete 1-D range [lo, hi] of neighbour offsets with a weight. */
+typedef struct { int lo, hi; double w; } drange;
+
+/* The neighbour offsets d with x - (x + d) = -d in the closed continuous
+ * interval [a, b] (value v inside, v/2 at an integer endpoint):
+ * d in [-b, -a].  Written as one or two integer ranges with weights. */
+static int piece_to_ranges(double a, double b, double v, drange *out)
+{
+    double na = -b, nb = -a;
+    int lo_in = (int)ceil(na), hi_in = (int)floor(nb);          /* endpoints included */
+    int lo_ex = (int)floor(na) + 1, hi_ex = (int)ceil(nb) - 1;  /* endpoints excluded */
+    if (lo_in == lo_ex && hi_in == hi_ex) { out[0].lo = lo_in; out[0].hi = hi_in; out[0].w = v; return 1; }
+    out[0].lo = lo_in; out[0].hi = hi_in; out[0].w = 0.5 * v;
+    out[1].lo = lo_ex; out[1].hi = hi_ex; out[1].w = 0.5 * v;
+    return 2;
+}
+
+/* Pieces of one 1-D Haar function as neighbour-offset ranges (App. A:
+ * phi -> A, psi -> +A_1, -A_2). */
+static int haar_ranges(int lev, int k, double T, drange *out)
+{
+    double lo, mid, hi;
+    haar_support(lev, k, T, &lo, &mid, &hi);
+    if (lev < 0) return piece_to_ranges(lo, hi, 1.0, out);
+    int n = piece_to_ranges(lo, mid, 1.0, out);
+    n += piece_to_ranges(mid, hi, -1.0, out + n);
+    return n;
+}
+
+/* 2-D summed-area table with a zero row/column in front: S[(y+1)(W+1) + x+1]. */
+static void sat_build(const double *g, int H, int W, double *S)
+{
+    for (int x = 0; x <= W; x++) S[x] = 0.0;
+    for (int y = 0; y < H; y++) {
+        double c = 0.0;
+        S[(size_t)(y + 1) * (W + 1)] = 0.0;
+        for (int x = 0; x < W; x++) {
+            c += g[(size_t)y * W + x];
+            S[(size_t)(y + 1) * (W + 1) + x + 1] = S[(size_t)y * (W + 1) + x + 1] + c;
+        }
+    }
+}
+
+/* Sum of g over rows [y0, y1] x cols [x0, x1], clipped to the image (Eq. (26)). */
+static double sat_rect(const double *S, int H, int W, int x0, int x1, int y0, int y1)
+{
+    if (x0 < 0) x0 = 0;
+    if (y0 < 0) y0 = 0;
+    if (x1 > W - 1) x1 = W - 1;
+    if (y1 > H - 1) y1 = H - 1;
+    if (x0 > x1 || y0 > y1) return 0.0;
+    size_t P1 = (size_t)W + 1;
+    return S[(size_t)(y1 + 1) * P1 + x1 + 1] - S[(size_t)y0 * P1 + x1 + 1] - S[(size_t)(y1 + 1) * P1 + x0] + S[(size_t)y0 * P1 + x0];
+}
+
+typedef struct { int x0, x1, y0, y1; double c; } dbox;
+
+int orc_approx_fast(const double *I, int H, int W,
+                    int skind, double sigma_s, int radius, int ns_terms,
+                    int rkind, double sigma_r, double t_r, int nr_terms, int policy, double data_range,
+                    double *out, int *ndegen, int nthreads)
+{
+    if (!I || !out || H < 0 || W < 0) return ORC_EINVAL;
+    orc_plan p;
+    int st = plan_build(&p, skind, sigma_s, radius, ns_terms, rkind, sigma_r, t_r, nr_terms, policy, data_range);
+    if (st) { plan_free(&p); return st; }
+    size_t np = (size_t)H * W;
+    if (np == 0) { if (ndegen) *ndegen = 0; plan_free(&p); return ORC_OK; }
+
+    /* signed discrete boxes of Eq. (37): products of the 1-D piece ranges */
+    dbox *boxes = malloc(sizeof(dbox) * 16 * p.ns);
+    int nb = 0;
+    for (int i = 0; i < p.ns; i++) {
+        drange rx[4], ry[4];
+        int nx = haar_ranges(p.sl1[i], p.sk1[i], p.Ts, rx);
+        int ny = haar_ranges(p.sl2[i], p.sk2[i], p.Ts, ry);
+        for (int a = 0; a < nx; a++)
+            for (int b = 0; b < ny; b++) {
+                if (rx[a].lo > rx[a].hi || ry[b].lo > ry[b].hi) continue;
+                dbox *e = &boxes[nb++];
+                e->x0 = rx[a].lo; e->x1 = rx[a].hi; e->y0 = ry[b].lo; e->y1 = ry[b].hi;
+                e->c = p.sc[i] * rx[a].w * ry[b].w;
+            }
+    }
+
+    double *num = calloc(np, sizeof(double)), *den = calloc(np, sizeof(double));
+    double *g = malloc(sizeof(double) * np * 4);
+    double *S = malloc(sizeof(double) * (size_t)(H + 1) * (W + 1) * 4);
+    double *cb = malloc(sizeof(double) * np), *sb = malloc(sizeof(double) * np);
+    if (!num || !den || !g || !S || !cb || !sb || !boxes) {
+        free(num); free(den); free(g); free(S); free(cb); free(sb); free(boxes); plan_free(&p); return ORC_ECAP;
+    }
+    int nt = nthreads > 0 ? nthreads : 1;
+    for (int r = 0; r < p.nr; r++) {
+        double wk = ORC_PI * p.ks[r] / p.P, ak = p.ak[r];
+        /* basis images (Eq. (34)): cos(w I) I, sin(w I) I, cos(w I), sin(w I) */
+        for (size_t i = 0; i < np; i++) {
+            cb[i] = cos(wk * I[i]); sb[i] = sin(wk * I[i]);
+            g[i] = cb[i] * I[i]; g[np + i] = sb[i] * I[i]; g[2 * np + i] = cb[i]; g[3 * np + i] = sb[i];
+        }
+#pragma omp parallel for num_threads(nt)
+        for (int q = 0; q < 4; q++) sat_build(g + q * np, H, W, S + (size_t)q * (H + 1) * (W + 1));
+#pragma omp parallel for schedule(static) num_threads(nt)
+        for (int y = 0; y < H; y++)
+            for (int x = 0; x < W; x++) {
+                double F[4] = { 0, 0, 0, 0 };
+                for (int b = 0; b < nb; b++) {
+                    const dbox *e = &boxes[b];
+                    for (int q = 0; q < 4; q++)
+                        F[q] += e->c * sat_rect(S + (size_t)q * (H + 1) * (W + 1), H, W, x + e->x0, x + e->x1, y + e->y0, y + e->y1);
+                }
+                size_t i = (size_t)y * W + x;
+                num[i] += ak * (cb[i] * F[0] + sb[i] * F[1]);
+                den[i] += ak * (cb[i] * F[2] + sb[i] * F[3]);
+            }
+    }
+    int degen = 0;
+    for (size_t i = 0; i < np; i++) {
+        if (den[i] <= p.den_eps) { out[i] = I[i]; degen++; }
+        else out[i] = num[i] / den[i];
+    }
+    if (ndegen) *ndegen = degen;
+    free(num); free(den); free(g); free(S); free(cb); free(sb); free(boxes);
+    plan_free(&p);
+    return ORC_OK;
+}
+
+/* Number of signed discrete boxes O3 uses (for the cost report). */
+int orc_box_count(int skind, double sigma_s, int radius, int ns_terms,
+                  int rkind, double sigma_r, double t_r, int nr_terms, int policy, double data_range)
+{
+    orc_plan p;
+    int st = plan_build(&p, skind, sigma_s, radius, ns_terms, rkind, sigma_r, t_r, nr_terms, policy, data_range);
+    if (st) { plan_free(&p); return -st; }
+    int nb = 0;
+    for (int i = 0; i < p.ns; i++) {
+        drange rx[4], ry[4];
+        int nx = haar_ranges(p.sl1[i], p.sk1[i], p.Ts, rx);
+        int ny = haar_ranges(p.sl2[i], p.sk2[i], p.Ts, ry);
+        for (int a = 0; a < nx; a++)
+            for (int b = 0; b < ny; b++)
+                if (rx[a].lo <= rx[a].hi && ry[b].lo <= ry[b].hi) nb++;
+    }
+    plan_free(&p);
+    return nb;
+}
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,237 @@
+"""FP64 CPU oracle for the joint-acceleration bilateral filter.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by ``__graft_entry__.smoke()``
+and by the CPU-baseline leg of ``bench.py``.  The product library never loads
+it.  This wrapper compiles ``bf_oracle.c`` with gcc into ``oracle/_build`` and
+exposes numpy-level functions:
+
+* ``exact_bf``       -- O1, Eq. (1) by brute force;
+* ``approx_direct``  -- O2, Eq. (1) with the approximated kernels (Eqs. (30), (33));
+* ``approx_fast``    -- O3, the paper's algorithm (Eqs. (34)-(36), App. A boxes);
+* ``range_coeffs``, ``haar1d``, ``plan_info`` -- coefficient and selection steps.
+
+Every function follows the paper step by step; the C file header lists the
+passages and the readings taken where the paper is silent.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bf_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liborc.so")
+
+GAUSSIAN, EXPONENTIAL, BOX = 0, 1, 2
+TRUNCATED_MIN_PERIOD, UNTRUNCATED_FULL, PAPER_TRUNCATED = 0, 1, 3
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (gcc, -O2, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = C.CDLL(build())
+        d, i = C.c_double, C.c_int
+        pd, pi = C.POINTER(C.c_double), C.POINTER(C.c_int)
+        lib.orc_range_coeffs.argtypes = [i, d, d, d, i, pd]
+        lib.orc_haar1d.argtypes = [i, d, d, i, pd, pi, pi]
+        lib.orc_haar_eval.argtypes = [i, i, d, d]
+        lib.orc_haar_eval.restype = d
+        lib.orc_haar_levels.argtypes = [d]
+        lib.orc_default_tr.argtypes = [i, d]
+        lib.orc_default_tr.restype = d
+        lib.orc_period.argtypes = [i, d, d]
+        lib.orc_period.restype = d
+        lib.orc_select_range.argtypes = [pd, i, i, pi, pd]
+        lib.orc_plan_info.argtypes = [i, d, i, i, i, d, d, i, i, d, pi, pd, pi, pd, pi, pd, pd, i]
+        lib.orc_exact_bf.argtypes = [pd, i, i, i, d, i, i, d, pd, pi, i, i]
+        common = [pd, i, i, i, d, i, i, i, d, d, i, i, d, pd, pi, i]
+        lib.orc_approx_direct.argtypes = common
+        lib.orc_approx_fast.argtypes = common
+        lib.orc_box_count.argtypes = [i, d, i, i, i, d, d, i, i, d]
+        _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def max_threads() -> int:
+    return int(_load().orc_max_threads())
+
+
+@dataclass(frozen=True)
+class Desc:
+    """Filter parameters (mirrors the product's plan descriptor, defined separately)."""
+    spatial: int = GAUSSIAN
+    sigma_s: float = 4.0
+    radius: int = 0          # 0 -> round(3 sigma_s)
+    ns_terms: int = 5
+    range: int = GAUSSIAN
+    sigma_r: float = 0.1
+    t_r: float = 0.0         # 0 -> default truncation point
+    nr_terms: int = 8
+    policy: int = TRUNCATED_MIN_PERIOD
+    data_range: float = 1.0
+
+    def args(self):
+        return (self.spatial, self.sigma_s, self.radius, self.ns_terms, self.range,
+                self.sigma_r, self.t_r, self.nr_terms, self.policy, self.data_range)
+
+
+def range_coeffs(kind: int, sigma_r: float, t_r: float, period: float, ncand: int) -> np.ndarray:
+    a = np.zeros(ncand)
+    st = _load().orc_range_coeffs(kind, sigma_r, t_r, period, ncand, _dp(a))
+    if st:
+        raise ValueError("orc_range_coeffs status %d" % st)
+    return a
+
+
+def haar_levels(T: float) -> int:
+    return int(_load().orc_haar_levels(T))
+
+
+def haar1d(kind: int, sigma_s: float, T: float, J: int | None = None):
+    """1-D Haar coefficients in dictionary order; returns (c, level, k)."""
+    if J is None:
+        J = haar_levels(T)
+    n = 1 << (J + 1)
+    c = np.zeros(n)
+    lev = np.zeros(n, dtype=np.int32)
+    kk = np.zeros(n, dtype=np.int32)
+    st = _load().orc_haar1d(kind, sigma_s, T, J, _dp(c), _ip(lev), _ip(kk))
+    if st:
+        raise ValueError("orc_haar1d status %d" % st)
+    return c, lev, kk
+
+
+def haar_eval(lev: int, k: int, T: float, x: float) -> float:
+    return float(_load().orc_haar_eval(lev, k, T, x))
+
+
+def default_tr(kind: int, sigma_r: float) -> float:
+    return float(_load().orc_default_tr(kind, sigma_r))
+
+
+def period(policy: int, t_r: float, data_range: float = 1.0) -> float:
+    return float(_load().orc_period(policy, t_r, data_range))
+
+
+def select_range(a: np.ndarray, nr: int):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    ks = np.zeros(nr, dtype=np.int32)
+    aks = np.zeros(nr)
+    n = _load().orc_select_range(_dp(a), len(a), nr, _ip(ks), _dp(aks))
+    return ks[:n].copy(), aks[:n].copy()
+
+
+@dataclass
+class PlanInfo:
+    R: int
+    J: int
+    Ts: float
+    Tr: float
+    P: float
+    den_eps: float
+    ks: np.ndarray
+    ak: np.ndarray
+    terms: np.ndarray      # (ns, 4): lev1, k1, lev2, k2  (first factor: column offset)
+    term_c: np.ndarray
+    tie_split: bool
+    Ks: np.ndarray         # (2R+1, 2R+1) indexed [dy+R, dx+R] = K~_s(dx, dy)
+
+
+def plan_info(desc: Desc) -> PlanInfo:
+    lib = _load()
+    R = int(np.floor(3.0 * desc.sigma_s + 0.5)) if desc.radius == 0 else desc.radius
+    w = 2 * R + 1
+    ints = np.zeros(5, dtype=np.int32)
+    dbl = np.zeros(4)
+    ks = np.zeros(desc.nr_terms, dtype=np.int32)
+    ak = np.zeros(desc.nr_terms)
+    tid = np.zeros(4 * desc.ns_terms, dtype=np.int32)
+    tc = np.zeros(desc.ns_terms)
+    Ks = np.zeros(w * w)
+    st = lib.orc_plan_info(*desc.args(), _ip(ints), _dp(dbl), _ip(ks), _dp(ak), _ip(tid), _dp(tc), _dp(Ks), w * w)
+    if st:
+        raise ValueError("orc_plan_info status %d" % st)
+    nr, ns = int(ints[2]), int(ints[3])
+    return PlanInfo(R=int(ints[0]), J=int(ints[1]), Ts=float(dbl[0]), Tr=float(dbl[1]), P=float(dbl[2]),
+                    den_eps=float(dbl[3]), ks=ks[:nr].copy(), ak=ak[:nr].copy(),
+                    terms=tid[:4 * ns].reshape(ns, 4).copy(), term_c=tc[:ns].copy(),
+                    tie_split=bool(ints[4]), Ks=Ks.reshape(w, w))
+
+
+def _img(I):
+    I = np.ascontiguousarray(I, dtype=np.float64)
+    if I.ndim != 2:
+        raise ValueError("image must be 2-D")
+    return I
+
+
+def exact_bf(I, desc: Desc, rows=None, threads: int = 1) -> np.ndarray:
+    """O1: Eq. (1), Gaussian/box spatial kernel on the (2R+1)^2 square, untruncated range kernel."""
+    I = _img(I)
+    H, W = I.shape
+    if rows is None:
+        out = np.zeros((H, W))
+        rp, nr = None, 0
+    else:
+        rows = np.ascontiguousarray(rows, dtype=np.int32)
+        out = np.zeros((len(rows), W))
+        rp, nr = _ip(rows), len(rows)
+    st = _load().orc_exact_bf(_dp(I), H, W, desc.spatial, desc.sigma_s, desc.radius, desc.range,
+                              desc.sigma_r, _dp(out), rp, nr, threads)
+    if st:
+        raise ValueError("orc_exact_bf status %d" % st)
+    return out
+
+
+def approx_direct(I, desc: Desc, threads: int = 1):
+    """O2: returns (output, number of pixels where the denominator guard fired)."""
+    I = _img(I)
+    H, W = I.shape
+    out = np.zeros((H, W))
+    nd = np.zeros(1, dtype=np.int32)
+    st = _load().orc_approx_direct(_dp(I), H, W, *desc.args(), _dp(out), _ip(nd), threads)
+    if st:
+        raise ValueError("orc_approx_direct status %d" % st)
+    return out, int(nd[0])
+
+
+def approx_fast(I, desc: Desc, threads: int = 1):
+    """O3: returns (output, number of pixels where the denominator guard fired)."""
+    I = _img(I)
+    H, W = I.shape
+    out = np.zeros((H, W))
+    nd = np.zeros(1, dtype=np.int32)
+    st = _load().orc_approx_fast(_dp(I), H, W, *desc.args(), _dp(out), _ip(nd), threads)
+    if st:
+        raise ValueError("orc_approx_fast status %d" % st)
+    return out, int(nd[0])
+
+
+def box_count(desc: Desc) -> int:
+    return int(_load().orc_box_count(*desc.args()))
