@@ -1,0 +1,328 @@
+"""Benchmark of the GB300 bilateral filter (one JSON line on stdout).
+
+Workload (the 1920x1080 sweep): a seeded 1920x1080 float32 image of uniform
+rectangles and ellipses plus N(0, 0.03^2) noise; one step filters it once with
+each of the nine (sigma_s, sigma_r) in {2, 8, 32} x {0.05, 0.1, 0.3} (Gaussian
+kernels, N_r = 8 cosine terms, N_s = 5 Haar terms), i.e. 9 x 2,073,600 pixels.
+The metric is Mpixel/s over the step; every combination's PSNR against the exact
+bilateral filter (GPU brute force, untimed) is checked to be >= 40 dB.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the paper's algorithm, plain C) on
+the host cores, on a band of the same image.  Under torchrun each rank filters
+its own copy of the workload (weak scaling, replicas: the method has no
+exchange step); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H, W = 1080, 1920
+SIGMA_S = (2.0, 8.0, 32.0)
+SIGMA_R = (0.05, 0.1, 0.3)
+NR, NS = 8, 5
+METRIC = "Mpixel/s at >=40 dB vs exact BF (1920x1080, 9 sigma combos)"
+WORKLOAD = "1920x1080 shapes+noise(0.03), Gaussian/Gaussian, sigma_s in {2,8,32} x sigma_r in {0.05,0.1,0.3}, N_r=8, N_s=5"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(s[1]) for s in self.samples if num(s[1]) is not None]
+        mx = [num(s[2]) for s in self.samples if num(s[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[5 + i].lower() == "active"})
+        loaded = sorted(sm)[len(sm) // 4:] if sm else []
+        return {"sm_mhz": float(np.median(loaded)) if loaded else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def algorithmic_ops_per_pixel(coeffs: dict) -> float:
+    """FP32 operations per pixel of a separable running-sum evaluation of Eq. (36):
+    per basis image, 2 adds per vertical window, the window mixing (nonzero weights),
+    2 adds per horizontal window, one FMA into numerator/denominator; per cosine term
+    6 for the basis (angle-addition step and two products); the divide."""
+    nv, nh = len(coeffs["vwin"]), len(coeffs["hwin"])
+    nnz = sum(1 for r in coeffs["wcoef"] for v in r if abs(v) > 0)
+    nk = len(coeffs["k"])
+    nimg = 4 * nk - (2 if 0 in coeffs["k"] else 0)
+    per_img = 2 * nv + nnz + 2 * nh + 1
+    return nimg * per_img + 6 * nk + 2
+
+
+def run_ours(args):
+    import torch
+    import paper_1803_00004_gb300 as bf
+    from paper_1803_00004_gb300 import synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    img = synth.shapes(H, W, seed=0)
+    src = torch.from_numpy(img).to(dev)
+    plans = [bf.Plan(sigma_s=ss, sigma_r=sr, nr_terms=NR, ns_terms=NS, device=local) for ss in SIGMA_S for sr in SIGMA_R]
+    coeffs = [p.coeffs() for p in plans]
+    outs = [torch.empty_like(src) for _ in plans]
+    launches_per_step = sum(c["passes"] for c in coeffs)
+    stream = torch.cuda.current_stream(dev)
+
+    # accuracy against the exact filter (untimed)
+    psnr = []
+    ex = torch.empty_like(src)
+    for p, o, (ss, sr) in zip(plans, outs, [(a, b) for a in SIGMA_S for b in SIGMA_R]):
+        bf.bf_filter(p, src, o)
+        bf.bf_exact(src, ex, sigma_s=ss, sigma_r=sr)
+        torch.cuda.synchronize()
+        mse = torch.mean((o.double() - ex.double()) ** 2).item()
+        psnr.append(10 * np.log10(1.0 / mse) if mse > 0 else float("inf"))
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+
+    def step():
+        for p, o in zip(plans, outs):
+            bf.bf_filter(p, src, o, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    per_step = []
+    # per-launch device time of the dominant kernel: events around each launch
+    launch_ms = []
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(plans) + 1)]
+        e0.record(stream)
+        ev[0].record(stream)
+        for j, (p, o) in enumerate(zip(plans, outs)):
+            bf.bf_filter(p, src, o, stream=stream)
+            ev[j + 1].record(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per_step.append(e0.elapsed_time(e1))
+        launch_ms.append([ev[j].elapsed_time(ev[j + 1]) for j in range(len(plans))])
+    torch.cuda.synchronize()
+    sampler.stop()
+    total_ms = float(np.sum(per_step))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    px_step = len(plans) * H * W
+    value = world * px_step * args.steps / (total_ms * 1e-3) / 1e6
+    ms_per_step = total_ms / args.steps
+
+    # roofline of the dominant kernel (the fused filter kernel, one launch per plan)
+    lm = np.array(launch_ms)  # steps x plans
+    ops = sum(algorithmic_ops_per_pixel(c) for c in coeffs) * H * W
+    mean_launch_s = lm.mean() * 1e-3
+    ops_per_launch = ops / len(plans)
+    clocks = sampler.summary()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = clocks.get("sm_max_mhz") or 2070.0
+    alu_peak = sms * 128 * max_mhz * 1e6 / 1e12  # FP32 lanes x clock, T op/s
+    achieved = ops_per_launch / mean_launch_s / 1e12
+    hbm_gbs = 8.0 * H * W / mean_launch_s / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, bf, plans, img, dev, stream)
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "height": H, "width": W, "images_per_step": len(plans),
+                   "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "single"},
+        "psnr_db_vs_exact": [round(x, 2) for x in psnr], "min_psnr_db": round(min(psnr), 2),
+        "per_combo_ms": [round(x, 4) for x in lm.mean(0)],
+        "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
+                     "frac": round(achieved / alu_peak, 4), "traffic": None,
+                     "note": "FP32 lane-ops/s of the fused kernel (algorithmic count) vs SMs x 128 x max SM clock"},
+        "hbm": {"achieved_gbs": round(hbm_gbs, 1), "peak_gbs": hbm_peak, "frac": round(hbm_gbs / hbm_peak, 5),
+                "bytes_per_px": 8},
+        "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
+        "e2e": e2e,
+    }
+    if rank == 0:
+        if os.environ.get("BENCH_CPU_BASELINE", "1") == "1" and world == 1:
+            line["cpu_baseline"] = cpu_baseline(img)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_e2e(args, bf, plans, img, dev, stream):
+    """Same metric through the public API with host buffers: each step copies the image
+    host->device (pinned), filters it with the nine plans and copies the nine results back."""
+    import torch
+    h_in = torch.from_numpy(img).pin_memory()
+    h_out = [torch.empty(img.shape, dtype=torch.float32).pin_memory() for _ in plans]
+    d_in = torch.empty(img.shape, dtype=torch.float32, device=dev)
+    d_out = [torch.empty_like(d_in) for _ in plans]
+
+    def step():
+        d_in.copy_(h_in, non_blocking=True)
+        for p, o, ho in zip(plans, d_out, h_out):
+            bf.bf_filter(p, d_in, o, stream=stream)
+            ho.copy_(o, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    value = len(plans) * H * W * args.steps / (ms * 1e-3) / 1e6
+    return {"value": round(value, 3), "unit": "Mpixel/s", "h2d_bytes_per_step": 4 * H * W,
+            "d2h_bytes_per_step": 4 * H * W * len(plans)}
+
+
+def cpu_baseline(img, rows: int = 1080, combos=None):
+    """The FP64 oracle (paper's box-filter algorithm, plain C, OpenMP over rows) on the host cores."""
+    from oracle import oracle as O
+    threads = os.cpu_count() or 1
+    band = np.ascontiguousarray(img[:rows].astype(np.float64))
+    combos = combos or [(a, b) for a in SIGMA_S for b in SIGMA_R]
+    O.approx_fast(band[:64], O.Desc(sigma_s=2.0, nr_terms=NR, ns_terms=NS), threads=threads)  # warm-up
+    t0 = time.perf_counter()
+    for ss, sr in combos:
+        O.approx_fast(band, O.Desc(sigma_s=ss, sigma_r=sr, nr_terms=NR, ns_terms=NS), threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": round(len(combos) * band.shape[0] * band.shape[1] / dt / 1e6, 4), "unit": "Mpixel/s",
+            "cores": threads, "kind": "oracle",
+            "sample": "%d combos on a %dx%d band of the image, FP64 approx_fast, %.1f s" % (len(combos), band.shape[0],
+                                                                                          band.shape[1], dt)}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    from paper_1803_00004_gb300 import synth
+    img = synth.shapes(H, W, seed=0)
+    rows = 120  # bounded sample per step: a 120-row band, all nine combinations
+    for _ in range(args.warmup):
+        cpu_baseline(img, rows=rows)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(img, rows=rows))
+    dt = time.perf_counter() - t0
+    value = args.steps * 9 * rows * W / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Mpixel/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "height": H, "width": W},
+            "cpu_baseline": {"value": round(value, 4), "unit": "Mpixel/s", "cores": vals[-1]["cores"],
+                             "kind": "oracle", "sample": "per step: 9 combos on a %dx%d band" % (rows, W)},
+            "e2e": {"value": round(value, 4), "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,258 @@
+/*
+ * bf.h -- C ABI of the GB300 joint-acceleration bilateral filter.
+ *
+ * Method: Dai, Yuan, Zhang, "Speeding up the Bilateral Filter: A Joint
+ * Acceleration Way".  The bilateral filter of Eq. (1),
+ *
+ *   I^(x) = sum_y K_s(x - y) K_r(I(x) - I(y)) I(y) / sum_y K_s(x - y) K_r(I(x) - I(y)),
+ *
+ * is evaluated with both kernels truncated (Sec. IV-A), the spatial kernel
+ * replaced by its best N-term 2-D Haar expansion, which is a signed sum of
+ * boxes (Eqs. (30)-(32), App. A), and the range kernel by its best N-term
+ * cosine series (Eq. (33)).  The cosine difference identity (Eq. (34)) turns
+ * the range term into per-term basis images cos(w_k I), sin(w_k I) and their
+ * products with I; every basis image is box-filtered and the results are
+ * weighted by cos/sin(w_k I(x)) and summed into numerator and denominator
+ * (Eq. (36)) before the final divide.
+ *
+ * Conventions for every entry point:
+ *   - Status codes only; nothing throws or aborts across this boundary.  A
+ *     human-readable detail for the last failing call on the calling thread
+ *     is available from bf_last_error().
+ *   - Images are single-channel float32, row-major, with a row pitch in
+ *     bytes (a multiple of 4, >= width * 4).  Input values are expected in
+ *     [i_lo, i_hi] of the plan (default [0, 1]); values outside are filtered
+ *     but the accuracy statements of the plan no longer hold.
+ *   - Device pointers are CUDA device memory on the plan's device; the
+ *     caller owns them.  "stream" is a cudaStream_t (NULL = legacy default
+ *     stream).  Filtering calls are asynchronous with respect to the host.
+ *   - In-place filtering (input and output overlapping) is rejected with
+ *     BF_ERR_INVALID_ARG: neighbours would be read after being overwritten.
+ *   - Plans are immutable after creation and may be shared across threads
+ *     and streams.
+ */
+#ifndef BF_H
+#define BF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BF_OK = 0,
+    BF_ERR_INVALID_ARG = 1,     /* bad pointer, size, pitch or parameter */
+    BF_ERR_UNSUPPORTED = 2,     /* valid request this build does not implement */
+    BF_ERR_OOM = 3,             /* host or device allocation failed */
+    BF_ERR_CUDA = 4,            /* a CUDA runtime call failed (detail in bf_last_error) */
+    BF_ERR_ADMISSION = 5,       /* server: request can never fit the memory budget */
+    BF_ERR_TIMEOUT = 6,         /* server: poll timed out; the request is still in flight */
+    BF_ERR_DEVICE_TIMEOUT = 7,  /* a bounded device-side wait gave up */
+    BF_ERR_RANGE = 8,           /* value outside the supported range */
+    BF_ERR_NO_DEVICE = 9,       /* no usable CUDA device */
+    BF_ERR_NOT_FOUND = 10,      /* server: unknown or already collected ticket */
+    BF_ERR_CANCELLED = 11       /* server: request cancelled before it ran */
+} bf_status;
+
+typedef enum {
+    BF_KERNEL_GAUSSIAN = 0,     /* exp(-t^2 / (2 sigma^2)) */
+    BF_KERNEL_EXPONENTIAL = 1,  /* exp(-|t| / sigma) (range kernel only) */
+    BF_KERNEL_BOX = 2           /* 1 on [-sigma, sigma] (range) or on the whole window (spatial) */
+} bf_kernel;
+
+typedef enum {
+    /* Cosine series on [-P, P] with P = max(T_r, (dI + T_r) / 2), dI = i_hi - i_lo:
+     * the kernel truncated at T_r is fitted and no periodic copy reaches an
+     * intensity difference inside the data range, so the range box of
+     * Eq. (33) is identically one (the "extended truncation region" of
+     * Sec. V-C, Case 1).  Default. */
+    BF_RANGE_TRUNCATED_MIN_PERIOD = 0,
+    /* P = dI and the kernel is fitted untruncated on [-dI, dI]. */
+    BF_RANGE_UNTRUNCATED_FULL = 1,
+    /* P = T_r with the range box applied by dimension promotion over
+     * intensity bins (Eqs. (35)-(36) with z).  Not implemented in this build:
+     * bf_plan_create returns BF_ERR_UNSUPPORTED. */
+    BF_RANGE_PAPER_3D = 2
+} bf_range_policy;
+
+typedef enum {
+    BF_PREC_FP32 = 0,           /* all arithmetic and on-chip exchange in fp32 */
+    BF_PREC_BF16_EXCHANGE = 1,  /* window sums exchanged between threads as bf16, fp32 running sums */
+    BF_PREC_FP16_EXCHANGE = 2   /* window sums exchanged between threads as fp16, fp32 running sums */
+} bf_precision;
+
+/* Plan parameters (Sec. IV-A..C).  Fill with bf_plan_desc_default() first. */
+typedef struct {
+    int spatial;        /* bf_kernel: GAUSSIAN or BOX (separable on the square window) */
+    double sigma_s;     /* spatial bandwidth, pixels, > 0 */
+    int radius;         /* window half-width R (square |y - x|_inf <= R); 0 -> round(3 sigma_s) */
+    int ns_terms;       /* N_s: Haar terms kept (best N-term), >= 1 */
+    int range;          /* bf_kernel */
+    double sigma_r;     /* range bandwidth in intensity units, > 0 */
+    double t_r;         /* range truncation T_r; 0 -> 3 sigma_r (Gaussian), sigma_r ln 100
+                           (exponential, eps = 0.01 of Sec. IV-A), sigma_r (box) */
+    int nr_terms;       /* N_r: cosine terms kept (best N-term over the first 20 N_r), >= 1 */
+    int policy;         /* bf_range_policy */
+    float i_lo, i_hi;   /* data range of the images; default 0, 1 */
+    int precision;      /* bf_precision */
+    int kahan;          /* 1: compensated vertical running sums */
+    int device;         /* CUDA device ordinal; -1: host-only plan (bf_coeffs works,
+                           filtering returns BF_ERR_NO_DEVICE) */
+} bf_plan_desc;
+
+typedef struct bf_plan bf_plan;
+
+/* Fills *desc with defaults: Gaussian/Gaussian, sigma_s = 4, R = 0 (auto),
+ * N_s = 5 (the paper's three-box setting, Sec. V-C), sigma_r = 0.1, N_r = 8,
+ * truncated-min-period policy, data range [0, 1], fp32, no Kahan, device 0. */
+void bf_plan_desc_default(bf_plan_desc *desc);
+
+/* Builds a plan (Sec. IV-A..C; App. B): truncation points, range cosine
+ * coefficients a_k on [-P, P] (Eqs. (14)-(15)), 2-D Haar coefficients of the
+ * truncated spatial kernel (Eq. (22)), best N-term selection by |coefficient|,
+ * and the signed-box representation of the selected Haar terms (App. A),
+ * compiled into nested horizontal and vertical box windows for the kernel.
+ * Host memory only; the coefficient tables travel to the device as kernel
+ * parameters.  *out receives a plan the caller releases with bf_plan_destroy.
+ * Errors: BF_ERR_INVALID_ARG (NULL, sigma <= 0, N < 1, i_hi <= i_lo, bad enum),
+ * BF_ERR_UNSUPPORTED (BF_RANGE_PAPER_3D, exponential spatial kernel),
+ * BF_ERR_OOM, BF_ERR_NO_DEVICE (device >= 0 that does not exist). */
+bf_status bf_plan_create(const bf_plan_desc *desc, bf_plan **out);
+
+/* Releases a plan (NULL is a no-op).  No filtering call using the plan may be
+ * in flight on any stream. */
+void bf_plan_destroy(bf_plan *plan);
+
+/* Host view of a plan's coefficients (App. A/B); all pointers point into the
+ * plan and stay valid until bf_plan_destroy. */
+typedef struct {
+    int radius;                 /* R */
+    double t_s;                 /* Haar interval half-width T_s = R + 1/2 */
+    int haar_levels;            /* J = ceil(log2(2 T_s)) */
+    double t_r;                 /* range truncation point used */
+    double period;              /* cosine half-period P */
+    int nr;                     /* selected range terms */
+    const int *k;               /* [nr] cosine indices, ascending */
+    const double *a;            /* [nr] a_k */
+    int ns;                     /* selected Haar terms, in ranking order */
+    const int *haar_terms;      /* [4 ns] level_x, k_x, level_y, k_y (level -1 = phi) */
+    const double *haar_coef;    /* [ns] c */
+    int tie_split;              /* 1 if N_s cut a group of equal |c| (asymmetric kernel) */
+    const double *kernel;       /* [(2R+1)^2] K~_s(dx, dy) at [(dy+R)(2R+1) + dx+R] */
+    int n_vwin, n_hwin;         /* box windows of the kernel compilation */
+    const int *vwin;            /* [2 n_vwin] first/last neighbour row offset */
+    const int *hwin;            /* [2 n_hwin] first/last neighbour column offset */
+    const double *wcoef;        /* [n_vwin * n_hwin] weight of window pair (v, h) */
+    double range_max_err;       /* max |K_r - K~_r| over [-dI, dI] (sampled) */
+    double spatial_max_err;     /* max |K_s - K~_s| over the integer window */
+    double den_eps;             /* denominator guard: den <= den_eps -> output I(x) */
+    int passes;                 /* kernel launches per image */
+} bf_coeff_view;
+
+/* Fills *out with the plan's coefficients.  Errors: BF_ERR_INVALID_ARG. */
+bf_status bf_coeffs(const bf_plan *plan, bf_coeff_view *out);
+
+/* Filters one image on the device (hot path, Eq. (36) then divide).
+ * d_in / d_out: device buffers of height rows with the given pitches.
+ * height, width >= 0 (0 is a no-op).  Asynchronous on `stream`.
+ * Errors: BF_ERR_INVALID_ARG (NULL, pitch, overlap), BF_ERR_NO_DEVICE
+ * (host-only plan), BF_ERR_CUDA (launch failure), BF_ERR_OOM (scratch for
+ * multi-pass plans could not be allocated). */
+bf_status bf_filter(const bf_plan *plan, const float *d_in, size_t in_pitch_bytes,
+                    float *d_out, size_t out_pitch_bytes, int height, int width, void *stream);
+
+/* One image of a batch. */
+typedef struct {
+    const float *d_in;
+    size_t in_pitch_bytes;
+    float *d_out;
+    size_t out_pitch_bytes;
+    int height, width;
+} bf_image;
+
+/* Filters n images, image i with plans[i] (plans may differ per image), in
+ * one persistent launch per kernel class that walks a work list of
+ * (image, tile) items across uneven images; the launch sequence is captured
+ * once into a CUDA graph per batch shape and replayed.  Each image's result
+ * equals bf_filter's for the same plan within fp32 rounding.  All plans must
+ * be on the same device.  Errors: as bf_filter. */
+bf_status bf_filter_batch(const bf_plan *const *plans, const bf_image *images, int n, void *stream);
+
+/* Exact bilateral filter of Eq. (1) by brute force on the device (fp32,
+ * |y - x|_inf <= radius, untruncated range kernel): the accuracy reference
+ * for images too large for the CPU.  O(radius^2) per pixel. */
+bf_status bf_exact(const float *d_in, size_t in_pitch_bytes, float *d_out, size_t out_pitch_bytes,
+                   int height, int width, int spatial, double sigma_s, int radius,
+                   int range, double sigma_r, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Serving: continuous batching of filter requests                         */
+/* ---------------------------------------------------------------------- */
+
+typedef struct bf_server bf_server;
+
+typedef struct {
+    size_t hbm_budget_bytes;    /* device bytes the server may hold for request buffers; 0 -> 1/2 of free */
+    int max_slots;              /* requests resident on the device at once; 0 -> 64 */
+    int n_streams;              /* CUDA streams the server launches on; 0 -> 4 */
+    int device;                 /* CUDA device ordinal */
+    int max_batch;              /* requests merged into one batched launch; 0 -> 16 */
+} bf_serve_config;
+
+typedef struct {
+    bf_plan_desc desc;          /* filter parameters; plans are cached by value */
+    const float *h_in;          /* host input (pinned memory recommended), row-major, packed */
+    float *h_out;               /* host output, row-major, packed */
+    int height, width;
+} bf_request;
+
+typedef struct {
+    int status;                 /* bf_status of the request */
+    double latency_ms;          /* submit -> result on host */
+    double queue_ms;            /* submit -> admitted */
+    double device_ms;           /* device time of the request's launch group */
+} bf_result;
+
+/* Starts a server thread for one device.  Errors: BF_ERR_INVALID_ARG,
+ * BF_ERR_NO_DEVICE, BF_ERR_CUDA, BF_ERR_OOM. */
+bf_status bf_serve_create(const bf_serve_config *cfg, bf_server **out);
+
+/* Queues a request; never waits for GPU work.  The host buffers must stay
+ * valid until the request's result has been polled.  Errors:
+ * BF_ERR_INVALID_ARG, BF_ERR_ADMISSION (larger than the whole budget),
+ * plan errors of bf_plan_create. */
+bf_status bf_serve_submit(bf_server *server, const bf_request *req, uint64_t *ticket);
+
+/* Waits up to timeout_ms (0: just check; < 0: wait without limit) for a
+ * request.  BF_OK: *out holds the result and the ticket is released.
+ * BF_ERR_TIMEOUT: still in flight.  BF_ERR_NOT_FOUND: unknown ticket. */
+bf_status bf_serve_poll(bf_server *server, uint64_t ticket, int timeout_ms, bf_result *out);
+
+/* Cancels a request that has not been admitted yet (BF_OK), else
+ * BF_ERR_NOT_FOUND.  A cancelled request polls as BF_ERR_CANCELLED. */
+bf_status bf_serve_cancel(bf_server *server, uint64_t ticket);
+
+/* Drains all admitted requests and stops the server (NULL is a no-op). */
+void bf_serve_destroy(bf_server *server);
+
+/* ---------------------------------------------------------------------- */
+
+const char *bf_status_string(bf_status status);
+
+/* Detail of the last failing call on the calling thread ("" if none). */
+const char *bf_last_error(void);
+
+/* Library version, (major << 16) | minor. */
+int bf_version(void);
+
+/* Test hook for failure handling: while set to n > 0, the next n kernel
+ * launches report BF_ERR_CUDA without launching.  Process-wide. */
+void bf_debug_fail_launches(int n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BF_H */

@@ -513,6 +513,45 @@ int orc_approx_direct(const double *I, int H, int W,
     return ORC_OK;
 }
 
+/* O2 at the listed pixels only (pts: npts (row, col) pairs; out[i] for pixel i):
+ * the same definition as orc_approx_direct, for sampled checks of large images. */
+int orc_approx_direct_at(const double *I, int H, int W,
+                         int skind, double sigma_s, int radius, int ns_terms,
+                         int rkind, double sigma_r, double t_r, int nr_terms, int policy, double data_range,
+                         const int *pts, int npts, double *out, int nthreads)
+{
+    if (!I || !out || !pts || H < 1 || W < 1 || npts < 0) return ORC_EINVAL;
+    orc_plan p;
+    int st = plan_build(&p, skind, sigma_s, radius, ns_terms, rkind, sigma_r, t_r, nr_terms, policy, data_range);
+    if (st) { plan_free(&p); return st; }
+    int R = p.R, w = 2 * R + 1;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+:bad) num_threads(nthreads > 0 ? nthreads : 1)
+    for (int n = 0; n < npts; n++) {
+        int y = pts[2 * n], x = pts[2 * n + 1];
+        if (y < 0 || y >= H || x < 0 || x >= W) { out[n] = 0.0; bad++; continue; }
+        double ix = I[(size_t)y * W + x], num = 0.0, den = 0.0;
+        for (int dy = -R; dy <= R; dy++) {
+            int yy = y + dy;
+            if (yy < 0 || yy >= H) continue;
+            for (int dx = -R; dx <= R; dx++) {
+                int xx = x + dx;
+                if (xx < 0 || xx >= W) continue;
+                double iy = I[(size_t)yy * W + xx];
+                double ks = p.Ks[(-dy + R) * w + (-dx + R)];
+                if (ks == 0.0) continue;
+                double kr = 0.0, t = ix - iy;
+                for (int i = 0; i < p.nr; i++) kr += p.ak[i] * cos(ORC_PI * p.ks[i] * t / p.P);
+                num += ks * kr * iy;
+                den += ks * kr;
+            }
+        }
+        out[n] = (den <= p.den_eps) ? ix : num / den;
+    }
+    plan_free(&p);
+    return bad ? ORC_EINVAL : ORC_OK;
+}
+
 /* ------------------------------------------------------------------ */
 /* O3: the paper's algorithm, Eqs. (34)-(36) with App. A boxes          */
 /* ------------------------------------------------------------------ */

@@ -66,6 +66,7 @@ def _load():
         lib.orc_approx_direct.argtypes = common
         lib.orc_approx_fast.argtypes = common
         lib.orc_box_count.argtypes = [i, d, i, i, i, d, d, i, i, d]
+        lib.orc_approx_direct_at.argtypes = [pd, i, i, i, d, i, i, i, d, d, i, i, d, pi, i, pd, i]
         _lib = lib
     return _lib
 
@@ -231,6 +232,18 @@ def approx_fast(I, desc: Desc, threads: int = 1):
     if st:
         raise ValueError("orc_approx_fast status %d" % st)
     return out, int(nd[0])
+
+
+def approx_direct_at(I, desc: Desc, pts, threads: int = 1) -> np.ndarray:
+    """O2 at the given (row, col) pixels only."""
+    I = _img(I)
+    H, W = I.shape
+    pts = np.ascontiguousarray(pts, dtype=np.int32).reshape(-1, 2)
+    out = np.zeros(len(pts))
+    st = _load().orc_approx_direct_at(_dp(I), H, W, *desc.args(), _ip(pts), len(pts), _dp(out), threads)
+    if st:
+        raise ValueError("orc_approx_direct_at status %d" % st)
+    return out
 
 
 def box_count(desc: Desc) -> int:

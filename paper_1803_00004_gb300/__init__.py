@@ -1,0 +1,11 @@
+"""GB300-native joint-acceleration bilateral filter (Dai, Yuan, Zhang).
+
+The filter runs in libbf.so (hand-written CUDA for sm_103a behind the C ABI of
+include/bf.h); this package is its thin Python binding plus the seeded input
+generators in ``synth``.  Importing the package does not load the library; the
+first call does, and raises if it has not been built.
+"""
+from ._binding import (BFError, Plan, Server, bf_coeffs, bf_exact, bf_filter, bf_filter_batch, bf_version,  # noqa: F401
+                       bf_debug_fail_launches, desc, lib, LIB_PATH, EXPORTS)
+from ._binding import (KERNEL_GAUSSIAN, KERNEL_EXPONENTIAL, KERNEL_BOX, RANGE_TRUNCATED_MIN_PERIOD,  # noqa: F401
+                       RANGE_UNTRUNCATED_FULL, RANGE_PAPER_3D, PREC_FP32, PREC_BF16_EXCHANGE, PREC_FP16_EXCHANGE)

@@ -1,0 +1,280 @@
+"""ctypes binding of include/bf.h (argument marshalling only).
+
+Every computation happens in libbf.so; this module converts Python values and
+PyTorch CUDA tensors (data pointer, row pitch, current stream) into the C ABI's
+plain pointers and sizes.  If the library has not been built, every entry point
+raises ``RuntimeError``: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libbf.so")
+
+# ---- enums (mirrors include/bf.h)
+OK = 0
+ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA, ERR_ADMISSION = 1, 2, 3, 4, 5
+ERR_TIMEOUT, ERR_DEVICE_TIMEOUT, ERR_RANGE, ERR_NO_DEVICE, ERR_NOT_FOUND, ERR_CANCELLED = 6, 7, 8, 9, 10, 11
+KERNEL_GAUSSIAN, KERNEL_EXPONENTIAL, KERNEL_BOX = 0, 1, 2
+RANGE_TRUNCATED_MIN_PERIOD, RANGE_UNTRUNCATED_FULL, RANGE_PAPER_3D = 0, 1, 2
+PREC_FP32, PREC_BF16_EXCHANGE, PREC_FP16_EXCHANGE = 0, 1, 2
+
+
+class bf_plan_desc(C.Structure):
+    _fields_ = [("spatial", C.c_int), ("sigma_s", C.c_double), ("radius", C.c_int), ("ns_terms", C.c_int),
+                ("range", C.c_int), ("sigma_r", C.c_double), ("t_r", C.c_double), ("nr_terms", C.c_int),
+                ("policy", C.c_int), ("i_lo", C.c_float), ("i_hi", C.c_float), ("precision", C.c_int),
+                ("kahan", C.c_int), ("device", C.c_int)]
+
+
+class bf_coeff_view(C.Structure):
+    _fields_ = [("radius", C.c_int), ("t_s", C.c_double), ("haar_levels", C.c_int), ("t_r", C.c_double),
+                ("period", C.c_double), ("nr", C.c_int), ("k", C.POINTER(C.c_int)), ("a", C.POINTER(C.c_double)),
+                ("ns", C.c_int), ("haar_terms", C.POINTER(C.c_int)), ("haar_coef", C.POINTER(C.c_double)),
+                ("tie_split", C.c_int), ("kernel", C.POINTER(C.c_double)), ("n_vwin", C.c_int),
+                ("n_hwin", C.c_int), ("vwin", C.POINTER(C.c_int)), ("hwin", C.POINTER(C.c_int)),
+                ("wcoef", C.POINTER(C.c_double)), ("range_max_err", C.c_double), ("spatial_max_err", C.c_double),
+                ("den_eps", C.c_double), ("passes", C.c_int)]
+
+
+class bf_image(C.Structure):
+    _fields_ = [("d_in", C.c_void_p), ("in_pitch_bytes", C.c_size_t), ("d_out", C.c_void_p),
+                ("out_pitch_bytes", C.c_size_t), ("height", C.c_int), ("width", C.c_int)]
+
+
+class bf_serve_config(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_slots", C.c_int), ("n_streams", C.c_int),
+                ("device", C.c_int), ("max_batch", C.c_int)]
+
+
+class bf_request(C.Structure):
+    _fields_ = [("desc", bf_plan_desc), ("h_in", C.c_void_p), ("h_out", C.c_void_p), ("height", C.c_int),
+                ("width", C.c_int)]
+
+
+class bf_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("latency_ms", C.c_double), ("queue_ms", C.c_double), ("device_ms", C.c_double)]
+
+
+EXPORTS = ["bf_plan_desc_default", "bf_plan_create", "bf_plan_destroy", "bf_coeffs", "bf_filter", "bf_filter_batch",
+           "bf_exact", "bf_serve_create", "bf_serve_submit", "bf_serve_poll", "bf_serve_cancel", "bf_serve_destroy",
+           "bf_status_string", "bf_last_error", "bf_version", "bf_debug_fail_launches"]
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Loads libbf.so (raises RuntimeError if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libbf.so is not built (%s); run `python -c 'import __graft_entry__ as g; g.build()'`"
+                               % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        P, vp, sz, i, d = C.POINTER, C.c_void_p, C.c_size_t, C.c_int, C.c_double
+        L.bf_plan_desc_default.argtypes = [P(bf_plan_desc)]
+        L.bf_plan_desc_default.restype = None
+        L.bf_plan_create.argtypes = [P(bf_plan_desc), P(vp)]
+        L.bf_plan_destroy.argtypes = [vp]
+        L.bf_plan_destroy.restype = None
+        L.bf_coeffs.argtypes = [vp, P(bf_coeff_view)]
+        L.bf_filter.argtypes = [vp, vp, sz, vp, sz, i, i, vp]
+        L.bf_filter_batch.argtypes = [P(vp), P(bf_image), i, vp]
+        L.bf_exact.argtypes = [vp, sz, vp, sz, i, i, i, d, i, i, d, vp]
+        L.bf_serve_create.argtypes = [P(bf_serve_config), P(vp)]
+        L.bf_serve_submit.argtypes = [vp, P(bf_request), P(C.c_uint64)]
+        L.bf_serve_poll.argtypes = [vp, C.c_uint64, i, P(bf_result)]
+        L.bf_serve_cancel.argtypes = [vp, C.c_uint64]
+        L.bf_serve_destroy.argtypes = [vp]
+        L.bf_serve_destroy.restype = None
+        L.bf_status_string.argtypes = [i]
+        L.bf_status_string.restype = C.c_char_p
+        L.bf_last_error.argtypes = []
+        L.bf_last_error.restype = C.c_char_p
+        L.bf_version.restype = i
+        L.bf_debug_fail_launches.argtypes = [i]
+        L.bf_debug_fail_launches.restype = None
+        _lib = L
+    return _lib
+
+
+class BFError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        L = lib()
+        self.status = status
+        msg = L.bf_status_string(status).decode()
+        detail = L.bf_last_error().decode()
+        super().__init__("%s: %s%s" % (where, msg, (" (" + detail + ")") if detail else ""))
+
+
+def _check(st: int, where: str) -> None:
+    if st != OK:
+        raise BFError(st, where)
+
+
+def desc(**kw) -> bf_plan_desc:
+    """A bf_plan_desc with the library defaults, overridden by keyword arguments."""
+    d = bf_plan_desc()
+    lib().bf_plan_desc_default(C.byref(d))
+    for k, v in kw.items():
+        if not hasattr(d, k):
+            raise TypeError("unknown plan field %r" % k)
+        setattr(d, k, v)
+    return d
+
+
+class Plan:
+    """Owns a bf_plan*."""
+
+    def __init__(self, d: bf_plan_desc | None = None, **kw):
+        if d is None:
+            d = desc(**kw)
+        elif kw:
+            raise TypeError("pass either a desc or keyword fields")
+        self.desc = d
+        h = C.c_void_p()
+        _check(lib().bf_plan_create(C.byref(d), C.byref(h)), "bf_plan_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().bf_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def coeffs(self) -> dict:
+        return bf_coeffs(self)
+
+
+def bf_coeffs(plan: Plan) -> dict:
+    v = bf_coeff_view()
+    _check(lib().bf_coeffs(plan.handle, C.byref(v)), "bf_coeffs")
+    R = v.radius
+    w = 2 * R + 1
+    arr = lambda p, n: [p[j] for j in range(n)]
+    return {
+        "radius": R, "t_s": v.t_s, "haar_levels": v.haar_levels, "t_r": v.t_r, "period": v.period,
+        "k": arr(v.k, v.nr), "a": arr(v.a, v.nr),
+        "haar_terms": [tuple(v.haar_terms[4 * t + j] for j in range(4)) for t in range(v.ns)],
+        "haar_coef": arr(v.haar_coef, v.ns), "tie_split": bool(v.tie_split),
+        "kernel": [[v.kernel[r * w + c] for c in range(w)] for r in range(w)],
+        "vwin": [(v.vwin[2 * j], v.vwin[2 * j + 1]) for j in range(v.n_vwin)],
+        "hwin": [(v.hwin[2 * j], v.hwin[2 * j + 1]) for j in range(v.n_hwin)],
+        "wcoef": [[v.wcoef[a * v.n_hwin + b] for b in range(v.n_hwin)] for a in range(v.n_vwin)],
+        "range_max_err": v.range_max_err, "spatial_max_err": v.spatial_max_err, "den_eps": v.den_eps,
+        "passes": v.passes,
+    }
+
+
+def _ptr_pitch(t):
+    """(device pointer, row pitch in bytes, height, width) of a 2-D float32 tensor or a raw tuple."""
+    if isinstance(t, tuple):
+        return t
+    if t.dim() != 2 or t.dtype.itemsize != 4 or t.stride(1) != 1:
+        raise ValueError("expected a 2-D float32 tensor with unit column stride")
+    return t.data_ptr(), t.stride(0) * 4, t.shape[0], t.shape[1]
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def bf_filter(plan: Plan, src, dst, stream=None) -> None:
+    """Filters src into dst (CUDA float32 2-D tensors or (ptr, pitch, h, w) tuples)."""
+    ip, ipitch, h, w = _ptr_pitch(src)
+    op, opitch, h2, w2 = _ptr_pitch(dst)
+    if (h, w) != (h2, w2):
+        raise ValueError("input and output shapes differ")
+    _check(lib().bf_filter(plan.handle, ip, ipitch, op, opitch, h, w, _stream_handle(stream)), "bf_filter")
+
+
+def bf_filter_batch(plans, srcs, dsts, stream=None) -> None:
+    n = len(srcs)
+    if len(plans) != n or len(dsts) != n:
+        raise ValueError("plans, inputs and outputs must have the same length")
+    imgs = (bf_image * max(n, 1))()
+    hs = (C.c_void_p * max(n, 1))()
+    for j in range(n):
+        ip, ipitch, h, w = _ptr_pitch(srcs[j])
+        op, opitch, h2, w2 = _ptr_pitch(dsts[j])
+        if (h, w) != (h2, w2):
+            raise ValueError("image %d: input and output shapes differ" % j)
+        imgs[j] = bf_image(ip, ipitch, op, opitch, h, w)
+        hs[j] = plans[j].handle
+    _check(lib().bf_filter_batch(hs, imgs, n, _stream_handle(stream)), "bf_filter_batch")
+
+
+def bf_exact(src, dst, spatial=KERNEL_GAUSSIAN, sigma_s=4.0, radius=0, range=KERNEL_GAUSSIAN, sigma_r=0.1,
+             stream=None) -> None:
+    ip, ipitch, h, w = _ptr_pitch(src)
+    op, opitch, _, _ = _ptr_pitch(dst)
+    _check(lib().bf_exact(ip, ipitch, op, opitch, h, w, spatial, sigma_s, radius, range, sigma_r,
+                          _stream_handle(stream)), "bf_exact")
+
+
+def bf_version() -> int:
+    return int(lib().bf_version())
+
+
+def bf_debug_fail_launches(n: int) -> None:
+    lib().bf_debug_fail_launches(int(n))
+
+
+class Server:
+    """Owns a bf_server* (continuous-batching request loop on one device)."""
+
+    def __init__(self, hbm_budget_bytes=0, max_slots=0, n_streams=0, device=0, max_batch=0):
+        cfg = bf_serve_config(hbm_budget_bytes, max_slots, n_streams, device, max_batch)
+        h = C.c_void_p()
+        _check(lib().bf_serve_create(C.byref(cfg), C.byref(h)), "bf_serve_create")
+        self._h = h
+
+    def submit(self, d: bf_plan_desc, h_in_ptr: int, h_out_ptr: int, height: int, width: int) -> int:
+        req = bf_request(d, h_in_ptr, h_out_ptr, height, width)
+        t = C.c_uint64()
+        _check(lib().bf_serve_submit(self._h, C.byref(req), C.byref(t)), "bf_serve_submit")
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = -1):
+        r = bf_result()
+        st = lib().bf_serve_poll(self._h, ticket, timeout_ms, C.byref(r))
+        return st, r
+
+    def cancel(self, ticket: int) -> int:
+        return lib().bf_serve_cancel(self._h, ticket)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().bf_serve_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,86 @@
+// Internal declarations shared by the host plan builder, the C ABI layer and
+// the CUDA kernels.  Not installed; the public interface is include/bf.h.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/bf.h"
+
+namespace bfi {
+
+// Largest number of box windows per axis a kernel class handles, and the
+// largest number of cosine terms one pass of the fused kernel carries.
+constexpr int kMaxWin = 6;
+constexpr int kMaxSlots = 16;
+
+// Everything one launch of the fused filter needs, passed by value (it lands
+// in the kernel's constant parameter bank; no device allocation per plan).
+//
+// Vertical windows [v0[r], v1[r]] and horizontal windows [u0[q], u1[q]] are
+// neighbour offsets d = y - x (rows / columns); the spatial weight of the
+// neighbour at offset (dx, dy) is sum_{r,q} C[r][q] [v0_r <= dy <= v1_r][u0_q <= dx <= u1_q].
+struct FilterParams {
+    float inv_p;              // 1 / P: basis angle of term k is pi * k * (I - i_lo) / P
+    float i_lo;               // intensity origin
+    float den_eps;            // denominator guard
+    int nk;                   // cosine terms used in this pass (<= slots of the class)
+    int k[kMaxSlots];         // ascending; padded slots repeat the last k with a = 0
+    float a[kMaxSlots];
+    int m;                    // windows per axis of this kernel class
+    int v0[kMaxWin], v1[kMaxWin];
+    int u0[kMaxWin], u1[kMaxWin];
+    float C[kMaxWin][kMaxWin];
+    int rx;                   // max |u| (horizontal reach)
+    int vlo, vhi;             // min v0, max v1
+};
+
+// Tile geometry chosen by the host for one launch.
+struct TileConfig {
+    int tw;        // output columns per CTA (multiple of seg)
+    int th;        // output rows per CTA
+    int seg;       // columns per horizontal work item
+    int threads;   // CTA size (>= tw + 2 rx, multiple of 32)
+    size_t smem;   // dynamic shared memory bytes
+};
+
+// Which pass of a multi-pass filter a launch is.
+enum PassMode { kPassOnly = 0, kPassFirst = 1, kPassMid = 2, kPassLast = 3 };
+
+void set_error(const std::string &msg);
+bf_status fail(bf_status st, const std::string &msg);
+
+// ---- device side (bf_filter.cu) ----
+bool kernel_class_supported(int m);
+int slots_per_pass(int m);
+TileConfig choose_tile(int m, int rx, int vspan, int height, int width, int precision);
+bf_status launch_filter_pass(const FilterParams &p, int precision, int kahan, const TileConfig &tc,
+                             const float *d_in, size_t in_pitch_elems, float *d_out, size_t out_pitch_elems,
+                             float *d_acc, int height, int width, int mode, void *stream);
+bf_status launch_exact(const float *d_in, size_t in_pitch_elems, float *d_out, size_t out_pitch_elems,
+                       int height, int width, int spatial, float sigma_s, int radius, int range, float sigma_r,
+                       void *stream);
+bool debug_consume_launch_failure();
+
+}  // namespace bfi
+
+struct bf_plan {
+    bf_plan_desc desc;
+    int R = 0;
+    double Ts = 0, Tr = 0, P = 0;
+    int J = 0;
+    std::vector<int> k;             // selected cosine indices, ascending
+    std::vector<double> a;
+    std::vector<int> terms;         // 4 per selected Haar term (ranking order)
+    std::vector<double> tcoef;
+    int tie_split = 0;
+    std::vector<double> kernel;     // K~_s(dx, dy), [(dy+R)(2R+1) + dx+R]
+    int nv = 0, nh = 0;
+    std::vector<int> vwin, hwin;    // 2 per window
+    std::vector<double> wcoef;      // nv x nh
+    double range_max_err = 0, spatial_max_err = 0, den_eps = 0;
+    int m = 0;                      // kernel class (windows per axis)
+    std::vector<bfi::FilterParams> passes;
+};

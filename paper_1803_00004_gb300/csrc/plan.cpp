@@ -1,0 +1,441 @@
+// Plan construction: truncation, coefficient fit, best N-term selection and
+// the compilation of the selected Haar terms into box windows for the kernel.
+//
+// Paper passages: kernel truncation Sec. IV-A; truncated cosine series
+// Eqs. (13)-(15) and its best N-term form Eq. (33); Haar system
+// Eqs. (17)-(22), best N-term spatial form Eq. (30); Haar terms as signed
+// boxes App. A / Eq. (37); best N-term by largest coefficients Sec. III-A
+// (Eq. (11)) with the first-20N candidate rule of App. B.
+//
+// The integrals are done here by composite Gauss-Legendre quadrature, so the
+// same code serves any separable spatial profile and any range profile.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <new>
+
+#include "bf_internal.h"
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// ---------------------------------------------------------------- quadrature
+
+struct GaussLegendre {
+    std::vector<double> x, w;  // nodes / weights on [-1, 1]
+    explicit GaussLegendre(int n) : x(n), w(n) {
+        // Newton iteration on P_n from the Chebyshev-like initial guess.
+        for (int i = 0; i < n; ++i) {
+            double z = std::cos(kPi * (i + 0.75) / (n + 0.5)), dp = 1.0;
+            for (int it = 0; it < 100; ++it) {
+                double p0 = 1.0, p1 = z;
+                for (int j = 2; j <= n; ++j) {
+                    double p2 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p0) / j;
+                    p0 = p1;
+                    p1 = p2;
+                }
+                dp = n * (z * p1 - p0) / (z * z - 1.0);
+                double dz = p1 / dp;
+                z -= dz;
+                if (std::fabs(dz) < 1e-16) break;
+            }
+            x[i] = z;
+            w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+        }
+    }
+};
+
+const GaussLegendre &gl20() {
+    static const GaussLegendre g(20);
+    return g;
+}
+
+// int_a^b f over `pieces` equal sub-intervals, 20-point rule on each.
+double integrate(const std::function<double(double)> &f, double a, double b, int pieces) {
+    if (!(b > a)) return 0.0;
+    const GaussLegendre &g = gl20();
+    double h = (b - a) / pieces, s = 0.0;
+    for (int p = 0; p < pieces; ++p) {
+        double lo = a + p * h, hi = (p == pieces - 1) ? b : lo + h;
+        double c = 0.5 * (lo + hi), r = 0.5 * (hi - lo), t = 0.0;
+        for (size_t i = 0; i < g.x.size(); ++i) t += g.w[i] * f(c + r * g.x[i]);
+        s += r * t;
+    }
+    return s;
+}
+
+// ---------------------------------------------------------------- kernels
+
+double range_value(int kind, double sigma, double t) {
+    double a = std::fabs(t);
+    switch (kind) {
+        case BF_KERNEL_GAUSSIAN: return std::exp(-t * t / (2.0 * sigma * sigma));
+        case BF_KERNEL_EXPONENTIAL: return std::exp(-a / sigma);
+        case BF_KERNEL_BOX: return a <= sigma ? 1.0 : 0.0;
+    }
+    return 0.0;
+}
+
+double spatial_profile(int kind, double sigma, double x) {
+    if (kind == BF_KERNEL_BOX) return 1.0;
+    return std::exp(-x * x / (2.0 * sigma * sigma));
+}
+
+// ---------------------------------------------------------------- Haar system
+
+// One 1-D Haar function on [-T, T]: +1 on [lo, mid], -1 on [mid, hi]; phi has lev = -1.
+struct Haar1 {
+    int lev, k;
+    double lo, mid, hi;
+};
+
+Haar1 haar_fn(int lev, int k, double T) {
+    Haar1 h{lev, k, -T, T, T};
+    if (lev < 0) return h;
+    double Z = lev == 0 ? 0.0 : (k > 0 ? 1.0 : -1.0) * (2.0 * std::abs(k) - 1.0) * T;  // App. A
+    double s = std::ldexp(1.0, -lev);
+    h.lo = s * (Z - T);
+    h.mid = s * Z;
+    h.hi = s * (Z + T);
+    return h;
+}
+
+// Dictionary: phi, psi_00, then levels 1..J with k = -2^{j-1}..-1, 1..2^{j-1}.
+std::vector<Haar1> haar_dictionary(int J, double T) {
+    std::vector<Haar1> d;
+    d.push_back(haar_fn(-1, 0, T));
+    d.push_back(haar_fn(0, 0, T));
+    for (int j = 1; j <= J; ++j) {
+        int half = 1 << (j - 1);
+        for (int k = -half; k <= half; ++k)
+            if (k != 0) d.push_back(haar_fn(j, k, T));
+    }
+    return d;
+}
+
+// Value at x with the mean of one-sided limits at a jump.
+double haar_value(const Haar1 &h, double x) {
+    if (h.lev < 0) return (x > h.lo && x < h.hi) ? 1.0 : ((x == h.lo || x == h.hi) ? 0.5 : 0.0);
+    if (x < h.lo || x > h.hi) return 0.0;
+    if (x == h.lo) return 0.5;
+    if (x == h.hi) return -0.5;
+    if (x == h.mid) return 0.0;
+    return x < h.mid ? 1.0 : -1.0;
+}
+
+struct Cand {
+    double mag, c;
+    int key[5];
+    int a, b;  // indices (1-D dictionary, or k for range terms)
+};
+
+bool key_less(const Cand &x, const Cand &y) {
+    for (int i = 0; i < 5; ++i)
+        if (x.key[i] != y.key[i]) return x.key[i] < y.key[i];
+    return false;
+}
+
+// Best N-term ranking: |c| descending; values within relative 1e-12 of the
+// first member of a run form a tie group, ordered by key; |c| < 1e-14 max dropped.
+void rank(std::vector<Cand> &v) {
+    double mx = 0;
+    for (auto &e : v) mx = std::max(mx, e.mag);
+    v.erase(std::remove_if(v.begin(), v.end(), [&](const Cand &e) { return !(e.mag > 0) || e.mag < 1e-14 * mx; }),
+            v.end());
+    std::sort(v.begin(), v.end(), [](const Cand &x, const Cand &y) {
+        if (x.mag != y.mag) return x.mag > y.mag;
+        return key_less(x, y);
+    });
+    size_t i = 0;
+    while (i < v.size()) {
+        size_t j = i + 1;
+        while (j < v.size() && v[j].mag >= v[i].mag * (1.0 - 1e-12)) ++j;
+        std::sort(v.begin() + i, v.begin() + j, key_less);
+        i = j;
+    }
+}
+
+// ---------------------------------------------------------------- windows
+
+// Splits a set of 1-D profiles p_i(d), d in [-R, R], into shared windows:
+// nested centred windows [-b, b] when every profile is even, otherwise the
+// maximal runs on which no profile changes.  coef[i][j] is the weight of
+// window j in profile i, so that p_i(d) = sum_j coef[i][j] [d in window j].
+void split_profiles(const std::vector<std::vector<double>> &prof, int R, double tol,
+                    std::vector<std::pair<int, int>> &win, std::vector<std::vector<double>> &coef) {
+    const int w = 2 * R + 1;
+    auto at = [&](const std::vector<double> &p, int d) { return (d < -R || d > R) ? 0.0 : p[d + R]; };
+    bool even = true;
+    for (auto &p : prof)
+        for (int d = 1; d <= R; ++d)
+            if (std::fabs(at(p, d) - at(p, -d)) > tol) even = false;
+    win.clear();
+    coef.assign(prof.size(), {});
+    if (even) {
+        std::vector<int> b;
+        for (int c = 0; c < R; ++c) {
+            bool change = false;
+            for (auto &p : prof)
+                if (std::fabs(at(p, c) - at(p, c + 1)) > tol) change = true;
+            if (change) b.push_back(c);
+        }
+        b.push_back(R);
+        for (size_t j = 0; j < b.size(); ++j) {
+            win.push_back({-b[j], b[j]});
+            for (size_t i = 0; i < prof.size(); ++i) {
+                double nxt = (j + 1 < b.size()) ? at(prof[i], b[j + 1]) : 0.0;
+                coef[i].push_back(at(prof[i], b[j]) - nxt);
+            }
+        }
+    } else {
+        int start = -R;
+        for (int d = -R; d <= R; ++d) {
+            bool change = (d == R);
+            if (!change)
+                for (auto &p : prof)
+                    if (std::fabs(at(p, d) - at(p, d + 1)) > tol) change = true;
+            if (change) {
+                win.push_back({start, d});
+                for (size_t i = 0; i < prof.size(); ++i) coef[i].push_back(at(prof[i], start));
+                start = d + 1;
+            }
+        }
+    }
+    // drop windows no profile uses
+    std::vector<std::pair<int, int>> w2;
+    std::vector<std::vector<double>> c2(prof.size());
+    for (size_t j = 0; j < win.size(); ++j) {
+        bool used = false;
+        for (size_t i = 0; i < prof.size(); ++i)
+            if (std::fabs(coef[i][j]) > tol) used = true;
+        if (!used) continue;
+        w2.push_back(win[j]);
+        for (size_t i = 0; i < prof.size(); ++i) c2[i].push_back(coef[i][j]);
+    }
+    win.swap(w2);
+    coef.swap(c2);
+    (void)w;
+}
+
+bf_status build(const bf_plan_desc &d, bf_plan &p) {
+    using bfi::fail;
+    if (!(d.sigma_s > 0) || !(d.sigma_r > 0) || !std::isfinite(d.sigma_s) || !std::isfinite(d.sigma_r))
+        return fail(BF_ERR_INVALID_ARG, "sigma_s and sigma_r must be finite and > 0");
+    if (d.ns_terms < 1 || d.nr_terms < 1) return fail(BF_ERR_INVALID_ARG, "ns_terms and nr_terms must be >= 1");
+    if (d.nr_terms > 4096) return fail(BF_ERR_INVALID_ARG, "nr_terms too large");
+    if (d.radius < 0 || d.radius > 1024) return fail(BF_ERR_INVALID_ARG, "radius must be in [0, 1024]");
+    if (!(d.i_hi > d.i_lo)) return fail(BF_ERR_INVALID_ARG, "i_hi must exceed i_lo");
+    if (d.t_r < 0 || !std::isfinite(d.t_r)) return fail(BF_ERR_INVALID_ARG, "t_r must be >= 0");
+    if (d.spatial != BF_KERNEL_GAUSSIAN && d.spatial != BF_KERNEL_BOX) {
+        if (d.spatial == BF_KERNEL_EXPONENTIAL)
+            return fail(BF_ERR_UNSUPPORTED, "non-separable (exponential) spatial kernel is not implemented");
+        return fail(BF_ERR_INVALID_ARG, "unknown spatial kernel");
+    }
+    if (d.range < BF_KERNEL_GAUSSIAN || d.range > BF_KERNEL_BOX) return fail(BF_ERR_INVALID_ARG, "unknown range kernel");
+    if (d.policy == BF_RANGE_PAPER_3D)
+        return fail(BF_ERR_UNSUPPORTED, "BF_RANGE_PAPER_3D (z-binned range box) is not implemented");
+    if (d.policy != BF_RANGE_TRUNCATED_MIN_PERIOD && d.policy != BF_RANGE_UNTRUNCATED_FULL)
+        return fail(BF_ERR_INVALID_ARG, "unknown range policy");
+    if (d.precision < BF_PREC_FP32 || d.precision > BF_PREC_FP16_EXCHANGE)
+        return fail(BF_ERR_INVALID_ARG, "unknown precision");
+
+    p.desc = d;
+    const double dI = (double)d.i_hi - (double)d.i_lo;
+    // ---- truncation (Sec. IV-A)
+    p.R = d.radius > 0 ? d.radius : (int)std::floor(3.0 * d.sigma_s + 0.5);
+    p.Ts = p.R + 0.5;
+    p.J = (int)std::ceil(std::log2(2.0 * p.Ts));
+    double tr = d.t_r > 0 ? d.t_r
+                          : (d.range == BF_KERNEL_GAUSSIAN ? 3.0 * d.sigma_r
+                             : d.range == BF_KERNEL_EXPONENTIAL ? d.sigma_r * std::log(100.0) : d.sigma_r);
+    if (d.policy == BF_RANGE_UNTRUNCATED_FULL) {
+        p.P = dI;
+        p.Tr = dI;
+    } else {
+        p.P = std::max(tr, 0.5 * (dI + tr));
+        p.Tr = tr;
+    }
+
+    // ---- range coefficients a_k on [-P, P] (Eqs. (14), (15)), first 20 N_r candidates (App. B)
+    const int ncand = 20 * d.nr_terms;
+    double L = std::min(p.Tr, p.P);
+    if (d.range == BF_KERNEL_BOX) L = std::min(L, d.sigma_r);
+    std::vector<Cand> rc(ncand);
+    for (int k = 0; k < ncand; ++k) {
+        double w = kPi * k / p.P;
+        int pieces = 4 + (int)std::ceil(2.0 * k * L / p.P);
+        double s = integrate(
+            [&](double t) { return (d.range == BF_KERNEL_BOX ? 1.0 : range_value(d.range, d.sigma_r, t)) * std::cos(w * t); },
+            0.0, L, pieces);
+        double ak = (k == 0 ? 1.0 : 2.0) * s / p.P;
+        rc[k] = Cand{std::fabs(ak), ak, {k, 0, 0, 0, 0}, k, 0};
+    }
+    rank(rc);
+    int nr = std::min<int>(d.nr_terms, (int)rc.size());
+    if (nr < 1) return fail(BF_ERR_INVALID_ARG, "range kernel has no non-zero coefficient");
+    std::vector<std::pair<int, double>> sel;
+    for (int i = 0; i < nr; ++i) sel.push_back({rc[i].a, rc[i].c});
+    std::sort(sel.begin(), sel.end());
+    for (auto &e : sel) {
+        p.k.push_back(e.first);
+        p.a.push_back(e.second);
+    }
+
+    // ---- 1-D Haar coefficients of the spatial profile (Eq. (20)); 2-D by separability (Eq. (22))
+    if (p.J > 12) return fail(BF_ERR_UNSUPPORTED, "radius too large for the Haar dictionary");
+    std::vector<Haar1> dict = haar_dictionary(p.J, p.Ts);
+    const int n1 = (int)dict.size();
+    auto prof_int = [&](double a, double b) {
+        if (d.spatial == BF_KERNEL_BOX) return b - a;
+        int pieces = std::max(1, (int)std::ceil((b - a) / (0.5 * d.sigma_s)));
+        return integrate([&](double x) { return spatial_profile(d.spatial, d.sigma_s, x); }, a, b, pieces);
+    };
+    std::vector<double> c1(n1);
+    for (int i = 0; i < n1; ++i) {
+        const Haar1 &h = dict[i];
+        if (h.lev < 0) c1[i] = prof_int(h.lo, h.hi) / (2.0 * p.Ts);
+        else c1[i] = std::ldexp(1.0, h.lev) * (prof_int(h.lo, h.mid) - prof_int(h.mid, h.hi)) / (2.0 * p.Ts);
+    }
+    std::vector<Cand> sc;
+    sc.reserve((size_t)n1 * n1);
+    for (int i1 = 0; i1 < n1; ++i1)
+        for (int i2 = 0; i2 < n1; ++i2) {
+            double c = c1[i1] * c1[i2];
+            int j1 = dict[i1].lev, j2 = dict[i2].lev;
+            sc.push_back(Cand{std::fabs(c), c, {std::max(j1, j2), j1, j2, dict[i1].k, dict[i2].k}, i1, i2});
+        }
+    rank(sc);
+    int ns = std::min<int>(d.ns_terms, (int)sc.size());
+    p.tie_split = (ns < (int)sc.size() && sc[ns].mag >= sc[ns - 1].mag * (1.0 - 1e-12)) ? 1 : 0;
+    const int R = p.R, w = 2 * R + 1;
+    p.kernel.assign((size_t)w * w, 0.0);
+    for (int t = 0; t < ns; ++t) {
+        const Haar1 &hx = dict[sc[t].a], &hy = dict[sc[t].b];
+        p.terms.insert(p.terms.end(), {hx.lev, hx.k, hy.lev, hy.k});
+        p.tcoef.push_back(sc[t].c);
+        std::vector<double> ux(w), uy(w);
+        for (int dd = -R; dd <= R; ++dd) {
+            ux[dd + R] = haar_value(hx, dd);
+            uy[dd + R] = haar_value(hy, dd);
+        }
+        for (int dy = 0; dy < w; ++dy)
+            for (int dx = 0; dx < w; ++dx) p.kernel[(size_t)dy * w + dx] += sc[t].c * ux[dx] * uy[dy];
+    }
+
+    // ---- compile into windows.  Weight of the neighbour at offset d = y - x is K~_s(x - y) (Eq. (32)).
+    double kmax = 0;
+    for (double v : p.kernel) kmax = std::max(kmax, std::fabs(v));
+    const double tol = 1e-13 * std::max(kmax, 1e-300);
+    auto Kd = [&](int dx, int dy) { return p.kernel[(size_t)(-dy + R) * w + (-dx + R)]; };
+    std::vector<std::vector<double>> rows(w, std::vector<double>(w));
+    for (int dy = -R; dy <= R; ++dy)
+        for (int dx = -R; dx <= R; ++dx) rows[dy + R][dx + R] = Kd(dx, dy);
+    // vertical: treat each column offset dx as a profile over dy
+    std::vector<std::vector<double>> colprof(w, std::vector<double>(w));
+    for (int dx = 0; dx < w; ++dx)
+        for (int dy = 0; dy < w; ++dy) colprof[dx][dy] = rows[dy][dx];
+    std::vector<std::pair<int, int>> vw;
+    std::vector<std::vector<double>> vcoef;  // [dx][v]
+    split_profiles(colprof, R, tol, vw, vcoef);
+    // horizontal profile of each vertical window: hp[v](dx) = vcoef[dx][v]
+    std::vector<std::vector<double>> hp(vw.size(), std::vector<double>(w));
+    for (size_t v = 0; v < vw.size(); ++v)
+        for (int dx = 0; dx < w; ++dx) hp[v][dx] = vcoef[dx][v];
+    std::vector<std::pair<int, int>> hw;
+    std::vector<std::vector<double>> hcoef;  // [v][h]
+    split_profiles(hp, R, tol, hw, hcoef);
+    p.nv = (int)vw.size();
+    p.nh = (int)hw.size();
+    for (auto &e : vw) p.vwin.insert(p.vwin.end(), {e.first, e.second});
+    for (auto &e : hw) p.hwin.insert(p.hwin.end(), {e.first, e.second});
+    for (int v = 0; v < p.nv; ++v)
+        for (int h = 0; h < p.nh; ++h) p.wcoef.push_back(hcoef[v][h]);
+    // verify the compilation reproduces the kernel
+    double maxdiff = 0;
+    for (int dy = -R; dy <= R; ++dy)
+        for (int dx = -R; dx <= R; ++dx) {
+            double s = 0;
+            for (int v = 0; v < p.nv; ++v)
+                if (dy >= vw[v].first && dy <= vw[v].second)
+                    for (int h = 0; h < p.nh; ++h)
+                        if (dx >= hw[h].first && dx <= hw[h].second) s += hcoef[v][h];
+            maxdiff = std::max(maxdiff, std::fabs(s - Kd(dx, dy)));
+        }
+    if (maxdiff > 1e-12 * std::max(kmax, 1e-300))
+        return fail(BF_ERR_UNSUPPORTED, "internal: box-window compilation does not reproduce the kernel");
+
+    // ---- reports
+    double sk = 0, sa = 0;
+    for (double v : p.kernel) sk += std::fabs(v);
+    for (double v : p.a) sa += std::fabs(v);
+    p.den_eps = 1e-6 * sk * sa;
+    p.range_max_err = 0;
+    for (int i = 0; i <= 4000; ++i) {
+        double t = -dI + 2.0 * dI * i / 4000.0, s = 0;
+        for (size_t j = 0; j < p.k.size(); ++j) s += p.a[j] * std::cos(kPi * p.k[j] * t / p.P);
+        p.range_max_err = std::max(p.range_max_err, std::fabs(s - range_value(d.range, d.sigma_r, t)));
+    }
+    p.spatial_max_err = 0;
+    for (int dy = -R; dy <= R; ++dy)
+        for (int dx = -R; dx <= R; ++dx) {
+            double ks = d.spatial == BF_KERNEL_BOX ? 1.0 : std::exp(-(double)(dx * dx + dy * dy) / (2.0 * d.sigma_s * d.sigma_s));
+            p.spatial_max_err = std::max(p.spatial_max_err, std::fabs(ks - p.kernel[(size_t)(dy + R) * w + dx + R]));
+        }
+
+    // ---- kernel passes
+    p.m = std::max(p.nv, p.nh);
+    if (!bfi::kernel_class_supported(p.m))
+        return fail(BF_ERR_UNSUPPORTED, "spatial approximation needs " + std::to_string(p.m) +
+                                            " box windows per axis; this build supports up to " +
+                                            std::to_string(bfi::kMaxWin) + " (reduce ns_terms)");
+    const int slots = bfi::slots_per_pass(p.m);
+    bfi::FilterParams base;
+    std::memset(&base, 0, sizeof(base));
+    base.inv_p = (float)(1.0 / p.P);
+    base.i_lo = d.i_lo;
+    base.den_eps = (float)p.den_eps;
+    base.m = p.m;
+    int rx = 0, vlo = 0, vhi = 0;
+    for (int r = 0; r < p.m; ++r) {
+        if (r < p.nv) {
+            base.v0[r] = vw[r].first;
+            base.v1[r] = vw[r].second;
+        } else {
+            base.v0[r] = 0;  // padding window, zero weight
+            base.v1[r] = 0;
+        }
+        if (r < p.nh) {
+            base.u0[r] = hw[r].first;
+            base.u1[r] = hw[r].second;
+        } else {
+            base.u0[r] = 0;
+            base.u1[r] = 0;
+        }
+        for (int q = 0; q < p.m; ++q) base.C[r][q] = (r < p.nv && q < p.nh) ? (float)hcoef[r][q] : 0.0f;
+        rx = std::max({rx, std::abs(base.u0[r]), std::abs(base.u1[r])});
+        vlo = std::min(vlo, base.v0[r]);
+        vhi = std::max(vhi, base.v1[r]);
+    }
+    base.rx = rx;
+    base.vlo = vlo;
+    base.vhi = vhi;
+    for (int s0 = 0; s0 < nr; s0 += slots) {
+        bfi::FilterParams fp = base;
+        fp.nk = std::min(slots, nr - s0);
+        for (int i = 0; i < slots; ++i) {
+            int src = std::min(s0 + i, nr - 1);
+            fp.k[i] = p.k[src];
+            fp.a[i] = (s0 + i < nr) ? (float)p.a[src] : 0.0f;
+        }
+        p.passes.push_back(fp);
+    }
+    return BF_OK;
+}
+
+}  // namespace
+
+namespace bfi {
+bf_status plan_build(const bf_plan_desc &d, bf_plan &p) { return build(d, p); }
+}  // namespace bfi

@@ -1,0 +1,134 @@
+"""C-ABI library checks that need no GPU: it loads, exports every symbol the
+header declares, validates arguments, and its host-side plan (coefficients,
+best N-term selection, kernel table, window compilation) agrees with the
+independent FP64 oracle."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1803_00004_gb300 as bf
+from oracle import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1803_00004_gb300 import _build
+    _build.build()
+
+
+def test_exports_every_declared_symbol():
+    hdr = open(os.path.join(ROOT, "include", "bf.h")).read()
+    names = set(re.findall(r"\b(bf_[a-z_0-9]+)\s*\(", hdr))
+    assert names, "no declarations found"
+    L = bf.lib()
+    for n in sorted(names):
+        assert hasattr(L, n), "missing export %s" % n
+    assert set(bf.EXPORTS) <= names
+
+
+def test_status_strings_and_version():
+    L = bf.lib()
+    for s in range(12):
+        assert L.bf_status_string(s)
+    assert bf.bf_version() >= 1
+
+
+DESCS = [
+    dict(),
+    dict(sigma_s=2.0, ns_terms=13, sigma_r=0.05),
+    dict(sigma_s=8.0, ns_terms=25, nr_terms=16),
+    dict(sigma_s=32.0, sigma_r=0.3),
+    dict(sigma_s=4.0, ns_terms=2),
+    dict(sigma_s=3.0, ns_terms=3, nr_terms=5),
+    dict(range=bf.KERNEL_EXPONENTIAL, sigma_r=0.1, nr_terms=12),
+    dict(range=bf.KERNEL_BOX, sigma_r=0.2, nr_terms=10),
+    dict(policy=bf.RANGE_UNTRUNCATED_FULL, sigma_r=0.2, nr_terms=6),
+    dict(spatial=bf.KERNEL_BOX, sigma_s=2.0, ns_terms=4),
+    dict(sigma_s=2.0, radius=4, ns_terms=25, nr_terms=16, sigma_r=0.07),
+]
+
+
+def _odesc(kw):
+    m = dict(kw)
+    od = {}
+    for k, v in m.items():
+        od[{"spatial": "spatial", "range": "range", "policy": "policy"}.get(k, k)] = v
+    return O.Desc(**od)
+
+
+@pytest.mark.parametrize("kw", DESCS)
+def test_plan_matches_oracle(kw):
+    p = bf.Plan(device=-1, **kw)
+    c = p.coeffs()
+    o = O.plan_info(_odesc(kw))
+    assert c["radius"] == o.R
+    assert abs(c["t_r"] - o.Tr) < 1e-15 and abs(c["period"] - o.P) < 1e-15
+    # same selected cosine terms (the product lists them by k, the oracle by rank)
+    order = np.argsort(o.ks)
+    assert list(c["k"]) == list(o.ks[order])
+    assert np.max(np.abs(np.array(c["a"]) - o.ak[order])) < 1e-13
+    # same Haar terms in the same ranking order
+    assert [list(t) for t in c["haar_terms"]] == [list(t) for t in o.terms]
+    assert np.max(np.abs(np.array(c["haar_coef"]) - o.term_c)) < 1e-14
+    assert c["tie_split"] == o.tie_split
+    assert np.max(np.abs(np.array(c["kernel"]) - o.Ks)) < 1e-14
+    assert abs(c["den_eps"] - o.den_eps) < 1e-12 * max(1.0, o.den_eps)
+
+
+@pytest.mark.parametrize("kw", DESCS)
+def test_window_compilation_reproduces_kernel(kw):
+    c = bf.Plan(device=-1, **kw).coeffs()
+    R = c["radius"]
+    K = np.array(c["kernel"])
+    rec = np.zeros_like(K)   # indexed [dy + R, dx + R] over neighbour offsets d = y - x
+    for v, (v0, v1) in enumerate(c["vwin"]):
+        for h, (u0, u1) in enumerate(c["hwin"]):
+            rec[v0 + R:v1 + R + 1, u0 + R:u1 + R + 1] += c["wcoef"][v][h]
+    # weight of neighbour offset d is K~_s(-d)
+    assert np.max(np.abs(rec - K[::-1, ::-1])) < 1e-12 * np.max(np.abs(K))
+
+
+def test_paper_five_terms_compile_to_two_nested_windows():
+    c = bf.Plan(device=-1).coeffs()
+    assert c["vwin"] == [(-6, 6), (-12, 12)] and c["hwin"] == [(-6, 6), (-12, 12)]
+    assert abs(c["wcoef"][0][0]) < 1e-15   # no inner x inner box: three box shapes, Sec. V-A
+    assert c["passes"] == 1
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(sigma_s=0.0), 1), (dict(sigma_r=-1.0), 1), (dict(ns_terms=0), 1), (dict(nr_terms=0), 1),
+    (dict(i_lo=1.0, i_hi=1.0), 1), (dict(policy=bf.RANGE_PAPER_3D), 2), (dict(spatial=bf.KERNEL_EXPONENTIAL), 2),
+    (dict(spatial=7), 1), (dict(precision=9), 1), (dict(radius=-2), 1),
+])
+def test_plan_create_rejects(kw, status):
+    with pytest.raises(bf.BFError) as ei:
+        bf.Plan(device=-1, **kw)
+    assert ei.value.status == status
+
+
+def test_filter_argument_checks_without_gpu():
+    p = bf.Plan(device=-1)
+    L = bf.lib()
+    # overlapping input/output -> invalid argument before any device work
+    assert L.bf_filter(p.handle, 4096, 256, 4096 + 128, 256, 4, 64, None) == 1
+    # bad pitch
+    assert L.bf_filter(p.handle, 4096, 6, 1 << 20, 256, 4, 64, None) == 1
+    assert L.bf_filter(p.handle, 4096, 64, 1 << 20, 256, 4, 64, None) == 1
+    # empty image is a no-op
+    assert L.bf_filter(p.handle, 0, 0, 0, 0, 0, 5, None) == 0
+    # host-only plan cannot filter
+    assert L.bf_filter(p.handle, 4096, 256, 1 << 20, 256, 4, 64, None) == 9
+    assert L.bf_filter(None, 4096, 256, 1 << 20, 256, 4, 64, None) == 1
+    assert L.bf_coeffs(None, None) == 1
+
+
+def test_range_and_spatial_errors_reported():
+    c = bf.Plan(device=-1, sigma_r=0.1, nr_terms=8).coeffs()
+    assert 0 < c["range_max_err"] < 0.05
+    c2 = bf.Plan(device=-1, sigma_r=0.3, nr_terms=8, policy=bf.RANGE_UNTRUNCATED_FULL).coeffs()
+    assert c2["range_max_err"] < 1e-2

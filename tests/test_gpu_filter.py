@@ -1,0 +1,169 @@
+"""GPU parity of bf_filter / bf_exact against the FP64 oracle (needs a CUDA GPU).
+
+Element-wise comparisons on seeded images that span several tiles with ragged
+tails, edge cases (tiny images, kernels wider than the image, pitched buffers,
+asymmetric kernels, multi-pass plans), and sampled comparisons at the full
+1920x1080 benchmark size.  Tolerance: 1e-5 max-abs for the fp32 path (the bar
+the method's FP32 evaluation is held to on [0, 1] images).
+"""
+import numpy as np
+import pytest
+
+import paper_1803_00004_gb300 as bf
+from oracle import oracle as O
+from paper_1803_00004_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+THREADS = 16
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1803_00004_gb300 import _build
+    _build.build()
+    torch.cuda.init()
+
+
+def run(img, **kw):
+    plan = bf.Plan(device=0, **kw)
+    src = torch.from_numpy(np.ascontiguousarray(img, dtype=np.float32)).cuda()
+    dst = torch.full_like(src, float("nan"))
+    bf.bf_filter(plan, src, dst)
+    torch.cuda.synchronize()
+    return dst.cpu().numpy().astype(np.float64)
+
+
+def odesc(**kw):
+    return O.Desc(**kw)
+
+
+CASES = [
+    ("cfg1_blocks_256", synth.blocks(256, 256, 0), dict()),
+    ("shapes_m3", synth.shapes(300, 517, 1, scale=0.2), dict(sigma_s=2.0, ns_terms=13, sigma_r=0.05)),
+    ("m4_multipass", synth.shapes(333, 270, 2, scale=0.2), dict(sigma_s=8.0, ns_terms=25, nr_terms=16)),
+    ("tie_split_asym", synth.blocks(257, 129, 3), dict(sigma_s=4.0, ns_terms=2)),
+    ("tie_split_m3", synth.uniform(77, 301, 4), dict(sigma_s=3.0, ns_terms=7, nr_terms=5)),
+    ("exp_range_2pass", synth.shapes(190, 260, 5, scale=0.2), dict(range=bf.KERNEL_EXPONENTIAL, sigma_r=0.1, nr_terms=12)),
+    ("box_range", synth.shapes(150, 170, 6, scale=0.2), dict(range=bf.KERNEL_BOX, sigma_r=0.2, nr_terms=10)),
+    ("untruncated", synth.blocks(128, 300, 7), dict(policy=bf.RANGE_UNTRUNCATED_FULL, sigma_r=0.2, nr_terms=6)),
+    ("box_spatial_m1", synth.blocks(140, 150, 8), dict(spatial=bf.KERNEL_BOX, sigma_s=2.0, ns_terms=4, nr_terms=20)),
+    ("sigma32_R96", synth.shapes(400, 300, 9, scale=0.3), dict(sigma_s=32.0, sigma_r=0.3)),
+    ("sigma8_nr32", synth.shapes(200, 220, 10, scale=0.2), dict(sigma_s=8.0, sigma_r=0.05, nr_terms=32)),
+    ("m5", synth.shapes(160, 140, 11, scale=0.2), dict(sigma_s=4.0, ns_terms=41, nr_terms=6)),
+]
+
+
+@pytest.mark.parametrize("name,img,kw", CASES, ids=[c[0] for c in CASES])
+def test_parity_with_oracle(name, img, kw):
+    got = run(img, **kw)
+    ref, _ = O.approx_fast(img.astype(np.float64), odesc(**kw), threads=THREADS)
+    err = np.max(np.abs(got - ref))
+    assert err < TOL, "%s: max err %.3g" % (name, err)
+
+
+@pytest.mark.parametrize("H,W", [(1, 1), (1, 200), (200, 1), (5, 3), (24, 7), (3, 129), (31, 17)])
+def test_tiny_and_narrow_images(H, W):
+    img = synth.uniform(H, W, seed=H * 1000 + W)
+    for kw in (dict(), dict(sigma_s=2.0, ns_terms=13), dict(sigma_s=4.0, ns_terms=2)):
+        got = run(img, **kw)
+        ref, _ = O.approx_fast(img.astype(np.float64), odesc(**kw))
+        assert np.max(np.abs(got - ref)) < TOL
+
+
+def test_constant_image_unchanged():
+    img = np.full((150, 333), 0.625, dtype=np.float32)
+    for kw in (dict(), dict(sigma_s=8.0, ns_terms=13, nr_terms=16), dict(sigma_s=2.0, ns_terms=2)):
+        assert np.max(np.abs(run(img, **kw) - 0.625)) < 1e-6
+
+
+def test_pitched_buffers_and_offset_range():
+    """Row pitch larger than the width, and data range [2, 3]: the filter commutes with
+    an intensity shift, so the result is the oracle's on I - 2, plus 2."""
+    img = synth.shapes(120, 200, 12, scale=0.2)
+    plan = bf.Plan(device=0, i_lo=2.0, i_hi=3.0)
+    big = torch.zeros((120, 256), dtype=torch.float32, device="cuda")
+    big[:, :200] = torch.from_numpy(img + 2.0).cuda()
+    out = torch.full((120, 264), float("nan"), dtype=torch.float32, device="cuda")
+    bf.bf_filter(plan, big[:, :200], out[:, :200])
+    torch.cuda.synchronize()
+    got = out[:, :200].cpu().numpy().astype(np.float64) - 2.0
+    ref, _ = O.approx_fast(img.astype(np.float64), odesc())
+    assert np.max(np.abs(got - ref)) < 2e-5
+    assert torch.isnan(out[:, 200:]).all()  # nothing written past the width
+
+
+def test_full_size_sampled_parity():
+    """1920x1080 (the benchmark workload) at each (sigma_s, sigma_r) of the sweep: sampled
+    pixels, including the image border rows/columns, against the oracle's direct evaluation."""
+    img = synth.shapes(1080, 1920, seed=0)
+    rng = np.random.default_rng(0)
+    pts = np.concatenate([
+        np.stack([rng.integers(0, 1080, 160), rng.integers(0, 1920, 160)], 1),
+        np.array([[0, 0], [1079, 1919], [0, 1919], [1079, 0], [540, 0], [0, 960], [1079, 1000], [600, 1919]]),
+    ])
+    for ss in (2.0, 8.0, 32.0):
+        for sr in (0.05, 0.1, 0.3):
+            kw = dict(sigma_s=ss, sigma_r=sr, nr_terms=8, ns_terms=5)
+            got = run(img, **kw)[pts[:, 0], pts[:, 1]]
+            ref = O.approx_direct_at(img.astype(np.float64), odesc(**kw), pts, threads=THREADS)
+            err = np.max(np.abs(got - ref))
+            assert err < TOL, "sigma_s=%g sigma_r=%g: %.3g" % (ss, sr, err)
+
+
+def test_deterministic_and_stream():
+    img = synth.shapes(300, 400, 13, scale=0.2)
+    plan = bf.Plan(device=0, sigma_s=8.0, ns_terms=13, nr_terms=16)
+    src = torch.from_numpy(img).cuda()
+    a = torch.empty_like(src)
+    b = torch.empty_like(src)
+    bf.bf_filter(plan, src, a)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        bf.bf_filter(plan, src, b, stream=s)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+def test_in_place_rejected_and_injected_failure():
+    img = synth.blocks(64, 64, 0)
+    plan = bf.Plan(device=0)
+    src = torch.from_numpy(img).cuda()
+    with pytest.raises(bf.BFError) as ei:
+        bf.bf_filter(plan, src, src)
+    assert ei.value.status == 1
+    dst = torch.empty_like(src)
+    bf.bf_debug_fail_launches(1)
+    with pytest.raises(bf.BFError) as ei:
+        bf.bf_filter(plan, src, dst)
+    assert ei.value.status == 4
+    bf.bf_filter(plan, src, dst)  # recovers
+    torch.cuda.synchronize()
+    ref, _ = O.approx_fast(img.astype(np.float64), odesc())
+    assert np.max(np.abs(dst.cpu().numpy() - ref)) < TOL
+
+
+@pytest.mark.parametrize("kw", [dict(sigma_s=2.0, sigma_r=0.1), dict(sigma_s=3.0, sigma_r=0.2, range=bf.KERNEL_EXPONENTIAL),
+                                dict(sigma_s=1.0, sigma_r=0.15, spatial=bf.KERNEL_BOX, radius=4)])
+def test_exact_helper_matches_oracle(kw):
+    img = synth.shapes(90, 130, 14, scale=0.1)
+    src = torch.from_numpy(img).cuda()
+    dst = torch.empty_like(src)
+    bf.bf_exact(src, dst, **kw)
+    torch.cuda.synchronize()
+    od = dict(kw)
+    ref = O.exact_bf(img.astype(np.float64), O.Desc(**od), threads=THREADS)
+    assert np.max(np.abs(dst.cpu().numpy() - ref)) < 2e-5
+
+
+def test_config1_accuracy_against_exact_bf():
+    """Config 1: the approximation is >= 40 dB PSNR against the exact bilateral filter."""
+    img = synth.blocks(256, 256, 0)
+    got = run(img)
+    ex = O.exact_bf(img.astype(np.float64), O.Desc(), threads=THREADS)
+    psnr = 10 * np.log10(1.0 / np.mean((got - ex) ** 2))
+    assert psnr >= 40.0, psnr

@@ -172,3 +172,11 @@ def test_accuracy_improves_with_spatial_terms():
         out = O.approx_fast(I, D(sigma_s=2.0, ns_terms=ns, sigma_r=0.1, nr_terms=16, policy=O.UNTRUNCATED_FULL))[0]
         errs.append(np.mean((out - ex) ** 2))
     assert all(errs[i + 1] < errs[i] for i in range(len(errs) - 1))
+
+
+def test_direct_at_points_matches_full():
+    I = synth.shapes(30, 41, seed=3, scale=0.05).astype(np.float64)
+    desc = D(sigma_s=2.0, ns_terms=13)
+    full, _ = O.approx_direct(I, desc)
+    pts = np.array([[0, 0], [29, 40], [15, 7], [3, 39], [29, 0]])
+    assert np.array_equal(O.approx_direct_at(I, desc, pts), full[pts[:, 0], pts[:, 1]])
