@@ -43,7 +43,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
+    ap.add_argument("--no-psnr", action="store_true", help="skip the exact-filter accuracy check")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--only", default=None, help="restrict to one combination 'sigma_s,sigma_r' (profiling)")
+    ap.add_argument("--no-ramp", action="store_true", help="skip the untimed clock-ramp load (profiling)")
     return ap.parse_args()
 
 
@@ -138,7 +142,10 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     img = synth.shapes(H, W, seed=0)
     src = torch.from_numpy(img).to(dev)
-    plans = [bf.Plan(sigma_s=ss, sigma_r=sr, nr_terms=NR, ns_terms=NS, device=local) for ss in SIGMA_S for sr in SIGMA_R]
+    combos = [(a, b) for a in SIGMA_S for b in SIGMA_R]
+    if args.only:
+        combos = [tuple(float(v) for v in args.only.split(","))]
+    plans = [bf.Plan(sigma_s=ss, sigma_r=sr, nr_terms=NR, ns_terms=NS, device=local) for ss, sr in combos]
     coeffs = [p.coeffs() for p in plans]
     outs = [torch.empty_like(src) for _ in plans]
     launches_per_step = sum(c["passes"] for c in coeffs)
@@ -147,7 +154,7 @@ def run_ours(args):
     # accuracy against the exact filter (untimed)
     psnr = []
     ex = torch.empty_like(src)
-    for p, o, (ss, sr) in zip(plans, outs, [(a, b) for a in SIGMA_S for b in SIGMA_R]):
+    for p, o, (ss, sr) in zip(plans, outs, combos if not args.no_psnr else []):
         bf.bf_filter(p, src, o)
         bf.bf_exact(src, ex, sigma_s=ss, sigma_r=sr)
         torch.cuda.synchronize()
@@ -167,7 +174,10 @@ def run_ours(args):
         torch.distributed.barrier()
     sampler = ClockSampler(local)
     sampler.start()
-    time.sleep(0.3)
+    t_ramp = time.perf_counter()
+    while not args.no_ramp and time.perf_counter() - t_ramp < 1.5:  # untimed load: sampler sees loaded clocks
+        step()
+        torch.cuda.synchronize()
     per_step = []
     # per-launch device time of the dominant kernel: events around each launch
     launch_ms = []
@@ -223,9 +233,10 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 3), "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "height": H, "width": W, "images_per_step": len(plans),
+        "config": {"workload": WORKLOAD if not args.only else "1920x1080, sigma_s,sigma_r = " + args.only,
+                   "height": H, "width": W, "images_per_step": len(plans),
                    "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "single"},
-        "psnr_db_vs_exact": [round(x, 2) for x in psnr], "min_psnr_db": round(min(psnr), 2),
+        "psnr_db_vs_exact": [round(x, 2) for x in psnr], "min_psnr_db": round(min(psnr), 2) if psnr else None,
         "per_combo_ms": [round(x, 4) for x in lm.mean(0)],
         "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
                      "frac": round(achieved / alu_peak, 4), "traffic": None,
@@ -236,7 +247,7 @@ def run_ours(args):
         "e2e": e2e,
     }
     if rank == 0:
-        if os.environ.get("BENCH_CPU_BASELINE", "1") == "1" and world == 1:
+        if not args.no_cpu and world == 1:
             line["cpu_baseline"] = cpu_baseline(img)
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -554,6 +554,7 @@ int orc_approx_direct_at(const double *I, int H, int W,
 
 /* ------------------------------------------------------------------ */
 /* O3: the paper's algorithm, Eqs. (34)-(36) with App. A boxes          */
+/* (den_out, if not NULL, receives the denominator of Eq. (1))          */
 /* ------------------------------------------------------------------ */
 
 /* A discrete 1-D range [lo, hi] of neighbour offsets with a weight. */
@@ -616,7 +617,7 @@ typedef struct { int x0, x1, y0, y1; double c; } dbox;
 int orc_approx_fast(const double *I, int H, int W,
                     int skind, double sigma_s, int radius, int ns_terms,
                     int rkind, double sigma_r, double t_r, int nr_terms, int policy, double data_range,
-                    double *out, int *ndegen, int nthreads)
+                    double *out, int *ndegen, int nthreads, double *den_out)
 {
     if (!I || !out || H < 0 || W < 0) return ORC_EINVAL;
     orc_plan p;
@@ -676,6 +677,7 @@ int orc_approx_fast(const double *I, int H, int W,
     for (size_t i = 0; i < np; i++) {
         if (den[i] <= p.den_eps) { out[i] = I[i]; degen++; }
         else out[i] = num[i] / den[i];
+        if (den_out) den_out[i] = den[i];
     }
     if (ndegen) *ndegen = degen;
     free(num); free(den); free(g); free(S); free(cb); free(sb); free(boxes);

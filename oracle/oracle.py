@@ -64,7 +64,7 @@ def _load():
         lib.orc_exact_bf.argtypes = [pd, i, i, i, d, i, i, d, pd, pi, i, i]
         common = [pd, i, i, i, d, i, i, i, d, d, i, i, d, pd, pi, i]
         lib.orc_approx_direct.argtypes = common
-        lib.orc_approx_fast.argtypes = common
+        lib.orc_approx_fast.argtypes = common + [pd]
         lib.orc_box_count.argtypes = [i, d, i, i, i, d, d, i, i, d]
         lib.orc_approx_direct_at.argtypes = [pd, i, i, i, d, i, i, i, d, d, i, i, d, pi, i, pd, i]
         _lib = lib
@@ -222,15 +222,20 @@ def approx_direct(I, desc: Desc, threads: int = 1):
     return out, int(nd[0])
 
 
-def approx_fast(I, desc: Desc, threads: int = 1):
-    """O3: returns (output, number of pixels where the denominator guard fired)."""
+def approx_fast(I, desc: Desc, threads: int = 1, return_den: bool = False):
+    """O3: returns (output, number of pixels where the denominator guard fired)
+    [, denominator of Eq. (1) per pixel if return_den]."""
     I = _img(I)
     H, W = I.shape
     out = np.zeros((H, W))
+    den = np.zeros((H, W)) if return_den else None
     nd = np.zeros(1, dtype=np.int32)
-    st = _load().orc_approx_fast(_dp(I), H, W, *desc.args(), _dp(out), _ip(nd), threads)
+    st = _load().orc_approx_fast(_dp(I), H, W, *desc.args(), _dp(out), _ip(nd), threads,
+                                 _dp(den) if return_den else None)
     if st:
         raise ValueError("orc_approx_fast status %d" % st)
+    if return_den:
+        return out, int(nd[0]), den
     return out, int(nd[0])
 
 

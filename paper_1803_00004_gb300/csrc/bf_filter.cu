@@ -39,6 +39,42 @@ namespace {
 
 std::atomic<int> g_fail_launches{0};
 
+// Basis at one pixel: base rotation (cos, sin)(pi t) and the starting value
+// (cos, sin)(pi k0 t), t = v / P.  t is carried as th + tl (two floats; the
+// rounding of v / P would otherwise cost pi k |t| 2^-24 of phase at term k)
+// and each sincospi is corrected to first order in its low part.  Invalid
+// pixels start from (0, 0), so every basis image is zero there.
+__device__ __forceinline__ void basis_start(float v, float inv_p, float inv_p_lo, int k0, bool valid, float &c1,
+                                            float &s1, float &c0, float &s0) {
+    constexpr float kPiF = 3.14159265358979f;
+    const float th = v * inv_p;
+    const float tl = fmaf(v, inv_p, -th) + v * inv_p_lo;
+    float sb, cb;
+    sincospif(th, &sb, &cb);
+    const float d = kPiF * tl;
+    c1 = fmaf(-d, sb, cb);
+    s1 = fmaf(d, cb, sb);
+    if (!valid) {
+        c0 = 0.f;
+        s0 = 0.f;
+    } else if (k0 == 0) {
+        c0 = 1.f;
+        s0 = 0.f;
+    } else if (k0 == 1) {
+        c0 = c1;
+        s0 = s1;
+    } else {
+        const float kf = (float)k0;
+        const float kh = kf * th;
+        const float kl = fmaf(kf, th, -kh) + kf * tl;
+        float sk, ck;
+        sincospif(kh, &sk, &ck);
+        const float dk = kPiF * kl;
+        c0 = fmaf(-dk, sk, ck);
+        s0 = fmaf(dk, ck, sk);
+    }
+}
+
 template <int NK, int M>
 __global__ void __launch_bounds__(512, 1)
 bf_fused_kernel(const float *__restrict__ in, size_t in_pitch, float *__restrict__ out, size_t out_pitch,
@@ -73,21 +109,17 @@ bf_fused_kernel(const float *__restrict__ in, size_t in_pitch, float *__restrict
     for (int y = ys; y < y_end; ++y) {
         const bool outrow = (y >= y0);
         float Ie[NE], c1[NE], s1[NE], ce[NE], se[NE];
+        const int k0 = p.k[0];
 #pragma unroll
         for (int e = 0; e < NE; ++e) {
             const int off = e < M ? p.v1[e] : (e < 2 * M ? p.v0[e - M] - 1 : 0);
             const int row = y + off;
             const bool valid = (e < 2 * M) ? (colv && row >= y_lo && row < H) : (colv && outrow);
             const float v = valid ? __ldg(in + (size_t)row * in_pitch + xcol) - p.i_lo : 0.f;
-            float sn, cs;
-            sincospif(v * p.inv_p, &sn, &cs);
             Ie[e] = v;
-            c1[e] = cs;
-            s1[e] = sn;
-            ce[e] = valid ? 1.f : 0.f;
-            se[e] = 0.f;
+            basis_start(v, p.inv_p, p.inv_p_lo, k0, valid, c1[e], s1[e], ce[e], se[e]);
         }
-        int kcur = 0;
+        int kcur = k0;
 #pragma unroll
         for (int i = 0; i < NK; ++i) {
             const int steps = p.k[i] - kcur;

@@ -24,6 +24,7 @@ constexpr int kMaxSlots = 16;
 // neighbour at offset (dx, dy) is sum_{r,q} C[r][q] [v0_r <= dy <= v1_r][u0_q <= dx <= u1_q].
 struct FilterParams {
     float inv_p;              // 1 / P: basis angle of term k is pi * k * (I - i_lo) / P
+    float inv_p_lo;           // 1 / P - inv_p (two-float representation of 1 / P)
     float i_lo;               // intensity origin
     float den_eps;            // denominator guard
     int nk;                   // cosine terms used in this pass (<= slots of the class)

@@ -394,6 +394,7 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
     bfi::FilterParams base;
     std::memset(&base, 0, sizeof(base));
     base.inv_p = (float)(1.0 / p.P);
+    base.inv_p_lo = (float)(1.0 / p.P - (double)base.inv_p);
     base.i_lo = d.i_lo;
     base.den_eps = (float)p.den_eps;
     base.m = p.m;

@@ -180,3 +180,20 @@ def test_direct_at_points_matches_full():
     full, _ = O.approx_direct(I, desc)
     pts = np.array([[0, 0], [29, 40], [15, 7], [3, 39], [29, 0]])
     assert np.array_equal(O.approx_direct_at(I, desc, pts), full[pts[:, 0], pts[:, 1]])
+
+
+def test_fast_denominator_is_eq1_denominator():
+    """The denominator O3 reports equals the direct sum of K~_s K~_r over the window."""
+    I = synth.uniform(9, 11, seed=5).astype(np.float64)
+    desc = D(sigma_s=1.0)
+    _, _, den = O.approx_fast(I, desc, return_den=True)
+    p = O.plan_info(desc)
+    R = p.R
+    y, x = 4, 6
+    s = 0.0
+    for dy in range(-R, R + 1):
+        for dx in range(-R, R + 1):
+            if 0 <= y + dy < 9 and 0 <= x + dx < 11:
+                t = I[y, x] - I[y + dy, x + dx]
+                s += p.Ks[-dy + R, -dx + R] * np.sum(p.ak * np.cos(np.pi * p.ks * t / p.P))
+    assert abs(den[y, x] - s) < 1e-12
