@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--only", default=None, help="restrict to one combination 'sigma_s,sigma_r' (profiling)")
     ap.add_argument("--no-ramp", action="store_true", help="skip the untimed clock-ramp load (profiling)")
+    ap.add_argument("--no-tune", action="store_true", help="use the cost-model geometry instead of autotuning")
     return ap.parse_args()
 
 
@@ -148,7 +149,6 @@ def run_ours(args):
     plans = [bf.Plan(sigma_s=ss, sigma_r=sr, nr_terms=NR, ns_terms=NS, device=local) for ss, sr in combos]
     coeffs = [p.coeffs() for p in plans]
     outs = [torch.empty_like(src) for _ in plans]
-    launches_per_step = sum(c["passes"] for c in coeffs)
     stream = torch.cuda.current_stream(dev)
 
     # accuracy against the exact filter (untimed)
@@ -161,6 +161,13 @@ def run_ours(args):
         mse = torch.mean((o.double() - ex.double()) ** 2).item()
         psnr.append(10 * np.log10(1.0 / mse) if mse > 0 else float("inf"))
 
+    tiles = []
+    if not args.no_tune:  # autotuned launch geometry per plan (untimed)
+        for p in plans:
+            tiles.append(bf.bf_autotune(p, H, W))
+    else:
+        tiles = [bf.bf_launch_info(p, H, W) for p in plans]
+    launches_per_step = sum(t["launches"] for t in tiles)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
 
     def step():
@@ -238,6 +245,7 @@ def run_ours(args):
                    "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "single"},
         "psnr_db_vs_exact": [round(x, 2) for x in psnr], "min_psnr_db": round(min(psnr), 2) if psnr else None,
         "per_combo_ms": [round(x, 4) for x in lm.mean(0)],
+        "tiles": [[t["tw"], t["th"], t["threads"], t["nk"], t["groups"]] for t in tiles],
         "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
                      "frac": round(achieved / alu_peak, 4), "traffic": None,
                      "note": "FP32 lane-ops/s of the fused kernel (algorithmic count) vs SMs x 128 x max SM clock"},

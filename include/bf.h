@@ -148,7 +148,7 @@ typedef struct {
     double range_max_err;       /* max |K_r - K~_r| over [-dI, dI] (sampled) */
     double spatial_max_err;     /* max |K_s - K~_s| over the integer window */
     double den_eps;             /* denominator guard: den <= den_eps -> output I(x) */
-    int passes;                 /* kernel launches per image */
+    int passes;                 /* term groups at the largest group size (ceil(nr / 16)) */
 } bf_coeff_view;
 
 /* Fills *out with the plan's coefficients.  Errors: BF_ERR_INVALID_ARG. */
@@ -162,6 +162,24 @@ bf_status bf_coeffs(const bf_plan *plan, bf_coeff_view *out);
  * multi-pass plans could not be allocated). */
 bf_status bf_filter(const bf_plan *plan, const float *d_in, size_t in_pitch_bytes,
                     float *d_out, size_t out_pitch_bytes, int height, int width, void *stream);
+
+/* Launch geometry bf_filter would use for this plan on a height x width image:
+ * info[0] tile width, [1] tile height, [2] threads per CTA, [3] cosine terms per
+ * CTA, [4] term groups (grid depth), [5] kernel launches, [6] shared memory
+ * bytes per CTA, [7] scratch KiB.  info must hold 8 ints.  Host only; needs no
+ * device for host-only plans (uses 152 SMs as the device size then).
+ * Errors: BF_ERR_INVALID_ARG. */
+bf_status bf_launch_info(const bf_plan *plan, int height, int width, int *info);
+
+/* Autotuner: times up to 12 candidate launch geometries (tile width, tile
+ * height, cosine terms per CTA) for this plan on a synthetic height x width
+ * image and remembers the fastest for later bf_filter / bf_filter_batch calls
+ * with the same kernel class, reach and image size on this device.  Allocates
+ * and frees its own device buffers and synchronizes `stream`; do not call it
+ * during stream capture.  info (8 ints, may be NULL) receives the chosen
+ * geometry as in bf_launch_info.  BF_TUNE_CACHE=<file> persists results.
+ * Errors: BF_ERR_INVALID_ARG, BF_ERR_NO_DEVICE, BF_ERR_OOM, BF_ERR_CUDA. */
+bf_status bf_autotune(const bf_plan *plan, int height, int width, void *stream, int *info);
 
 /* One image of a batch. */
 typedef struct {

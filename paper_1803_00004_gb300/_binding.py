@@ -59,7 +59,9 @@ class bf_result(C.Structure):
     _fields_ = [("status", C.c_int), ("latency_ms", C.c_double), ("queue_ms", C.c_double), ("device_ms", C.c_double)]
 
 
-EXPORTS = ["bf_plan_desc_default", "bf_plan_create", "bf_plan_destroy", "bf_coeffs", "bf_filter", "bf_filter_batch",
+EXPORTS = ["bf_plan_desc_default", "bf_plan_create", "bf_plan_destroy", "bf_coeffs", "bf_launch_info", "bf_autotune",
+           "bf_filter",
+           "bf_filter_batch",
            "bf_exact", "bf_serve_create", "bf_serve_submit", "bf_serve_poll", "bf_serve_cancel", "bf_serve_destroy",
            "bf_status_string", "bf_last_error", "bf_version", "bf_debug_fail_launches"]
 
@@ -87,6 +89,8 @@ def lib():
         L.bf_plan_destroy.restype = None
         L.bf_coeffs.argtypes = [vp, P(bf_coeff_view)]
         L.bf_filter.argtypes = [vp, vp, sz, vp, sz, i, i, vp]
+        L.bf_launch_info.argtypes = [vp, i, i, P(i)]
+        L.bf_autotune.argtypes = [vp, i, i, vp, P(i)]
         L.bf_filter_batch.argtypes = [P(vp), P(bf_image), i, vp]
         L.bf_exact.argtypes = [vp, sz, vp, sz, i, i, i, d, i, i, d, vp]
         L.bf_serve_create.argtypes = [P(bf_serve_config), P(vp)]
@@ -181,6 +185,20 @@ def bf_coeffs(plan: Plan) -> dict:
         "range_max_err": v.range_max_err, "spatial_max_err": v.spatial_max_err, "den_eps": v.den_eps,
         "passes": v.passes,
     }
+
+
+def bf_launch_info(plan: Plan, height: int, width: int) -> dict:
+    info = (C.c_int * 8)()
+    _check(lib().bf_launch_info(plan.handle, height, width, info), "bf_launch_info")
+    keys = ("tw", "th", "threads", "nk", "groups", "launches", "smem", "scratch_kib")
+    return dict(zip(keys, list(info)))
+
+
+def bf_autotune(plan: Plan, height: int, width: int, stream=None) -> dict:
+    info = (C.c_int * 8)()
+    _check(lib().bf_autotune(plan.handle, height, width, _stream_handle(stream), info), "bf_autotune")
+    keys = ("tw", "th", "threads", "nk", "groups", "launches", "smem", "scratch_kib")
+    return dict(zip(keys, list(info)))
 
 
 def _ptr_pitch(t):

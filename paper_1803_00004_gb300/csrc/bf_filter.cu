@@ -1,41 +1,47 @@
-// Fused single-pass evaluation of the box-filter form of the bilateral filter
-// (Eq. (36) and the final divide of Eq. (1)) for sm_103a.
+// Fused evaluation of the box-filter form of the bilateral filter (Eq. (36)
+// and the final divide of Eq. (1)) for sm_103a.
 //
-// Per CTA: a tile of `tw` output columns and `th` output rows.  One thread per
-// image column of the tile plus a horizontal halo of `rx` columns on each side
-// walks down the rows:
+// One CTA covers `tw` output columns x `th` output rows for one group of
+// cosine terms (blockIdx.z).  It has `ncols` column threads (one per image
+// column of the tile plus a horizontal halo of `rx` columns each side) and two
+// scan warps.  Per output row y:
 //
-//  1. Vertical pass.  For every cosine term k of the pass and every basis image
-//     g in {cos(w_k I) I, sin(w_k I) I, cos(w_k I), sin(w_k I)} (Eq. (34)), the
-//     thread keeps one running sum per vertical box window [v0, v1]:
+//  1. Vertical pass (column threads).  For every term k of the group and basis
+//     image g in {cos(w_k I) I, sin(w_k I) I, cos(w_k I), sin(w_k I)} (Eq. (34))
+//     a column thread keeps one running sum per vertical box window [v0, v1]:
 //         V(y) = V(y-1) + g(y + v1) - g(y + v0 - 1).
-//     The basis values at the entering / leaving rows are recomputed from the
-//     input pixel (sincospi of the base angle, then the angle-addition
-//     recurrence up to k), so only the raw image is read and no basis image is
-//     ever stored.
-//  2. The vertical sums are mixed into one value per horizontal window,
-//     Z_q = sum_r C[r][q] V_r, and published in shared memory.
-//  3. Horizontal pass.  Work items (term, segment of `seg` output columns) run
-//     horizontal running sums over the published row and weight the four
-//     filtered images with a_k cos(w_k I(x)), a_k sin(w_k I(x)) into partial
-//     numerator / denominator (Eq. (36)).
-//  4. One thread per output column sums the partials over the terms and
-//     divides (or accumulates into a scratch buffer for multi-pass plans).
+//     Basis values at the entering / leaving rows are recomputed from the raw
+//     pixel (sincospi of the base angle, angle-addition recurrence), so only
+//     the image itself is read and no basis image exists in memory.  The sums
+//     are mixed per horizontal window, Z_q = sum_r C[r][q] V_r, and published
+//     in one of two shared-memory exchange buffers.
+//  2. Horizontal pass (scan warps, one exchange row per lane, concurrently with
+//     the next row's vertical pass): the sliding window sum of the row's
+//     window, Kahan-compensated per block of 8 columns, written in place over
+//     the values it has consumed.
+//  3. Range accumulation (column threads of output columns): the filtered images are
+//     weighted with a_k cos(w_k I(x)), a_k sin(w_k I(x)) into numerator and
+//     denominator (Eq. (36)), then divided (one group) or stored as partial
+//     planes that a finalize kernel sums in a fixed order (several groups).
 //
-// Rows above the first window of the tile are treated as zero, so the walk
-// starts (vhi - vlo) rows early and needs no explicit initialisation; pixels
-// outside the image contribute zero to numerator and denominator.
+// The running sums of the first output row are initialised directly (one
+// basis evaluation per row of the window span); pixels outside the image
+// contribute zero to numerator and denominator.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
-#include <cstdio>
+#include <cmath>
 #include <string>
+#include <vector>
 
 #include "bf_internal.h"
 
 namespace bfi {
 
 namespace {
+
+constexpr int kScanThreads = 64;  // two warps: one exchange row per lane (<= 64 rows)
 
 std::atomic<int> g_fail_launches{0};
 
@@ -75,28 +81,62 @@ __device__ __forceinline__ void basis_start(float v, float inv_p, float inv_p_lo
     }
 }
 
+// Compensated (Kahan) accumulation s += x with running error term c.
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// Advances (c, s) = (cos, sin)(pi k t) by `steps` multiples of the base rotation.
+__device__ __forceinline__ void rotate(float &c, float &s, float c1, float s1, int steps) {
+    for (int n = 0; n < steps; ++n) {
+        const float cn = fmaf(c, c1, -s * s1);
+        const float sn = fmaf(s, c1, c * s1);
+        c = cn;
+        s = sn;
+    }
+}
+
 template <int NK, int M>
 __global__ void __launch_bounds__(512, 1)
 bf_fused_kernel(const float *__restrict__ in, size_t in_pitch, float *__restrict__ out, size_t out_pitch,
-                float *__restrict__ acc, int H, int W, int tw, int th, int seg, int mode, const FilterParams p) {
+                float *__restrict__ part, int H, int W, int tw, int th, int ncols, const FilterParams p) {
+    constexpr int NROW = M * NK * 4;  // exchange rows per image row: windows x terms x basis images
+    constexpr int NE = 2 * M + 1;     // edges per step: M entering rows, M leaving rows, the output row
     extern __shared__ float smem[];
-    const int nthr = blockDim.x;
-    const int ZP = nthr + 1;
-    const int WP = tw + 1;
-    float *zbuf = smem;                      // [M][NK][4][ZP]
-    float *wbuf = zbuf + M * NK * 4 * ZP;    // [NK][2][WP]
-    float *pbuf = wbuf + NK * 2 * WP;        // [NK][2][WP]
+    const int ZP = ncols + 3;         // odd: scan lanes (rows) hit distinct banks
+    float *zb0 = smem;                // [2][NROW][ZP]: column c of the tile at index c + 1; 0, ncols+1, ncols+2 stay 0
+    float *wb0 = smem + 2 * NROW * ZP;  // [2][NK][2][tw]: a_k cos, a_k sin at the output row
 
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * tw;
-    const int y0 = blockIdx.y * th;
+    const bool is_col = tid < ncols;
+    const int g = blockIdx.z;
+    const int x0 = blockIdx.x * tw, y0 = blockIdx.y * th;
     const int xcol = x0 - p.rx + tid;
-    const bool colv = (tid < tw + 2 * p.rx) && xcol >= 0 && xcol < W;
-    const int y_end = min(y0 + th, H);
-    const int y_lo = max(0, y0 + p.vlo);
-    const int ys = y0 + p.vlo - p.vhi;
-    const int nseg = tw / seg;
-    constexpr int NE = 2 * M + 1;  // edges: M entering rows, M leaving rows, the centre row
+    const bool colv = is_col && tid < tw + 2 * p.rx && xcol >= 0 && xcol < W;
+    const int nout = min(y0 + th, H) - y0;
+    const int xl = tid - p.rx;
+    const bool is_out = is_col && xl >= 0 && xl < tw && x0 + xl < W;
+    const bool grouped = gridDim.z > 1;
+
+    for (int i = tid; i < 2 * NROW; i += blockDim.x) {
+        zb0[i * ZP] = 0.f;
+        zb0[i * ZP + ncols + 1] = 0.f;
+        zb0[i * ZP + ncols + 2] = 0.f;
+    }
+
+    // this group's terms
+    int kk[NK];
+    float aa[NK];
+#pragma unroll
+    for (int i = 0; i < NK; ++i) {
+        const int j = g * NK + i;
+        const bool ok = j < p.nr;
+        kk[i] = p.k[ok ? j : p.nr - 1];
+        aa[i] = ok ? p.a[j] : 0.f;
+    }
 
     float V[NK][4][M];
 #pragma unroll
@@ -106,153 +146,197 @@ bf_fused_kernel(const float *__restrict__ in, size_t in_pitch, float *__restrict
 #pragma unroll
             for (int r = 0; r < M; ++r) V[i][t][r] = 0.f;
 
-    for (int y = ys; y < y_end; ++y) {
-        const bool outrow = (y >= y0);
-        float Ie[NE], c1[NE], s1[NE], ce[NE], se[NE];
-        const int k0 = p.k[0];
+    // window sums at the first output row: every row of the span once
+    if (is_col) {
+        for (int off = p.vlo; off <= p.vhi; ++off) {
+            const int row = y0 + off;
+            if (row < 0 || row >= H) continue;
+            const float v = colv ? __ldg(in + (size_t)row * in_pitch + xcol) - p.i_lo : 0.f;
+            float c1, s1, c, s;
+            basis_start(v, p.inv_p, p.inv_p_lo, kk[0], colv, c1, s1, c, s);
+            int kc = kk[0];
 #pragma unroll
-        for (int e = 0; e < NE; ++e) {
-            const int off = e < M ? p.v1[e] : (e < 2 * M ? p.v0[e - M] - 1 : 0);
-            const int row = y + off;
-            const bool valid = (e < 2 * M) ? (colv && row >= y_lo && row < H) : (colv && outrow);
-            const float v = valid ? __ldg(in + (size_t)row * in_pitch + xcol) - p.i_lo : 0.f;
-            Ie[e] = v;
-            basis_start(v, p.inv_p, p.inv_p_lo, k0, valid, c1[e], s1[e], ce[e], se[e]);
+            for (int i = 0; i < NK; ++i) {
+                rotate(c, s, c1, s1, kk[i] - kc);
+                kc = kk[i];
+                const float gi[4] = {c * v, s * v, c, s};
+#pragma unroll
+                for (int r = 0; r < M; ++r)
+                    if (off >= p.v0[r] && off <= p.v1[r]) {
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) V[i][t][r] += gi[t];
+                    }
+            }
         }
-        int kcur = k0;
+    }
+
+    for (int j = 0; j <= nout; ++j) {
+        const int y = y0 + j;
+        if (is_col && j < nout) {
+            float Ie[NE], c1[NE], s1[NE], ce[NE], se[NE];
 #pragma unroll
-        for (int i = 0; i < NK; ++i) {
-            const int steps = p.k[i] - kcur;
-            kcur = p.k[i];
-            for (int s = 0; s < steps; ++s) {
+            for (int e = 0; e < NE; ++e) {
+                const int off = e < M ? p.v1[e] : (e < 2 * M ? p.v0[e - M] - 1 : 0);
+                const int row = y + off;
+                // at j == 0 the sums already hold row y0: only the output-row edge is live
+                const bool valid = colv && row >= 0 && row < H && (j > 0 || e == 2 * M);
+                const float v = valid ? __ldg(in + (size_t)row * in_pitch + xcol) - p.i_lo : 0.f;
+                Ie[e] = v;
+                basis_start(v, p.inv_p, p.inv_p_lo, kk[0], valid, c1[e], s1[e], ce[e], se[e]);
+            }
+            float *zb = zb0 + (j & 1) * NROW * ZP + tid + 1;
+            float *wb = wb0 + (j & 1) * NK * 2 * tw;
+            int kc = kk[0];
 #pragma unroll
-                for (int e = 0; e < NE; ++e) {
-                    const float c = ce[e] * c1[e] - se[e] * s1[e];
-                    const float sv = se[e] * c1[e] + ce[e] * s1[e];
-                    ce[e] = c;
-                    se[e] = sv;
+            for (int i = 0; i < NK; ++i) {
+                const int steps = kk[i] - kc;
+                kc = kk[i];
+#pragma unroll
+                for (int e = 0; e < NE; ++e) rotate(ce[e], se[e], c1[e], s1[e], steps);
+#pragma unroll
+                for (int r = 0; r < M; ++r) {
+                    const int ei = r, eo = M + r;
+                    V[i][0][r] += fmaf(ce[ei], Ie[ei], -ce[eo] * Ie[eo]);
+                    V[i][1][r] += fmaf(se[ei], Ie[ei], -se[eo] * Ie[eo]);
+                    V[i][2][r] += ce[ei] - ce[eo];
+                    V[i][3][r] += se[ei] - se[eo];
                 }
-            }
-#pragma unroll
-            for (int r = 0; r < M; ++r) {
-                const int ei = r, eo = M + r;
-                V[i][0][r] += ce[ei] * Ie[ei] - ce[eo] * Ie[eo];
-                V[i][1][r] += se[ei] * Ie[ei] - se[eo] * Ie[eo];
-                V[i][2][r] += ce[ei] - ce[eo];
-                V[i][3][r] += se[ei] - se[eo];
-            }
-            if (outrow) {
 #pragma unroll
                 for (int t = 0; t < 4; ++t)
 #pragma unroll
                     for (int q = 0; q < M; ++q) {
                         float z = 0.f;
 #pragma unroll
-                        for (int r = 0; r < M; ++r) z += p.C[r][q] * V[i][t][r];
-                        zbuf[((q * NK + i) * 4 + t) * ZP + tid] = z;
+                        for (int r = 0; r < M; ++r) z = fmaf(p.C[r][q], V[i][t][r], z);
+                        zb[((q * NK + i) * 4 + t) * ZP] = z;
                     }
-                const int xl = tid - p.rx;
-                if (xl >= 0 && xl < tw) {
-                    wbuf[(i * 2 + 0) * WP + xl] = p.a[i] * ce[2 * M];
-                    wbuf[(i * 2 + 1) * WP + xl] = p.a[i] * se[2 * M];
+                if (is_out) {
+                    wb[(i * 2 + 0) * tw + xl] = aa[i] * ce[2 * M];
+                    wb[(i * 2 + 1) * tw + xl] = aa[i] * se[2 * M];
+                }
+            }
+        } else if (!is_col && j >= 1) {
+            const int r = tid - ncols;
+            if (r < NROW) {
+                // sliding sum of window q over the row; S(c) replaces Z(c + u0), which the
+                // slide has consumed (index c + u0 + 1 in buffer coordinates)
+                const int q = r / (NK * 4);
+                const int u0 = p.u0[q], u1 = p.u1[q];
+                float *row = zb0 + ((j - 1) & 1) * NROW * ZP + r * ZP;
+                float S = 0.f, comp = 0.f;
+                int b = p.rx + u0 + 1;
+                const int bend = p.rx + u1 + 1;
+                for (; b + 7 <= bend; b += 8) {
+                    float v[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) v[u] = row[b + u];
+                    kahan_add(S, comp, ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])));
+                }
+                float rest = 0.f;
+                for (; b <= bend; ++b) rest += row[b];
+                kahan_add(S, comp, rest);
+                for (int c0 = p.rx; c0 < p.rx + tw; c0 += 8) {
+                    float d[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) d[u] = row[c0 + u + u1 + 2] - row[c0 + u + u0 + 1];
+                    float pd = -comp;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        row[c0 + u + u0 + 1] = S + pd;
+                        pd += d[u];
+                    }
+                    kahan_add(S, comp, pd + comp);
                 }
             }
         }
-        if (!outrow) continue;  // warm-up rows: uniform over the CTA
         __syncthreads();
-
-        // horizontal pass: items (term i, segment sg)
-        for (int item = tid; item < NK * nseg; item += nthr) {
-            const int i = item % NK, sg = item / NK;
-            const int xs = sg * seg;
-            float S[4][M];
+        if (is_out && j >= 1) {
+            const int yo = y - 1;
+            const float *zp = zb0 + ((j - 1) & 1) * NROW * ZP + tid;
+            const float *wp = wb0 + ((j - 1) & 1) * NK * 2 * tw + xl;
+            float num = 0.f, den = 0.f;
 #pragma unroll
-            for (int t = 0; t < 4; ++t)
-#pragma unroll
-                for (int q = 0; q < M; ++q) {
-                    const float *zr = zbuf + ((q * NK + i) * 4 + t) * ZP + xs + p.rx;
-                    float s = 0.f;
-                    for (int dx = p.u0[q]; dx <= p.u1[q]; ++dx) s += zr[dx];
-                    S[t][q] = s;
-                }
-            for (int j = 0; j < seg; ++j) {
-                const int xl = xs + j;
+            for (int i = 0; i < NK; ++i) {
                 float F[4];
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                     float f = 0.f;
 #pragma unroll
-                    for (int q = 0; q < M; ++q) f += S[t][q];
+                    for (int q = 0; q < M; ++q) f += zp[((q * NK + i) * 4 + t) * ZP + p.u0[q] + 1];
                     F[t] = f;
                 }
-                const float wc = wbuf[(i * 2 + 0) * WP + xl], ws = wbuf[(i * 2 + 1) * WP + xl];
-                pbuf[(i * 2 + 0) * WP + xl] = wc * F[0] + ws * F[1];
-                pbuf[(i * 2 + 1) * WP + xl] = wc * F[2] + ws * F[3];
-                if (j + 1 < seg) {
-#pragma unroll
-                    for (int t = 0; t < 4; ++t)
-#pragma unroll
-                        for (int q = 0; q < M; ++q) {
-                            const float *zr = zbuf + ((q * NK + i) * 4 + t) * ZP + xl + p.rx;
-                            S[t][q] += zr[p.u1[q] + 1] - zr[p.u0[q]];
-                        }
-                }
+                const float wc = wp[(i * 2 + 0) * tw], ws = wp[(i * 2 + 1) * tw];
+                num = fmaf(wc, F[0], fmaf(ws, F[1], num));
+                den = fmaf(wc, F[2], fmaf(ws, F[3], den));
+            }
+            const int x = x0 + xl;
+            if (grouped) {
+                const size_t plane = (size_t)H * W;
+                float *pp = part + (size_t)(2 * g) * plane + (size_t)yo * W + x;
+                pp[0] = num;
+                pp[plane] = den;
+            } else {
+                const float ix = __ldg(in + (size_t)yo * in_pitch + x);
+                out[(size_t)yo * out_pitch + x] = (den > p.den_eps) ? num / den + p.i_lo : ix;
             }
         }
         __syncthreads();
-
-        if (tid < tw) {
-            const int x = x0 + tid;
-            if (x < W) {
-                float num = 0.f, den = 0.f;
-#pragma unroll
-                for (int i = 0; i < NK; ++i) {
-                    num += pbuf[(i * 2 + 0) * WP + tid];
-                    den += pbuf[(i * 2 + 1) * WP + tid];
-                }
-                const size_t plane = (size_t)H * W;
-                float *an = acc + (size_t)y * W + x;
-                if (mode == kPassFirst) {
-                    an[0] = num;
-                    an[plane] = den;
-                } else if (mode == kPassMid) {
-                    an[0] += num;
-                    an[plane] += den;
-                } else {
-                    if (mode == kPassLast) {
-                        num += an[0];
-                        den += an[plane];
-                    }
-                    const float ix = __ldg(in + (size_t)y * in_pitch + x);
-                    out[(size_t)y * out_pitch + x] = (den > p.den_eps) ? num / den + p.i_lo : ix;
-                }
-            }
-        }
     }
 }
 
-// Slots (cosine terms) per pass for each window count: keeps the per-thread
-// running-sum state at 4 * slots * M <= 64 floats.
-constexpr int kSlots[kMaxWin + 1] = {0, 16, 8, 5, 4, 3, 2};
-
-template <int M>
-void *kernel_for_m() {
-    return (void *)bf_fused_kernel<kSlots[M], M>;
+// Sums the partial numerator / denominator planes of the term groups (in group
+// order, so the result does not depend on scheduling) and divides.
+__global__ void bf_finalize_kernel(const float *__restrict__ in, size_t in_pitch, float *__restrict__ out,
+                                   size_t out_pitch, const float *__restrict__ part, int H, int W, int groups,
+                                   float den_eps, float i_lo) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= W || y >= H) return;
+    const size_t plane = (size_t)H * W, o = (size_t)y * W + x;
+    float num = 0.f, den = 0.f;
+    for (int g = 0; g < groups; ++g) {
+        num += part[(size_t)(2 * g) * plane + o];
+        den += part[(size_t)(2 * g + 1) * plane + o];
+    }
+    out[(size_t)y * out_pitch + x] = (den > den_eps) ? num / den + i_lo : in[(size_t)y * in_pitch + x];
 }
 
-void *kernel_ptr(int m) {
-    switch (m) {
-        case 1: return kernel_for_m<1>();
-        case 2: return kernel_for_m<2>();
-        case 3: return kernel_for_m<3>();
-        case 4: return kernel_for_m<4>();
-        case 5: return kernel_for_m<5>();
-        case 6: return kernel_for_m<6>();
-    }
+// Kernel classes: windows per axis M and terms per group NK (NK * M <= 16, and
+// no class spills registers).
+struct KernelClass {
+    int m, nk;
+    const void *fn;
+};
+
+#define BF_CLASS(M, NK) {M, NK, (const void *)bf_fused_kernel<NK, M>}
+const KernelClass kClasses[] = {
+    BF_CLASS(1, 16), BF_CLASS(1, 8), BF_CLASS(1, 4), BF_CLASS(1, 2),
+    BF_CLASS(2, 8),  BF_CLASS(2, 4), BF_CLASS(2, 2), BF_CLASS(3, 5), BF_CLASS(3, 4), BF_CLASS(3, 2),
+    BF_CLASS(4, 2),  BF_CLASS(5, 2), BF_CLASS(6, 1),
+};
+#undef BF_CLASS
+
+const void *find_kernel(int m, int nk) {
+    for (const auto &c : kClasses)
+        if (c.m == m && c.nk == nk) return c.fn;
     return nullptr;
 }
 
-// ---------------------------------------------------------------- exact BF
+size_t smem_bytes(int m, int nk, int ncols, int tw) {
+    return sizeof(float) * (2 * (size_t)m * nk * 4 * (ncols + 3) + 2 * (size_t)nk * 2 * tw);
+}
+
+int device_sms() {
+    static int sms = [] {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return 152;
+        }
+        return n;
+    }();
+    return sms;
+}
 
 __global__ void bf_exact_kernel(const float *__restrict__ in, size_t in_pitch, float *__restrict__ out,
                                 size_t out_pitch, int H, int W, int spatial, float inv2ss, int R, int range,
@@ -303,49 +387,92 @@ void debug_set_fail_launches(int n) { g_fail_launches.store(n > 0 ? n : 0); }
 
 bool kernel_class_supported(int m) { return m >= 1 && m <= kMaxWin; }
 
-int slots_per_pass(int m) { return (m >= 1 && m <= kMaxWin) ? kSlots[m] : 0; }
-
-TileConfig choose_tile(int m, int rx, int vspan, int height, int width, int precision) {
+// Launch geometries ranked by a simple cost model: per-CTA work ~ columns x
+// (rows + 0.3 x window span for the initialisation) x (edge cost + per-term
+// cost), times the number of waves the grid needs on this device.
+std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int width, int precision, int max_n) {
     (void)precision;
-    TileConfig tc;
-    tc.seg = 16;
-    int tw = 128;
-    if (width < tw) tw = ((width + tc.seg - 1) / tc.seg) * tc.seg;
-    if (tw < tc.seg) tw = tc.seg;
-    tc.tw = tw;
-    int th = 64;
-    if (vspan > 64) th = 128;
-    if (vspan > 128) th = 256;
-    if (height < th) th = height > 0 ? height : 1;
-    tc.th = th;
-    int thr = tw + 2 * rx;
-    tc.threads = ((thr + 31) / 32) * 32;
-    const int nk = kSlots[m];
-    tc.smem = sizeof(float) * ((size_t)m * nk * 4 * (tc.threads + 1) + (size_t)nk * 4 * (tw + 1));
-    return tc;
+    const int sms = device_sms();
+    const int vspan = p.vhi - p.vlo + 1;
+    std::vector<std::pair<double, TileConfig>> all;
+    for (const auto &cls : kClasses) {
+        if (cls.m != p.m) continue;
+        const int groups = (p.nr + cls.nk - 1) / cls.nk;
+        for (int tw : {64, 128, 192, 256, 320, 384}) {
+            const int twe = std::min(tw, ((width + 31) / 32) * 32);
+            const int ncols = ((twe + 2 * p.rx + 31) / 32) * 32;
+            if (ncols + kScanThreads > 512) continue;
+            const size_t smem = smem_bytes(p.m, cls.nk, ncols, twe);
+            if (smem > 227 * 1024) continue;
+            const int by_smem = (int)((228 * 1024) / (smem + 1024));
+            const int by_threads = 2048 / (ncols + kScanThreads);
+            const int by_regs = 65536 / (128 * (ncols + kScanThreads));
+            const int cps = std::max(1, std::min({by_smem, by_threads, by_regs}));
+            for (int th : {16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 1024}) {
+                const int the = std::min(th, std::max(height, 1));
+                const long ctas = (long)((width + twe - 1) / twe) * ((height + the - 1) / the) * groups;
+                const double per_cta = (double)ncols * (the + 0.3 * vspan) * (60.0 * (2 * p.m + 1) + 40.0 * cls.nk * p.m);
+                const double waves = std::ceil((double)ctas / (sms * cps));
+                const double cost = waves * per_cta * cps + (groups > 1 ? 16.0 * groups * (double)height * width : 0.0);
+                TileConfig tc;
+                tc.tw = twe;
+                tc.th = the;
+                tc.ncols = ncols;
+                tc.threads = ncols + kScanThreads;
+                tc.nk = cls.nk;
+                tc.groups = groups;
+                tc.smem = smem;
+                all.push_back({cost, tc});
+                if (the >= height) break;
+            }
+            if (twe >= width) break;
+        }
+    }
+    std::stable_sort(all.begin(), all.end(), [](const auto &a, const auto &b) { return a.first < b.first; });
+    std::vector<TileConfig> out;
+    for (size_t i = 0; i < all.size() && (int)out.size() < max_n; ++i) out.push_back(all[i].second);
+    return out;
 }
 
-bf_status launch_filter_pass(const FilterParams &p, int precision, int kahan, const TileConfig &tc,
-                             const float *d_in, size_t in_pitch, float *d_out, size_t out_pitch, float *d_acc,
-                             int height, int width, int mode, void *stream) {
+TileConfig model_tile(const FilterParams &p, int height, int width, int precision) {
+    std::vector<TileConfig> c = tile_candidates(p, height, width, precision, 1);
+    return c.empty() ? TileConfig{} : c[0];
+}
+
+size_t scratch_bytes(const TileConfig &tc, int height, int width) {
+    return tc.groups > 1 ? sizeof(float) * 2 * (size_t)tc.groups * height * width : 0;
+}
+
+bf_status launch_filter(const FilterParams &p, int precision, int kahan, const TileConfig &tc, const float *d_in,
+                        size_t in_pitch, float *d_out, size_t out_pitch, float *d_scratch, int height, int width,
+                        void *stream) {
     (void)precision;
     (void)kahan;
     if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");
-    void *fn = kernel_ptr(p.m);
-    if (!fn) return fail(BF_ERR_UNSUPPORTED, "no kernel for this window count");
-    if (tc.threads > 512) return fail(BF_ERR_UNSUPPORTED, "horizontal reach too large for one CTA (radius > 192)");
+    const void *fn = find_kernel(p.m, tc.nk);
+    if (!fn || tc.ncols <= 0) return fail(BF_ERR_UNSUPPORTED, "no kernel class for this plan and image");
+    if (tc.threads > 512) return fail(BF_ERR_UNSUPPORTED, "horizontal reach too large for one CTA");
     if (tc.smem > 227 * 1024) return fail(BF_ERR_UNSUPPORTED, "tile needs more than 227 KB of shared memory");
+    if (tc.groups > 1 && !d_scratch) return fail(BF_ERR_INVALID_ARG, "missing scratch for grouped launch");
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc.smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-    dim3 grid((width + tc.tw - 1) / tc.tw, (height + tc.th - 1) / tc.th);
-    int tw = tc.tw, th = tc.th, seg = tc.seg, H = height, W = width;
+    dim3 grid((width + tc.tw - 1) / tc.tw, (height + tc.th - 1) / tc.th, tc.groups);
+    int tw = tc.tw, th = tc.th, ncols = tc.ncols, H = height, W = width;
     const float *in = d_in;
-    float *out = d_out, *acc = d_acc;
+    float *out = d_out, *part = d_scratch;
     FilterParams pp = p;
-    void *args[] = {(void *)&in, (void *)&in_pitch, (void *)&out, (void *)&out_pitch, (void *)&acc, (void *)&H,
-                    (void *)&W, (void *)&tw, (void *)&th, (void *)&seg, (void *)&mode, (void *)&pp};
+    void *args[] = {(void *)&in, (void *)&in_pitch, (void *)&out, (void *)&out_pitch, (void *)&part, (void *)&H,
+                    (void *)&W, (void *)&tw, (void *)&th, (void *)&ncols, (void *)&pp};
     e = cudaLaunchKernel(fn, grid, dim3(tc.threads), args, tc.smem, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "filter launch");
+    if (tc.groups > 1) {
+        if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");
+        dim3 fg((width + 255) / 256, height);
+        bf_finalize_kernel<<<fg, 256, 0, (cudaStream_t)stream>>>(d_in, in_pitch, d_out, out_pitch, d_scratch, height,
+                                                                 width, tc.groups, p.den_eps, p.i_lo);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "finalize launch");
+    }
     return BF_OK;
 }
 

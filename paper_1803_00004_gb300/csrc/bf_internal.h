@@ -11,13 +11,15 @@
 
 namespace bfi {
 
-// Largest number of box windows per axis a kernel class handles, and the
-// largest number of cosine terms one pass of the fused kernel carries.
+// Largest number of box windows per axis a kernel class handles, the largest
+// number of cosine terms one plan carries, and the per-thread budget of
+// running sums (terms per group x windows <= kSlotBudget; 4 basis images each).
 constexpr int kMaxWin = 6;
-constexpr int kMaxSlots = 16;
+constexpr int kMaxTerms = 64;
+constexpr int kSlotBudget = 16;
 
-// Everything one launch of the fused filter needs, passed by value (it lands
-// in the kernel's constant parameter bank; no device allocation per plan).
+// Everything a launch of the fused filter needs, passed by value (it lands in
+// the kernel's constant parameter bank; no device allocation per plan).
 //
 // Vertical windows [v0[r], v1[r]] and horizontal windows [u0[q], u1[q]] are
 // neighbour offsets d = y - x (rows / columns); the spatial weight of the
@@ -27,9 +29,9 @@ struct FilterParams {
     float inv_p_lo;           // 1 / P - inv_p (two-float representation of 1 / P)
     float i_lo;               // intensity origin
     float den_eps;            // denominator guard
-    int nk;                   // cosine terms used in this pass (<= slots of the class)
-    int k[kMaxSlots];         // ascending; padded slots repeat the last k with a = 0
-    float a[kMaxSlots];
+    int nr;                   // cosine terms
+    int k[kMaxTerms];         // ascending
+    float a[kMaxTerms];
     int m;                    // windows per axis of this kernel class
     int v0[kMaxWin], v1[kMaxWin];
     int u0[kMaxWin], u1[kMaxWin];
@@ -38,28 +40,33 @@ struct FilterParams {
     int vlo, vhi;             // min v0, max v1
 };
 
-// Tile geometry chosen by the host for one launch.
+// Launch geometry chosen by the host.
 struct TileConfig {
-    int tw;        // output columns per CTA (multiple of seg)
+    int tw;        // output columns per CTA
     int th;        // output rows per CTA
-    int seg;       // columns per horizontal work item
-    int threads;   // CTA size (>= tw + 2 rx, multiple of 32)
+    int ncols;     // column threads (>= tw + 2 rx, multiple of 32)
+    int threads;   // ncols + scan warps
+    int nk;        // cosine terms per group (template slot count)
+    int groups;    // term groups (grid.z); > 1 writes partial planes + finalize
     size_t smem;   // dynamic shared memory bytes
 };
-
-// Which pass of a multi-pass filter a launch is.
-enum PassMode { kPassOnly = 0, kPassFirst = 1, kPassMid = 2, kPassLast = 3 };
 
 void set_error(const std::string &msg);
 bf_status fail(bf_status st, const std::string &msg);
 
 // ---- device side (bf_filter.cu) ----
 bool kernel_class_supported(int m);
-int slots_per_pass(int m);
-TileConfig choose_tile(int m, int rx, int vspan, int height, int width, int precision);
-bf_status launch_filter_pass(const FilterParams &p, int precision, int kahan, const TileConfig &tc,
-                             const float *d_in, size_t in_pitch_elems, float *d_out, size_t out_pitch_elems,
-                             float *d_acc, int height, int width, int mode, void *stream);
+// Ranked launch geometries from the cost model, the model's pick, and the
+// geometry bf_filter uses (an autotuned one when bf_autotune measured this
+// kernel class, reach and image size on this device, else the model's pick).
+std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int width, int precision, int max_n);
+TileConfig model_tile(const FilterParams &p, int height, int width, int precision);
+TileConfig choose_tile(const FilterParams &p, int height, int width, int precision);
+void remember_tile(const FilterParams &p, int height, int width, int precision, const TileConfig &tc);
+size_t scratch_bytes(const TileConfig &tc, int height, int width);
+bf_status launch_filter(const FilterParams &p, int precision, int kahan, const TileConfig &tc, const float *d_in,
+                        size_t in_pitch_elems, float *d_out, size_t out_pitch_elems, float *d_scratch, int height,
+                        int width, void *stream);
 bf_status launch_exact(const float *d_in, size_t in_pitch_elems, float *d_out, size_t out_pitch_elems,
                        int height, int width, int spatial, float sigma_s, int radius, int range, float sigma_r,
                        void *stream);
@@ -83,5 +90,5 @@ struct bf_plan {
     std::vector<double> wcoef;      // nv x nh
     double range_max_err = 0, spatial_max_err = 0, den_eps = 0;
     int m = 0;                      // kernel class (windows per axis)
-    std::vector<bfi::FilterParams> passes;
+    bfi::FilterParams kp;           // kernel parameters (all terms)
 };

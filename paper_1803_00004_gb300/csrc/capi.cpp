@@ -63,21 +63,12 @@ bf_status check_image(const float *d_in, size_t in_pitch, const float *d_out, si
     return BF_OK;
 }
 
-// Launch sequence of one image (no argument checks).  d_acc: 2 * h * w floats
-// of scratch when the plan has more than one pass, else ignored.
-bf_status filter_image(const bf_plan *plan, const float *d_in, size_t in_pitch, float *d_out, size_t out_pitch, int h,
-                       int w, float *d_acc, void *stream) {
-    const FilterParams &p0 = plan->passes[0];
-    TileConfig tc = choose_tile(plan->m, p0.rx, p0.vhi - p0.vlo, h, w, plan->desc.precision);
-    const int np = (int)plan->passes.size();
-    for (int i = 0; i < np; ++i) {
-        int mode = np == 1 ? kPassOnly : (i == 0 ? kPassFirst : (i == np - 1 ? kPassLast : kPassMid));
-        bf_status st = launch_filter_pass(plan->passes[i], plan->desc.precision, plan->desc.kahan, tc, d_in,
-                                          in_pitch / sizeof(float), d_out, out_pitch / sizeof(float), d_acc, h, w,
-                                          mode, stream);
-        if (st != BF_OK) return st;
-    }
-    return BF_OK;
+// Launch sequence of one image (no argument checks).  d_scratch: at least
+// scratch_bytes(tc, h, w) bytes when the configuration has several term groups.
+bf_status filter_image(const bf_plan *plan, const TileConfig &tc, const float *d_in, size_t in_pitch, float *d_out,
+                       size_t out_pitch, int h, int w, float *d_scratch, void *stream) {
+    return launch_filter(plan->kp, plan->desc.precision, plan->desc.kahan, tc, d_in, in_pitch / sizeof(float), d_out,
+                         out_pitch / sizeof(float), d_scratch, h, w, stream);
 }
 
 }  // namespace bfi
@@ -156,7 +147,7 @@ bf_status bf_coeffs(const bf_plan *p, bf_coeff_view *o) {
     o->range_max_err = p->range_max_err;
     o->spatial_max_err = p->spatial_max_err;
     o->den_eps = p->den_eps;
-    o->passes = (int)p->passes.size();
+    o->passes = (int)((p->k.size() + 15) / 16);
     return BF_OK;
 }
 
@@ -167,19 +158,35 @@ bf_status bf_filter(const bf_plan *plan, const float *d_in, size_t in_pitch, flo
     if (st != BF_OK || height == 0 || width == 0) return st;
     if (plan->desc.device < 0) return fail(BF_ERR_NO_DEVICE, "host-only plan (device = -1)");
     return with_device(plan->desc.device, [&]() -> bf_status {
-        float *acc = nullptr;
+        TileConfig tc = choose_tile(plan->kp, height, width, plan->desc.precision);
+        float *scratch = nullptr;
         cudaStream_t s = (cudaStream_t)stream;
-        if (plan->passes.size() > 1) {
-            cudaError_t e = cudaMallocAsync((void **)&acc, sizeof(float) * 2 * (size_t)height * width, s);
+        size_t need = scratch_bytes(tc, height, width);
+        if (need) {
+            cudaError_t e = cudaMallocAsync((void **)&scratch, need, s);
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 return fail(BF_ERR_OOM, std::string("scratch allocation: ") + cudaGetErrorString(e));
             }
         }
-        bf_status r = filter_image(plan, d_in, in_pitch, d_out, out_pitch, height, width, acc, stream);
-        if (acc) cudaFreeAsync(acc, s);
+        bf_status r = filter_image(plan, tc, d_in, in_pitch, d_out, out_pitch, height, width, scratch, stream);
+        if (scratch) cudaFreeAsync(scratch, s);
         return r;
     });
+}
+
+bf_status bf_launch_info(const bf_plan *plan, int height, int width, int *info) {
+    if (!plan || !info || height < 1 || width < 1) return fail(BF_ERR_INVALID_ARG, "bad launch-info arguments");
+    TileConfig tc = choose_tile(plan->kp, height, width, plan->desc.precision);
+    info[0] = tc.tw;
+    info[1] = tc.th;
+    info[2] = tc.threads;
+    info[3] = tc.nk;
+    info[4] = tc.groups;
+    info[5] = tc.groups > 1 ? 2 : 1;
+    info[6] = (int)tc.smem;
+    info[7] = (int)(scratch_bytes(tc, height, width) >> 10);
+    return BF_OK;
 }
 
 bf_status bf_exact(const float *d_in, size_t in_pitch, float *d_out, size_t out_pitch, int height, int width,

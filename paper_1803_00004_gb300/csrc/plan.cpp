@@ -390,48 +390,35 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
         return fail(BF_ERR_UNSUPPORTED, "spatial approximation needs " + std::to_string(p.m) +
                                             " box windows per axis; this build supports up to " +
                                             std::to_string(bfi::kMaxWin) + " (reduce ns_terms)");
-    const int slots = bfi::slots_per_pass(p.m);
-    bfi::FilterParams base;
-    std::memset(&base, 0, sizeof(base));
-    base.inv_p = (float)(1.0 / p.P);
-    base.inv_p_lo = (float)(1.0 / p.P - (double)base.inv_p);
-    base.i_lo = d.i_lo;
-    base.den_eps = (float)p.den_eps;
-    base.m = p.m;
+    if ((int)p.k.size() > bfi::kMaxTerms)
+        return fail(BF_ERR_UNSUPPORTED, "more than " + std::to_string(bfi::kMaxTerms) + " cosine terms per plan");
+    bfi::FilterParams &kp = p.kp;
+    std::memset(&kp, 0, sizeof(kp));
+    kp.inv_p = (float)(1.0 / p.P);
+    kp.inv_p_lo = (float)(1.0 / p.P - (double)kp.inv_p);
+    kp.i_lo = d.i_lo;
+    kp.den_eps = (float)p.den_eps;
+    kp.nr = nr;
+    for (int i = 0; i < nr; ++i) {
+        kp.k[i] = p.k[i];
+        kp.a[i] = (float)p.a[i];
+    }
+    kp.m = p.m;
     int rx = 0, vlo = 0, vhi = 0;
     for (int r = 0; r < p.m; ++r) {
-        if (r < p.nv) {
-            base.v0[r] = vw[r].first;
-            base.v1[r] = vw[r].second;
-        } else {
-            base.v0[r] = 0;  // padding window, zero weight
-            base.v1[r] = 0;
-        }
-        if (r < p.nh) {
-            base.u0[r] = hw[r].first;
-            base.u1[r] = hw[r].second;
-        } else {
-            base.u0[r] = 0;
-            base.u1[r] = 0;
-        }
-        for (int q = 0; q < p.m; ++q) base.C[r][q] = (r < p.nv && q < p.nh) ? (float)hcoef[r][q] : 0.0f;
-        rx = std::max({rx, std::abs(base.u0[r]), std::abs(base.u1[r])});
-        vlo = std::min(vlo, base.v0[r]);
-        vhi = std::max(vhi, base.v1[r]);
+        // windows beyond an axis' count are zero-weight padding
+        kp.v0[r] = r < p.nv ? vw[r].first : 0;
+        kp.v1[r] = r < p.nv ? vw[r].second : 0;
+        kp.u0[r] = r < p.nh ? hw[r].first : 0;
+        kp.u1[r] = r < p.nh ? hw[r].second : 0;
+        for (int q = 0; q < p.m; ++q) kp.C[r][q] = (r < p.nv && q < p.nh) ? (float)hcoef[r][q] : 0.0f;
+        rx = std::max({rx, std::abs(kp.u0[r]), std::abs(kp.u1[r])});
+        vlo = std::min(vlo, kp.v0[r]);
+        vhi = std::max(vhi, kp.v1[r]);
     }
-    base.rx = rx;
-    base.vlo = vlo;
-    base.vhi = vhi;
-    for (int s0 = 0; s0 < nr; s0 += slots) {
-        bfi::FilterParams fp = base;
-        fp.nk = std::min(slots, nr - s0);
-        for (int i = 0; i < slots; ++i) {
-            int src = std::min(s0 + i, nr - 1);
-            fp.k[i] = p.k[src];
-            fp.a[i] = (s0 + i < nr) ? (float)p.a[src] : 0.0f;
-        }
-        p.passes.push_back(fp);
-    }
+    kp.rx = rx;
+    kp.vlo = vlo;
+    kp.vhi = vhi;
     return BF_OK;
 }
 

@@ -1,0 +1,178 @@
+// Autotuner for the fused filter's launch geometry (tile width and height,
+// cosine terms per CTA).  Candidates come ranked from the cost model; each is
+// timed with CUDA events on a synthetic image of the requested size, and the
+// fastest is remembered per (device, kernel class, reach, image size) for
+// later bf_filter / bf_filter_batch calls.  BF_TUNE_CACHE=<file> persists the
+// table across processes (one line per entry).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "bf_internal.h"
+
+namespace bfi {
+namespace {
+
+using Key = std::tuple<int, int, int, int, int, int, int, int, int>;
+
+std::mutex g_mu;
+std::map<Key, TileConfig> g_table;
+bool g_loaded = false;
+
+Key make_key(const FilterParams &p, int h, int w, int precision) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = -1;
+    }
+    return Key{dev, p.m, p.nr, p.rx, p.vlo, p.vhi, h, w, precision};
+}
+
+void load_locked() {
+    if (g_loaded) return;
+    g_loaded = true;
+    const char *path = std::getenv("BF_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    int k[9];
+    TileConfig tc;
+    unsigned long smem;
+    while (std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %lu", &k[0], &k[1], &k[2], &k[3], &k[4],
+                       &k[5], &k[6], &k[7], &k[8], &tc.tw, &tc.th, &tc.ncols, &tc.threads, &tc.nk, &tc.groups,
+                       &smem) == 16) {
+        tc.smem = smem;
+        g_table[Key{k[0], k[1], k[2], k[3], k[4], k[5], k[6], k[7], k[8]}] = tc;
+    }
+    std::fclose(f);
+}
+
+void save_locked(const Key &key, const TileConfig &tc) {
+    const char *path = std::getenv("BF_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %lu\n", std::get<0>(key), std::get<1>(key),
+                 std::get<2>(key), std::get<3>(key), std::get<4>(key), std::get<5>(key), std::get<6>(key),
+                 std::get<7>(key), std::get<8>(key), tc.tw, tc.th, tc.ncols, tc.threads, tc.nk, tc.groups,
+                 (unsigned long)tc.smem);
+    std::fclose(f);
+}
+
+// Deterministic pseudo-random pixels in [lo, hi] (a hash of the index).
+__global__ void fill_kernel(float *img, size_t n, float lo, float hi) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        uint32_t x = (uint32_t)i * 2654435761u + 0x9e3779b9u;
+        x ^= x >> 16;
+        x *= 0x85ebca6bu;
+        x ^= x >> 13;
+        img[i] = lo + (hi - lo) * (float)(x >> 8) * (1.0f / 16777216.0f);
+    }
+}
+
+}  // namespace
+
+TileConfig choose_tile(const FilterParams &p, int height, int width, int precision) {
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        load_locked();
+        auto it = g_table.find(make_key(p, height, width, precision));
+        if (it != g_table.end()) return it->second;
+    }
+    return model_tile(p, height, width, precision);
+}
+
+void remember_tile(const FilterParams &p, int height, int width, int precision, const TileConfig &tc) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    load_locked();
+    Key k = make_key(p, height, width, precision);
+    g_table[k] = tc;
+    save_locked(k, tc);
+}
+
+}  // namespace bfi
+
+using namespace bfi;
+
+extern "C" bf_status bf_autotune(const bf_plan *plan, int height, int width, void *stream, int *info) {
+    if (!plan || height < 1 || width < 1) return fail(BF_ERR_INVALID_ARG, "bad autotune arguments");
+    if (plan->desc.device < 0) return fail(BF_ERR_NO_DEVICE, "host-only plan (device = -1)");
+    int prev = 0;
+    if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(plan->desc.device) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BF_ERR_NO_DEVICE, "cannot select the plan's device");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<TileConfig> cands = tile_candidates(plan->kp, height, width, plan->desc.precision, 12);
+    bf_status st = BF_OK;
+    float *in = nullptr, *out = nullptr, *scratch = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    size_t n = (size_t)height * width, need = 0;
+    for (const auto &c : cands) need = std::max(need, scratch_bytes(c, height, width));
+    if (cands.empty()) st = fail(BF_ERR_UNSUPPORTED, "no launch geometry for this plan");
+    if (st == BF_OK && (cudaMalloc((void **)&in, n * sizeof(float)) != cudaSuccess ||
+                        cudaMalloc((void **)&out, n * sizeof(float)) != cudaSuccess ||
+                        (need && cudaMalloc((void **)&scratch, need) != cudaSuccess))) {
+        cudaGetLastError();
+        st = fail(BF_ERR_OOM, "autotune buffers");
+    }
+    if (st == BF_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) {
+        cudaGetLastError();
+        st = fail(BF_ERR_CUDA, "autotune events");
+    }
+    TileConfig best{};
+    float best_ms = 1e30f;
+    if (st == BF_OK) {
+        fill_kernel<<<256, 256, 0, s>>>(in, n, plan->desc.i_lo, plan->desc.i_hi);
+        for (const auto &c : cands) {
+            bf_status r = launch_filter(plan->kp, plan->desc.precision, plan->desc.kahan, c, in, width, out, width,
+                                        scratch, height, width, stream);  // warm-up
+            if (r != BF_OK) continue;
+            float t[3];
+            bool ok = true;
+            for (int rep = 0; rep < 3 && ok; ++rep) {
+                cudaEventRecord(e0, s);
+                ok = launch_filter(plan->kp, plan->desc.precision, plan->desc.kahan, c, in, width, out, width, scratch,
+                                   height, width, stream) == BF_OK;
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+                else cudaEventElapsedTime(&t[rep], e0, e1);
+            }
+            if (!ok) continue;
+            std::sort(t, t + 3);
+            if (t[1] < best_ms) {
+                best_ms = t[1];
+                best = c;
+            }
+        }
+        if (best.ncols == 0) st = fail(BF_ERR_CUDA, "no candidate geometry ran");
+    }
+    if (st == BF_OK) {
+        remember_tile(plan->kp, height, width, plan->desc.precision, best);
+        if (info) {
+            info[0] = best.tw;
+            info[1] = best.th;
+            info[2] = best.threads;
+            info[3] = best.nk;
+            info[4] = best.groups;
+            info[5] = best.groups > 1 ? 2 : 1;
+            info[6] = (int)best.smem;
+            info[7] = (int)(scratch_bytes(best, height, width) >> 10);
+        }
+    }
+    cudaStreamSynchronize(s);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(in);
+    cudaFree(out);
+    cudaFree(scratch);
+    cudaSetDevice(prev);
+    return st;
+}
