@@ -99,27 +99,28 @@ __device__ __forceinline__ void rotate(float &c, float &s, float c1, float s1, i
     }
 }
 
+// One tile: output columns [x0, x0 + tw) x rows [y0, y0 + th) of one image,
+// cosine terms [g NK, g NK + NK) of p.  All threads of the CTA call it; it
+// ends on a barrier, so the shared memory can be reused right after.  `grouped`:
+// store partial numerator / denominator planes (part) instead of dividing.
 template <int NK, int M>
-__global__ void __launch_bounds__(512, 1)
-bf_fused_kernel(const float *__restrict__ in, size_t in_pitch, float *__restrict__ out, size_t out_pitch,
-                float *__restrict__ part, int H, int W, int tw, int th, int ncols, const FilterParams p) {
+__device__ __forceinline__ void tile_body(const FilterParams &p, const float *__restrict__ in, size_t in_pitch,
+                                          float *__restrict__ out, size_t out_pitch, float *__restrict__ part, int H,
+                                          int W, int x0, int y0, int tw, int th, int ncols, int g, bool grouped,
+                                          float *smem) {
     constexpr int NROW = M * NK * 4;  // exchange rows per image row: windows x terms x basis images
     constexpr int NE = 2 * M + 1;     // edges per step: M entering rows, M leaving rows, the output row
-    extern __shared__ float smem[];
     const int ZP = ncols + 3;         // odd: scan lanes (rows) hit distinct banks
     float *zb0 = smem;                // [2][NROW][ZP]: column c of the tile at index c + 1; 0, ncols+1, ncols+2 stay 0
     float *wb0 = smem + 2 * NROW * ZP;  // [2][NK][2][tw]: a_k cos, a_k sin at the output row
 
     const int tid = threadIdx.x;
     const bool is_col = tid < ncols;
-    const int g = blockIdx.z;
-    const int x0 = blockIdx.x * tw, y0 = blockIdx.y * th;
     const int xcol = x0 - p.rx + tid;
     const bool colv = is_col && tid < tw + 2 * p.rx && xcol >= 0 && xcol < W;
     const int nout = min(y0 + th, H) - y0;
     const int xl = tid - p.rx;
     const bool is_out = is_col && xl >= 0 && xl < tw && x0 + xl < W;
-    const bool grouped = gridDim.z > 1;
 
     for (int i = tid; i < 2 * NROW; i += blockDim.x) {
         zb0[i * ZP] = 0.f;
@@ -284,6 +285,57 @@ bf_fused_kernel(const float *__restrict__ in, size_t in_pitch, float *__restrict
     }
 }
 
+template <int NK, int M>
+__global__ void __launch_bounds__(512, 1)
+bf_fused_kernel(const float *__restrict__ in, size_t in_pitch, float *__restrict__ out, size_t out_pitch,
+                float *__restrict__ part, int H, int W, int tw, int th, int ncols, const __grid_constant__ FilterParams p) {
+    extern __shared__ float smem[];
+    tile_body<NK, M>(p, in, in_pitch, out, out_pitch, part, H, W, blockIdx.x * tw, blockIdx.y * th, tw, th, ncols,
+                     blockIdx.z, gridDim.z > 1, smem);
+}
+
+// Persistent batched form: each CTA repeatedly takes the next work item from
+// the cursor (largest items first, as the host ordered them) and runs the
+// tile body with that image's parameters staged in shared memory.  The loop is
+// bounded by the item count.
+template <int NK, int M>
+__global__ void __launch_bounds__(512, 1)
+bf_batch_kernel(const BatchImage *__restrict__ imgs, const FilterParams *__restrict__ params,
+                const WorkItem *__restrict__ items, int n_items, int *__restrict__ cursor, int ncols) {
+    extern __shared__ float smem[];
+    __shared__ FilterParams sp;
+    __shared__ int s_item;
+    for (int iter = 0; iter < n_items; ++iter) {
+        if (threadIdx.x == 0) s_item = atomicAdd(cursor, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const WorkItem w = items[it];
+        const BatchImage im = imgs[w.img];
+        const int *src = reinterpret_cast<const int *>(params + im.params);
+        int *dst = reinterpret_cast<int *>(&sp);
+        for (int i = threadIdx.x; i < (int)(sizeof(FilterParams) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+        __syncthreads();
+        tile_body<NK, M>(sp, im.in, im.in_pitch, im.out, im.out_pitch, im.part, im.H, im.W, w.x0, w.y0, w.tw, w.th,
+                         ncols, w.g, im.groups > 1, smem);
+    }
+}
+
+__global__ void bf_batch_finalize_kernel(const BatchImage *__restrict__ imgs, const int *__restrict__ list,
+                                         const FilterParams *__restrict__ params) {
+    const BatchImage im = imgs[list[blockIdx.z]];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= im.W || y >= im.H) return;
+    const FilterParams &p = params[im.params];
+    const size_t plane = (size_t)im.H * im.W, o = (size_t)y * im.W + x;
+    float num = 0.f, den = 0.f;
+    for (int g = 0; g < im.groups; ++g) {
+        num += im.part[(size_t)(2 * g) * plane + o];
+        den += im.part[(size_t)(2 * g + 1) * plane + o];
+    }
+    im.out[(size_t)y * im.out_pitch + x] = (den > p.den_eps) ? num / den + p.i_lo : im.in[(size_t)y * im.in_pitch + x];
+}
+
 // Sums the partial numerator / denominator planes of the term groups (in group
 // order, so the result does not depend on scheduling) and divides.
 __global__ void bf_finalize_kernel(const float *__restrict__ in, size_t in_pitch, float *__restrict__ out,
@@ -306,9 +358,10 @@ __global__ void bf_finalize_kernel(const float *__restrict__ in, size_t in_pitch
 struct KernelClass {
     int m, nk;
     const void *fn;
+    const void *batch_fn;
 };
 
-#define BF_CLASS(M, NK) {M, NK, (const void *)bf_fused_kernel<NK, M>}
+#define BF_CLASS(M, NK) {M, NK, (const void *)bf_fused_kernel<NK, M>, (const void *)bf_batch_kernel<NK, M>}
 const KernelClass kClasses[] = {
     BF_CLASS(1, 16), BF_CLASS(1, 8), BF_CLASS(1, 4), BF_CLASS(1, 2),
     BF_CLASS(2, 8),  BF_CLASS(2, 4), BF_CLASS(2, 2), BF_CLASS(3, 5), BF_CLASS(3, 4), BF_CLASS(3, 2),
@@ -437,6 +490,54 @@ std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int w
 TileConfig model_tile(const FilterParams &p, int height, int width, int precision) {
     std::vector<TileConfig> c = tile_candidates(p, height, width, precision, 1);
     return c.empty() ? TileConfig{} : c[0];
+}
+
+int device_sm_count() { return device_sms(); }
+
+size_t batch_smem_bytes(int m, int nk, int ncols) { return smem_bytes(m, nk, ncols, ncols); }
+
+int batch_class_nk(int m, int ncols) {
+    for (const auto &c : kClasses)  // classes are listed with the largest term count first
+        if (c.m == m && batch_smem_bytes(m, c.nk, ncols) <= 220 * 1024) return c.nk;
+    return 0;
+}
+
+int batch_ctas_per_sm(int m, int nk, int ncols) {
+    const size_t smem = batch_smem_bytes(m, nk, ncols) + sizeof(FilterParams) + 64;
+    const int threads = ncols + kScanThreads;
+    const int by_smem = (int)((228 * 1024) / (smem + 1024));
+    const int by_threads = 2048 / threads;
+    const int by_regs = 65536 / (128 * threads);
+    return std::max(1, std::min({by_smem, by_threads, by_regs}));
+}
+
+bf_status launch_batch_class(int m, int nk, int ncols, const BatchImage *d_imgs, const FilterParams *d_params,
+                             const WorkItem *d_items, int n_items, int *d_cursor, int grid, void *stream) {
+    if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");
+    const void *fn = nullptr;
+    for (const auto &c : kClasses)
+        if (c.m == m && c.nk == nk) fn = c.batch_fn;
+    if (!fn) return fail(BF_ERR_UNSUPPORTED, "no batched kernel for this class");
+    const size_t smem = batch_smem_bytes(m, nk, ncols);
+    if (ncols + kScanThreads > 512 || smem > 220 * 1024) return fail(BF_ERR_UNSUPPORTED, "batched tile too large");
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    void *args[] = {(void *)&d_imgs, (void *)&d_params, (void *)&d_items, (void *)&n_items, (void *)&d_cursor,
+                    (void *)&ncols};
+    e = cudaLaunchKernel(fn, dim3(grid), dim3(ncols + kScanThreads), args, smem, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batched filter launch");
+    return BF_OK;
+}
+
+bf_status launch_batch_finalize(const BatchImage *d_imgs, const int *d_list, int n_list, int max_h, int max_w,
+                                const FilterParams *d_params, void *stream) {
+    if (n_list == 0) return BF_OK;
+    if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");
+    dim3 grid((max_w + 255) / 256, max_h, n_list);
+    bf_batch_finalize_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(d_imgs, d_list, d_params);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "batched finalize launch");
+    return BF_OK;
 }
 
 size_t scratch_bytes(const TileConfig &tc, int height, int width) {

@@ -51,6 +51,24 @@ struct TileConfig {
     size_t smem;   // dynamic shared memory bytes
 };
 
+// One image of a persistent batched launch (device copy).
+struct BatchImage {
+    const float *in;
+    float *out;
+    float *part;          // partial planes (2 x groups x H x W floats) when groups > 1
+    size_t in_pitch, out_pitch;  // elements
+    int H, W;
+    int params;           // index into the launch's FilterParams array
+    int groups;
+};
+
+// One unit of work of a persistent launch: one tile of one image for one term group.
+struct WorkItem {
+    int img;
+    int x0, y0, tw, th;
+    int g;
+};
+
 void set_error(const std::string &msg);
 bf_status fail(bf_status st, const std::string &msg);
 
@@ -71,6 +89,27 @@ bf_status launch_exact(const float *d_in, size_t in_pitch_elems, float *d_out, s
                        int height, int width, int spatial, float sigma_s, int radius, int range, float sigma_r,
                        void *stream);
 bool debug_consume_launch_failure();
+
+// ---- persistent batched launch (bf_filter.cu) ----
+// Terms per CTA used for kernel class m in batched launches, the shared-memory
+// bytes a launch with `ncols` column threads needs, and the resident CTAs per SM.
+int batch_class_nk(int m, int ncols);
+size_t batch_smem_bytes(int m, int nk, int ncols);
+int batch_ctas_per_sm(int m, int nk, int ncols);
+int device_sm_count();
+// Enqueues the persistent kernel of class (m, nk) over n_items items (cursor: one
+// device int set to 0 before the launch) on `stream`.
+bf_status launch_batch_class(int m, int nk, int ncols, const BatchImage *d_imgs, const FilterParams *d_params,
+                             const WorkItem *d_items, int n_items, int *d_cursor, int grid, void *stream);
+// Batch of images in persistent launches without graph capture (device
+// buffers allocated and freed stream-ordered on `stream`), and the device bytes
+// such a batch needs.
+bf_status enqueue_batch_direct(const bf_plan *const *plans, const bf_image *images, int n, void *stream);
+size_t batch_device_bytes(const bf_plan *const *plans, const bf_image *images, int n);
+bf_status check_image(const float *d_in, size_t in_pitch, const float *d_out, size_t out_pitch, int h, int w);
+// Sums and divides the partial planes of the listed images (d_list: n_list indices).
+bf_status launch_batch_finalize(const BatchImage *d_imgs, const int *d_list, int n_list, int max_h, int max_w,
+                                const FilterParams *d_params, void *stream);
 
 }  // namespace bfi
 

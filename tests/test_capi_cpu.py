@@ -132,3 +132,32 @@ def test_range_and_spatial_errors_reported():
     assert 0 < c["range_max_err"] < 0.05
     c2 = bf.Plan(device=-1, sigma_r=0.3, nr_terms=8, policy=bf.RANGE_UNTRUNCATED_FULL).coeffs()
     assert c2["range_max_err"] < 1e-2
+
+
+def test_batch_and_server_argument_checks_without_gpu():
+    import ctypes as C
+    L = bf.lib()
+    assert L.bf_filter_batch(None, None, 0, None) == 0          # empty batch is a no-op
+    assert L.bf_filter_batch(None, None, -1, None) == 1
+    assert L.bf_filter_batch(None, None, 2, None) == 1
+    p = bf.Plan(device=-1)
+    plans = (C.c_void_p * 1)(p.handle.value)
+    imgs = (bf._binding.bf_image * 1)(bf._binding.bf_image(4096, 256, 1 << 20, 256, 4, 64))
+    assert L.bf_filter_batch(plans, imgs, 1, None) == 9          # host-only plan
+    cfg = bf._binding.bf_serve_config(0, 0, 0, 0, 0)
+    h = C.c_void_p()
+    assert L.bf_serve_create(C.byref(cfg), C.byref(h)) == 9      # no device here
+    assert L.bf_serve_create(None, C.byref(h)) == 1
+    assert L.bf_serve_submit(None, None, None) == 1
+    assert L.bf_serve_poll(None, 1, 0, None) == 1
+    L.bf_serve_destroy(None)
+
+
+def test_launch_info_and_autotune_without_gpu():
+    p = bf.Plan(device=-1)
+    info = bf.bf_launch_info(p, 1080, 1920)
+    assert info["threads"] <= 512 and info["tw"] % 8 == 0 and info["groups"] >= 1
+    assert info["threads"] >= info["tw"] + 2 * 12
+    with pytest.raises(bf.BFError) as ei:
+        bf.bf_autotune(p, 64, 64)
+    assert ei.value.status == 9
