@@ -163,6 +163,23 @@ bf_status bf_coeffs(const bf_plan *plan, bf_coeff_view *out);
 bf_status bf_filter(const bf_plan *plan, const float *d_in, size_t in_pitch_bytes,
                     float *d_out, size_t out_pitch_bytes, int height, int width, void *stream);
 
+/* bf_filter without any device allocation, for callers that cannot allocate
+ * device memory while filtering: hosts that reserve all their device memory up
+ * front (a framework's caching allocator owning the GPU, a real-time loop where
+ * an allocation may synchronise or fail mid-frame).  The paper has no
+ * counterpart; this is a deployment variant of the same computation.
+ * Plans whose cosine terms are split into groups need partial numerator and
+ * denominator planes (2 x groups x height x width floats); here they live in a
+ * fixed 64 MiB array inside the library (16,777,216 floats), which every GPU
+ * that loads the library holds until the process exits.  The first call on a
+ * device looks the array's address up; make that call before any stream
+ * capture.  All calls share the array: calls whose work overlaps on the GPU
+ * (other streams, other threads) race, so order them.  Arguments, layout,
+ * ownership and results as bf_filter.  Errors: as bf_filter, plus
+ * BF_ERR_RANGE when no launch geometry's planes fit the array. */
+bf_status bf_filter_noalloc(const bf_plan *plan, const float *d_in, size_t in_pitch_bytes,
+                            float *d_out, size_t out_pitch_bytes, int height, int width, void *stream);
+
 /* Launch geometry bf_filter would use for this plan on a height x width image:
  * info[0] tile width, [1] tile height, [2] threads per CTA, [3] cosine terms per
  * CTA, [4] term groups (grid depth), [5] kernel launches, [6] shared memory

@@ -60,7 +60,7 @@ class bf_result(C.Structure):
 
 
 EXPORTS = ["bf_plan_desc_default", "bf_plan_create", "bf_plan_destroy", "bf_coeffs", "bf_launch_info", "bf_autotune",
-           "bf_filter",
+           "bf_filter", "bf_filter_noalloc",
            "bf_filter_batch",
            "bf_exact", "bf_serve_create", "bf_serve_submit", "bf_serve_poll", "bf_serve_cancel", "bf_serve_destroy",
            "bf_status_string", "bf_last_error", "bf_version", "bf_debug_fail_launches"]
@@ -90,6 +90,7 @@ def lib():
         L.bf_coeffs.argtypes = [vp, P(bf_coeff_view)]
         L.bf_filter.argtypes = [vp, vp, sz, vp, sz, i, i, vp]
         L.bf_launch_info.argtypes = [vp, i, i, P(i)]
+        L.bf_filter_noalloc.argtypes = [vp, vp, sz, vp, sz, i, i, vp]
         L.bf_autotune.argtypes = [vp, i, i, vp, P(i)]
         L.bf_filter_batch.argtypes = [P(vp), P(bf_image), i, vp]
         L.bf_exact.argtypes = [vp, sz, vp, sz, i, i, i, d, i, i, d, vp]
