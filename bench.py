@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--only", default=None, help="restrict to one combination 'sigma_s,sigma_r' (profiling)")
     ap.add_argument("--no-ramp", action="store_true", help="skip the untimed clock-ramp load (profiling)")
     ap.add_argument("--no-tune", action="store_true", help="use the cost-model geometry instead of autotuning")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving sub-measurements")
     return ap.parse_args()
 
 
@@ -236,6 +237,11 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = run_e2e(args, bf, plans, img, dev, stream)
 
+    batched = serving = None
+    if not args.no_extras and world == 1:
+        batched = run_batched(bf, dev)
+        serving = run_serving(bf, dev)
+
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
@@ -252,6 +258,7 @@ def run_ours(args):
         "hbm": {"achieved_gbs": round(hbm_gbs, 1), "peak_gbs": hbm_peak, "frac": round(hbm_gbs / hbm_peak, 5),
                 "bytes_per_px": 8},
         "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
+        "batched": batched, "serving": serving,
         "e2e": e2e,
     }
     if rank == 0:
@@ -291,6 +298,103 @@ def run_e2e(args, bf, plans, img, dev, stream):
     value = len(plans) * H * W * args.steps / (ms * 1e-3) / 1e6
     return {"value": round(value, 3), "unit": "Mpixel/s", "h2d_bytes_per_step": 4 * H * W,
             "d2h_bytes_per_step": 4 * H * W * len(plans)}
+
+
+def mixed_requests(n, lo, hi, seed):
+    """Config-4/5 style requests: log-uniform square-ish images with per-image
+    sigma_s ~ U[2,32], sigma_r ~ U[0.05,0.3], Gaussian or exponential range kernel, N_r in {8,16}."""
+    from paper_1803_00004_gb300 import synth
+    rng = np.random.default_rng(seed)
+    out = []
+    for i, s in enumerate(synth.batch_sizes(n, lo, hi, seed=seed)):
+        img = synth.shapes(s, s, seed=seed * 7919 + i, scale=s / 1080.0)
+        kw = dict(sigma_s=float(rng.uniform(2, 32)), sigma_r=float(rng.uniform(0.05, 0.3)),
+                  range=int(rng.integers(0, 2)), nr_terms=int(rng.choice([8, 16])), ns_terms=NS)
+        out.append((img, kw))
+    return out
+
+
+def run_batched(bf, dev, n=512, lo=64, hi=2048, reps=3):
+    """One bf_filter_batch call over n images (persistent launch, graph replay) vs a
+    sequential bf_filter loop over the same images."""
+    import torch
+    work = mixed_requests(n, lo, hi, seed=1234)
+    plans = [bf.Plan(device=dev.index or 0, **kw) for _, kw in work]
+    srcs = [torch.from_numpy(img).to(dev) for img, _ in work]
+    dsts = [torch.empty_like(x) for x in srcs]
+    px = sum(img.size for img, _ in work)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    t_batch = timed(lambda: bf.bf_filter_batch(plans, srcs, dsts, stream=stream))
+    t_seq = timed(lambda: [bf.bf_filter(p, x, y, stream=stream) for p, x, y in zip(plans, srcs, dsts)])
+    return {"images": n, "sides": [lo, hi], "mpix": round(px / 1e6, 2),
+            "batched_mpix_s": round(px / (t_batch * 1e-3) / 1e6, 1), "batched_ms": round(t_batch, 3),
+            "sequential_mpix_s": round(px / (t_seq * 1e-3) / 1e6, 1), "sequential_ms": round(t_seq, 3)}
+
+
+def run_serving(bf, dev, n=160, lo=128, hi=2048, load=0.8):
+    """Poisson stream at `load` x the measured saturation rate through the continuous-batching
+    server (pinned host buffers): p50/p99 latency and Mpixel/s; plus the plain per-image path
+    (H2D, bf_filter, D2H, one request at a time) on the same requests."""
+    import torch
+    work = mixed_requests(n, lo, hi, seed=4321)
+    hin = [torch.from_numpy(img).pin_memory() for img, _ in work]
+    hout = [torch.empty_like(x).pin_memory() for x in hin]
+    descs = [bf.desc(**kw) for _, kw in work]
+    px = sum(img.size for img, _ in work)
+    srv = bf.Server(device=dev.index or 0, max_slots=32, n_streams=4, max_batch=8)
+
+    def burst(delays):
+        t0 = time.perf_counter()
+        tickets = []
+        for d, (img, _), hi_, ho in zip(descs, work, hin, hout):
+            if delays is not None:
+                time.sleep(delays.pop())
+            tickets.append(srv.submit(d, hi_.data_ptr(), ho.data_ptr(), img.shape[0], img.shape[1]))
+        lat = []
+        for t in tickets:
+            st, r = srv.poll(t, -1)
+            if st != 0 or r.status != 0:
+                raise RuntimeError("serving request failed: %d/%d" % (st, r.status))
+            lat.append(r.latency_ms)
+        return time.perf_counter() - t0, lat
+
+    burst(None)                                   # warm-up (plans, memory pool)
+    t_sat, _ = burst(None)                        # saturation: all requests at once
+    rate = load * n / t_sat                       # requests/s
+    rng = np.random.default_rng(7)
+    delays = list(rng.exponential(1.0 / rate, n))[::-1]
+    t_run, lat = burst(delays)
+    srv.close()
+    # plain per-image path
+    plans = [bf.Plan(d) for d in descs]
+    stream = torch.cuda.current_stream(dev)
+    d_in = [torch.empty(img.shape, dtype=torch.float32, device=dev) for img, _ in work]
+    d_out = [torch.empty_like(x) for x in d_in]
+    t0 = time.perf_counter()
+    for p, hi_, ho, di, do in zip(plans, hin, hout, d_in, d_out):
+        di.copy_(hi_, non_blocking=True)
+        bf.bf_filter(p, di, do, stream=stream)
+        ho.copy_(do, non_blocking=True)
+        torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    return {"requests": n, "sides": [lo, hi], "load": load, "rate_req_s": round(rate, 1),
+            "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+            "mpix_s": round(px / t_run / 1e6, 1), "saturation_mpix_s": round(px / t_sat / 1e6, 1),
+            "plain_per_image_mpix_s": round(px / t_plain / 1e6, 1)}
 
 
 def cpu_baseline(img, rows: int = 1080, combos=None):
