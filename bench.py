@@ -118,6 +118,22 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+def reduce_max_ms(ms: float, device=None) -> float:
+    """Max of a per-rank time over all ranks (no-op without an initialised process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(px_per_rank_step: float, steps: int, max_ms: float, world: int) -> float:
+    """Mpixel/s of the whole job: every rank's pixels over the slowest rank's time (weak scaling)."""
+    return world * px_per_rank_step * steps / (max_ms * 1e-3) / 1e6
+
+
 def algorithmic_ops_per_pixel(coeffs: dict) -> float:
     """FP32 operations per pixel of a separable running-sum evaluation of Eq. (36):
     per basis image, 2 adds per vertical window, the window mixing (nonzero weights),
@@ -206,13 +222,9 @@ def run_ours(args):
         launch_ms.append([ev[j].elapsed_time(ev[j + 1]) for j in range(len(plans))])
     torch.cuda.synchronize()
     sampler.stop()
-    total_ms = float(np.sum(per_step))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max_ms(float(np.sum(per_step)), dev)
     px_step = len(plans) * H * W
-    value = world * px_step * args.steps / (total_ms * 1e-3) / 1e6
+    value = whole_job_value(px_step, args.steps, total_ms, world)
     ms_per_step = total_ms / args.steps
 
     # roofline of the dominant kernel (the fused filter kernel, one launch per plan)
@@ -251,7 +263,7 @@ def run_ours(args):
                    "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "single"},
         "psnr_db_vs_exact": [round(x, 2) for x in psnr], "min_psnr_db": round(min(psnr), 2) if psnr else None,
         "per_combo_ms": [round(x, 4) for x in lm.mean(0)],
-        "tiles": [[t["tw"], t["th"], t["threads"], t["nk"], t["groups"]] for t in tiles],
+        "tiles": [[t["tw"], t["th"], t["threads"], t["nk"], t["groups"], t.get("variant", 0)] for t in tiles],
         "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
                      "frac": round(achieved / alu_peak, 4), "traffic": None,
                      "note": "FP32 lane-ops/s of the fused kernel (algorithmic count) vs SMs x 128 x max SM clock"},

@@ -188,8 +188,9 @@ bf_status bf_filter_noalloc(const bf_plan *plan, const float *d_in, size_t in_pi
  * Errors: BF_ERR_INVALID_ARG. */
 bf_status bf_launch_info(const bf_plan *plan, int height, int width, int *info);
 
-/* Autotuner: times up to 12 candidate launch geometries (tile width, tile
- * height, cosine terms per CTA) for this plan on a synthetic height x width
+/* Autotuner: times candidate launch geometries (the cost model's best five of
+ * each family: tile width, tile height, cosine terms per CTA, with or without
+ * the shared-memory ring of basis inputs) for this plan on a synthetic height x width
  * image and remembers the fastest for later bf_filter / bf_filter_batch calls
  * with the same kernel class, reach and image size on this device.  Allocates
  * and frees its own device buffers and synchronizes `stream`; do not call it

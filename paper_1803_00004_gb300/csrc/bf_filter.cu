@@ -81,6 +81,21 @@ __device__ __forceinline__ void basis_start(float v, float inv_p, float inv_p_lo
     }
 }
 
+__device__ __forceinline__ int pos_mod(int a, int d) {
+    const int r = a % d;
+    return r < 0 ? r + d : r;
+}
+
+__device__ __forceinline__ void ring_put(float *ring, int D, int ncols, int row, int tid, float v, float c1, float s1,
+                                         float c0, float s0) {
+    float *r = ring + (size_t)(pos_mod(row, D) * 5) * ncols + tid;
+    r[0] = v;
+    r[ncols] = c1;
+    r[2 * ncols] = s1;
+    r[3 * ncols] = c0;
+    r[4 * ncols] = s0;
+}
+
 // Compensated (Kahan) accumulation s += x with running error term c.
 __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
     const float y = x - c;
@@ -91,6 +106,12 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
 
 // Advances (c, s) = (cos, sin)(pi k t) by `steps` multiples of the base rotation.
 __device__ __forceinline__ void rotate(float &c, float &s, float c1, float s1, int steps) {
+    if (steps == 1) {  // consecutive terms (the usual case): no loop
+        const float cn = fmaf(c, c1, -s * s1);
+        s = fmaf(s, c1, c * s1);
+        c = cn;
+        return;
+    }
     for (int n = 0; n < steps; ++n) {
         const float cn = fmaf(c, c1, -s * s1);
         const float sn = fmaf(s, c1, c * s1);
@@ -103,16 +124,22 @@ __device__ __forceinline__ void rotate(float &c, float &s, float c1, float s1, i
 // cosine terms [g NK, g NK + NK) of p.  All threads of the CTA call it; it
 // ends on a barrier, so the shared memory can be reused right after.  `grouped`:
 // store partial numerator / denominator planes (part) instead of dividing.
-template <int NK, int M>
+template <int NK, int M, bool RING>
 __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__restrict__ in, size_t in_pitch,
                                           float *__restrict__ out, size_t out_pitch, float *__restrict__ part, int H,
                                           int W, int x0, int y0, int tw, int th, int ncols, int g, bool grouped,
-                                          float *smem) {
+                                          int depth, float *smem) {
     constexpr int NROW = M * NK * 4;  // exchange rows per image row: windows x terms x basis images
     constexpr int NE = 2 * M + 1;     // edges per step: M entering rows, M leaving rows, the output row
     const int ZP = ncols + 3;         // odd: scan lanes (rows) hit distinct banks
-    float *zb0 = smem;                // [2][NROW][ZP]: column c of the tile at index c + 1; 0, ncols+1, ncols+2 stay 0
-    float *wb0 = smem + 2 * NROW * ZP;  // [2][NK][2][tw]: a_k cos, a_k sin at the output row
+    // `depth` exchange buffers: 2 -> the output phase reads the row the scan finished in the same step (two
+    // barriers per row); 3 -> it reads the row scanned one step earlier (one barrier per row)
+    float *zb0 = smem;                    // [depth][NROW][ZP]: tile column c at index c + 1; 0, ncols+1, ncols+2 stay 0
+    float *wb0 = smem + depth * NROW * ZP;  // [depth][NK][2][tw]: a_k cos, a_k sin at the output row
+    // RING: per column, the basis inputs of the last D rows (v, cos/sin(pi t), cos/sin(pi k0 t)), so each
+    // row's sincospi and load happen once instead of at every window edge: [D][5][ncols]
+    const int D = p.vhi - p.vlo + 2;
+    float *ring = wb0 + depth * NK * 2 * tw;
 
     const int tid = threadIdx.x;
     const bool is_col = tid < ncols;
@@ -122,7 +149,7 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
     const int xl = tid - p.rx;
     const bool is_out = is_col && xl >= 0 && xl < tw && x0 + xl < W;
 
-    for (int i = tid; i < 2 * NROW; i += blockDim.x) {
+    for (int i = tid; i < depth * NROW; i += blockDim.x) {
         zb0[i * ZP] = 0.f;
         zb0[i * ZP + ncols + 1] = 0.f;
         zb0[i * ZP + ncols + 2] = 0.f;
@@ -155,6 +182,7 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
             const float v = colv ? __ldg(in + (size_t)row * in_pitch + xcol) - p.i_lo : 0.f;
             float c1, s1, c, s;
             basis_start(v, p.inv_p, p.inv_p_lo, kk[0], colv, c1, s1, c, s);
+            if (RING) ring_put(ring, D, ncols, row, tid, v, c1, s1, c, s);
             int kc = kk[0];
 #pragma unroll
             for (int i = 0; i < NK; ++i) {
@@ -171,22 +199,42 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
         }
     }
 
-    for (int j = 0; j <= nout; ++j) {
+    const int lag = depth - 1;  // steps between a row's vertical pass and its output phase
+    for (int j = 0; j < nout + lag; ++j) {
         const int y = y0 + j;
         if (is_col && j < nout) {
             float Ie[NE], c1[NE], s1[NE], ce[NE], se[NE];
+            if (RING && j > 0) {  // the newest row of the span enters the ring
+                const int row = y + p.vhi;
+                if (row < H) {
+                    const float v = colv ? __ldg(in + (size_t)row * in_pitch + xcol) - p.i_lo : 0.f;
+                    float a, b, c, s;
+                    basis_start(v, p.inv_p, p.inv_p_lo, kk[0], colv, a, b, c, s);
+                    ring_put(ring, D, ncols, row, tid, v, a, b, c, s);
+                }
+            }
 #pragma unroll
             for (int e = 0; e < NE; ++e) {
                 const int off = e < M ? p.v1[e] : (e < 2 * M ? p.v0[e - M] - 1 : 0);
                 const int row = y + off;
                 // at j == 0 the sums already hold row y0: only the output-row edge is live
                 const bool valid = colv && row >= 0 && row < H && (j > 0 || e == 2 * M);
-                const float v = valid ? __ldg(in + (size_t)row * in_pitch + xcol) - p.i_lo : 0.f;
-                Ie[e] = v;
-                basis_start(v, p.inv_p, p.inv_p_lo, kk[0], valid, c1[e], s1[e], ce[e], se[e]);
+                if (RING) {
+                    // slots of rows outside the image were never written: do not read them
+                    const float *rr = ring + (size_t)(pos_mod(row, D) * 5) * ncols + tid;
+                    Ie[e] = valid ? rr[0] : 0.f;
+                    c1[e] = valid ? rr[ncols] : 1.f;
+                    s1[e] = valid ? rr[2 * ncols] : 0.f;
+                    ce[e] = valid ? rr[3 * ncols] : 0.f;
+                    se[e] = valid ? rr[4 * ncols] : 0.f;
+                } else {
+                    const float v = valid ? __ldg(in + (size_t)row * in_pitch + xcol) - p.i_lo : 0.f;
+                    Ie[e] = v;
+                    basis_start(v, p.inv_p, p.inv_p_lo, kk[0], valid, c1[e], s1[e], ce[e], se[e]);
+                }
             }
-            float *zb = zb0 + (j & 1) * NROW * ZP + tid + 1;
-            float *wb = wb0 + (j & 1) * NK * 2 * tw;
+            float *zb = zb0 + (j % depth) * NROW * ZP + tid + 1;
+            float *wb = wb0 + (j % depth) * NK * 2 * tw;
             int kc = kk[0];
 #pragma unroll
             for (int i = 0; i < NK; ++i) {
@@ -216,14 +264,14 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
                     wb[(i * 2 + 1) * tw + xl] = aa[i] * se[2 * M];
                 }
             }
-        } else if (!is_col && j >= 1) {
+        } else if (!is_col && j >= 1 && j - 1 < nout) {
             const int r = tid - ncols;
             if (r < NROW) {
                 // sliding sum of window q over the row; S(c) replaces Z(c + u0), which the
                 // slide has consumed (index c + u0 + 1 in buffer coordinates)
                 const int q = r / (NK * 4);
                 const int u0 = p.u0[q], u1 = p.u1[q];
-                float *row = zb0 + ((j - 1) & 1) * NROW * ZP + r * ZP;
+                float *row = zb0 + ((j - 1) % depth) * NROW * ZP + r * ZP;
                 float S = 0.f, comp = 0.f;
                 int b = p.rx + u0 + 1;
                 const int bend = p.rx + u1 + 1;
@@ -250,11 +298,11 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
                 }
             }
         }
-        __syncthreads();
-        if (is_out && j >= 1) {
-            const int yo = y - 1;
-            const float *zp = zb0 + ((j - 1) & 1) * NROW * ZP + tid;
-            const float *wp = wb0 + ((j - 1) & 1) * NK * 2 * tw + xl;
+        if (depth == 2) __syncthreads();
+        if (is_out && j >= lag) {
+            const int yo = y - lag;
+            const float *zp = zb0 + ((j - lag) % depth) * NROW * ZP + tid;
+            const float *wp = wb0 + ((j - lag) % depth) * NK * 2 * tw + xl;
             float num = 0.f, den = 0.f;
 #pragma unroll
             for (int i = 0; i < NK; ++i) {
@@ -285,13 +333,14 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
     }
 }
 
-template <int NK, int M>
+template <int NK, int M, bool RING>
 __global__ void __launch_bounds__(512, 1)
 bf_fused_kernel(const float *__restrict__ in, size_t in_pitch, float *__restrict__ out, size_t out_pitch,
-                float *__restrict__ part, int H, int W, int tw, int th, int ncols, const __grid_constant__ FilterParams p) {
+                float *__restrict__ part, int H, int W, int tw, int th, int ncols, int depth,
+                const __grid_constant__ FilterParams p) {
     extern __shared__ float smem[];
-    tile_body<NK, M>(p, in, in_pitch, out, out_pitch, part, H, W, blockIdx.x * tw, blockIdx.y * th, tw, th, ncols,
-                     blockIdx.z, gridDim.z > 1, smem);
+    tile_body<NK, M, RING>(p, in, in_pitch, out, out_pitch, part, H, W, blockIdx.x * tw, blockIdx.y * th, tw, th, ncols,
+                           blockIdx.z, gridDim.z > 1, depth, smem);
 }
 
 // Persistent batched form: each CTA repeatedly takes the next work item from
@@ -316,8 +365,8 @@ bf_batch_kernel(const BatchImage *__restrict__ imgs, const FilterParams *__restr
         int *dst = reinterpret_cast<int *>(&sp);
         for (int i = threadIdx.x; i < (int)(sizeof(FilterParams) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
         __syncthreads();
-        tile_body<NK, M>(sp, im.in, im.in_pitch, im.out, im.out_pitch, im.part, im.H, im.W, w.x0, w.y0, w.tw, w.th,
-                         ncols, w.g, im.groups > 1, smem);
+        tile_body<NK, M, false>(sp, im.in, im.in_pitch, im.out, im.out_pitch, im.part, im.H, im.W, w.x0, w.y0, w.tw,
+                                w.th, ncols, w.g, im.groups > 1, 2, smem);
     }
 }
 
@@ -357,26 +406,33 @@ __global__ void bf_finalize_kernel(const float *__restrict__ in, size_t in_pitch
 // no class spills registers).
 struct KernelClass {
     int m, nk;
-    const void *fn;
+    const void *fn;       // tile kernel, edges recomputed
+    const void *fn_ring;  // tile kernel with the per-column basis ring
     const void *batch_fn;
 };
 
-#define BF_CLASS(M, NK) {M, NK, (const void *)bf_fused_kernel<NK, M>, (const void *)bf_batch_kernel<NK, M>}
+#define BF_CLASS(M, NK)                                                                                   \
+    {M, NK, (const void *)bf_fused_kernel<NK, M, false>, (const void *)bf_fused_kernel<NK, M, true>,     \
+     (const void *)bf_batch_kernel<NK, M>}
 const KernelClass kClasses[] = {
     BF_CLASS(1, 16), BF_CLASS(1, 8), BF_CLASS(1, 4), BF_CLASS(1, 2),
     BF_CLASS(2, 8),  BF_CLASS(2, 4), BF_CLASS(2, 2), BF_CLASS(3, 5), BF_CLASS(3, 4), BF_CLASS(3, 2),
-    BF_CLASS(4, 2),  BF_CLASS(5, 2), BF_CLASS(6, 1),
+    BF_CLASS(4, 2),  BF_CLASS(5, 1), BF_CLASS(6, 1),
 };
 #undef BF_CLASS
 
-const void *find_kernel(int m, int nk) {
+const void *find_kernel(int m, int nk, bool ring) {
     for (const auto &c : kClasses)
-        if (c.m == m && c.nk == nk) return c.fn;
+        if (c.m == m && c.nk == nk) return ring ? c.fn_ring : c.fn;
     return nullptr;
 }
 
-size_t smem_bytes(int m, int nk, int ncols, int tw) {
-    return sizeof(float) * (2 * (size_t)m * nk * 4 * (ncols + 3) + 2 * (size_t)nk * 2 * tw);
+size_t smem_bytes(int m, int nk, int ncols, int tw, int depth = 2) {
+    return sizeof(float) * ((size_t)depth * m * nk * 4 * (ncols + 3) + (size_t)depth * nk * 2 * tw);
+}
+
+size_t ring_bytes(const FilterParams &p, int ncols) {
+    return sizeof(float) * 5 * (size_t)(p.vhi - p.vlo + 2) * ncols;
 }
 
 int device_sms() {
@@ -447,38 +503,49 @@ std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int w
     (void)precision;
     const int sms = device_sms();
     const int vspan = p.vhi - p.vlo + 1;
+    const int wpad = ((width + 7) / 8) * 8;
     std::vector<std::pair<double, TileConfig>> all;
     for (const auto &cls : kClasses) {
         if (cls.m != p.m) continue;
         const int groups = (p.nr + cls.nk - 1) / cls.nk;
-        for (int tw : {64, 128, 192, 256, 320, 384}) {
-            const int twe = std::min(tw, ((width + 31) / 32) * 32);
-            const int ncols = ((twe + 2 * p.rx + 31) / 32) * 32;
-            if (ncols + kScanThreads > 512) continue;
-            const size_t smem = smem_bytes(p.m, cls.nk, ncols, twe);
-            if (smem > 227 * 1024) continue;
-            const int by_smem = (int)((228 * 1024) / (smem + 1024));
-            const int by_threads = 2048 / (ncols + kScanThreads);
-            const int by_regs = 65536 / (128 * (ncols + kScanThreads));
-            const int cps = std::max(1, std::min({by_smem, by_threads, by_regs}));
-            for (int th : {16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 1024}) {
-                const int the = std::min(th, std::max(height, 1));
-                const long ctas = (long)((width + twe - 1) / twe) * ((height + the - 1) / the) * groups;
-                const double per_cta = (double)ncols * (the + 0.3 * vspan) * (60.0 * (2 * p.m + 1) + 40.0 * cls.nk * p.m);
-                const double waves = std::ceil((double)ctas / (sms * cps));
-                const double cost = waves * per_cta * cps + (groups > 1 ? 16.0 * groups * (double)height * width : 0.0);
-                TileConfig tc;
-                tc.tw = twe;
-                tc.th = the;
-                tc.ncols = ncols;
-                tc.threads = ncols + kScanThreads;
-                tc.nk = cls.nk;
-                tc.groups = groups;
-                tc.smem = smem;
-                all.push_back({cost, tc});
-                if (the >= height) break;
+        // column threads in whole warps; the tile takes what the halo leaves
+        for (int ncols = 32; ncols + kScanThreads <= 512; ncols += 32) {
+            int tw = ((ncols - 2 * p.rx) / 8) * 8;
+            if (tw < 8) continue;
+            tw = std::min(tw, wpad);
+            if (ncols > ((tw + 2 * p.rx + 31) / 32) * 32) break;  // wider tiles than the image gain nothing
+            for (int variant = 0; variant < 4; ++variant) {
+                const int ring = variant & 1, depth = 2 + (variant >> 1);
+                // the ring serves the output row too, so it must lie inside the window span
+                if (ring && !(p.vlo <= 0 && p.vhi >= 0)) continue;
+                const size_t smem = smem_bytes(p.m, cls.nk, ncols, tw, depth) + (ring ? ring_bytes(p, ncols) : 0);
+                if (smem > 227 * 1024) continue;
+                const int by_smem = (int)((228 * 1024) / (smem + 1024));
+                const int by_threads = 2048 / (ncols + kScanThreads);
+                const int by_regs = 65536 / (128 * (ncols + kScanThreads));
+                const int cps = std::max(1, std::min({by_smem, by_threads, by_regs}));
+                const double edge = (ring ? 60.0 + 12.0 * (2 * p.m + 1) : 60.0 * (2 * p.m + 1)) * (depth == 3 ? 0.9 : 1.0);
+                for (int th : {16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 1024}) {
+                    const int the = std::min(th, std::max(height, 1));
+                    const long ctas = (long)((width + tw - 1) / tw) * ((height + the - 1) / the) * groups;
+                    const double per_cta = (double)ncols * (the + 0.3 * vspan) * (edge + 40.0 * cls.nk * p.m);
+                    const double waves = std::ceil((double)ctas / (sms * cps));
+                    const double cost =
+                        waves * per_cta * cps + (groups > 1 ? 16.0 * groups * (double)height * width : 0.0);
+                    TileConfig tc;
+                    tc.tw = tw;
+                    tc.th = the;
+                    tc.ncols = ncols;
+                    tc.threads = ncols + kScanThreads;
+                    tc.nk = cls.nk;
+                    tc.groups = groups;
+                    tc.ring = ring;
+                    tc.depth = depth;
+                    tc.smem = smem;
+                    all.push_back({cost, tc});
+                    if (the >= height) break;
+                }
             }
-            if (twe >= width) break;
         }
     }
     std::stable_sort(all.begin(), all.end(), [](const auto &a, const auto &b) { return a.first < b.first; });
@@ -550,7 +617,7 @@ bf_status launch_filter(const FilterParams &p, int precision, int kahan, const T
     (void)precision;
     (void)kahan;
     if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");
-    const void *fn = find_kernel(p.m, tc.nk);
+    const void *fn = find_kernel(p.m, tc.nk, tc.ring != 0);
     if (!fn || tc.ncols <= 0) return fail(BF_ERR_UNSUPPORTED, "no kernel class for this plan and image");
     if (tc.threads > 512) return fail(BF_ERR_UNSUPPORTED, "horizontal reach too large for one CTA");
     if (tc.smem > 227 * 1024) return fail(BF_ERR_UNSUPPORTED, "tile needs more than 227 KB of shared memory");
@@ -558,12 +625,12 @@ bf_status launch_filter(const FilterParams &p, int precision, int kahan, const T
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc.smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     dim3 grid((width + tc.tw - 1) / tc.tw, (height + tc.th - 1) / tc.th, tc.groups);
-    int tw = tc.tw, th = tc.th, ncols = tc.ncols, H = height, W = width;
+    int tw = tc.tw, th = tc.th, ncols = tc.ncols, H = height, W = width, depth = tc.depth;
     const float *in = d_in;
     float *out = d_out, *part = d_scratch;
     FilterParams pp = p;
     void *args[] = {(void *)&in, (void *)&in_pitch, (void *)&out, (void *)&out_pitch, (void *)&part, (void *)&H,
-                    (void *)&W, (void *)&tw, (void *)&th, (void *)&ncols, (void *)&pp};
+                    (void *)&W, (void *)&tw, (void *)&th, (void *)&ncols, (void *)&depth, (void *)&pp};
     e = cudaLaunchKernel(fn, grid, dim3(tc.threads), args, tc.smem, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "filter launch");
     if (tc.groups > 1) {

@@ -48,6 +48,8 @@ struct TileConfig {
     int threads;   // ncols + scan warps
     int nk;        // cosine terms per group (template slot count)
     int groups;    // term groups (grid.z); > 1 writes partial planes + finalize
+    int ring;      // 1: per-column ring of basis inputs in shared memory
+    int depth;     // exchange buffers: 2 (two barriers per row) or 3 (one barrier per row)
     size_t smem;   // dynamic shared memory bytes
 };
 

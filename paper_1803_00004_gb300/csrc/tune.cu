@@ -45,9 +45,9 @@ void load_locked() {
     int k[9];
     TileConfig tc;
     unsigned long smem;
-    while (std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %lu", &k[0], &k[1], &k[2], &k[3], &k[4],
+    while (std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %lu", &k[0], &k[1], &k[2], &k[3], &k[4],
                        &k[5], &k[6], &k[7], &k[8], &tc.tw, &tc.th, &tc.ncols, &tc.threads, &tc.nk, &tc.groups,
-                       &smem) == 16) {
+                       &tc.ring, &tc.depth, &smem) == 18) {
         tc.smem = smem;
         g_table[Key{k[0], k[1], k[2], k[3], k[4], k[5], k[6], k[7], k[8]}] = tc;
     }
@@ -59,10 +59,10 @@ void save_locked(const Key &key, const TileConfig &tc) {
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %lu\n", std::get<0>(key), std::get<1>(key),
+    std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %lu\n", std::get<0>(key), std::get<1>(key),
                  std::get<2>(key), std::get<3>(key), std::get<4>(key), std::get<5>(key), std::get<6>(key),
-                 std::get<7>(key), std::get<8>(key), tc.tw, tc.th, tc.ncols, tc.threads, tc.nk, tc.groups,
-                 (unsigned long)tc.smem);
+                 std::get<7>(key), std::get<8>(key), tc.tw, tc.th, tc.ncols, tc.threads, tc.nk, tc.groups, tc.ring,
+                 tc.depth, (unsigned long)tc.smem);
     std::fclose(f);
 }
 
@@ -110,7 +110,11 @@ extern "C" bf_status bf_autotune(const bf_plan *plan, int height, int width, voi
         return fail(BF_ERR_NO_DEVICE, "cannot select the plan's device");
     }
     cudaStream_t s = (cudaStream_t)stream;
-    std::vector<TileConfig> cands = tile_candidates(plan->kp, height, width, plan->desc.precision, 12);
+    // the cost model is coarse: keep the best few of every family (ring or not, terms per CTA)
+    std::vector<TileConfig> ranked = tile_candidates(plan->kp, height, width, plan->desc.precision, 100000), cands;
+    std::map<std::pair<int, int>, int> per_family;
+    for (const auto &c : ranked)
+        if (per_family[{c.ring * 4 + c.depth, c.nk}]++ < 4) cands.push_back(c);
     bf_status st = BF_OK;
     float *in = nullptr, *out = nullptr, *scratch = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -14,6 +14,9 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
+# alone vs in the mix: different tile geometries round differently; each result is
+# within TOL of the oracle, so the two are within 2 TOL of each other
+MIX_TOL = 2e-5
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -57,7 +60,7 @@ def test_batch_matches_single_image_results():
     torch.cuda.synchronize()
     for (img, kw), d in zip(work, dsts):
         ref = alone(img, kw)
-        assert np.max(np.abs(d.cpu().numpy() - ref)) < TOL, kw
+        assert np.max(np.abs(d.cpu().numpy() - ref)) < MIX_TOL, kw
 
 
 def test_batch_against_oracle_small():
@@ -89,7 +92,7 @@ def test_graph_replay_tracks_new_input():
     torch.cuda.synchronize()
     for (img, kw), d in zip(work, dsts):
         ref = alone(np.ascontiguousarray(img[:, ::-1]), kw)
-        assert np.max(np.abs(d.cpu().numpy() - ref)) < TOL
+        assert np.max(np.abs(d.cpu().numpy() - ref)) < MIX_TOL
 
 
 def test_batch_edge_cases():
@@ -99,7 +102,7 @@ def test_batch_edge_cases():
     out = torch.empty_like(a)
     bf.bf_filter_batch([p, p], [e, a], [torch.empty_like(e), out])  # empty image is skipped
     torch.cuda.synchronize()
-    assert np.max(np.abs(out.cpu().numpy() - alone(a.cpu().numpy(), {}))) < TOL
+    assert np.max(np.abs(out.cpu().numpy() - alone(a.cpu().numpy(), {}))) < MIX_TOL
     bf.bf_filter_batch([], [], [])
     with pytest.raises(bf.BFError):
         bf.bf_filter_batch([p], [a], [a])              # in place
@@ -130,7 +133,7 @@ def test_server_results_equal_alone_under_concurrency():
         assert st == 0 and r.status == 0
         lat.append(r.latency_ms)
     for (img, kw), (hin, hout) in zip(work, bufs):
-        assert np.max(np.abs(hout.numpy() - alone(img, kw))) < TOL
+        assert np.max(np.abs(hout.numpy() - alone(img, kw))) < MIX_TOL
     srv.close()
     assert all(x > 0 for x in lat)
 
@@ -157,7 +160,7 @@ def test_server_admission_cancel_timeout_and_errors():
         assert st == 0 and r.status == 0
     ref = alone(img, dict(sigma_s=8.0))
     for i, o in bufs[:-1]:
-        assert np.max(np.abs(o.numpy() - ref)) < TOL
+        assert np.max(np.abs(o.numpy() - ref)) < MIX_TOL
     assert srv.poll(123456789, 0)[0] == 10                  # unknown ticket
     # an injected launch failure fails that request only; the server keeps serving
     bf.bf_debug_fail_launches(1)
