@@ -60,6 +60,7 @@ class bf_result(C.Structure):
 
 
 EXPORTS = ["bf_plan_desc_default", "bf_plan_create", "bf_plan_destroy", "bf_coeffs", "bf_launch_info", "bf_autotune",
+           "bf_launch_candidates", "bf_set_launch",
            "bf_filter", "bf_filter_noalloc",
            "bf_filter_batch",
            "bf_exact", "bf_serve_create", "bf_serve_submit", "bf_serve_poll", "bf_serve_cancel", "bf_serve_destroy",
@@ -90,6 +91,8 @@ def lib():
         L.bf_coeffs.argtypes = [vp, P(bf_coeff_view)]
         L.bf_filter.argtypes = [vp, vp, sz, vp, sz, i, i, vp]
         L.bf_launch_info.argtypes = [vp, i, i, P(i)]
+        L.bf_launch_candidates.argtypes = [vp, i, i, i, P(i), P(i)]
+        L.bf_set_launch.argtypes = [vp, i, i, P(i)]
         L.bf_filter_noalloc.argtypes = [vp, vp, sz, vp, sz, i, i, vp]
         L.bf_autotune.argtypes = [vp, i, i, vp, P(i)]
         L.bf_filter_batch.argtypes = [P(vp), P(bf_image), i, vp]
@@ -188,17 +191,36 @@ def bf_coeffs(plan: Plan) -> dict:
     }
 
 
+INFO_KEYS = ("tw", "th", "threads", "nk", "groups", "launches", "smem", "scratch_kib", "ring", "depth",
+             "cluster", "ncols")
+
+
 def bf_launch_info(plan: Plan, height: int, width: int) -> dict:
-    info = (C.c_int * 8)()
+    info = (C.c_int * 12)()
     _check(lib().bf_launch_info(plan.handle, height, width, info), "bf_launch_info")
-    keys = ("tw", "th", "threads", "nk", "groups", "launches", "smem", "scratch_kib")
+    keys = INFO_KEYS
     return dict(zip(keys, list(info)))
 
 
+def bf_launch_candidates(plan: Plan, height: int, width: int, max_n: int = 4096) -> list:
+    """Launch geometries for this plan and image size, best first by the cost model."""
+    buf = (C.c_int * (12 * max_n))()
+    n = C.c_int(0)
+    _check(lib().bf_launch_candidates(plan.handle, height, width, max_n, buf, C.byref(n)), "bf_launch_candidates")
+    vals = list(buf)
+    return [dict(zip(INFO_KEYS, vals[12 * k:12 * k + 12])) for k in range(n.value)]
+
+
+def bf_set_launch(plan: Plan, height: int, width: int, info: dict) -> None:
+    """Pins one geometry of bf_launch_candidates for later filter calls."""
+    arr = (C.c_int * 12)(*[int(info[k]) for k in INFO_KEYS])
+    _check(lib().bf_set_launch(plan.handle, height, width, arr), "bf_set_launch")
+
+
 def bf_autotune(plan: Plan, height: int, width: int, stream=None) -> dict:
-    info = (C.c_int * 8)()
+    info = (C.c_int * 12)()
     _check(lib().bf_autotune(plan.handle, height, width, _stream_handle(stream), info), "bf_autotune")
-    keys = ("tw", "th", "threads", "nk", "groups", "launches", "smem", "scratch_kib")
+    keys = INFO_KEYS
     return dict(zip(keys, list(info)))
 
 

@@ -31,7 +31,8 @@ def _nvcc() -> str:
 
 
 def _headers() -> list[str]:
-    return glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    return (glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
+            glob.glob(os.path.join(INCLUDE, "*.h")))
 
 
 def _stale(src: str, obj: str, hdr_mtime: float) -> bool:

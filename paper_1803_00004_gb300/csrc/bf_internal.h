@@ -38,6 +38,7 @@ struct FilterParams {
     float C[kMaxWin][kMaxWin];
     int rx;                   // max |u| (horizontal reach)
     int vlo, vhi;             // min v0, max v1
+    int kahan;                // 1: compensated horizontal sliding sums
 };
 
 // Launch geometry chosen by the host.
@@ -50,6 +51,7 @@ struct TileConfig {
     int groups;    // term groups (grid.z); > 1 writes partial planes + finalize
     int ring;      // 1: per-column ring of basis inputs in shared memory
     int depth;     // exchange buffers: 2 (two barriers per row) or 3 (one barrier per row)
+    int cluster;   // > 0: CTAs per thread-block cluster spanning the image width (no halo columns)
     size_t smem;   // dynamic shared memory bytes
 };
 
@@ -79,6 +81,9 @@ bool kernel_class_supported(int m);
 // Ranked launch geometries from the cost model, the model's pick, and the
 // geometry bf_filter uses (an autotuned one when bf_autotune measured this
 // kernel class, reach and image size on this device, else the model's pick).
+// Writes the 12-int geometry record of bf_launch_info / bf_autotune.
+void fill_info(const TileConfig &tc, int height, int width, int *info);
+
 std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int width, int precision, int max_n);
 TileConfig model_tile(const FilterParams &p, int height, int width, int precision);
 TileConfig choose_tile(const FilterParams &p, int height, int width, int precision);

@@ -92,7 +92,7 @@ void bf_plan_desc_default(bf_plan_desc *d) {
     d->i_lo = 0.0f;
     d->i_hi = 1.0f;
     d->precision = BF_PREC_FP32;
-    d->kahan = 0;
+    d->kahan = 1;
     d->device = 0;
 }
 
@@ -178,14 +178,7 @@ bf_status bf_filter(const bf_plan *plan, const float *d_in, size_t in_pitch, flo
 bf_status bf_launch_info(const bf_plan *plan, int height, int width, int *info) {
     if (!plan || !info || height < 1 || width < 1) return fail(BF_ERR_INVALID_ARG, "bad launch-info arguments");
     TileConfig tc = choose_tile(plan->kp, height, width, plan->desc.precision);
-    info[0] = tc.tw;
-    info[1] = tc.th;
-    info[2] = tc.threads;
-    info[3] = tc.nk;
-    info[4] = tc.groups;
-    info[5] = tc.groups > 1 ? 2 : 1;
-    info[6] = (int)tc.smem;
-    info[7] = (int)(scratch_bytes(tc, height, width) >> 10);
+    fill_info(tc, height, width, info);
     return BF_OK;
 }
 

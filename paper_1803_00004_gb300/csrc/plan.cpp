@@ -240,6 +240,9 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
         return fail(BF_ERR_INVALID_ARG, "unknown range policy");
     if (d.precision < BF_PREC_FP32 || d.precision > BF_PREC_FP16_EXCHANGE)
         return fail(BF_ERR_INVALID_ARG, "unknown precision");
+    if (d.precision != BF_PREC_FP32)
+        return fail(BF_ERR_UNSUPPORTED, "16-bit exchange is not built: the kernel stores no basis image and is bound by "
+                                        "fp32 issue, which 16-bit storage does not relieve");
 
     p.desc = d;
     const double dI = (double)d.i_hi - (double)d.i_lo;
@@ -419,6 +422,7 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
     kp.rx = rx;
     kp.vlo = vlo;
     kp.vhi = vhi;
+    kp.kahan = d.kahan ? 1 : 0;
     return BF_OK;
 }
 

@@ -45,9 +45,9 @@ void load_locked() {
     int k[9];
     TileConfig tc;
     unsigned long smem;
-    while (std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %lu", &k[0], &k[1], &k[2], &k[3], &k[4],
+    while (std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %lu", &k[0], &k[1], &k[2], &k[3], &k[4],
                        &k[5], &k[6], &k[7], &k[8], &tc.tw, &tc.th, &tc.ncols, &tc.threads, &tc.nk, &tc.groups,
-                       &tc.ring, &tc.depth, &smem) == 18) {
+                       &tc.ring, &tc.depth, &tc.cluster, &smem) == 19) {
         tc.smem = smem;
         g_table[Key{k[0], k[1], k[2], k[3], k[4], k[5], k[6], k[7], k[8]}] = tc;
     }
@@ -59,10 +59,10 @@ void save_locked(const Key &key, const TileConfig &tc) {
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %lu\n", std::get<0>(key), std::get<1>(key),
+    std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %lu\n", std::get<0>(key), std::get<1>(key),
                  std::get<2>(key), std::get<3>(key), std::get<4>(key), std::get<5>(key), std::get<6>(key),
                  std::get<7>(key), std::get<8>(key), tc.tw, tc.th, tc.ncols, tc.threads, tc.nk, tc.groups, tc.ring,
-                 tc.depth, (unsigned long)tc.smem);
+                 tc.depth, tc.cluster, (unsigned long)tc.smem);
     std::fclose(f);
 }
 
@@ -114,7 +114,7 @@ extern "C" bf_status bf_autotune(const bf_plan *plan, int height, int width, voi
     std::vector<TileConfig> ranked = tile_candidates(plan->kp, height, width, plan->desc.precision, 100000), cands;
     std::map<std::pair<int, int>, int> per_family;
     for (const auto &c : ranked)
-        if (per_family[{c.ring * 4 + c.depth, c.nk}]++ < 4) cands.push_back(c);
+        if (per_family[{c.ring * 4 + c.depth + 16 * (c.cluster > 0), c.nk}]++ < 4) cands.push_back(c);
     bf_status st = BF_OK;
     float *in = nullptr, *out = nullptr, *scratch = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -161,14 +161,7 @@ extern "C" bf_status bf_autotune(const bf_plan *plan, int height, int width, voi
     if (st == BF_OK) {
         remember_tile(plan->kp, height, width, plan->desc.precision, best);
         if (info) {
-            info[0] = best.tw;
-            info[1] = best.th;
-            info[2] = best.threads;
-            info[3] = best.nk;
-            info[4] = best.groups;
-            info[5] = best.groups > 1 ? 2 : 1;
-            info[6] = (int)best.smem;
-            info[7] = (int)(scratch_bytes(best, height, width) >> 10);
+            fill_info(best, height, width, info);
         }
     }
     cudaStreamSynchronize(s);
@@ -179,4 +172,53 @@ extern "C" bf_status bf_autotune(const bf_plan *plan, int height, int width, voi
     cudaFree(scratch);
     cudaSetDevice(prev);
     return st;
+}
+
+namespace {
+
+// Selects the plan's device for a table look-up (the table is keyed per device);
+// host-only plans use whatever device is current.
+struct DeviceScope {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceScope(int device) {
+        if (device < 0) return;
+        if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(device) != cudaSuccess) {
+            cudaGetLastError();
+            ok = false;
+            prev = -1;
+        }
+    }
+    ~DeviceScope() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+extern "C" bf_status bf_launch_candidates(const bf_plan *plan, int height, int width, int max_n, int *infos,
+                                          int *n_out) {
+    if (!plan || height < 1 || width < 1 || max_n < 0 || !n_out || (max_n > 0 && !infos))
+        return fail(BF_ERR_INVALID_ARG, "bad launch-candidate arguments");
+    std::vector<TileConfig> c = tile_candidates(plan->kp, height, width, plan->desc.precision, max_n);
+    for (size_t i = 0; i < c.size(); ++i) fill_info(c[i], height, width, infos + 12 * i);
+    *n_out = (int)c.size();
+    return BF_OK;
+}
+
+extern "C" bf_status bf_set_launch(const bf_plan *plan, int height, int width, const int *info) {
+    if (!plan || height < 1 || width < 1 || !info) return fail(BF_ERR_INVALID_ARG, "bad set-launch arguments");
+    DeviceScope dev(plan->desc.device);
+    if (!dev.ok) return fail(BF_ERR_NO_DEVICE, "cannot select the plan's device");
+    for (const auto &c : tile_candidates(plan->kp, height, width, plan->desc.precision, 100000)) {
+        int got[12];
+        fill_info(c, height, width, got);
+        // the fields a caller chooses; the rest (threads, launches, bytes) follow from them
+        if (got[0] == info[0] && got[1] == info[1] && got[3] == info[3] && got[8] == info[8] && got[9] == info[9] &&
+            got[10] == info[10] && got[11] == info[11]) {
+            remember_tile(plan->kp, height, width, plan->desc.precision, c);
+            return BF_OK;
+        }
+    }
+    return fail(BF_ERR_INVALID_ARG, "not a launch geometry of this plan and image size (see bf_launch_candidates)");
 }

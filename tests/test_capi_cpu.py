@@ -103,7 +103,7 @@ def test_paper_five_terms_compile_to_two_nested_windows():
 @pytest.mark.parametrize("kw,status", [
     (dict(sigma_s=0.0), 1), (dict(sigma_r=-1.0), 1), (dict(ns_terms=0), 1), (dict(nr_terms=0), 1),
     (dict(i_lo=1.0, i_hi=1.0), 1), (dict(policy=bf.RANGE_PAPER_3D), 2), (dict(spatial=bf.KERNEL_EXPONENTIAL), 2),
-    (dict(spatial=7), 1), (dict(precision=9), 1), (dict(radius=-2), 1),
+    (dict(spatial=7), 1), (dict(precision=9), 1), (dict(radius=-2), 1), (dict(precision=1), 2), (dict(precision=2), 2),
 ])
 def test_plan_create_rejects(kw, status):
     with pytest.raises(bf.BFError) as ei:
@@ -161,3 +161,36 @@ def test_launch_info_and_autotune_without_gpu():
     with pytest.raises(bf.BFError) as ei:
         bf.bf_autotune(p, 64, 64)
     assert ei.value.status == 9
+
+
+def test_launch_candidates_and_pinning_host_only():
+    # host-only plan: the geometry table is keyed without a device
+    plan = bf.Plan(device=-1, sigma_s=32.0, sigma_r=0.3)
+    H, W = 1080, 1913
+    cands = bf.bf_launch_candidates(plan, H, W)
+    assert len(cands) > 10
+    assert set(cands[0]) == set(bf._binding.INFO_KEYS)
+    default = bf.bf_launch_info(plan, H, W)
+    assert default == next(c for c in cands if c["cluster"] == 0)  # the model never picks a cluster itself
+    cl = [c for c in cands if c["cluster"] > 0]
+    assert cl and all(c["cluster"] <= 8 and c["cluster"] * c["tw"] >= W and c["ncols"] == c["tw"] for c in cl)
+    halo = [c for c in cands if c["cluster"] == 0]
+    assert all(c["ncols"] >= c["tw"] + 2 * 96 for c in halo)       # R = 96 columns each side
+    assert {c["depth"] for c in halo} == {2, 3}
+    assert {c["ring"] for c in cands} == {0}      # a ring of 2R + 2 rows does not fit shared memory at R = 96
+    small = bf.bf_launch_candidates(bf.Plan(device=-1, sigma_s=8.0), H, W)
+    assert {c["ring"] for c in small} == {0, 1}
+    other = next(c for c in halo if (c["tw"], c["th"], c["ring"]) != (default["tw"], default["th"], default["ring"]))
+    try:
+        bf.bf_set_launch(plan, H, W, other)
+        got = bf.bf_launch_info(plan, H, W)
+        assert {k: got[k] for k in ("tw", "th", "nk", "ring", "depth", "cluster", "ncols")} == \
+               {k: other[k] for k in ("tw", "th", "nk", "ring", "depth", "cluster", "ncols")}
+        bad = dict(other, tw=other["tw"] + 3)
+        with pytest.raises(bf.BFError) as ei:
+            bf.bf_set_launch(plan, H, W, bad)
+        assert ei.value.status == 1
+    finally:
+        bf.bf_set_launch(plan, H, W, default)
+    assert bf.bf_launch_info(plan, H, W) == default
+    assert bf.bf_launch_candidates(plan, H, W, max_n=3).__len__() == 3
