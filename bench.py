@@ -263,7 +263,7 @@ def run_ours(args):
                    "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "single"},
         "psnr_db_vs_exact": [round(x, 2) for x in psnr], "min_psnr_db": round(min(psnr), 2) if psnr else None,
         "per_combo_ms": [round(x, 4) for x in lm.mean(0)],
-        "tiles": [[t["tw"], t["th"], t["threads"], t["nk"], t["groups"], t["ring"], t["depth"], t["cluster"]] for t in tiles],
+        "tiles": [[t["tw"], t["th"], t["threads"], t["nk"], t["groups"], t["ring"], t["depth"], t["ncols"]] for t in tiles],
         "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
                      "frac": round(achieved / alu_peak, 4), "traffic": None,
                      "note": "FP32 lane-ops/s of the fused kernel (algorithmic count) vs SMs x 128 x max SM clock"},

@@ -192,38 +192,35 @@ bf_status bf_filter_noalloc(const bf_plan *plan, const float *d_in, size_t in_pi
  * info[0] tile width, [1] tile height, [2] threads per CTA, [3] cosine terms per
  * CTA, [4] term groups (grid depth), [5] kernel launches, [6] shared memory
  * bytes per CTA, [7] scratch KiB, [8] 1 when the basis inputs are kept in a
- * shared-memory ring per column, [9] exchange buffer depth, [10] thread-block
- * cluster size (0: no cluster; tiles then re-read a halo of columns), [11]
- * columns per CTA (tile width plus halo).  info must hold 12 ints.  Host only; needs no
+ * shared-memory ring per column, [9] exchange buffer depth, [10] columns per
+ * CTA (tile width plus the halo of 2 x horizontal reach, in whole warps).
+ * info must hold 11 ints.  Host only; needs no
  * device for host-only plans (uses 152 SMs as the device size then).
  * Errors: BF_ERR_INVALID_ARG. */
 bf_status bf_launch_info(const bf_plan *plan, int height, int width, int *info);
 
 /* Autotuner: times candidate launch geometries (the cost model's best five of
  * each family: tile width, tile height, cosine terms per CTA, with or without
- * the shared-memory ring of basis inputs, exchange depth, cluster spanning the
- * image width) for this plan on a synthetic height x width
+ * the shared-memory ring of basis inputs, exchange depth) for this plan on a synthetic height x width
  * image and remembers the fastest for later bf_filter / bf_filter_batch calls
  * with the same kernel class, reach and image size on this device.  Allocates
  * and frees its own device buffers and synchronizes `stream`; do not call it
- * during stream capture.  info (12 ints, may be NULL) receives the chosen
+ * during stream capture.  info (11 ints, may be NULL) receives the chosen
  * geometry as in bf_launch_info.  BF_TUNE_CACHE=<file> persists results.
  * Errors: BF_ERR_INVALID_ARG, BF_ERR_NO_DEVICE, BF_ERR_OOM, BF_ERR_CUDA. */
 bf_status bf_autotune(const bf_plan *plan, int height, int width, void *stream, int *info);
 
 /* Launch geometries of this plan for a height x width image, best first by the
- * cost model: up to max_n records of 12 ints each (as in bf_launch_info) into
- * infos (caller-owned, 12 x max_n ints); *n_out receives how many were written.
- * Geometries with a thread-block cluster (info[10] > 0) fail with
- * BF_ERR_UNSUPPORTED at launch on a device that cannot co-schedule the cluster.
+ * cost model: up to max_n records of 11 ints each (as in bf_launch_info) into
+ * infos (caller-owned, 11 x max_n ints); *n_out receives how many were written.
  * Host only.
  * Errors: BF_ERR_INVALID_ARG. */
 bf_status bf_launch_candidates(const bf_plan *plan, int height, int width, int max_n, int *infos, int *n_out);
 
 /* Pins the launch geometry bf_filter / bf_filter_noalloc use for this plan's
  * kernel class on height x width images of the plan's device (as bf_autotune
- * does with the fastest one).  info (12 ints, caller-owned) must match one
- * record of bf_launch_candidates in fields 0, 1, 3, 8, 9, 10 and 11; the other
+ * does with the fastest one).  info (11 ints, caller-owned) must match one
+ * record of bf_launch_candidates in fields 0, 1, 3, 8, 9 and 10; the other
  * fields are ignored.  The geometry changes rounding order only: every one gives
  * the result within the same error bound.  BF_TUNE_CACHE=<file> persists it.
  * Errors: BF_ERR_INVALID_ARG (no such geometry), BF_ERR_NO_DEVICE. */

@@ -191,12 +191,11 @@ def bf_coeffs(plan: Plan) -> dict:
     }
 
 
-INFO_KEYS = ("tw", "th", "threads", "nk", "groups", "launches", "smem", "scratch_kib", "ring", "depth",
-             "cluster", "ncols")
+INFO_KEYS = ("tw", "th", "threads", "nk", "groups", "launches", "smem", "scratch_kib", "ring", "depth", "ncols")
 
 
 def bf_launch_info(plan: Plan, height: int, width: int) -> dict:
-    info = (C.c_int * 12)()
+    info = (C.c_int * len(INFO_KEYS))()
     _check(lib().bf_launch_info(plan.handle, height, width, info), "bf_launch_info")
     keys = INFO_KEYS
     return dict(zip(keys, list(info)))
@@ -204,21 +203,22 @@ def bf_launch_info(plan: Plan, height: int, width: int) -> dict:
 
 def bf_launch_candidates(plan: Plan, height: int, width: int, max_n: int = 4096) -> list:
     """Launch geometries for this plan and image size, best first by the cost model."""
-    buf = (C.c_int * (12 * max_n))()
+    buf = (C.c_int * (len(INFO_KEYS) * max_n))()
     n = C.c_int(0)
     _check(lib().bf_launch_candidates(plan.handle, height, width, max_n, buf, C.byref(n)), "bf_launch_candidates")
     vals = list(buf)
-    return [dict(zip(INFO_KEYS, vals[12 * k:12 * k + 12])) for k in range(n.value)]
+    n_keys = len(INFO_KEYS)
+    return [dict(zip(INFO_KEYS, vals[n_keys * k:n_keys * (k + 1)])) for k in range(n.value)]
 
 
 def bf_set_launch(plan: Plan, height: int, width: int, info: dict) -> None:
     """Pins one geometry of bf_launch_candidates for later filter calls."""
-    arr = (C.c_int * 12)(*[int(info[k]) for k in INFO_KEYS])
+    arr = (C.c_int * len(INFO_KEYS))(*[int(info[k]) for k in INFO_KEYS])
     _check(lib().bf_set_launch(plan.handle, height, width, arr), "bf_set_launch")
 
 
 def bf_autotune(plan: Plan, height: int, width: int, stream=None) -> dict:
-    info = (C.c_int * 12)()
+    info = (C.c_int * len(INFO_KEYS))()
     _check(lib().bf_autotune(plan.handle, height, width, _stream_handle(stream), info), "bf_autotune")
     keys = INFO_KEYS
     return dict(zip(keys, list(info)))

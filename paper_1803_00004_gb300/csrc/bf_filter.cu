@@ -91,18 +91,18 @@ const std::vector<KernelClass> &classes() {
     return c.v;
 }
 
-const void *find_kernel(int m, int nk, bool ring, bool cluster) {
+const void *find_kernel(int m, int nk, bool ring) {
     for (const auto &c : classes())
-        if (c.m == m && c.nk == nk) return c.fn[ring ? 1 : 0][cluster ? 1 : 0];
+        if (c.m == m && c.nk == nk) return c.fn[ring ? 1 : 0];
     return nullptr;
 }
 
 size_t smem_bytes(int m, int nk, int ncols, int tw, int depth = 2) {
-    return sizeof(float) * ((size_t)depth * (m * nk * 4 + 1) * (ncols + 2) + (size_t)depth * nk * 2 * tw);
+    return sizeof(float) * ((size_t)depth * (m * nk * 4 + 2) * (ncols + 2) + (size_t)depth * nk * 2 * tw);
 }
 
 size_t ring_bytes(const FilterParams &p, int ncols) {
-    return sizeof(float) * 5 * (size_t)(p.vhi - p.vlo + 2) * ncols;
+    return sizeof(float) * 6 * (size_t)(p.vhi - p.vlo + 2) * ncols;
 }
 
 int device_sms() {
@@ -211,48 +211,6 @@ std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int w
                     tc.groups = groups;
                     tc.ring = ring;
                     tc.depth = depth;
-                    tc.cluster = 0;
-                    tc.smem = smem;
-                    all.push_back({cost, tc});
-                    if (the >= height) break;
-                }
-            }
-        }
-    }
-    // cluster family: CTAs of one cluster tile the whole image width, no halo columns
-    for (const auto &cls : classes()) {
-        if (cls.m != p.m) continue;
-        const int groups = (p.nr + cls.nk - 1) / cls.nk;
-        for (int tw = 64; tw + kScanThreads <= 512; tw += 32) {
-            const int cs = (width + tw - 1) / tw;
-            if (cs > 8 || tw < p.rx) continue;
-            if (cs > 1 && (cs - 1) * tw >= width) continue;
-            for (int ring = 0; ring <= 1; ++ring) {
-                if (ring && !(p.vlo <= 0 && p.vhi >= 0)) continue;
-                const int nrow = p.m * cls.nk * 4;
-                const size_t smem = smem_bytes(p.m, cls.nk, tw, tw, 2) + (ring ? ring_bytes(p, tw) : 0) +
-                                    sizeof(float) * (size_t)(nrow + 1) * tw;
-                if (smem > 227 * 1024) continue;
-                const double edge = ring ? 60.0 + 12.0 * (2 * p.m + 1) : 60.0 * (2 * p.m + 1);
-                for (int th : {16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 1024}) {
-                    const int the = std::min(th, std::max(height, 1));
-                    const long ctas = (long)cs * ((height + the - 1) / the) * groups;
-                    // clusters of cs CTAs, one CTA per SM: assume 7/8 of the SMs usable
-                    const double slots = std::max(1.0, std::floor(sms * 0.875 / cs)) * cs;
-                    const double per_cta = (double)tw * (the + 0.3 * vspan) * (edge + 40.0 * cls.nk * p.m) +
-                                           2000.0 * tw * the / 32.0;
-                    const double waves = std::ceil((double)ctas / slots);
-                    const double cost = waves * per_cta + (groups > 1 ? 16.0 * groups * (double)height * width : 0.0);
-                    TileConfig tc;
-                    tc.tw = tw;
-                    tc.th = the;
-                    tc.ncols = tw;
-                    tc.threads = tw + kScanThreads;
-                    tc.nk = cls.nk;
-                    tc.groups = groups;
-                    tc.ring = ring;
-                    tc.depth = 2;
-                    tc.cluster = cs;
                     tc.smem = smem;
                     all.push_back({cost, tc});
                     if (the >= height) break;
@@ -266,12 +224,10 @@ std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int w
     return out;
 }
 
-// The model's pick among geometries that always launch (cluster geometries are used
-// only after the autotuner has run them on this device).
+// The model's pick.
 TileConfig model_tile(const FilterParams &p, int height, int width, int precision) {
-    for (const auto &c : tile_candidates(p, height, width, precision, 100000))
-        if (c.cluster == 0) return c;
-    return TileConfig{};
+    const auto c = tile_candidates(p, height, width, precision, 1);
+    return c.empty() ? TileConfig{} : c[0];
 }
 
 int device_sm_count() { return device_sms(); }
@@ -333,8 +289,7 @@ void fill_info(const TileConfig &tc, int height, int width, int *info) {
     info[7] = (int)(scratch_bytes(tc, height, width) >> 10);
     info[8] = tc.ring ? 1 : 0;
     info[9] = tc.depth;
-    info[10] = tc.cluster;
-    info[11] = tc.ncols;
+    info[10] = tc.ncols;
 }
 
 size_t scratch_bytes(const TileConfig &tc, int height, int width) {
@@ -347,7 +302,7 @@ bf_status launch_filter(const FilterParams &p, int precision, int kahan, const T
     (void)precision;
     (void)kahan;
     if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");
-    const void *fn = find_kernel(p.m, tc.nk, tc.ring != 0, tc.cluster > 0);
+    const void *fn = find_kernel(p.m, tc.nk, tc.ring != 0);
     if (!fn || tc.ncols <= 0) return fail(BF_ERR_UNSUPPORTED, "no kernel class for this plan and image");
     if (tc.threads > 512) return fail(BF_ERR_UNSUPPORTED, "horizontal reach too large for one CTA");
     if (tc.smem > 227 * 1024) return fail(BF_ERR_UNSUPPORTED, "tile needs more than 227 KB of shared memory");
@@ -361,30 +316,7 @@ bf_status launch_filter(const FilterParams &p, int precision, int kahan, const T
     FilterParams pp = p;
     void *args[] = {(void *)&in, (void *)&in_pitch, (void *)&out, (void *)&out_pitch, (void *)&part, (void *)&H,
                     (void *)&W, (void *)&tw, (void *)&th, (void *)&ncols, (void *)&depth, (void *)&pp};
-    if (tc.cluster > 0) {
-        if (grid.x != (unsigned)tc.cluster) return fail(BF_ERR_UNSUPPORTED, "cluster must span the image width");
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = grid;
-        cfg.blockDim = dim3(tc.threads);
-        cfg.dynamicSmemBytes = tc.smem;
-        cfg.stream = (cudaStream_t)stream;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = tc.cluster;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        int active = 0;
-        e = cudaOccupancyMaxActiveClusters(&active, fn, &cfg);
-        if (e != cudaSuccess || active < 1) {
-            cudaGetLastError();
-            return fail(BF_ERR_UNSUPPORTED, "the device cannot co-schedule a cluster of this geometry");
-        }
-        e = cudaLaunchKernelExC(&cfg, fn, args);
-    } else {
-        e = cudaLaunchKernel(fn, grid, dim3(tc.threads), args, tc.smem, (cudaStream_t)stream);
-    }
+    e = cudaLaunchKernel(fn, grid, dim3(tc.threads), args, tc.smem, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "filter launch");
     if (tc.groups > 1) {
         if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");

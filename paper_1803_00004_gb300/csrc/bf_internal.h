@@ -51,7 +51,6 @@ struct TileConfig {
     int groups;    // term groups (grid.z); > 1 writes partial planes + finalize
     int ring;      // 1: per-column ring of basis inputs in shared memory
     int depth;     // exchange buffers: 2 (two barriers per row) or 3 (one barrier per row)
-    int cluster;   // > 0: CTAs per thread-block cluster spanning the image width (no halo columns)
     size_t smem;   // dynamic shared memory bytes
 };
 
@@ -81,7 +80,8 @@ bool kernel_class_supported(int m);
 // Ranked launch geometries from the cost model, the model's pick, and the
 // geometry bf_filter uses (an autotuned one when bf_autotune measured this
 // kernel class, reach and image size on this device, else the model's pick).
-// Writes the 12-int geometry record of bf_launch_info / bf_autotune.
+// Writes the geometry record (kInfoInts ints) of bf_launch_info / bf_autotune.
+constexpr int kInfoInts = 11;
 void fill_info(const TileConfig &tc, int height, int width, int *info);
 
 std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int width, int precision, int max_n);

@@ -3,7 +3,6 @@
 // that they compile in parallel.  See bf_filter.cu for the algorithm.
 #pragma once
 
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "bf_internal.h"
@@ -55,14 +54,12 @@ __device__ __forceinline__ int pos_mod(int a, int d) {
     return r < 0 ? r + d : r;
 }
 
-__device__ __forceinline__ void ring_put(float *ring, int D, int ncols, int row, int tid, float v, float c1, float s1,
-                                         float c0, float s0) {
-    float *r = ring + (size_t)(pos_mod(row, D) * 5) * ncols + tid;
-    r[0] = v;
-    r[ncols] = c1;
-    r[2 * ncols] = s1;
-    r[3 * ncols] = c0;
-    r[4 * ncols] = s0;
+// Ring slot of row y + off given ys = y mod D and off in [-D, D].
+__device__ __forceinline__ int ring_slot(int ys, int off, int D) {
+    int s = ys + off;
+    s += s < 0 ? D : 0;
+    s -= s >= D ? D : 0;
+    return s;
 }
 
 // Compensated (Kahan) accumulation s += x with running error term c.
@@ -79,50 +76,45 @@ __device__ __forceinline__ void sum_add(float &s, float &c, int compensated, flo
     else s += x;
 }
 
-// Advances (c, s) = (cos, sin)(pi k t) by `steps` multiples of the base rotation.
-__device__ __forceinline__ void rotate(float &c, float &s, float c1, float s1, int steps) {
-    if (steps == 1) {  // consecutive terms (the usual case): no loop
-        const float cn = fmaf(c, c1, -s * s1);
-        s = fmaf(s, c1, c * s1);
-        c = cn;
-        return;
-    }
-    for (int n = 0; n < steps; ++n) {
-        const float cn = fmaf(c, c1, -s * s1);
-        const float sn = fmaf(s, c1, c * s1);
-        c = cn;
-        s = sn;
-    }
+// (c, s) = (cos, sin)(pi k t) advanced by one multiple of the base rotation (c1, s1) = (cos, sin)(pi t).
+__device__ __forceinline__ void rot1(float &c, float &s, float c1, float s1) {
+    const float cn = fmaf(c, c1, -s * s1);
+    s = fmaf(s, c1, c * s1);
+    c = cn;
+}
+
+// The same by `steps` multiples (terms that are not consecutive).
+__device__ __forceinline__ void rotn(float &c, float &s, float c1, float s1, int steps) {
+    for (int n = 0; n < steps; ++n) rot1(c, s, c1, s1);
 }
 
 // One tile: output columns [x0, x0 + tw) x rows [y0, y0 + th) of one image,
 // cosine terms [g NK, g NK + NK) of p.  All threads of the CTA call it; it
 // ends on a barrier, so the shared memory can be reused right after.  `grouped`:
 // store partial numerator / denominator planes (part) instead of dividing.
-template <int NK, int M, bool RING, bool CL>
+template <int NK, int M, bool RING>
 __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__restrict__ in, size_t in_pitch,
                                           float *__restrict__ out, size_t out_pitch, float *__restrict__ part, int H,
                                           int W, int x0, int y0, int tw, int th, int ncols, int g, bool grouped,
                                           int depth, float *smem) {
     constexpr int NROW = M * NK * 4;  // exchange rows per image row: windows x terms x basis images
     constexpr int NE = 2 * M + 1;     // edges per step: M entering rows, M leaving rows, the output row
-    constexpr int NRP = NROW + 1;     // column pitch of the exchange, odd: a warp's lanes hit distinct banks
-    const int ZC = ncols + 2;         // exchange columns: tile column c at index c + 1; 0 and ncols + 1 stay 0
+    // Exchange [depth][ZC][NRP], column-major so that every row offset is a compile-time constant: column
+    // threads store a column, scan lanes walk along a row, output threads read a column.  NRP is even so
+    // that row pairs move as float2, and NRP / 2 is odd so that a warp's float2 accesses to consecutive
+    // columns, and its lanes' float accesses along a column, hit distinct banks.
+    constexpr int NRP = NROW + 2;
+    const int ZC = ncols + 2;  // tile column c at index c + 1; columns 0 and ncols + 1 stay 0
     // `depth` exchange buffers: 2 -> the output phase reads the row the scan finished in the same step (two
     // barriers per row); 3 -> it reads the row scanned one step earlier (one barrier per row)
-    // exchange [depth][ZC][NRP], column-major so that every row offset is a compile-time constant: column
-    // threads store a column, scan lanes walk along a row, output threads read a column
     float *zb0 = smem;
-    float *wb0 = smem + depth * ZC * NRP;  // [depth][NK][2][tw]: a_k cos, a_k sin at the output row
-    // RING: per column, the basis inputs of the last D rows (v, cos/sin(pi t), cos/sin(pi k0 t)), so each
-    // row's sincospi and load happen once instead of at every window edge: [D][5][ncols]
+    float2 *wb0 = reinterpret_cast<float2 *>(smem + depth * ZC * NRP);  // [depth][NK][tw]: a_k (cos, sin) at the output row
+    // RING: per column, the basis inputs of the last D rows, so each row's load and sincospi happen once
+    // instead of at every window edge: (v, cos pi t, sin pi t) in ringA, (cos, sin)(pi k0 t) in ringB
     const int D = p.vhi - p.vlo + 2;
-    float *ring = wb0 + depth * NK * 2 * tw;
-    // CL (thread-block cluster across the image width): no halo columns; the scan reads the
-    // neighbouring CTAs' exchange rows through distributed shared memory and writes its window
-    // sums to sb ([tw][NRP]) because the neighbours still read the raw rows
-    float *sb = ring + (RING ? 5 * (size_t)D * ncols : 0);
-    const int halo = CL ? 0 : p.rx;
+    float4 *ringA = reinterpret_cast<float4 *>(wb0 + depth * NK * tw);  // [D][ncols]
+    float2 *ringB = reinterpret_cast<float2 *>(ringA + (RING ? D * ncols : 0));  // [D][ncols]
+    const int halo = p.rx;
 
     const int tid = threadIdx.x;
     const bool is_col = tid < ncols;
@@ -148,6 +140,7 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
         kk[i] = p.k[ok ? j : p.nr - 1];
         aa[i] = ok ? p.a[j] : 0.f;
     }
+    const int k0 = kk[0];
 
     float V[NK][4][M];
 #pragma unroll
@@ -164,17 +157,22 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
             if (row < 0 || row >= H) continue;
             const float v = colv ? __ldg(in + (size_t)row * in_pitch + xcol) - p.i_lo : 0.f;
             float c1, s1, c, s;
-            basis_start(v, p.inv_p, p.inv_p_lo, kk[0], colv, c1, s1, c, s);
-            if (RING) ring_put(ring, D, ncols, row, tid, v, c1, s1, c, s);
-            int kc = kk[0];
+            basis_start(v, p.inv_p, p.inv_p_lo, k0, colv, c1, s1, c, s);
+            if (RING) {
+                const int sl = pos_mod(row, D) * ncols + tid;
+                ringA[sl] = make_float4(v, c1, s1, 0.f);
+                ringB[sl] = make_float2(c, s);
+            }
+            bool in_w[M];
+#pragma unroll
+            for (int r = 0; r < M; ++r) in_w[r] = off >= p.v0[r] && off <= p.v1[r];
 #pragma unroll
             for (int i = 0; i < NK; ++i) {
-                rotate(c, s, c1, s1, kk[i] - kc);
-                kc = kk[i];
+                if (i > 0) rotn(c, s, c1, s1, kk[i] - kk[i - 1]);
                 const float gi[4] = {c * v, s * v, c, s};
 #pragma unroll
                 for (int r = 0; r < M; ++r)
-                    if (off >= p.v0[r] && off <= p.v1[r]) {
+                    if (in_w[r]) {
 #pragma unroll
                         for (int t = 0; t < 4; ++t) V[i][t][r] += gi[t];
                     }
@@ -183,6 +181,10 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
     }
 
     const int lag = depth - 1;  // steps between a row's vertical pass and its output phase
+    int ys = RING ? pos_mod(y0, D) : 0;  // ring slot of row y (advanced each step)
+    const float2 *zq[M];                 // output thread: column of window q's sliding sum
+#pragma unroll
+    for (int q = 0; q < M; ++q) zq[q] = reinterpret_cast<const float2 *>(zb0 + (tid + p.u0[q] + 1) * NRP);
     for (int j = 0; j < nout + lag; ++j) {
         const int y = y0 + j;
         if (is_col && j < nout) {
@@ -192,8 +194,10 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
                 if (row < H) {
                     const float v = colv ? __ldg(in + (size_t)row * in_pitch + xcol) - p.i_lo : 0.f;
                     float a, b, c, s;
-                    basis_start(v, p.inv_p, p.inv_p_lo, kk[0], colv, a, b, c, s);
-                    ring_put(ring, D, ncols, row, tid, v, a, b, c, s);
+                    basis_start(v, p.inv_p, p.inv_p_lo, k0, colv, a, b, c, s);
+                    const int sl = ring_slot(ys, p.vhi, D) * ncols + tid;
+                    ringA[sl] = make_float4(v, a, b, 0.f);
+                    ringB[sl] = make_float2(c, s);
                 }
             }
 #pragma unroll
@@ -204,93 +208,65 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
                 const bool valid = colv && row >= 0 && row < H && (j > 0 || e == 2 * M);
                 if (RING) {
                     // slots of rows outside the image were never written: do not read them
-                    const float *rr = ring + (size_t)(pos_mod(row, D) * 5) * ncols + tid;
-                    Ie[e] = valid ? rr[0] : 0.f;
-                    c1[e] = valid ? rr[ncols] : 1.f;
-                    s1[e] = valid ? rr[2 * ncols] : 0.f;
-                    ce[e] = valid ? rr[3 * ncols] : 0.f;
-                    se[e] = valid ? rr[4 * ncols] : 0.f;
+                    const int sl = ring_slot(ys, off, D) * ncols + tid;
+                    const float4 A = valid ? ringA[sl] : make_float4(0.f, 1.f, 0.f, 0.f);
+                    Ie[e] = A.x;
+                    c1[e] = A.y;
+                    s1[e] = A.z;
+                    if (k0 == 0) {
+                        ce[e] = valid ? 1.f : 0.f;
+                        se[e] = 0.f;
+                    } else if (k0 == 1) {
+                        ce[e] = valid ? A.y : 0.f;
+                        se[e] = valid ? A.z : 0.f;
+                    } else {
+                        const float2 B = valid ? ringB[sl] : make_float2(0.f, 0.f);
+                        ce[e] = B.x;
+                        se[e] = B.y;
+                    }
                 } else {
                     const float v = valid ? __ldg(in + (size_t)row * in_pitch + xcol) - p.i_lo : 0.f;
                     Ie[e] = v;
-                    basis_start(v, p.inv_p, p.inv_p_lo, kk[0], valid, c1[e], s1[e], ce[e], se[e]);
+                    basis_start(v, p.inv_p, p.inv_p_lo, k0, valid, c1[e], s1[e], ce[e], se[e]);
                 }
             }
-            float *zb = zb0 + ((j % depth) * ZC + tid + 1) * NRP;
-            float *wb = wb0 + (j % depth) * NK * 2 * tw;
-            int kc = kk[0];
+            float2 *zb = reinterpret_cast<float2 *>(zb0 + ((j % depth) * ZC + tid + 1) * NRP);
+            float2 *wb = wb0 + (j % depth) * NK * tw;
 #pragma unroll
             for (int i = 0; i < NK; ++i) {
-                const int steps = kk[i] - kc;
-                kc = kk[i];
+                if (i > 0) {  // one uniform branch per term
+                    const int steps = kk[i] - kk[i - 1];
+                    if (steps == 1) {
 #pragma unroll
-                for (int e = 0; e < NE; ++e) rotate(ce[e], se[e], c1[e], s1[e], steps);
+                        for (int e = 0; e < NE; ++e) rot1(ce[e], se[e], c1[e], s1[e]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < NE; ++e) rotn(ce[e], se[e], c1[e], s1[e], steps);
+                    }
+                }
 #pragma unroll
                 for (int r = 0; r < M; ++r) {
                     const int ei = r, eo = M + r;
-                    V[i][0][r] += fmaf(ce[ei], Ie[ei], -ce[eo] * Ie[eo]);
-                    V[i][1][r] += fmaf(se[ei], Ie[ei], -se[eo] * Ie[eo]);
+                    V[i][0][r] = fmaf(-ce[eo], Ie[eo], fmaf(ce[ei], Ie[ei], V[i][0][r]));
+                    V[i][1][r] = fmaf(-se[eo], Ie[eo], fmaf(se[ei], Ie[ei], V[i][1][r]));
                     V[i][2][r] += ce[ei] - ce[eo];
                     V[i][3][r] += se[ei] - se[eo];
                 }
 #pragma unroll
-                for (int t = 0; t < 4; ++t)
+                for (int q = 0; q < M; ++q) {
+                    float z[4];
 #pragma unroll
-                    for (int q = 0; q < M; ++q) {
-                        float z = 0.f;
+                    for (int t = 0; t < 4; ++t) {
+                        z[t] = 0.f;
 #pragma unroll
-                        for (int r = 0; r < M; ++r) z = fmaf(p.C[r][q], V[i][t][r], z);
-                        zb[(q * NK + i) * 4 + t] = z;
+                        for (int r = 0; r < M; ++r) z[t] = fmaf(p.C[r][q], V[i][t][r], z[t]);
                     }
-                if (is_out) {
-                    wb[(i * 2 + 0) * tw + xl] = aa[i] * ce[2 * M];
-                    wb[(i * 2 + 1) * tw + xl] = aa[i] * se[2 * M];
+                    zb[(q * NK + i) * 2 + 0] = make_float2(z[0], z[1]);
+                    zb[(q * NK + i) * 2 + 1] = make_float2(z[2], z[3]);
                 }
+                if (is_out) wb[i * tw + xl] = make_float2(aa[i] * ce[2 * M], aa[i] * se[2 * M]);
             }
-        } else if (CL && !is_col && j >= 1 && j - 1 < nout) {
-            const int r = tid - ncols;
-            if (r < NROW) {
-                // sliding sum of window q over this CTA's columns; columns left of 0 / right of tw
-                // live in the neighbouring CTAs of the cluster (zero at the image border)
-                namespace cg = cooperative_groups;
-                cg::cluster_group cl = cg::this_cluster();
-                const int rank = (int)cl.block_rank(), csize = (int)cl.num_blocks();
-                const int q = r / (NK * 4);
-                const int u0 = p.u0[q], u1 = p.u1[q];
-                float *own = zb0 + ((j - 1) % depth) * ZC * NRP + r;
-                const float *lft = rank > 0 ? cl.map_shared_rank(own, rank - 1) : nullptr;
-                const float *rgt = rank + 1 < csize ? cl.map_shared_rank(own, rank + 1) : nullptr;
-                auto fetch = [&](int pos) -> float {
-                    if (pos < 0) return lft ? lft[(tw + pos + 1) * NRP] : 0.f;
-                    if (pos < tw) return own[(pos + 1) * NRP];
-                    return rgt ? rgt[(pos - tw + 1) * NRP] : 0.f;
-                };
-                float S = 0.f, comp = 0.f;
-                int b = u0;
-                for (; b + 7 <= u1; b += 8) {
-                    float v[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) v[u] = fetch(b + u);
-                    sum_add(S, comp, p.kahan, ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])));
-                }
-                float rest = 0.f;
-                for (; b <= u1; ++b) rest += fetch(b);
-                sum_add(S, comp, p.kahan, rest);
-                float *outr = sb + r;
-                for (int c0 = 0; c0 < tw; c0 += 8) {
-                    float d[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) d[u] = fetch(c0 + u + u1 + 1) - fetch(c0 + u + u0);
-                    float pd = -comp;
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        outr[(c0 + u) * NRP] = S + pd;
-                        pd += d[u];
-                    }
-                    sum_add(S, comp, p.kahan, pd + comp);
-                }
-            }
-        } else if (!CL && !is_col && j >= 1 && j - 1 < nout) {
+        } else if (!is_col && j >= 1 && j - 1 < nout) {
             const int r = tid - ncols;
             if (r < NROW) {
                 // sliding sum of window q over the row; S(c) replaces Z(c + u0), which the
@@ -327,25 +303,24 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
         if (depth == 2) __syncthreads();
         if (is_out && j >= lag) {
             const int yo = y - lag;
-            const float *zp = zb0 + ((j - lag) % depth) * ZC * NRP + tid * NRP;
-            const float *wp = wb0 + ((j - lag) % depth) * NK * 2 * tw + xl;
+            const int zo = ((j - lag) % depth) * ZC * (NRP / 2);
+            const float2 *wp = wb0 + ((j - lag) % depth) * NK * tw + xl;
             float num = 0.f, den = 0.f;
 #pragma unroll
             for (int i = 0; i < NK; ++i) {
-                float F[4];
+                float F[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    float f = 0.f;
-#pragma unroll
-                    for (int q = 0; q < M; ++q) {
-                        if (CL) f += sb[xl * NRP + (q * NK + i) * 4 + t];
-                        else f += zp[(p.u0[q] + 1) * NRP + (q * NK + i) * 4 + t];
-                    }
-                    F[t] = f;
+                for (int q = 0; q < M; ++q) {
+                    const float2 a = zq[q][zo + (q * NK + i) * 2 + 0];
+                    const float2 b = zq[q][zo + (q * NK + i) * 2 + 1];
+                    F[0] += a.x;
+                    F[1] += a.y;
+                    F[2] += b.x;
+                    F[3] += b.y;
                 }
-                const float wc = wp[(i * 2 + 0) * tw], ws = wp[(i * 2 + 1) * tw];
-                num = fmaf(wc, F[0], fmaf(ws, F[1], num));
-                den = fmaf(wc, F[2], fmaf(ws, F[3], den));
+                const float2 w = wp[i * tw];
+                num = fmaf(w.x, F[0], fmaf(w.y, F[1], num));
+                den = fmaf(w.x, F[2], fmaf(w.y, F[3], den));
             }
             const int x = x0 + xl;
             if (grouped) {
@@ -358,23 +333,18 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
                 out[(size_t)yo * out_pitch + x] = (den > p.den_eps) ? num / den + p.i_lo : ix;
             }
         }
-        if (CL) {
-            // neighbours must have read this step's rows before they are overwritten, and must see the
-            // next rows before scanning them
-            cooperative_groups::this_cluster().sync();
-        } else {
-            __syncthreads();
-        }
+        if (RING) ys = ys + 1 == D ? 0 : ys + 1;
+        __syncthreads();
     }
 }
 
-template <int NK, int M, bool RING, bool CL>
+template <int NK, int M, bool RING>
 __global__ void __launch_bounds__(512, 1)
 bf_fused_kernel(const float *__restrict__ in, size_t in_pitch, float *__restrict__ out, size_t out_pitch,
                 float *__restrict__ part, int H, int W, int tw, int th, int ncols, int depth,
                 const __grid_constant__ FilterParams p) {
-    extern __shared__ float smem[];
-    tile_body<NK, M, RING, CL>(p, in, in_pitch, out, out_pitch, part, H, W, blockIdx.x * tw, blockIdx.y * th, tw, th, ncols,
+    extern __shared__ __align__(16) float smem[];
+    tile_body<NK, M, RING>(p, in, in_pitch, out, out_pitch, part, H, W, blockIdx.x * tw, blockIdx.y * th, tw, th, ncols,
                            blockIdx.z, gridDim.z > 1, depth, smem);
 }
 
@@ -386,7 +356,7 @@ template <int NK, int M>
 __global__ void __launch_bounds__(512, 1)
 bf_batch_kernel(const BatchImage *__restrict__ imgs, const FilterParams *__restrict__ params,
                 const WorkItem *__restrict__ items, int n_items, int *__restrict__ cursor, int ncols) {
-    extern __shared__ float smem[];
+    extern __shared__ __align__(16) float smem[];
     __shared__ FilterParams sp;
     __shared__ int s_item;
     for (int iter = 0; iter < n_items; ++iter) {
@@ -400,7 +370,7 @@ bf_batch_kernel(const BatchImage *__restrict__ imgs, const FilterParams *__restr
         int *dst = reinterpret_cast<int *>(&sp);
         for (int i = threadIdx.x; i < (int)(sizeof(FilterParams) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
         __syncthreads();
-        tile_body<NK, M, false, false>(sp, im.in, im.in_pitch, im.out, im.out_pitch, im.part, im.H, im.W, w.x0, w.y0, w.tw,
+        tile_body<NK, M, false>(sp, im.in, im.in_pitch, im.out, im.out_pitch, im.part, im.H, im.W, w.x0, w.y0, w.tw,
                                 w.th, ncols, w.g, im.groups > 1, 2, smem);
     }
 }
@@ -412,15 +382,12 @@ bf_batch_kernel(const BatchImage *__restrict__ imgs, const FilterParams *__restr
 // no class spills registers).
 struct KernelClass {
     int m, nk;
-    const void *fn[2][2];  // [ring][cluster] tile kernels
+    const void *fn[2];  // tile kernels without / with the basis ring
     const void *batch_fn;
 };
 
-#define BF_CLASS(M, NK)                                                                                    \
-    {M,                                                                                                    \
-     NK,                                                                                                   \
-     {{(const void *)bf_fused_kernel<NK, M, false, false>, (const void *)bf_fused_kernel<NK, M, false, true>}, \
-      {(const void *)bf_fused_kernel<NK, M, true, false>, (const void *)bf_fused_kernel<NK, M, true, true>}},   \
+#define BF_CLASS(M, NK)                                                                                 \
+    {M, NK, {(const void *)bf_fused_kernel<NK, M, false>, (const void *)bf_fused_kernel<NK, M, true>},  \
      (const void *)bf_batch_kernel<NK, M>}
 
 // Per-TU class tables (kernels_m*.cu).

@@ -45,9 +45,9 @@ void load_locked() {
     int k[9];
     TileConfig tc;
     unsigned long smem;
-    while (std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %lu", &k[0], &k[1], &k[2], &k[3], &k[4],
+    while (std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %lu", &k[0], &k[1], &k[2], &k[3], &k[4],
                        &k[5], &k[6], &k[7], &k[8], &tc.tw, &tc.th, &tc.ncols, &tc.threads, &tc.nk, &tc.groups,
-                       &tc.ring, &tc.depth, &tc.cluster, &smem) == 19) {
+                       &tc.ring, &tc.depth, &smem) == 18) {
         tc.smem = smem;
         g_table[Key{k[0], k[1], k[2], k[3], k[4], k[5], k[6], k[7], k[8]}] = tc;
     }
@@ -62,7 +62,7 @@ void save_locked(const Key &key, const TileConfig &tc) {
     std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %lu\n", std::get<0>(key), std::get<1>(key),
                  std::get<2>(key), std::get<3>(key), std::get<4>(key), std::get<5>(key), std::get<6>(key),
                  std::get<7>(key), std::get<8>(key), tc.tw, tc.th, tc.ncols, tc.threads, tc.nk, tc.groups, tc.ring,
-                 tc.depth, tc.cluster, (unsigned long)tc.smem);
+                 tc.depth, (unsigned long)tc.smem);
     std::fclose(f);
 }
 
@@ -114,7 +114,7 @@ extern "C" bf_status bf_autotune(const bf_plan *plan, int height, int width, voi
     std::vector<TileConfig> ranked = tile_candidates(plan->kp, height, width, plan->desc.precision, 100000), cands;
     std::map<std::pair<int, int>, int> per_family;
     for (const auto &c : ranked)
-        if (per_family[{c.ring * 4 + c.depth + 16 * (c.cluster > 0), c.nk}]++ < 4) cands.push_back(c);
+        if (per_family[{c.ring * 4 + c.depth, c.nk}]++ < 4) cands.push_back(c);
     bf_status st = BF_OK;
     float *in = nullptr, *out = nullptr, *scratch = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -201,7 +201,7 @@ extern "C" bf_status bf_launch_candidates(const bf_plan *plan, int height, int w
     if (!plan || height < 1 || width < 1 || max_n < 0 || !n_out || (max_n > 0 && !infos))
         return fail(BF_ERR_INVALID_ARG, "bad launch-candidate arguments");
     std::vector<TileConfig> c = tile_candidates(plan->kp, height, width, plan->desc.precision, max_n);
-    for (size_t i = 0; i < c.size(); ++i) fill_info(c[i], height, width, infos + 12 * i);
+    for (size_t i = 0; i < c.size(); ++i) fill_info(c[i], height, width, infos + kInfoInts * i);
     *n_out = (int)c.size();
     return BF_OK;
 }
@@ -211,11 +211,11 @@ extern "C" bf_status bf_set_launch(const bf_plan *plan, int height, int width, c
     DeviceScope dev(plan->desc.device);
     if (!dev.ok) return fail(BF_ERR_NO_DEVICE, "cannot select the plan's device");
     for (const auto &c : tile_candidates(plan->kp, height, width, plan->desc.precision, 100000)) {
-        int got[12];
+        int got[kInfoInts];
         fill_info(c, height, width, got);
         // the fields a caller chooses; the rest (threads, launches, bytes) follow from them
         if (got[0] == info[0] && got[1] == info[1] && got[3] == info[3] && got[8] == info[8] && got[9] == info[9] &&
-            got[10] == info[10] && got[11] == info[11]) {
+            got[10] == info[10]) {
             remember_tile(plan->kp, height, width, plan->desc.precision, c);
             return BF_OK;
         }

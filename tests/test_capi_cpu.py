@@ -171,21 +171,20 @@ def test_launch_candidates_and_pinning_host_only():
     assert len(cands) > 10
     assert set(cands[0]) == set(bf._binding.INFO_KEYS)
     default = bf.bf_launch_info(plan, H, W)
-    assert default == next(c for c in cands if c["cluster"] == 0)  # the model never picks a cluster itself
-    cl = [c for c in cands if c["cluster"] > 0]
-    assert cl and all(c["cluster"] <= 8 and c["cluster"] * c["tw"] >= W and c["ncols"] == c["tw"] for c in cl)
-    halo = [c for c in cands if c["cluster"] == 0]
-    assert all(c["ncols"] >= c["tw"] + 2 * 96 for c in halo)       # R = 96 columns each side
-    assert {c["depth"] for c in halo} == {2, 3}
+    assert default == cands[0]                                   # the cost model's first choice
+    assert all(c["ncols"] >= c["tw"] + 2 * 96 and c["ncols"] % 32 == 0 for c in cands)  # R = 96 each side
+    assert all(c["threads"] == c["ncols"] + 64 and c["threads"] <= 512 for c in cands)
+    assert {c["depth"] for c in cands} == {2, 3}
     assert {c["ring"] for c in cands} == {0}      # a ring of 2R + 2 rows does not fit shared memory at R = 96
     small = bf.bf_launch_candidates(bf.Plan(device=-1, sigma_s=8.0), H, W)
     assert {c["ring"] for c in small} == {0, 1}
-    other = next(c for c in halo if (c["tw"], c["th"], c["ring"]) != (default["tw"], default["th"], default["ring"]))
+    assert all(c["smem"] <= 227 * 1024 for c in cands + small)
+    other = next(c for c in cands if (c["tw"], c["th"], c["ring"]) != (default["tw"], default["th"], default["ring"]))
+    keys = ("tw", "th", "nk", "ring", "depth", "ncols")
     try:
         bf.bf_set_launch(plan, H, W, other)
         got = bf.bf_launch_info(plan, H, W)
-        assert {k: got[k] for k in ("tw", "th", "nk", "ring", "depth", "cluster", "ncols")} == \
-               {k: other[k] for k in ("tw", "th", "nk", "ring", "depth", "cluster", "ncols")}
+        assert {k: got[k] for k in keys} == {k: other[k] for k in keys}
         bad = dict(other, tw=other["tw"] + 3)
         with pytest.raises(bf.BFError) as ei:
             bf.bf_set_launch(plan, H, W, bad)
@@ -193,4 +192,4 @@ def test_launch_candidates_and_pinning_host_only():
     finally:
         bf.bf_set_launch(plan, H, W, default)
     assert bf.bf_launch_info(plan, H, W) == default
-    assert bf.bf_launch_candidates(plan, H, W, max_n=3).__len__() == 3
+    assert len(bf.bf_launch_candidates(plan, H, W, max_n=3)) == 3
