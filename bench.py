@@ -37,6 +37,12 @@ METRIC = "Mpixel/s at >=40 dB vs exact BF (1920x1080, 9 sigma combos)"
 WORKLOAD = "1920x1080 shapes+noise(0.03), Gaussian/Gaussian, sigma_s in {2,8,32} x sigma_r in {0.05,0.1,0.3}, N_r=8, N_s=5"
 
 
+# DRAM bytes (read + write) per launch of the fused kernel, from the ncu capture of this kernel version at 1920x1080
+# (sigma_s = 2: 8.364 MB, sigma_s = 32: 8.382 MB, writes 0: the output stays in L2 during the kernel).
+# Reset to None whenever the kernel changes until it is captured again.
+TRAFFIC_BYTES_PER_LAUNCH = 8.37e6
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -249,10 +255,12 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = run_e2e(args, bf, plans, img, dev, stream)
 
-    batched = serving = None
+    batched = serving = nr_sweep = large = None
     if not args.no_extras and world == 1:
         batched = run_batched(bf, dev)
         serving = run_serving(bf, dev)
+        nr_sweep = run_nr_sweep(bf, dev, src, flush)
+        large = run_large(bf, dev, flush)
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
@@ -265,12 +273,12 @@ def run_ours(args):
         "per_combo_ms": [round(x, 4) for x in lm.mean(0)],
         "tiles": [[t["tw"], t["th"], t["threads"], t["nk"], t["groups"], t["ring"], t["depth"], t["ncols"]] for t in tiles],
         "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
-                     "frac": round(achieved / alu_peak, 4), "traffic": None,
+                     "frac": round(achieved / alu_peak, 4), "traffic": TRAFFIC_BYTES_PER_LAUNCH,
                      "note": "FP32 lane-ops/s of the fused kernel (algorithmic count) vs SMs x 128 x max SM clock"},
         "hbm": {"achieved_gbs": round(hbm_gbs, 1), "peak_gbs": hbm_peak, "frac": round(hbm_gbs / hbm_peak, 5),
                 "bytes_per_px": 8},
         "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
-        "batched": batched, "serving": serving,
+        "batched": batched, "serving": serving, "nr_sweep": nr_sweep, "large_images": large,
         "e2e": e2e,
     }
     if rank == 0:
@@ -310,6 +318,66 @@ def run_e2e(args, bf, plans, img, dev, stream):
     value = len(plans) * H * W * args.steps / (ms * 1e-3) / 1e6
     return {"value": round(value, 3), "unit": "Mpixel/s", "h2d_bytes_per_step": 4 * H * W,
             "d2h_bytes_per_step": 4 * H * W * len(plans)}
+
+
+def timed_launches(bf, plan, src, out, flush, reps):
+    """Mean device time (ms) of bf_filter, events around each launch, L2 flushed before each."""
+    import torch
+    for _ in range(2):
+        bf.bf_filter(plan, src, out)
+    ms = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        bf.bf_filter(plan, src, out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return float(np.mean(ms))
+
+
+def run_nr_sweep(bf, dev, src, flush, reps=5):
+    """Mpixel/s on the 1920x1080 image for N_r in 4..32 at each sigma_s (sigma_r = 0.1), autotuned:
+    the per-pixel cost against sigma_s at fixed N_r."""
+    import torch
+    out = torch.empty_like(src)
+    res = {}
+    for nr in (4, 8, 12, 16, 24, 32):
+        row = {}
+        for ss in SIGMA_S:
+            p = bf.Plan(sigma_s=ss, sigma_r=0.1, nr_terms=nr, ns_terms=NS, device=dev.index)
+            bf.bf_autotune(p, H, W)
+            row[str(int(ss))] = round(H * W / (timed_launches(bf, p, src, out, flush, reps) * 1e-3) / 1e6, 1)
+        res[str(nr)] = row
+    return {"sigma_r": 0.1, "mpix_s_by_nr_then_sigma_s": res}
+
+
+def run_large(bf, dev, flush, reps=3):
+    """3840x2160 and 8192x8192 inputs (generator with objects scaled x2 / x4), sigma_s = 16, sigma_r = 0.1,
+    N_r = 16, fp32 path, autotuned: Mpixel/s, and max-abs / PSNR against the GPU exact filter."""
+    import torch
+    from paper_1803_00004_gb300 import synth
+    res = []
+    for h, w, scale in ((2160, 3840, 2.0), (8192, 8192, 4.0)):
+        img = synth.shapes(h, w, seed=0, scale=scale)
+        src = torch.from_numpy(img).to(dev)
+        out = torch.empty_like(src)
+        p = bf.Plan(sigma_s=16.0, sigma_r=0.1, nr_terms=16, ns_terms=NS, device=dev.index)
+        bf.bf_autotune(p, h, w)
+        ms = timed_launches(bf, p, src, out, flush, reps)
+        ex = torch.empty_like(src)
+        bf.bf_exact(src, ex, sigma_s=16.0, sigma_r=0.1)
+        torch.cuda.synchronize()
+        d = (out.double() - ex.double())
+        mse = torch.mean(d * d).item()
+        res.append({"height": h, "width": w, "ms": round(ms, 3), "mpix_s": round(h * w / (ms * 1e-3) / 1e6, 1),
+                    "max_abs_vs_exact": round(torch.max(torch.abs(d)).item(), 5),
+                    "psnr_db_vs_exact": round(10 * np.log10(1.0 / mse), 2) if mse > 0 else None})
+        del src, out, ex, d
+        torch.cuda.empty_cache()
+    return {"sigma_s": 16.0, "sigma_r": 0.1, "nr_terms": 16, "dtype": "f32", "images": res}
 
 
 def mixed_requests(n, lo, hi, seed):

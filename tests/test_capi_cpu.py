@@ -193,3 +193,34 @@ def test_launch_candidates_and_pinning_host_only():
         bf.bf_set_launch(plan, H, W, default)
     assert bf.bf_launch_info(plan, H, W) == default
     assert len(bf.bf_launch_candidates(plan, H, W, max_n=3)) == 3
+
+
+def test_tune_cache_file_round_trip(tmp_path):
+    # a pinned geometry is appended to BF_TUNE_CACHE and read back by a fresh process
+    cache = tmp_path / "tune.txt"
+    code = r'''
+import json, sys
+import paper_1803_00004_gb300 as bf
+mode = sys.argv[1]
+out = {}
+for ss in (2.0, 8.0, 32.0):
+    plan = bf.Plan(device=-1, sigma_s=ss)
+    if mode == "write":
+        cands = bf.bf_launch_candidates(plan, 720, 1280)
+        bf.bf_set_launch(plan, 720, 1280, cands[3])
+    out[str(ss)] = bf.bf_launch_info(plan, 720, 1280)
+print(json.dumps(out))
+'''
+    import json
+    import subprocess
+    import sys
+    env = dict(os.environ, BF_TUNE_CACHE=str(cache), PYTHONPATH=ROOT)
+    w = subprocess.run([sys.executable, "-c", code, "write"], env=env, capture_output=True, text=True, check=True)
+    r = subprocess.run([sys.executable, "-c", code, "read"], env=env, capture_output=True, text=True, check=True)
+    written, read = json.loads(w.stdout), json.loads(r.stdout)
+    assert written == read
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 3 and all(len(x.split()) == 18 for x in lines)
+    fresh = json.loads(subprocess.run([sys.executable, "-c", code, "read"], env=dict(os.environ, PYTHONPATH=ROOT),
+                                      capture_output=True, text=True, check=True).stdout)
+    assert fresh != read                               # without the file: the cost model's choice

@@ -98,22 +98,41 @@ def test_pitched_buffers_and_offset_range():
     assert torch.isnan(out[:, 200:]).all()  # nothing written past the width
 
 
+def sample_points(H, W, n, seed):
+    rng = np.random.default_rng(seed)
+    edge = np.array([[0, 0], [H - 1, W - 1], [0, W - 1], [H - 1, 0], [H // 2, 0], [0, W // 2], [H - 1, W // 2 + 40],
+                     [H // 2 + 60, W - 1]])
+    return np.concatenate([np.stack([rng.integers(0, H, n), rng.integers(0, W, n)], 1), edge])
+
+
 def test_full_size_sampled_parity():
-    """1920x1080 (the benchmark workload) at each (sigma_s, sigma_r) of the sweep: sampled
-    pixels, including the image border rows/columns, against the oracle's direct evaluation."""
+    """1920x1080 (the benchmark workload) at each (sigma_s, sigma_r) of the sweep, in the autotuned
+    launch geometry the benchmark times: sampled pixels, including the image border rows/columns,
+    against the oracle's direct evaluation."""
     img = synth.shapes(1080, 1920, seed=0)
-    rng = np.random.default_rng(0)
-    pts = np.concatenate([
-        np.stack([rng.integers(0, 1080, 160), rng.integers(0, 1920, 160)], 1),
-        np.array([[0, 0], [1079, 1919], [0, 1919], [1079, 0], [540, 0], [0, 960], [1079, 1000], [600, 1919]]),
-    ])
+    pts = sample_points(1080, 1920, 160, 0)
     for ss in (2.0, 8.0, 32.0):
         for sr in (0.05, 0.1, 0.3):
             kw = dict(sigma_s=ss, sigma_r=sr, nr_terms=8, ns_terms=5)
+            bf.bf_autotune(bf.Plan(device=0, **kw), 1080, 1920)
             got = run(img, **kw)[pts[:, 0], pts[:, 1]]
             ref = O.approx_direct_at(img.astype(np.float64), odesc(**kw), pts, threads=THREADS)
             err = np.max(np.abs(got - ref))
             assert err < TOL, "sigma_s=%g sigma_r=%g: %.3g" % (ss, sr, err)
+
+
+@pytest.mark.parametrize("H,W,scale", [(2160, 3840, 2.0), (8192, 8192, 4.0)])
+def test_large_images_sampled_parity(H, W, scale):
+    """3840x2160 and 8192x8192, sigma_s = 16 (R = 48), sigma_r = 0.1, N_r = 16 (two term groups,
+    partial planes), autotuned: sampled pixels against the oracle's direct evaluation."""
+    img = synth.shapes(H, W, seed=0, scale=scale)
+    kw = dict(sigma_s=16.0, sigma_r=0.1, nr_terms=16, ns_terms=5)
+    bf.bf_autotune(bf.Plan(device=0, **kw), H, W)
+    pts = sample_points(H, W, 120, 1)
+    got = run(img, **kw)[pts[:, 0], pts[:, 1]]
+    ref = O.approx_direct_at(img.astype(np.float64), odesc(**kw), pts, threads=THREADS)
+    err = np.max(np.abs(got - ref))
+    assert err < TOL, "%dx%d: %.3g" % (W, H, err)
 
 
 def test_deterministic_and_stream():
