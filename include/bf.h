@@ -57,8 +57,9 @@ typedef enum {
 } bf_status;
 
 typedef enum {
-    BF_KERNEL_GAUSSIAN = 0,     /* exp(-t^2 / (2 sigma^2)) */
-    BF_KERNEL_EXPONENTIAL = 1,  /* exp(-|t| / sigma) (range kernel only) */
+    BF_KERNEL_GAUSSIAN = 0,     /* exp(-t^2 / (2 sigma^2)); spatial: exp(-|d|_2^2 / (2 sigma^2)) */
+    BF_KERNEL_EXPONENTIAL = 1,  /* exp(-|t| / sigma); spatial: exp(-|d|_2 / sigma), radial and
+                                   not separable (R <= 255) */
     BF_KERNEL_BOX = 2           /* 1 on [-sigma, sigma] (range) or on the whole window (spatial) */
 } bf_kernel;
 
@@ -91,7 +92,8 @@ typedef enum {
 
 /* Plan parameters (Sec. IV-A..C).  Fill with bf_plan_desc_default() first. */
 typedef struct {
-    int spatial;        /* bf_kernel: GAUSSIAN or BOX (separable on the square window) */
+    int spatial;        /* bf_kernel: GAUSSIAN, BOX (separable on the square window) or
+                           EXPONENTIAL (radial, not separable) */
     double sigma_s;     /* spatial bandwidth, pixels, > 0 */
     int radius;         /* window half-width R (square |y - x|_inf <= R); 0 -> round(3 sigma_s) */
     int ns_terms;       /* N_s: Haar terms kept (best N-term), >= 1 */
@@ -119,13 +121,18 @@ void bf_plan_desc_default(bf_plan_desc *desc);
 
 /* Builds a plan (Sec. IV-A..C; App. B): truncation points, range cosine
  * coefficients a_k on [-P, P] (Eqs. (14)-(15)), 2-D Haar coefficients of the
- * truncated spatial kernel (Eq. (22)), best N-term selection by |coefficient|,
+ * truncated spatial kernel (Eqs. (21)-(22): products of 1-D coefficients for
+ * the separable kernels; for the radial exponential kernel each 2-D integral
+ * over the Haar cells is computed whole, by tensor Gauss-Legendre quadrature
+ * with the cells at its cone point graded toward the origin), best N-term
+ * selection by |coefficient|,
  * and the signed-box representation of the selected Haar terms (App. A),
  * compiled into nested horizontal and vertical box windows for the kernel.
  * Host memory only; the coefficient tables travel to the device as kernel
  * parameters.  *out receives a plan the caller releases with bf_plan_destroy.
  * Errors: BF_ERR_INVALID_ARG (NULL, sigma <= 0, N < 1, i_hi <= i_lo, bad enum),
- * BF_ERR_UNSUPPORTED (BF_RANGE_PAPER_3D, exponential spatial kernel),
+ * BF_ERR_UNSUPPORTED (BF_RANGE_PAPER_3D; exponential spatial kernel with
+ * R > 255; a selection needing more than 6 box windows per axis),
  * BF_ERR_OOM, BF_ERR_NO_DEVICE (device >= 0 that does not exist). */
 bf_status bf_plan_create(const bf_plan_desc *desc, bf_plan **out);
 

@@ -14,6 +14,11 @@
  *   - 1-D Haar dictionary and coefficients: Eqs. (17)-(20), Gaussian integrals by
  *     erf differences;
  *   - 2-D separable Haar coefficients: Eq. (22) (product of 1-D factors);
+ *   - 2-D coefficients of the non-separable radial exponential kernel
+ *     exp(-|x|_2 / sigma) (Eqs. (21)-(22) without the product form): integrals
+ *     over rectangles, each split into signed triangles with a vertex at the
+ *     origin, integrated in polar form (closed form in r, Romberg in the
+ *     edge parameter);
  *   - best N-term selection by largest |coefficient|: Sec. III-A, Eq. (11);
  *     candidates limited to the first 20N range coefficients, App. B;
  *   - O1 exact bilateral filter, Eq. (1);
@@ -64,6 +69,8 @@
 #define ORC_PAPER_TRUNCATED 3 /* P = T_r exactly (the paper's own series, used for Table VII) */
 
 static const double ORC_PI = 3.14159265358979323846;
+
+int orc_max_threads(void);
 
 /* ------------------------------------------------------------------ */
 /* Kernel profiles                                                      */
@@ -240,6 +247,128 @@ int orc_haar1d(int kind, double sigma_s, double T, int J, double *c, int *lev, i
 }
 
 /* ------------------------------------------------------------------ */
+/* Non-separable spatial kernel: K(x, y) = exp(-sqrt(x^2 + y^2) / sigma)  */
+/* ------------------------------------------------------------------ */
+
+/* F(rho) / rho^2 with F(rho) = int_0^rho exp(-r / sigma) r dr = sigma^2 (1 - (1 + u) e^{-u}), u = rho / sigma.
+ * F(rho) / rho^2 = (1 - (1 + u) e^{-u}) / u^2 -> 1/2 as u -> 0; the series
+ * sum_{n >= 2} (-1)^n (n - 1) u^{n-2} / n! avoids the cancellation for small u. */
+static double exp_radial_F_over_rho2(double sigma, double rho)
+{
+    double u = rho / sigma;
+    if (u < 0.5) {
+        double s = 0.0, t = 0.5; /* t = u^{n-2} / n!, n = 2 */
+        for (int n = 2; n < 30; n++) {
+            s += ((n & 1) ? -1.0 : 1.0) * (n - 1) * t;
+            t *= u / (n + 1);
+        }
+        return s;
+    }
+    return (1.0 - (1.0 + u) * exp(-u)) / (u * u);
+}
+
+typedef struct { double sigma, ax, ay, dx, dy, cr; } tri_integrand;
+
+/* Integrand in the edge parameter s of the triangle (origin, A, B): with P(s) = A + s (B - A),
+ * polar coordinates give  int_tri f = int_0^1 F(|P(s)|) / |P(s)|^2 * (A x B) ds. */
+static double tri_f(const tri_integrand *q, double s)
+{
+    double px = q->ax + s * q->dx, py = q->ay + s * q->dy;
+    double rho = sqrt(px * px + py * py);
+    return exp_radial_F_over_rho2(q->sigma, rho) * q->cr;
+}
+
+static double romberg_tri(const tri_integrand *q, double a, double b)
+{
+    double R[22][22];
+    double h = b - a;
+    R[0][0] = 0.5 * h * (tri_f(q, a) + tri_f(q, b));
+    for (int n = 1; n < 22; n++) {
+        h *= 0.5;
+        double s = 0.0;
+        long m = 1L << (n - 1);
+        for (long i = 1; i <= m; i++) s += tri_f(q, a + (2 * i - 1) * h);
+        R[n][0] = 0.5 * R[n - 1][0] + h * s;
+        double f4 = 1.0;
+        for (int j = 1; j <= n; j++) {
+            f4 *= 4.0;
+            R[n][j] = R[n][j - 1] + (R[n][j - 1] - R[n - 1][j - 1]) / (f4 - 1.0);
+        }
+        if (n >= 4 && fabs(R[n][n] - R[n - 1][n - 1]) <= 1e-16 * fabs(b - a) * fabs(q->cr) + 1e-15 * fabs(R[n][n]))
+            return R[n][n];
+    }
+    return R[21][21];
+}
+
+/* Signed integral of the kernel over the triangle (origin, A, B): positive when A -> B turns
+ * counter-clockwise about the origin.  The edge is split at its point closest to the origin and
+ * into pieces, so Romberg sees a smooth integrand on each piece. */
+static double tri_exp(double sigma, double ax, double ay, double bx, double by)
+{
+    tri_integrand q = { sigma, ax, ay, bx - ax, by - ay, ax * by - ay * bx };
+    if (q.cr == 0.0) return 0.0; /* degenerate: the edge's line passes through the origin */
+    double len2 = q.dx * q.dx + q.dy * q.dy;
+    double sc = -(ax * q.dx + ay * q.dy) / len2;
+    double cuts[3] = { 0.0, 1.0, 1.0 };
+    int nc = 2;
+    if (sc > 0.0 && sc < 1.0) { cuts[1] = sc; cuts[2] = 1.0; nc = 3; }
+    const int pieces = 4;
+    double total = 0.0;
+    for (int c = 0; c + 1 < nc; c++) {
+        double a = cuts[c], b = cuts[c + 1];
+        for (int i = 0; i < pieces; i++)
+            total += romberg_tri(&q, a + (b - a) * i / pieces, i == pieces - 1 ? b : a + (b - a) * (i + 1) / pieces);
+    }
+    return total;
+}
+
+/* int_{x0}^{x1} int_{y0}^{y1} exp(-sqrt(x^2 + y^2) / sigma) dy dx: the rectangle is the signed sum of
+ * the triangles (origin, edge) over its boundary taken counter-clockwise. */
+double orc_rect_int_exp(double sigma, double x0, double x1, double y0, double y1)
+{
+    return tri_exp(sigma, x0, y0, x1, y0) + tri_exp(sigma, x1, y0, x1, y1) + tri_exp(sigma, x1, y1, x0, y1) +
+           tri_exp(sigma, x0, y1, x0, y0);
+}
+
+/* 2-D Haar coefficient (Eqs. (21)-(22) with the 2-D integral kept whole) of the pair of 1-D dictionary
+ * entries (i1 along x, i2 along y) for the radial exponential kernel:
+ *   c = (s1 / 2T)(s2 / 2T) sum over the +/- halves of sign x sign' x int_{half x half'} K,
+ * s = 1 for phi, 2^j for psi_{j,k}. */
+static double haar2d_exp(double sigma, double T, int i1, int i2)
+{
+    int j1, k1, j2, k2;
+    double lo1, mid1, hi1, lo2, mid2, hi2;
+    haar_index(i1, &j1, &k1);
+    haar_index(i2, &j2, &k2);
+    haar_support(j1, k1, T, &lo1, &mid1, &hi1);
+    haar_support(j2, k2, T, &lo2, &mid2, &hi2);
+    double xs[2][2] = { { lo1, mid1 }, { mid1, hi1 } }, ys[2][2] = { { lo2, mid2 }, { mid2, hi2 } };
+    int nx = j1 < 0 ? 1 : 2, ny = j2 < 0 ? 1 : 2;
+    if (j1 < 0) xs[0][1] = hi1;
+    if (j2 < 0) ys[0][1] = hi2;
+    double sum = 0.0;
+    for (int a = 0; a < nx; a++)
+        for (int b = 0; b < ny; b++) {
+            double sgn = (a == 0 ? 1.0 : -1.0) * (b == 0 ? 1.0 : -1.0);
+            sum += sgn * orc_rect_int_exp(sigma, xs[a][0], xs[a][1], ys[b][0], ys[b][1]);
+        }
+    double s1 = j1 < 0 ? 1.0 : ldexp(1.0, j1), s2 = j2 < 0 ? 1.0 : ldexp(1.0, j2);
+    return s1 * s2 * sum / (4.0 * T * T);
+}
+
+/* All 2-D coefficients c[i2 * n + i1], n = 2^{J+1}, of the radial exponential kernel. */
+int orc_haar2d_exp(double sigma_s, double T, int J, double *c, int nthreads)
+{
+    if (!(sigma_s > 0) || !(T > 0) || J < 0 || J > 12 || !c) return ORC_EINVAL;
+    int n = 1 << (J + 1);
+    (void)nthreads;
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads > 0 ? nthreads : 1)
+    for (int i2 = 0; i2 < n; i2++)
+        for (int i1 = 0; i1 < n; i1++) c[(size_t)i2 * n + i1] = haar2d_exp(sigma_s, T, i1, i2);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
 /* Best N-term selection, Sec. III-A                                    */
 /* ------------------------------------------------------------------ */
 
@@ -327,7 +456,7 @@ static int plan_build(orc_plan *p, int skind, double sigma_s, int radius, int ns
     memset(p, 0, sizeof(*p));
     if (!(sigma_s > 0) || !(sigma_r > 0) || ns_terms < 1 || nr_terms < 1 || nr_terms > ORC_MAX_NR) return ORC_EINVAL;
     if (ns_terms > ORC_MAX_NS) return ORC_ECAP;
-    if (skind != ORC_GAUSSIAN && skind != ORC_BOX) return ORC_EINVAL;
+    if (skind != ORC_GAUSSIAN && skind != ORC_BOX && skind != ORC_EXPONENTIAL) return ORC_EINVAL;
     p->R = radius > 0 ? radius : (int)lround(3.0 * sigma_s);
     if (radius < 0) return ORC_EINVAL;
     p->Ts = p->R + 0.5;
@@ -346,18 +475,25 @@ static int plan_build(orc_plan *p, int skind, double sigma_s, int radius, int ns
     p->nr = orc_select_range(a, ncand, nr_terms, p->ks, p->ak);
     free(a);
 
-    /* spatial: separable 2-D Haar coefficients c(t1,t2) = c1(t1) c1(t2) (Eq. (22)) */
+    /* spatial: 2-D Haar coefficients; separable kernels: c(t1,t2) = c1(t1) c1(t2) (Eq. (22));
+     * the radial exponential: each 2-D integral computed whole */
     int n = p->n1d;
     double *c1 = malloc(sizeof(double) * n);
     int *lv = malloc(sizeof(int) * n), *kv = malloc(sizeof(int) * n);
     cand2d *v = malloc(sizeof(cand2d) * (size_t)n * n);
-    if (!c1 || !lv || !kv || !v) { free(c1); free(lv); free(kv); free(v); return ORC_ECAP; }
-    orc_haar1d(skind, sigma_s, p->Ts, p->J, c1, lv, kv);
+    double *c2 = skind == ORC_EXPONENTIAL ? malloc(sizeof(double) * (size_t)n * n) : NULL;
+    if (!c1 || !lv || !kv || !v || (skind == ORC_EXPONENTIAL && !c2)) {
+        free(c1); free(lv); free(kv); free(v); free(c2);
+        return ORC_ECAP;
+    }
+    for (int i = 0; i < n; i++) haar_index(i, &lv[i], &kv[i]);
+    if (skind == ORC_EXPONENTIAL) orc_haar2d_exp(sigma_s, p->Ts, p->J, c2, orc_max_threads());
+    else orc_haar1d(skind, sigma_s, p->Ts, p->J, c1, lv, kv);
     size_t m = 0;
     for (int i1 = 0; i1 < n; i1++)
         for (int i2 = 0; i2 < n; i2++) {
             cand2d *e = &v[m++];
-            e->c = c1[i1] * c1[i2];
+            e->c = c2 ? c2[(size_t)i2 * n + i1] : c1[i1] * c1[i2];
             e->mag = fabs(e->c);
             e->t1 = i1; e->t2 = i2;
             int j1 = lv[i1], j2 = lv[i2];
@@ -372,7 +508,7 @@ static int plan_build(orc_plan *p, int skind, double sigma_s, int radius, int ns
         p->sc[i] = v[i].c;
     }
     p->tie_split = (p->ns < kept && v[p->ns].mag >= v[p->ns - 1].mag * (1.0 - 1e-12)) ? 1 : 0;
-    free(c1); free(lv); free(kv); free(v);
+    free(c1); free(lv); free(kv); free(v); free(c2);
 
     /* K~_s(dx, dy) at integer offsets, Eq. (30) evaluated directly */
     int w = 2 * p->R + 1;
@@ -427,6 +563,7 @@ int orc_plan_info(int skind, double sigma_s, int radius, int ns_terms,
 static double spatial_kernel2d(int kind, double sigma, int dx, int dy)
 {
     if (kind == ORC_BOX) return 1.0;
+    if (kind == ORC_EXPONENTIAL) return exp(-sqrt((double)(dx * dx + dy * dy)) / sigma);
     return exp(-(double)(dx * dx + dy * dy) / (2.0 * sigma * sigma));
 }
 

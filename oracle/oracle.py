@@ -67,6 +67,9 @@ def _load():
         lib.orc_approx_fast.argtypes = common + [pd]
         lib.orc_box_count.argtypes = [i, d, i, i, i, d, d, i, i, d]
         lib.orc_approx_direct_at.argtypes = [pd, i, i, i, d, i, i, i, d, d, i, i, d, pi, i, pd, i]
+        lib.orc_rect_int_exp.argtypes = [d, d, d, d, d]
+        lib.orc_rect_int_exp.restype = d
+        lib.orc_haar2d_exp.argtypes = [d, d, i, pd, i]
         _lib = lib
     return _lib
 
@@ -126,6 +129,24 @@ def haar1d(kind: int, sigma_s: float, T: float, J: int | None = None):
     if st:
         raise ValueError("orc_haar1d status %d" % st)
     return c, lev, kk
+
+
+def rect_int_exp(sigma: float, x0: float, x1: float, y0: float, y1: float) -> float:
+    """Integral of exp(-sqrt(x^2 + y^2) / sigma) over [x0, x1] x [y0, y1] (signed triangle fan)."""
+    return float(_load().orc_rect_int_exp(sigma, x0, x1, y0, y1))
+
+
+def haar2d_exp(sigma_s: float, T: float, J: int | None = None, threads: int = 1) -> np.ndarray:
+    """2-D Haar coefficients of the radial exponential kernel: c[i2, i1] (i1 along x, i2 along y),
+    indices in the 1-D dictionary order of haar1d."""
+    if J is None:
+        J = haar_levels(T)
+    n = 1 << (J + 1)
+    c = np.zeros((n, n))
+    st = _load().orc_haar2d_exp(sigma_s, T, J, _dp(c), threads)
+    if st:
+        raise ValueError("orc_haar2d_exp status %d" % st)
+    return c
 
 
 def haar_eval(lev: int, k: int, T: float, x: float) -> float:

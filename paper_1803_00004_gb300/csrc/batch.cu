@@ -91,12 +91,13 @@ bf_status build_batch(const bf_plan *const *plans, const bf_image *images, int n
             const bf_plan *p = plans[i];
             const bf_image &im = images[i];
             const FilterParams &kp = p->kp;
-            const int groups = (kp.nr + nk - 1) / nk;
+            const int groups = term_groups(kp, nk);
             int tw = ((ncols - 2 * kp.rx) / 8) * 8;
             tw = std::min(tw, ((im.width + 7) / 8) * 8);
             const int vspan = kp.vhi - kp.vlo + 1;
             const int th = std::min(im.height, std::max(48, vspan));
-            L.params[i] = kp;
+            if (!term_layout(kp, nk, L.params[i]))
+                return fail(BF_ERR_UNSUPPORTED, "the plan's terms need more than 128 slots at this class");
             BatchImage &b = L.imgs[i];
             b.in = im.d_in;
             b.out = im.d_out;

@@ -118,8 +118,9 @@ int device_sms() {
 }
 
 __global__ void bf_exact_kernel(const float *__restrict__ in, size_t in_pitch, float *__restrict__ out,
-                                size_t out_pitch, int H, int W, int spatial, float inv2ss, int R, int range,
+                                size_t out_pitch, int H, int W, int spatial, float sigma_s, int R, int range,
                                 float sigma_r) {
+    const float inv2ss = 1.0f / (2.0f * sigma_s * sigma_s);
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= W || y >= H) return;
@@ -139,7 +140,10 @@ __global__ void bf_exact_kernel(const float *__restrict__ in, size_t in_pitch, f
             if (range == BF_KERNEL_GAUSSIAN) kr = expf(-t * t * inv2sr);
             else if (range == BF_KERNEL_EXPONENTIAL) kr = expf(-fabsf(t) / sigma_r);
             else kr = fabsf(t) <= sigma_r ? 1.f : 0.f;
-            const float ks = spatial == BF_KERNEL_BOX ? 1.f : expf(-(float)(dx * dx + dy * dy) * inv2ss);
+            const float r2 = (float)(dx * dx + dy * dy);
+            const float ks = spatial == BF_KERNEL_BOX           ? 1.f
+                             : spatial == BF_KERNEL_EXPONENTIAL ? expf(-sqrtf(r2) / sigma_s)
+                                                                : expf(-r2 * inv2ss);
             const float wgt = ks * kr;
             num += wgt * iy;
             den += wgt;
@@ -177,7 +181,8 @@ std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int w
     std::vector<std::pair<double, TileConfig>> all;
     for (const auto &cls : classes()) {
         if (cls.m != p.m) continue;
-        const int groups = (p.nr + cls.nk - 1) / cls.nk;
+        const int groups = term_groups(p, cls.nk);
+        if (groups * cls.nk > kMaxSlots) continue;
         // column threads in whole warps; the tile takes what the halo leaves
         for (int ncols = 32; ncols + kScanThreads <= 512; ncols += 32) {
             int tw = ((ncols - 2 * p.rx) / 8) * 8;
@@ -278,6 +283,37 @@ bf_status launch_batch_finalize(const BatchImage *d_imgs, const int *d_list, int
     return BF_OK;
 }
 
+int term_groups(const FilterParams &p, int nk) {
+    int groups = 0;
+    for (int i = 0; i < p.nr;) {
+        const int k0 = p.k[i];
+        ++groups;
+        while (i < p.nr && p.k[i] < k0 + nk) ++i;
+    }
+    return groups;
+}
+
+bool term_layout(const FilterParams &p, int nk, FilterParams &out) {
+    out = p;
+    int slot = 0;
+    for (int i = 0; i < p.nr;) {
+        const int k0 = p.k[i];
+        if (slot + nk > kMaxSlots) return false;
+        for (int s = 0; s < nk; ++s) {
+            out.k[slot + s] = k0 + s;
+            if (i < p.nr && p.k[i] == k0 + s) {
+                out.a[slot + s] = p.a[i];
+                ++i;
+            } else {
+                out.a[slot + s] = 0.f;
+            }
+        }
+        slot += nk;
+    }
+    out.nr = slot;
+    return true;
+}
+
 void fill_info(const TileConfig &tc, int height, int width, int *info) {
     info[0] = tc.tw;
     info[1] = tc.th;
@@ -305,6 +341,11 @@ bf_status launch_filter(const FilterParams &p, int precision, int kahan, const T
     const void *fn = find_kernel(p.m, tc.nk, tc.ring != 0);
     if (!fn || tc.ncols <= 0) return fail(BF_ERR_UNSUPPORTED, "no kernel class for this plan and image");
     if (tc.threads > 512) return fail(BF_ERR_UNSUPPORTED, "horizontal reach too large for one CTA");
+    // the tile body needs whole warps of column threads (its two scan warps meet on a 64-thread named
+    // barrier) and tile widths in blocks of 8 columns; geometries from a cache file are checked here
+    if (tc.ncols % 32 != 0 || tc.threads != tc.ncols + kScanThreads || tc.tw < 8 || tc.tw % 8 != 0 ||
+        tc.tw + 2 * p.rx > tc.ncols || tc.th < 1 || (tc.depth != 2 && tc.depth != 3) || tc.nk < 2 || tc.nk % 2 != 0)
+        return fail(BF_ERR_INVALID_ARG, "malformed launch geometry");
     if (tc.smem > 227 * 1024) return fail(BF_ERR_UNSUPPORTED, "tile needs more than 227 KB of shared memory");
     if (tc.groups > 1 && !d_scratch) return fail(BF_ERR_INVALID_ARG, "missing scratch for grouped launch");
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc.smem);
@@ -313,7 +354,9 @@ bf_status launch_filter(const FilterParams &p, int precision, int kahan, const T
     int tw = tc.tw, th = tc.th, ncols = tc.ncols, H = height, W = width, depth = tc.depth;
     const float *in = d_in;
     float *out = d_out, *part = d_scratch;
-    FilterParams pp = p;
+    FilterParams pp;
+    if (!term_layout(p, tc.nk, pp) || pp.nr != tc.groups * tc.nk)
+        return fail(BF_ERR_INVALID_ARG, "launch geometry does not match the plan's term groups");
     void *args[] = {(void *)&in, (void *)&in_pitch, (void *)&out, (void *)&out_pitch, (void *)&part, (void *)&H,
                     (void *)&W, (void *)&tw, (void *)&th, (void *)&ncols, (void *)&depth, (void *)&pp};
     e = cudaLaunchKernel(fn, grid, dim3(tc.threads), args, tc.smem, (cudaStream_t)stream);
@@ -334,7 +377,7 @@ bf_status launch_exact(const float *d_in, size_t in_pitch, float *d_out, size_t 
     if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");
     dim3 block(128), grid((width + 127) / 128, height);
     bf_exact_kernel<<<grid, block, 0, (cudaStream_t)stream>>>(d_in, in_pitch, d_out, out_pitch, height, width, spatial,
-                                                             1.0f / (2.0f * sigma_s * sigma_s), radius, range, sigma_r);
+                                                             sigma_s, radius, range, sigma_r);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "exact launch");
     return BF_OK;

@@ -15,7 +15,8 @@ namespace bfi {
 // number of cosine terms one plan carries, and the per-thread budget of
 // running sums (terms per group x windows <= kSlotBudget; 4 basis images each).
 constexpr int kMaxWin = 6;
-constexpr int kMaxTerms = 64;
+constexpr int kMaxTerms = 64;   // selected cosine terms per plan
+constexpr int kMaxSlots = 128;  // term slots of a launch (groups x terms per group)
 constexpr int kSlotBudget = 16;
 
 // Everything a launch of the fused filter needs, passed by value (it lands in
@@ -29,9 +30,12 @@ struct FilterParams {
     float inv_p_lo;           // 1 / P - inv_p (two-float representation of 1 / P)
     float i_lo;               // intensity origin
     float den_eps;            // denominator guard
-    int nr;                   // cosine terms
-    int k[kMaxTerms];         // ascending
-    float a[kMaxTerms];
+    // The plan stores the selected terms (k ascending, nr of them).  A launch with NK terms per group
+    // passes a copy laid out by term_layout: nr = groups x NK slots, group g's slots are the consecutive
+    // frequencies k[g NK] .. k[g NK] + NK - 1 with a = 0 where the selection has no term.
+    int nr;
+    int k[kMaxSlots];
+    float a[kMaxSlots];
     int m;                    // windows per axis of this kernel class
     int v0[kMaxWin], v1[kMaxWin];
     int u0[kMaxWin], u1[kMaxWin];
@@ -80,6 +84,12 @@ bool kernel_class_supported(int m);
 // Ranked launch geometries from the cost model, the model's pick, and the
 // geometry bf_filter uses (an autotuned one when bf_autotune measured this
 // kernel class, reach and image size on this device, else the model's pick).
+// Term groups of NK consecutive frequencies covering a plan's selected terms (greedy: each group starts
+// at the smallest selected frequency not yet covered), and the launch copy of the parameters laid out in
+// those groups (false if the slots exceed kMaxSlots).
+int term_groups(const FilterParams &p, int nk);
+bool term_layout(const FilterParams &p, int nk, FilterParams &out);
+
 // Writes the geometry record (kInfoInts ints) of bf_launch_info / bf_autotune.
 constexpr int kInfoInts = 11;
 void fill_info(const TileConfig &tc, int height, int width, int *info);

@@ -9,7 +9,7 @@
 
 namespace bfi {
 
-constexpr int kScanThreads = 64;  // two warps: one exchange row per lane (<= 64 rows)
+constexpr int kScanThreads = 64;  // two scan warps
 
 namespace {
 
@@ -62,57 +62,69 @@ __device__ __forceinline__ int ring_slot(int ys, int off, int D) {
     return s;
 }
 
-// Compensated (Kahan) accumulation s += x with running error term c.
-__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
-    const float y = x - c;
-    const float t = s + y;
-    c = (t - s) - y;
+// Packed fp32 pairs (Blackwell's two-wide fp32 instructions): each lane of a pair is rounded exactly
+// as the scalar instruction would round it.
+__device__ __forceinline__ float2 pair(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+// Compensated (Kahan) accumulation s += x with running error term c, on a pair.
+__device__ __forceinline__ void kahan_add2(float2 &s, float2 &c, float2 x) {
+    const float2 y = sub2(x, c);
+    const float2 t = add2(s, y);
+    c = sub2(sub2(t, s), y);
     s = t;
 }
 
-// Adds x to the sliding sum s: compensated, or plain (c then stays 0).
-__device__ __forceinline__ void sum_add(float &s, float &c, int compensated, float x) {
-    if (compensated) kahan_add(s, c, x);
-    else s += x;
+// Adds x to the sliding sums s: compensated, or plain (c then stays 0).
+__device__ __forceinline__ void sum_add2(float2 &s, float2 &c, int compensated, float2 x) {
+    if (compensated) kahan_add2(s, c, x);
+    else s = add2(s, x);
 }
 
-// (c, s) = (cos, sin)(pi k t) advanced by one multiple of the base rotation (c1, s1) = (cos, sin)(pi t).
-__device__ __forceinline__ void rot1(float &c, float &s, float c1, float s1) {
-    const float cn = fmaf(c, c1, -s * s1);
-    s = fmaf(s, c1, c * s1);
-    c = cn;
-}
-
-// The same by `steps` multiples (terms that are not consecutive).
-__device__ __forceinline__ void rotn(float &c, float &s, float c1, float s1, int steps) {
-    for (int n = 0; n < steps; ++n) rot1(c, s, c1, s1);
+// A term pair's (cos, sin), (C, S) = ((cos a, cos b), (sin a, sin b)), both angles advanced by the angle
+// whose (cos, sin) pair-broadcasts are (cs, ss) (nss = -ss).
+__device__ __forceinline__ void rot2(float2 &C, float2 &S, float2 cs, float2 ss, float2 nss) {
+    const float2 cn = fma2(S, nss, mul2(C, cs));
+    S = fma2(C, ss, mul2(S, cs));
+    C = cn;
 }
 
 // One tile: output columns [x0, x0 + tw) x rows [y0, y0 + th) of one image,
 // cosine terms [g NK, g NK + NK) of p.  All threads of the CTA call it; it
 // ends on a barrier, so the shared memory can be reused right after.  `grouped`:
 // store partial numerator / denominator planes (part) instead of dividing.
+//
+// The NK terms are processed as NK / 2 pairs of consecutive terms with the packed pair instructions:
+// pair p holds terms (2p, 2p + 1) of the group in the two lanes of every float2.
 template <int NK, int M, bool RING>
 __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__restrict__ in, size_t in_pitch,
                                           float *__restrict__ out, size_t out_pitch, float *__restrict__ part, int H,
                                           int W, int x0, int y0, int tw, int th, int ncols, int g, bool grouped,
                                           int depth, float *smem) {
-    constexpr int NROW = M * NK * 4;  // exchange rows per image row: windows x terms x basis images
+    static_assert(NK % 2 == 0, "terms are processed in pairs");
+    constexpr int NP = NK / 2;        // term pairs per group
+    constexpr int NROW = M * NK * 4;  // exchange rows per image row: windows x basis images x terms
     constexpr int NE = 2 * M + 1;     // edges per step: M entering rows, M leaving rows, the output row
-    // Exchange [depth][ZC][NRP], column-major so that every row offset is a compile-time constant: column
-    // threads store a column, scan lanes walk along a row, output threads read a column.  NRP is even so
-    // that row pairs move as float2, and NRP / 2 is odd so that a warp's float2 accesses to consecutive
-    // columns, and its lanes' float accesses along a column, hit distinct banks.
+    // Exchange [depth][ZC][NRP] floats, column-major so that every row offset is a compile-time constant:
+    // column threads store a column, scan lanes walk along rows, output threads read a column.  Row
+    // (q * 4 + t) * NK + i holds window q, basis image t (cos I, sin I, cos, sin) of term i, so a term
+    // pair is one float2.  NRP is even and NRP / 2 odd: a warp's float2 accesses to consecutive columns,
+    // and its lanes' float2 accesses along a column, hit distinct banks.
     constexpr int NRP = NROW + 2;
-    const int ZC = ncols + 2;  // tile column c at index c + 1; columns 0 and ncols + 1 stay 0
+    constexpr int NP2 = NRP / 2;      // column pitch in float2
+    const int ZC = ncols + 2;         // tile column c at index c + 1; columns 0 and ncols + 1 stay 0
     // `depth` exchange buffers: 2 -> the output phase reads the row the scan finished in the same step (two
     // barriers per row); 3 -> it reads the row scanned one step earlier (one barrier per row)
     float *zb0 = smem;
-    float2 *wb0 = reinterpret_cast<float2 *>(smem + depth * ZC * NRP);  // [depth][NK][tw]: a_k (cos, sin) at the output row
+    // [depth][NP][tw] float4: a_k cos, a_k' cos, a_k sin, a_k' sin of a term pair at the output row
+    float4 *wb0 = reinterpret_cast<float4 *>(smem + depth * ZC * NRP);
     // RING: per column, the basis inputs of the last D rows, so each row's load and sincospi happen once
     // instead of at every window edge: (v, cos pi t, sin pi t) in ringA, (cos, sin)(pi k0 t) in ringB
     const int D = p.vhi - p.vlo + 2;
-    float4 *ringA = reinterpret_cast<float4 *>(wb0 + depth * NK * tw);  // [D][ncols]
+    float4 *ringA = reinterpret_cast<float4 *>(wb0 + depth * NP * tw);  // [D][ncols]
     float2 *ringB = reinterpret_cast<float2 *>(ringA + (RING ? D * ncols : 0));  // [D][ncols]
     const int halo = p.rx;
 
@@ -123,6 +135,9 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
     const int nout = min(y0 + th, H) - y0;
     const int xl = tid - halo;
     const bool is_out = is_col && xl >= 0 && xl < tw && x0 + xl < W;
+    // the two scan warps: warp 0 slides left to right over tile columns [0, cB), warp 1 right to left over
+    // [cB, tw); each writes its sums in place (left: into the slot of Z(c + u0), right: of Z(c + u1))
+    const int cB = (tw >> 4) << 3;
 
     for (int i = tid; i < depth * NRP; i += blockDim.x) {
         const int b = i / NRP, r = i - b * NRP;
@@ -130,51 +145,66 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
         zb0[(b * ZC + ncols + 1) * NRP + r] = 0.f;
     }
 
-    // this group's terms
-    int kk[NK];
+    // this group's terms: k0 .. k0 + NK - 1 (consecutive; the host zero-weights the frequencies it pads with)
+    const int k0 = p.k[g * NK];
     float aa[NK];
 #pragma unroll
-    for (int i = 0; i < NK; ++i) {
-        const int j = g * NK + i;
-        const bool ok = j < p.nr;
-        kk[i] = p.k[ok ? j : p.nr - 1];
-        aa[i] = ok ? p.a[j] : 0.f;
-    }
-    const int k0 = kk[0];
+    for (int i = 0; i < NK; ++i) aa[i] = p.a[g * NK + i];
 
-    float V[NK][4][M];
+    float2 V[NP][4][M];
 #pragma unroll
-    for (int i = 0; i < NK; ++i)
+    for (int i = 0; i < NP; ++i)
 #pragma unroll
         for (int t = 0; t < 4; ++t)
 #pragma unroll
-            for (int r = 0; r < M; ++r) V[i][t][r] = 0.f;
+            for (int r = 0; r < M; ++r) V[i][t][r] = make_float2(0.f, 0.f);
+
+    // pair (C, S) of terms (k0, k0 + 1) from the base rotation (c1, s1) and the anchor (c0, s0) = (cos, sin)(pi k0 t),
+    // and the pair step (cos, sin)(2 pi t) broadcast to both lanes
+    auto start_pair = [&](float c1, float s1, float c0, float s0, float2 &C, float2 &S, float2 &cs, float2 &ss,
+                          float2 &nss) {
+        C = make_float2(c0, fmaf(c0, c1, -s0 * s1));
+        S = make_float2(s0, fmaf(s0, c1, c0 * s1));
+        const float c2 = fmaf(c1, c1, -s1 * s1), s2 = 2.f * c1 * s1;
+        cs = pair(c2);
+        ss = pair(s2);
+        nss = pair(-s2);
+    };
+    // pixel (minus i_lo) of this thread's column at image row `row`, 0 outside the image
+    auto pixel = [&](int row) -> float {
+        return (colv && row >= 0 && row < H) ? __ldg(in + (size_t)row * in_pitch + xcol) - p.i_lo : 0.f;
+    };
 
     // window sums at the first output row: every row of the span once
     if (is_col) {
+        float vn = pixel(y0 + p.vlo);  // the next row's pixel is loaded one iteration ahead
         for (int off = p.vlo; off <= p.vhi; ++off) {
             const int row = y0 + off;
+            const float v = vn;
+            if (off < p.vhi) vn = pixel(row + 1);
             if (row < 0 || row >= H) continue;
-            const float v = colv ? __ldg(in + (size_t)row * in_pitch + xcol) - p.i_lo : 0.f;
-            float c1, s1, c, s;
-            basis_start(v, p.inv_p, p.inv_p_lo, k0, colv, c1, s1, c, s);
+            float c1, s1, c0, s0;
+            basis_start(v, p.inv_p, p.inv_p_lo, k0, colv, c1, s1, c0, s0);
             if (RING) {
                 const int sl = pos_mod(row, D) * ncols + tid;
                 ringA[sl] = make_float4(v, c1, s1, 0.f);
-                ringB[sl] = make_float2(c, s);
+                ringB[sl] = make_float2(c0, s0);
             }
+            const float2 v2 = pair(v);
+            float2 C, S, cs, ss, nss;
+            start_pair(c1, s1, c0, s0, C, S, cs, ss, nss);
             bool in_w[M];
 #pragma unroll
             for (int r = 0; r < M; ++r) in_w[r] = off >= p.v0[r] && off <= p.v1[r];
 #pragma unroll
-            for (int i = 0; i < NK; ++i) {
-                if (i > 0) rotn(c, s, c1, s1, kk[i] - kk[i - 1]);
-                const float gi[4] = {c * v, s * v, c, s};
+            for (int i = 0; i < NP; ++i) {
+                if (i > 0) rot2(C, S, cs, ss, nss);
+                const float2 gi[4] = {mul2(C, v2), mul2(S, v2), C, S};
 #pragma unroll
                 for (int r = 0; r < M; ++r)
                     if (in_w[r]) {
 #pragma unroll
-                        for (int t = 0; t < 4; ++t) V[i][t][r] += gi[t];
+                        for (int t = 0; t < 4; ++t) V[i][t][r] = add2(V[i][t][r], gi[t]);
                     }
             }
         }
@@ -184,144 +214,215 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
     int ys = RING ? pos_mod(y0, D) : 0;  // ring slot of row y (advanced each step)
     const float2 *zq[M];                 // output thread: column of window q's sliding sum
 #pragma unroll
-    for (int q = 0; q < M; ++q) zq[q] = reinterpret_cast<const float2 *>(zb0 + (tid + p.u0[q] + 1) * NRP);
+    for (int q = 0; q < M; ++q)
+        zq[q] = reinterpret_cast<const float2 *>(zb0 + (tid + (xl < cB ? p.u0[q] : p.u1[q]) + 1) * NRP);
+    // edge offsets: M entering rows, M leaving rows, the output row
+    auto edge_off = [&](int e) -> int { return e < M ? p.v1[e] : (e < 2 * M ? p.v0[e - M] - 1 : 0); };
+    // The pixels a step needs from global memory are loaded one step ahead, so their latency overlaps the
+    // previous step: RING: the row entering the ring; otherwise the 2M + 1 edge rows.
+    float pf[RING ? 1 : NE];
+    if (RING) {
+        pf[0] = pixel(y0 + 1 + p.vhi);
+    } else {
+#pragma unroll
+        for (int e = 0; e < NE; ++e) pf[e] = e == 2 * M ? pixel(y0) : 0.f;  // at j == 0 only the output edge is live
+    }
     for (int j = 0; j < nout + lag; ++j) {
         const int y = y0 + j;
         if (is_col && j < nout) {
-            float Ie[NE], c1[NE], s1[NE], ce[NE], se[NE];
+            float Ie[NE];
+            float vr = 0.f;
+            if (RING) {
+                // pf[0] holds row y + vhi from step 1 on; step 0 inserts nothing
+                if (j > 0) {
+                    vr = pf[0];
+                    if (j + 1 < nout) pf[0] = pixel(y + 1 + p.vhi);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < NE; ++e) Ie[e] = pf[e];
+                if (j + 1 < nout) {
+#pragma unroll
+                    for (int e = 0; e < NE; ++e) pf[e] = pixel(y + 1 + edge_off(e));
+                }
+            }
             if (RING && j > 0) {  // the newest row of the span enters the ring
                 const int row = y + p.vhi;
                 if (row < H) {
-                    const float v = colv ? __ldg(in + (size_t)row * in_pitch + xcol) - p.i_lo : 0.f;
                     float a, b, c, s;
-                    basis_start(v, p.inv_p, p.inv_p_lo, k0, colv, a, b, c, s);
+                    basis_start(vr, p.inv_p, p.inv_p_lo, k0, colv, a, b, c, s);
                     const int sl = ring_slot(ys, p.vhi, D) * ncols + tid;
-                    ringA[sl] = make_float4(v, a, b, 0.f);
+                    ringA[sl] = make_float4(vr, a, b, 0.f);
                     ringB[sl] = make_float2(c, s);
                 }
             }
+            float2 *zb = reinterpret_cast<float2 *>(zb0 + ((j % depth) * ZC + tid + 1) * NRP);
+            float4 *wb = wb0 + (j % depth) * NP * tw;
+            // one edge at a time: its term pairs update the sums of its window (only one edge's state is live)
 #pragma unroll
             for (int e = 0; e < NE; ++e) {
-                const int off = e < M ? p.v1[e] : (e < 2 * M ? p.v0[e - M] - 1 : 0);
+                const int off = edge_off(e);
                 const int row = y + off;
                 // at j == 0 the sums already hold row y0: only the output-row edge is live
                 const bool valid = colv && row >= 0 && row < H && (j > 0 || e == 2 * M);
+                float v, c1, s1, c0, s0;
                 if (RING) {
                     // slots of rows outside the image were never written: do not read them
                     const int sl = ring_slot(ys, off, D) * ncols + tid;
                     const float4 A = valid ? ringA[sl] : make_float4(0.f, 1.f, 0.f, 0.f);
-                    Ie[e] = A.x;
-                    c1[e] = A.y;
-                    s1[e] = A.z;
+                    v = A.x;
+                    c1 = A.y;
+                    s1 = A.z;
                     if (k0 == 0) {
-                        ce[e] = valid ? 1.f : 0.f;
-                        se[e] = 0.f;
+                        c0 = valid ? 1.f : 0.f;
+                        s0 = 0.f;
                     } else if (k0 == 1) {
-                        ce[e] = valid ? A.y : 0.f;
-                        se[e] = valid ? A.z : 0.f;
+                        c0 = valid ? A.y : 0.f;
+                        s0 = valid ? A.z : 0.f;
                     } else {
                         const float2 B = valid ? ringB[sl] : make_float2(0.f, 0.f);
-                        ce[e] = B.x;
-                        se[e] = B.y;
+                        c0 = B.x;
+                        s0 = B.y;
                     }
                 } else {
-                    const float v = valid ? __ldg(in + (size_t)row * in_pitch + xcol) - p.i_lo : 0.f;
-                    Ie[e] = v;
-                    basis_start(v, p.inv_p, p.inv_p_lo, k0, valid, c1[e], s1[e], ce[e], se[e]);
+                    // the prefetched value is 0 outside the image; `valid` also masks the rows that the
+                    // sums already hold at j == 0
+                    v = valid ? Ie[e] : 0.f;
+                    basis_start(v, p.inv_p, p.inv_p_lo, k0, valid, c1, s1, c0, s0);
                 }
-            }
-            float2 *zb = reinterpret_cast<float2 *>(zb0 + ((j % depth) * ZC + tid + 1) * NRP);
-            float2 *wb = wb0 + (j % depth) * NK * tw;
+                float2 C, S, cs, ss, nss;
+                start_pair(c1, s1, c0, s0, C, S, cs, ss, nss);
+                const int r = e < M ? e : e - M;                          // window of an entering / leaving edge
+                const float2 Iv = pair(e >= M && e < 2 * M ? -v : v);    // leaving rows enter with a minus sign
 #pragma unroll
-            for (int i = 0; i < NK; ++i) {
-                if (i > 0) {  // one uniform branch per term
-                    const int steps = kk[i] - kk[i - 1];
-                    if (steps == 1) {
-#pragma unroll
-                        for (int e = 0; e < NE; ++e) rot1(ce[e], se[e], c1[e], s1[e]);
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < NE; ++e) rotn(ce[e], se[e], c1[e], s1[e], steps);
+                for (int i = 0; i < NP; ++i) {
+                    if (i > 0) rot2(C, S, cs, ss, nss);
+                    if (e < 2 * M) {
+                        V[i][0][r] = fma2(C, Iv, V[i][0][r]);
+                        V[i][1][r] = fma2(S, Iv, V[i][1][r]);
+                        if (e < M) {
+                            V[i][2][r] = add2(V[i][2][r], C);
+                            V[i][3][r] = add2(V[i][3][r], S);
+                        } else {
+                            V[i][2][r] = sub2(V[i][2][r], C);
+                            V[i][3][r] = sub2(V[i][3][r], S);
+                        }
+                    } else if (is_out) {
+                        const float2 a2 = make_float2(aa[2 * i], aa[2 * i + 1]);
+                        const float2 ca = mul2(a2, C), sa = mul2(a2, S);
+                        wb[i * tw + xl] = make_float4(ca.x, ca.y, sa.x, sa.y);
                     }
                 }
+            }
+            // mix per horizontal window and publish
 #pragma unroll
-                for (int r = 0; r < M; ++r) {
-                    const int ei = r, eo = M + r;
-                    V[i][0][r] = fmaf(-ce[eo], Ie[eo], fmaf(ce[ei], Ie[ei], V[i][0][r]));
-                    V[i][1][r] = fmaf(-se[eo], Ie[eo], fmaf(se[ei], Ie[ei], V[i][1][r]));
-                    V[i][2][r] += ce[ei] - ce[eo];
-                    V[i][3][r] += se[ei] - se[eo];
-                }
+            for (int i = 0; i < NP; ++i)
 #pragma unroll
-                for (int q = 0; q < M; ++q) {
-                    float z[4];
+                for (int q = 0; q < M; ++q)
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
-                        z[t] = 0.f;
+                        float2 z = mul2(pair(p.C[0][q]), V[i][t][0]);
 #pragma unroll
-                        for (int r = 0; r < M; ++r) z[t] = fmaf(p.C[r][q], V[i][t][r], z[t]);
+                        for (int r = 1; r < M; ++r) z = fma2(pair(p.C[r][q]), V[i][t][r], z);
+                        zb[(q * 4 + t) * NP + i] = z;
                     }
-                    zb[(q * NK + i) * 2 + 0] = make_float2(z[0], z[1]);
-                    zb[(q * NK + i) * 2 + 1] = make_float2(z[2], z[3]);
-                }
-                if (is_out) wb[i * tw + xl] = make_float2(aa[i] * ce[2 * M], aa[i] * se[2 * M]);
-            }
         } else if (!is_col && j >= 1 && j - 1 < nout) {
-            const int r = tid - ncols;
-            if (r < NROW) {
-                // sliding sum of window q over the row; S(c) replaces Z(c + u0), which the
-                // slide has consumed (index c + u0 + 1 in buffer coordinates)
-                const int q = r / (NK * 4);
+            const int st = tid - ncols;
+            const int seg = st >> 5, l = st & 31;  // scan warp, lane = row pair
+            float2 held = make_float2(0.f, 0.f);
+            float2 *hp = nullptr;
+            if (l < NROW / 2) {
+                const int q = (2 * l) / (4 * NK);
                 const int u0 = p.u0[q], u1 = p.u1[q];
-                float *row = zb0 + ((j - 1) % depth) * ZC * NRP + r;
-                float S = 0.f, comp = 0.f;
-                int b = p.rx + u0 + 1;
-                const int bend = p.rx + u1 + 1;
-                for (; b + 7 <= bend; b += 8) {
-                    float v[8];
+                float2 *row = reinterpret_cast<float2 *>(zb0 + ((j - 1) % depth) * ZC * NRP) + l;
+                // tile column c is buffer column c + rx + 1; Z(c) at row[(c + rx + 1) * NP2]
+                float2 S = make_float2(0.f, 0.f), comp = make_float2(0.f, 0.f);
+                if (seg == 0 && cB > 0) {
+                    // left to right: S(c + 1) = S(c) + Z(c + 1 + u1) - Z(c + u0); S(c) replaces Z(c + u0)
+                    int b = p.rx + u0 + 1;
+                    const int bend = p.rx + u1 + 1;
+                    for (; b + 7 <= bend; b += 8) {
+                        float2 v[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) v[u] = row[(b + u) * NRP];
-                    sum_add(S, comp, p.kahan, ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])));
-                }
-                float rest = 0.f;
-                for (; b <= bend; ++b) rest += row[b * NRP];
-                sum_add(S, comp, p.kahan, rest);
-                for (int c0 = p.rx; c0 < p.rx + tw; c0 += 8) {
-                    float d[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) d[u] = row[(c0 + u + u1 + 2) * NRP] - row[(c0 + u + u0 + 1) * NRP];
-                    float pd = -comp;
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        row[(c0 + u + u0 + 1) * NRP] = S + pd;
-                        pd += d[u];
+                        for (int u = 0; u < 8; ++u) v[u] = row[(b + u) * NP2];
+                        sum_add2(S, comp, p.kahan, add2(add2(add2(v[0], v[1]), add2(v[2], v[3])),
+                                                        add2(add2(v[4], v[5]), add2(v[6], v[7]))));
                     }
-                    sum_add(S, comp, p.kahan, pd + comp);
+                    float2 rest = make_float2(0.f, 0.f);
+                    for (; b <= bend; ++b) rest = add2(rest, row[b * NP2]);
+                    sum_add2(S, comp, p.kahan, rest);
+                    for (int c0 = p.rx; c0 < p.rx + cB; c0 += 8) {
+                        float2 d[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) d[u] = sub2(row[(c0 + u + u1 + 2) * NP2], row[(c0 + u + u0 + 1) * NP2]);
+                        float2 pd = make_float2(-comp.x, -comp.y);
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            row[(c0 + u + u0 + 1) * NP2] = add2(S, pd);
+                            pd = add2(pd, d[u]);
+                        }
+                        sum_add2(S, comp, p.kahan, add2(pd, comp));
+                    }
+                } else if (seg == 1) {
+                    // right to left from c = tw - 1: S(c - 1) = S(c) + Z(c - 1 + u0) - Z(c + u1); S(c) replaces
+                    // Z(c + u1).  The last sum, S(cB), goes into the slot of Z(cB + u1), which the left
+                    // warp reads last: it is held until both warps pass the named barrier below.
+                    int b = p.rx + tw - 1 + u0 + 1;
+                    const int bend = p.rx + tw - 1 + u1 + 1;
+                    for (; b + 7 <= bend; b += 8) {
+                        float2 v[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) v[u] = row[(b + u) * NP2];
+                        sum_add2(S, comp, p.kahan, add2(add2(add2(v[0], v[1]), add2(v[2], v[3])),
+                                                        add2(add2(v[4], v[5]), add2(v[6], v[7]))));
+                    }
+                    float2 rest = make_float2(0.f, 0.f);
+                    for (; b <= bend; ++b) rest = add2(rest, row[b * NP2]);
+                    sum_add2(S, comp, p.kahan, rest);
+                    for (int c0 = p.rx + tw - 1; c0 >= p.rx + cB; c0 -= 8) {
+                        float2 d[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) d[u] = sub2(row[(c0 - u + u0) * NP2], row[(c0 - u + u1 + 1) * NP2]);
+                        float2 pd = make_float2(-comp.x, -comp.y);
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const float2 o = add2(S, pd);
+                            if (u == 7 && c0 - 7 == p.rx + cB) {
+                                held = o;
+                                hp = &row[(c0 - u + u1 + 1) * NP2];
+                            } else {
+                                row[(c0 - u + u1 + 1) * NP2] = o;
+                            }
+                            pd = add2(pd, d[u]);
+                        }
+                        sum_add2(S, comp, p.kahan, add2(pd, comp));
+                    }
                 }
             }
+            asm volatile("bar.sync 1, 64;" ::: "memory");  // the two scan warps only
+            if (hp) *hp = held;
         }
         if (depth == 2) __syncthreads();
         if (is_out && j >= lag) {
             const int yo = y - lag;
-            const int zo = ((j - lag) % depth) * ZC * (NRP / 2);
-            const float2 *wp = wb0 + ((j - lag) % depth) * NK * tw + xl;
-            float num = 0.f, den = 0.f;
+            const int zo = ((j - lag) % depth) * ZC * NP2;
+            const float4 *wp = wb0 + ((j - lag) % depth) * NP * tw + xl;
+            float2 num2 = make_float2(0.f, 0.f), den2 = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int i = 0; i < NK; ++i) {
-                float F[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int i = 0; i < NP; ++i) {
+                float2 F[4];
 #pragma unroll
-                for (int q = 0; q < M; ++q) {
-                    const float2 a = zq[q][zo + (q * NK + i) * 2 + 0];
-                    const float2 b = zq[q][zo + (q * NK + i) * 2 + 1];
-                    F[0] += a.x;
-                    F[1] += a.y;
-                    F[2] += b.x;
-                    F[3] += b.y;
+                for (int t = 0; t < 4; ++t) {
+                    F[t] = zq[0][zo + t * NP + i];
+#pragma unroll
+                    for (int q = 1; q < M; ++q) F[t] = add2(F[t], zq[q][zo + (q * 4 + t) * NP + i]);
                 }
-                const float2 w = wp[i * tw];
-                num = fmaf(w.x, F[0], fmaf(w.y, F[1], num));
-                den = fmaf(w.x, F[2], fmaf(w.y, F[3], den));
+                const float4 w = wp[i * tw];
+                const float2 wc = make_float2(w.x, w.y), ws = make_float2(w.z, w.w);
+                num2 = fma2(wc, F[0], fma2(ws, F[1], num2));
+                den2 = fma2(wc, F[2], fma2(ws, F[3], den2));
             }
+            const float num = num2.x + num2.y, den = den2.x + den2.y;
             const int x = x0 + xl;
             if (grouped) {
                 const size_t plane = (size_t)H * W;
@@ -329,8 +430,10 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
                 pp[0] = num;
                 pp[plane] = den;
             } else {
-                const float ix = __ldg(in + (size_t)yo * in_pitch + x);
-                out[(size_t)yo * out_pitch + x] = (den > p.den_eps) ? num / den + p.i_lo : ix;
+                float r;
+                if (den > p.den_eps) r = num / den + p.i_lo;
+                else r = __ldg(in + (size_t)yo * in_pitch + x);  // guard (rare): the input pixel
+                out[(size_t)yo * out_pitch + x] = r;
             }
         }
         if (RING) ys = ys + 1 == D ? 0 : ys + 1;

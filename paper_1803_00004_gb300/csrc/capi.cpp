@@ -187,7 +187,7 @@ bf_status bf_exact(const float *d_in, size_t in_pitch, float *d_out, size_t out_
     bf_status st = check_image(d_in, in_pitch, d_out, out_pitch, height, width);
     if (st != BF_OK || height == 0 || width == 0) return st;
     if (!(sigma_s > 0) || !(sigma_r > 0) || radius < 0) return fail(BF_ERR_INVALID_ARG, "bad exact-filter parameters");
-    if (spatial != BF_KERNEL_GAUSSIAN && spatial != BF_KERNEL_BOX) return fail(BF_ERR_UNSUPPORTED, "spatial kernel");
+    if (spatial < BF_KERNEL_GAUSSIAN || spatial > BF_KERNEL_BOX) return fail(BF_ERR_INVALID_ARG, "spatial kernel");
     if (range < BF_KERNEL_GAUSSIAN || range > BF_KERNEL_BOX) return fail(BF_ERR_INVALID_ARG, "range kernel");
     int R = radius > 0 ? radius : (int)(3.0 * sigma_s + 0.5);
     return launch_exact(d_in, in_pitch / sizeof(float), d_out, out_pitch / sizeof(float), height, width, spatial,

@@ -4,7 +4,7 @@
 
 namespace bfi {
 
-const KernelClass kClassesM3[] = {BF_CLASS(3, 5), BF_CLASS(3, 4), BF_CLASS(3, 2)};
+const KernelClass kClassesM3[] = {BF_CLASS(3, 4), BF_CLASS(3, 2)};
 const int kNumClassesM3 = sizeof(kClassesM3) / sizeof(kClassesM3[0]);
 
 }  // namespace bfi

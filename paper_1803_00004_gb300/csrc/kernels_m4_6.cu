@@ -4,7 +4,7 @@
 
 namespace bfi {
 
-const KernelClass kClassesM4to6[] = {BF_CLASS(4, 2), BF_CLASS(5, 1), BF_CLASS(6, 1)};
+const KernelClass kClassesM4to6[] = {BF_CLASS(4, 2), BF_CLASS(5, 2), BF_CLASS(6, 2)};
 const int kNumClassesM4to6 = sizeof(kClassesM4to6) / sizeof(kClassesM4to6[0]);
 
 }  // namespace bfi

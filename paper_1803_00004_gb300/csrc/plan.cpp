@@ -125,6 +125,100 @@ double haar_value(const Haar1 &h, double x) {
     return x < h.mid ? 1.0 : -1.0;
 }
 
+// ---------------------------------------------------------------- non-separable spatial kernel
+
+// Tensor 20-point rule over the box [x0, x1] x [y0, y1] of exp(-|x|_2 / sigma).
+double box_rule_radial_exp(double sigma, double x0, double x1, double y0, double y1, const GaussLegendre &g) {
+    const double cx = 0.5 * (x0 + x1), rx = 0.5 * (x1 - x0), cy = 0.5 * (y0 + y1), ry = 0.5 * (y1 - y0);
+    double s = 0.0;
+    for (size_t i = 0; i < g.x.size(); ++i) {
+        const double x = cx + rx * g.x[i];
+        double t = 0.0;
+        for (size_t j = 0; j < g.x.size(); ++j) {
+            const double y = cy + ry * g.x[j];
+            t += g.w[j] * std::exp(-std::sqrt(x * x + y * y) / sigma);
+        }
+        s += g.w[i] * t;
+    }
+    return s * rx * ry;
+}
+
+// Integral over the cell [0, h] x [0, h] (the kernel's cone point at its corner): the cell is split
+// into its corner quarter and three quarters; the quarters away from the corner are smooth enough for
+// the tensor rule, and the corner quarter is split again (geometric grading, 48 levels: the last
+// corner piece is below 2^-96 of the cell).
+double corner_cell_radial_exp(double sigma, double h) {
+    const GaussLegendre &g = gl20();
+    double s = 0.0, a = h;
+    for (int lev = 0; lev < 48; ++lev) {
+        const double m = 0.5 * a;
+        s += box_rule_radial_exp(sigma, m, a, 0.0, m, g) + box_rule_radial_exp(sigma, 0.0, m, m, a, g) +
+             box_rule_radial_exp(sigma, m, a, m, a, g);
+        a = m;
+    }
+    return s;
+}
+
+// 2-D Haar coefficients of the radial exponential kernel for every pair of 1-D dictionary entries
+// (Eqs. (21)-(22), the 2-D integral kept whole): c[i2 * n + i1] with entry i1 along x and i2 along y.
+// The integrals of the kernel over the finest dyadic cells (width h = 2T / 2^(J+1)) are tabulated
+// once, by the tensor rule (the four cells at the origin by corner grading), then summed into an
+// extended-precision summed-area table, from which each half-support rectangle is read in O(1).
+std::vector<double> haar2d_radial_exp(const std::vector<Haar1> &dict, double sigma, double T, int J) {
+    const int N = 1 << (J + 1);  // finest cells per axis; the origin is grid point N / 2
+    const double h = 2.0 * T / N;
+    const int half = N / 2;
+    // first quadrant cells q[iy][ix] = integral over [ix h, (ix+1) h] x [iy h, (iy+1) h]; the rest by symmetry
+    std::vector<double> q((size_t)half * half);
+    for (int iy = 0; iy < half; ++iy)
+        for (int ix = 0; ix <= iy; ++ix) {
+            double v;
+            if (ix == 0 && iy == 0) {
+                v = corner_cell_radial_exp(sigma, h);
+            } else {
+                const GaussLegendre &g = gl20();
+                v = box_rule_radial_exp(sigma, ix * h, (ix + 1) * h, iy * h, (iy + 1) * h, g);
+            }
+            q[(size_t)iy * half + ix] = v;
+            q[(size_t)ix * half + iy] = v;
+        }
+    auto cell = [&](int gx, int gy) {  // cell (gx, gy) of the full grid, 0..N-1
+        const int ax = gx >= half ? gx - half : half - 1 - gx, ay = gy >= half ? gy - half : half - 1 - gy;
+        return q[(size_t)ay * half + ax];
+    };
+    std::vector<long double> sat((size_t)(N + 1) * (N + 1), 0.0L);
+    for (int gy = 0; gy < N; ++gy) {
+        long double row = 0.0L;
+        for (int gx = 0; gx < N; ++gx) {
+            row += cell(gx, gy);
+            sat[(size_t)(gy + 1) * (N + 1) + gx + 1] = sat[(size_t)gy * (N + 1) + gx + 1] + row;
+        }
+    }
+    auto grid = [&](double x) { return (int)std::lround((x + T) / h); };
+    auto rect = [&](double x0, double x1, double y0, double y1) {
+        const int a = grid(x0), b = grid(x1), c = grid(y0), d = grid(y1);
+        const long double v = sat[(size_t)d * (N + 1) + b] - sat[(size_t)c * (N + 1) + b] -
+                              sat[(size_t)d * (N + 1) + a] + sat[(size_t)c * (N + 1) + a];
+        return (double)v;
+    };
+    const int n = (int)dict.size();
+    std::vector<double> c((size_t)n * n);
+    for (int i2 = 0; i2 < n; ++i2)
+        for (int i1 = 0; i1 < n; ++i1) {
+            const Haar1 &hx = dict[i1], &hy = dict[i2];
+            const double xs[2][2] = {{hx.lo, hx.lev < 0 ? hx.hi : hx.mid}, {hx.mid, hx.hi}};
+            const double ys[2][2] = {{hy.lo, hy.lev < 0 ? hy.hi : hy.mid}, {hy.mid, hy.hi}};
+            const int nx = hx.lev < 0 ? 1 : 2, ny = hy.lev < 0 ? 1 : 2;
+            double sum = 0.0;
+            for (int a = 0; a < nx; ++a)
+                for (int b = 0; b < ny; ++b)
+                    sum += (a == b ? 1.0 : -1.0) * rect(xs[a][0], xs[a][1], ys[b][0], ys[b][1]);
+            const double sx = hx.lev < 0 ? 1.0 : std::ldexp(1.0, hx.lev), sy = hy.lev < 0 ? 1.0 : std::ldexp(1.0, hy.lev);
+            c[(size_t)i2 * n + i1] = sx * sy * sum / (4.0 * T * T);
+        }
+    return c;
+}
+
 struct Cand {
     double mag, c;
     int key[5];
@@ -228,11 +322,8 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
     if (d.radius < 0 || d.radius > 1024) return fail(BF_ERR_INVALID_ARG, "radius must be in [0, 1024]");
     if (!(d.i_hi > d.i_lo)) return fail(BF_ERR_INVALID_ARG, "i_hi must exceed i_lo");
     if (d.t_r < 0 || !std::isfinite(d.t_r)) return fail(BF_ERR_INVALID_ARG, "t_r must be >= 0");
-    if (d.spatial != BF_KERNEL_GAUSSIAN && d.spatial != BF_KERNEL_BOX) {
-        if (d.spatial == BF_KERNEL_EXPONENTIAL)
-            return fail(BF_ERR_UNSUPPORTED, "non-separable (exponential) spatial kernel is not implemented");
+    if (d.spatial != BF_KERNEL_GAUSSIAN && d.spatial != BF_KERNEL_BOX && d.spatial != BF_KERNEL_EXPONENTIAL)
         return fail(BF_ERR_INVALID_ARG, "unknown spatial kernel");
-    }
     if (d.range < BF_KERNEL_GAUSSIAN || d.range > BF_KERNEL_BOX) return fail(BF_ERR_INVALID_ARG, "unknown range kernel");
     if (d.policy == BF_RANGE_PAPER_3D)
         return fail(BF_ERR_UNSUPPORTED, "BF_RANGE_PAPER_3D (z-binned range box) is not implemented");
@@ -286,7 +377,8 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
         p.a.push_back(e.second);
     }
 
-    // ---- 1-D Haar coefficients of the spatial profile (Eq. (20)); 2-D by separability (Eq. (22))
+    // ---- 1-D Haar coefficients of the spatial profile (Eq. (20)); 2-D by separability (Eq. (22)), or
+    // computed whole for the non-separable radial exponential
     if (p.J > 12) return fail(BF_ERR_UNSUPPORTED, "radius too large for the Haar dictionary");
     std::vector<Haar1> dict = haar_dictionary(p.J, p.Ts);
     const int n1 = (int)dict.size();
@@ -296,16 +388,21 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
         return integrate([&](double x) { return spatial_profile(d.spatial, d.sigma_s, x); }, a, b, pieces);
     };
     std::vector<double> c1(n1);
-    for (int i = 0; i < n1; ++i) {
+    for (int i = 0; i < n1 && d.spatial != BF_KERNEL_EXPONENTIAL; ++i) {
         const Haar1 &h = dict[i];
         if (h.lev < 0) c1[i] = prof_int(h.lo, h.hi) / (2.0 * p.Ts);
         else c1[i] = std::ldexp(1.0, h.lev) * (prof_int(h.lo, h.mid) - prof_int(h.mid, h.hi)) / (2.0 * p.Ts);
+    }
+    std::vector<double> c2;  // non-separable kernel: the 2-D coefficients computed whole
+    if (d.spatial == BF_KERNEL_EXPONENTIAL) {
+        if (p.J > 9) return fail(BF_ERR_UNSUPPORTED, "radius too large for the non-separable spatial kernel (R <= 255)");
+        c2 = haar2d_radial_exp(dict, d.sigma_s, p.Ts, p.J);
     }
     std::vector<Cand> sc;
     sc.reserve((size_t)n1 * n1);
     for (int i1 = 0; i1 < n1; ++i1)
         for (int i2 = 0; i2 < n1; ++i2) {
-            double c = c1[i1] * c1[i2];
+            double c = c2.empty() ? c1[i1] * c1[i2] : c2[(size_t)i2 * n1 + i1];
             int j1 = dict[i1].lev, j2 = dict[i2].lev;
             sc.push_back(Cand{std::fabs(c), c, {std::max(j1, j2), j1, j2, dict[i1].k, dict[i2].k}, i1, i2});
         }
@@ -383,7 +480,10 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
     p.spatial_max_err = 0;
     for (int dy = -R; dy <= R; ++dy)
         for (int dx = -R; dx <= R; ++dx) {
-            double ks = d.spatial == BF_KERNEL_BOX ? 1.0 : std::exp(-(double)(dx * dx + dy * dy) / (2.0 * d.sigma_s * d.sigma_s));
+            const double r2 = (double)(dx * dx + dy * dy);
+            double ks = d.spatial == BF_KERNEL_BOX           ? 1.0
+                        : d.spatial == BF_KERNEL_EXPONENTIAL ? std::exp(-std::sqrt(r2) / d.sigma_s)
+                                                             : std::exp(-r2 / (2.0 * d.sigma_s * d.sigma_s));
             p.spatial_max_err = std::max(p.spatial_max_err, std::fabs(ks - p.kernel[(size_t)(dy + R) * w + dx + R]));
         }
 

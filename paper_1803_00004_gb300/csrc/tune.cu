@@ -84,7 +84,8 @@ TileConfig choose_tile(const FilterParams &p, int height, int width, int precisi
         std::lock_guard<std::mutex> lk(g_mu);
         load_locked();
         auto it = g_table.find(make_key(p, height, width, precision));
-        if (it != g_table.end()) return it->second;
+        // an entry stays usable only while its term grouping matches this build's layout
+        if (it != g_table.end() && it->second.groups == term_groups(p, it->second.nk)) return it->second;
     }
     return model_tile(p, height, width, precision);
 }

@@ -50,6 +50,9 @@ DESCS = [
     dict(policy=bf.RANGE_UNTRUNCATED_FULL, sigma_r=0.2, nr_terms=6),
     dict(spatial=bf.KERNEL_BOX, sigma_s=2.0, ns_terms=4),
     dict(sigma_s=2.0, radius=4, ns_terms=25, nr_terms=16, sigma_r=0.07),
+    dict(spatial=bf.KERNEL_EXPONENTIAL, sigma_s=1.5),
+    dict(spatial=bf.KERNEL_EXPONENTIAL, sigma_s=3.0, ns_terms=13, nr_terms=6),
+    dict(spatial=bf.KERNEL_EXPONENTIAL, sigma_s=8.0, ns_terms=9),
 ]
 
 
@@ -102,7 +105,8 @@ def test_paper_five_terms_compile_to_two_nested_windows():
 
 @pytest.mark.parametrize("kw,status", [
     (dict(sigma_s=0.0), 1), (dict(sigma_r=-1.0), 1), (dict(ns_terms=0), 1), (dict(nr_terms=0), 1),
-    (dict(i_lo=1.0, i_hi=1.0), 1), (dict(policy=bf.RANGE_PAPER_3D), 2), (dict(spatial=bf.KERNEL_EXPONENTIAL), 2),
+    (dict(i_lo=1.0, i_hi=1.0), 1), (dict(policy=bf.RANGE_PAPER_3D), 2),
+    (dict(spatial=bf.KERNEL_EXPONENTIAL, sigma_s=100.0), 2),
     (dict(spatial=7), 1), (dict(precision=9), 1), (dict(radius=-2), 1), (dict(precision=1), 2), (dict(precision=2), 2),
 ])
 def test_plan_create_rejects(kw, status):
@@ -224,3 +228,30 @@ print(json.dumps(out))
     fresh = json.loads(subprocess.run([sys.executable, "-c", code, "read"], env=dict(os.environ, PYTHONPATH=ROOT),
                                       capture_output=True, text=True, check=True).stdout)
     assert fresh != read                               # without the file: the cost model's choice
+
+
+@pytest.mark.parametrize("kw", [dict(sigma_s=8.0, sigma_r=0.1, nr_terms=16), dict(sigma_s=8.0, sigma_r=0.3, nr_terms=16),
+                                dict(sigma_s=4.0, sigma_r=0.05, nr_terms=32), dict(range=bf.KERNEL_BOX, sigma_r=0.2, nr_terms=10),
+                                dict(sigma_s=4.0, nr_terms=8)])
+def test_term_groups_cover_the_selection(kw):
+    """A launch evaluates groups of NK consecutive frequencies (zero weight where nothing was selected); the
+    groups cover the selected terms greedily from the smallest uncovered frequency."""
+    plan = bf.Plan(device=-1, **kw)
+    k = list(plan.coeffs()["k"])
+
+    def greedy(nk):
+        groups, i = 0, 0
+        while i < len(k):
+            k0 = k[i]
+            groups += 1
+            while i < len(k) and k[i] < k0 + nk:
+                i += 1
+        return groups
+
+    seen = set()
+    for c in bf.bf_launch_candidates(plan, 300, 500):
+        assert c["groups"] == greedy(c["nk"]) and c["groups"] * c["nk"] <= 128
+        seen.add(c["nk"])
+    assert seen
+    if k == list(range(len(k))):                       # consecutive selection: ceil(N_r / NK) groups
+        assert all(greedy(nk) == -(-len(k) // nk) for nk in seen)

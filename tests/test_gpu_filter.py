@@ -56,6 +56,12 @@ CASES = [
     ("sigma32_R96", synth.shapes(400, 300, 9, scale=0.3), dict(sigma_s=32.0, sigma_r=0.3)),
     ("sigma8_nr32", synth.shapes(200, 220, 10, scale=0.2), dict(sigma_s=8.0, sigma_r=0.05, nr_terms=32)),
     ("m5", synth.shapes(160, 140, 11, scale=0.2), dict(sigma_s=4.0, ns_terms=41, nr_terms=6)),
+    # the non-separable radial exponential spatial kernel (2-D Haar coefficients computed whole)
+    ("exp_spatial", synth.shapes(210, 330, 15, scale=0.2), dict(spatial=bf.KERNEL_EXPONENTIAL, sigma_s=3.0)),
+    ("exp_spatial_m3", synth.shapes(150, 260, 16, scale=0.2),
+     dict(spatial=bf.KERNEL_EXPONENTIAL, sigma_s=2.0, ns_terms=13, nr_terms=6)),
+    ("exp_spatial_r48", synth.shapes(260, 300, 17, scale=0.3),
+     dict(spatial=bf.KERNEL_EXPONENTIAL, sigma_s=16.0, ns_terms=9, sigma_r=0.2)),
 ]
 
 
@@ -168,7 +174,8 @@ def test_in_place_rejected_and_injected_failure():
 
 
 @pytest.mark.parametrize("kw", [dict(sigma_s=2.0, sigma_r=0.1), dict(sigma_s=3.0, sigma_r=0.2, range=bf.KERNEL_EXPONENTIAL),
-                                dict(sigma_s=1.0, sigma_r=0.15, spatial=bf.KERNEL_BOX, radius=4)])
+                                dict(sigma_s=1.0, sigma_r=0.15, spatial=bf.KERNEL_BOX, radius=4),
+                                dict(sigma_s=2.5, sigma_r=0.1, spatial=bf.KERNEL_EXPONENTIAL)])
 def test_exact_helper_matches_oracle(kw):
     img = synth.shapes(90, 130, 14, scale=0.1)
     src = torch.from_numpy(img).cuda()
