@@ -200,8 +200,11 @@ bf_status bf_filter_noalloc(const bf_plan *plan, const float *d_in, size_t in_pi
  * CTA, [4] term groups (grid depth), [5] kernel launches, [6] shared memory
  * bytes per CTA, [7] scratch KiB, [8] 1 when the basis inputs are kept in a
  * shared-memory ring per column, [9] exchange buffer depth, [10] columns per
- * CTA (tile width plus the halo of 2 x horizontal reach, in whole warps).
- * info must hold 11 ints.  Host only; needs no
+ * CTA (tile width plus the halo of 2 x horizontal reach, in whole warps), [11]
+ * kernel family: 1 packed (cosine terms in consecutive pairs on the two-wide
+ * fp32 instructions; a gapped selection is covered by groups of consecutive
+ * frequencies with zero weights), 0 scalar (any set of terms; offered only for
+ * gapped selections).  info must hold 12 ints.  Host only; needs no
  * device for host-only plans (uses 152 SMs as the device size then).
  * Errors: BF_ERR_INVALID_ARG. */
 bf_status bf_launch_info(const bf_plan *plan, int height, int width, int *info);
@@ -212,22 +215,22 @@ bf_status bf_launch_info(const bf_plan *plan, int height, int width, int *info);
  * image and remembers the fastest for later bf_filter / bf_filter_batch calls
  * with the same kernel class, reach and image size on this device.  Allocates
  * and frees its own device buffers and synchronizes `stream`; do not call it
- * during stream capture.  info (11 ints, may be NULL) receives the chosen
+ * during stream capture.  info (12 ints, may be NULL) receives the chosen
  * geometry as in bf_launch_info.  BF_TUNE_CACHE=<file> persists results.
  * Errors: BF_ERR_INVALID_ARG, BF_ERR_NO_DEVICE, BF_ERR_OOM, BF_ERR_CUDA. */
 bf_status bf_autotune(const bf_plan *plan, int height, int width, void *stream, int *info);
 
 /* Launch geometries of this plan for a height x width image, best first by the
- * cost model: up to max_n records of 11 ints each (as in bf_launch_info) into
- * infos (caller-owned, 11 x max_n ints); *n_out receives how many were written.
+ * cost model: up to max_n records of 12 ints each (as in bf_launch_info) into
+ * infos (caller-owned, 12 x max_n ints); *n_out receives how many were written.
  * Host only.
  * Errors: BF_ERR_INVALID_ARG. */
 bf_status bf_launch_candidates(const bf_plan *plan, int height, int width, int max_n, int *infos, int *n_out);
 
 /* Pins the launch geometry bf_filter / bf_filter_noalloc use for this plan's
  * kernel class on height x width images of the plan's device (as bf_autotune
- * does with the fastest one).  info (11 ints, caller-owned) must match one
- * record of bf_launch_candidates in fields 0, 1, 3, 8, 9 and 10; the other
+ * does with the fastest one).  info (12 ints, caller-owned) must match one
+ * record of bf_launch_candidates in fields 0, 1, 3, 8, 9, 10 and 11; the other
  * fields are ignored.  The geometry changes rounding order only: every one gives
  * the result within the same error bound.  BF_TUNE_CACHE=<file> persists it.
  * Errors: BF_ERR_INVALID_ARG (no such geometry), BF_ERR_NO_DEVICE. */
@@ -256,6 +259,20 @@ bf_status bf_filter_batch(const bf_plan *const *plans, const bf_image *images, i
 bf_status bf_exact(const float *d_in, size_t in_pitch_bytes, float *d_out, size_t out_pitch_bytes,
                    int height, int width, int spatial, double sigma_s, int radius,
                    int range, double sigma_r, void *stream);
+
+/* The brute-force baseline with a look-up table (Sec. V, Case 2): Eq. (1) as
+ * in bf_exact, but the range weight of a neighbour is read from a table of
+ * `levels` entries K_r(n * step), step = data_range / (levels - 1), at the
+ * entry nearest to |I(x) - I(y)| (index rounded to nearest-even in fp32).
+ * With images whose values lie on that grid (e.g. 8-bit data and levels =
+ * 256 over data_range 1) the table is exact.  Its cost grows with the window,
+ * (2R + 1)^2 taps per pixel, which is why it wins only at small radii.
+ * radius <= 32 (0: round(3 sigma_s)), 2 <= levels <= 4096.  Device buffers as
+ * bf_exact; asynchronous on `stream`.  Errors: BF_ERR_INVALID_ARG,
+ * BF_ERR_UNSUPPORTED (radius > 32), BF_ERR_CUDA. */
+bf_status bf_exact_lut(const float *d_in, size_t in_pitch_bytes, float *d_out, size_t out_pitch_bytes,
+                       int height, int width, int spatial, double sigma_s, int radius,
+                       int range, double sigma_r, double data_range, int levels, void *stream);
 
 /* ---------------------------------------------------------------------- */
 /* Serving: continuous batching of filter requests                         */

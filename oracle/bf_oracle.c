@@ -21,7 +21,8 @@
  *     edge parameter);
  *   - best N-term selection by largest |coefficient|: Sec. III-A, Eq. (11);
  *     candidates limited to the first 20N range coefficients, App. B;
- *   - O1 exact bilateral filter, Eq. (1);
+ *   - O1 exact bilateral filter, Eq. (1); its look-up-table form, the brute-force
+ *     baseline of Sec. V (Case 2);
  *   - O2 direct evaluation of Eq. (1) with the approximated kernels of
  *     Eqs. (30) and (33) (the definition of the approximation);
  *   - O3 the paper's fast algorithm, Eqs. (34)-(36): basis images, signed
@@ -567,13 +568,27 @@ static double spatial_kernel2d(int kind, double sigma, int dx, int dy)
     return exp(-(double)(dx * dx + dy * dy) / (2.0 * sigma * sigma));
 }
 
-/* out[y*W+x] for every pixel; window |y-x|_inf <= R (R = round(3 sigma_s) if radius == 0),
- * range kernel not truncated.  rows/nrows restrict the output to a subset of rows
- * (rows == NULL: all rows). */
-int orc_exact_bf(const double *I, int H, int W, int skind, double sigma_s, int radius,
-                 int rkind, double sigma_r, double *out, const int *rows, int nrows, int nthreads)
+/* Range weight of the difference t: the kernel itself (levels == 0), or the look-up-table form of the
+ * brute-force baseline (Sec. V, Case 2): a table of `levels` entries K_r(n * step), n = 0 .. levels-1,
+ * step = data_range / (levels - 1), read at the entry nearest to |t|.  The entry is chosen in fp32 (the
+ * image data are fp32: |I(x) - I(y)| times 1/step, rounded to nearest-even), the same decision the device
+ * makes; the table value is evaluated in fp64. */
+static double range_weight(int rkind, double sigma_r, double ix, double iy, int levels, double data_range)
+{
+    if (levels <= 0) return range_kernel(rkind, sigma_r, ix - iy);
+    const float d = fabsf((float)ix - (float)iy);
+    const float inv_step = (float)((levels - 1) / data_range);
+    int n = (int)nearbyintf(d * inv_step);
+    if (n > levels - 1) n = levels - 1;
+    return range_kernel(rkind, sigma_r, n * (data_range / (levels - 1)));
+}
+
+static int exact_bf_impl(const double *I, int H, int W, int skind, double sigma_s, int radius, int rkind,
+                         double sigma_r, int levels, double data_range, double *out, const int *rows, int nrows,
+                         int nthreads)
 {
     if (!I || !out || H < 0 || W < 0 || !(sigma_s > 0) || !(sigma_r > 0) || radius < 0) return ORC_EINVAL;
+    if (levels < 0 || levels == 1 || (levels > 0 && !(data_range > 0))) return ORC_EINVAL;
     int R = radius > 0 ? radius : (int)lround(3.0 * sigma_s);
     int w = 2 * R + 1;
     double *Ks = malloc(sizeof(double) * w * w);
@@ -594,7 +609,7 @@ int orc_exact_bf(const double *I, int H, int W, int skind, double sigma_s, int r
                     int xx = x + dx;
                     if (xx < 0 || xx >= W) continue;
                     double iy = I[(size_t)yy * W + xx];
-                    double wgt = Ks[(dy + R) * w + dx + R] * range_kernel(rkind, sigma_r, ix - iy);
+                    double wgt = Ks[(dy + R) * w + dx + R] * range_weight(rkind, sigma_r, ix, iy, levels, data_range);
                     num += wgt * iy;
                     den += wgt;
                 }
@@ -604,6 +619,24 @@ int orc_exact_bf(const double *I, int H, int W, int skind, double sigma_s, int r
     }
     free(Ks);
     return ORC_OK;
+}
+
+/* out[y*W+x] for every pixel; window |y-x|_inf <= R (R = round(3 sigma_s) if radius == 0),
+ * range kernel not truncated.  rows/nrows restrict the output to a subset of rows
+ * (rows == NULL: all rows). */
+int orc_exact_bf(const double *I, int H, int W, int skind, double sigma_s, int radius,
+                 int rkind, double sigma_r, double *out, const int *rows, int nrows, int nthreads)
+{
+    return exact_bf_impl(I, H, W, skind, sigma_s, radius, rkind, sigma_r, 0, 0.0, out, rows, nrows, nthreads);
+}
+
+/* The brute-force baseline with the range kernel read from a table (see range_weight). */
+int orc_exact_bf_lut(const double *I, int H, int W, int skind, double sigma_s, int radius, int rkind,
+                     double sigma_r, int levels, double data_range, double *out, int nthreads)
+{
+    if (levels < 2) return ORC_EINVAL;
+    return exact_bf_impl(I, H, W, skind, sigma_s, radius, rkind, sigma_r, levels, data_range, out, NULL, 0,
+                         nthreads);
 }
 
 /* ------------------------------------------------------------------ */

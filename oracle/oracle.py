@@ -67,6 +67,7 @@ def _load():
         lib.orc_approx_fast.argtypes = common + [pd]
         lib.orc_box_count.argtypes = [i, d, i, i, i, d, d, i, i, d]
         lib.orc_approx_direct_at.argtypes = [pd, i, i, i, d, i, i, i, d, d, i, i, d, pi, i, pd, i]
+        lib.orc_exact_bf_lut.argtypes = [pd, i, i, i, d, i, i, d, i, d, pd, i]
         lib.orc_rect_int_exp.argtypes = [d, d, d, d, d]
         lib.orc_rect_int_exp.restype = d
         lib.orc_haar2d_exp.argtypes = [d, d, i, pd, i]
@@ -228,6 +229,19 @@ def exact_bf(I, desc: Desc, rows=None, threads: int = 1) -> np.ndarray:
                               desc.sigma_r, _dp(out), rp, nr, threads)
     if st:
         raise ValueError("orc_exact_bf status %d" % st)
+    return out
+
+
+def exact_bf_lut(I, desc: Desc, levels: int, data_range: float = 1.0, threads: int = 1) -> np.ndarray:
+    """Eq. (1) with the range kernel read from a `levels`-entry table over [0, data_range] (nearest entry,
+    chosen in fp32): the look-up-table brute-force baseline."""
+    I = _img(I)
+    H, W = I.shape
+    out = np.zeros((H, W))
+    st = _load().orc_exact_bf_lut(_dp(I), H, W, desc.spatial, desc.sigma_s, desc.radius, desc.range, desc.sigma_r,
+                                  levels, data_range, _dp(out), threads)
+    if st:
+        raise ValueError("orc_exact_bf_lut status %d" % st)
     return out
 
 

@@ -63,7 +63,7 @@ EXPORTS = ["bf_plan_desc_default", "bf_plan_create", "bf_plan_destroy", "bf_coef
            "bf_launch_candidates", "bf_set_launch",
            "bf_filter", "bf_filter_noalloc",
            "bf_filter_batch",
-           "bf_exact", "bf_serve_create", "bf_serve_submit", "bf_serve_poll", "bf_serve_cancel", "bf_serve_destroy",
+           "bf_exact", "bf_exact_lut", "bf_serve_create", "bf_serve_submit", "bf_serve_poll", "bf_serve_cancel", "bf_serve_destroy",
            "bf_status_string", "bf_last_error", "bf_version", "bf_debug_fail_launches"]
 
 _lib = None
@@ -97,6 +97,7 @@ def lib():
         L.bf_autotune.argtypes = [vp, i, i, vp, P(i)]
         L.bf_filter_batch.argtypes = [P(vp), P(bf_image), i, vp]
         L.bf_exact.argtypes = [vp, sz, vp, sz, i, i, i, d, i, i, d, vp]
+        L.bf_exact_lut.argtypes = [vp, sz, vp, sz, i, i, i, d, i, i, d, d, i, vp]
         L.bf_serve_create.argtypes = [P(bf_serve_config), P(vp)]
         L.bf_serve_submit.argtypes = [vp, P(bf_request), P(C.c_uint64)]
         L.bf_serve_poll.argtypes = [vp, C.c_uint64, i, P(bf_result)]
@@ -191,7 +192,8 @@ def bf_coeffs(plan: Plan) -> dict:
     }
 
 
-INFO_KEYS = ("tw", "th", "threads", "nk", "groups", "launches", "smem", "scratch_kib", "ring", "depth", "ncols")
+INFO_KEYS = ("tw", "th", "threads", "nk", "groups", "launches", "smem", "scratch_kib", "ring", "depth", "ncols",
+             "packed")
 
 
 def bf_launch_info(plan: Plan, height: int, width: int) -> dict:
@@ -276,6 +278,14 @@ def bf_exact(src, dst, spatial=KERNEL_GAUSSIAN, sigma_s=4.0, radius=0, range=KER
     op, opitch, _, _ = _ptr_pitch(dst)
     _check(lib().bf_exact(ip, ipitch, op, opitch, h, w, spatial, sigma_s, radius, range, sigma_r,
                           _stream_handle(stream)), "bf_exact")
+
+
+def bf_exact_lut(src, dst, levels=256, data_range=1.0, spatial=KERNEL_GAUSSIAN, sigma_s=4.0, radius=0,
+                 range=KERNEL_GAUSSIAN, sigma_r=0.1, stream=None) -> None:
+    ip, ipitch, h, w = _ptr_pitch(src)
+    op, opitch, _, _ = _ptr_pitch(dst)
+    _check(lib().bf_exact_lut(ip, ipitch, op, opitch, h, w, spatial, sigma_s, radius, range, sigma_r, data_range,
+                              levels, _stream_handle(stream)), "bf_exact_lut")
 
 
 def bf_version() -> int:

@@ -31,6 +31,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct ClassLaunch {
     int m, nk, ncols, n_items, grid;
+    bool packed;
     size_t item_off;   // byte offset of the class's first item in the buffer
     size_t cursor_off;
 };
@@ -67,23 +68,29 @@ bf_status build_batch(const bf_plan *const *plans, const bf_image *images, int n
     L = BatchLayout();
     L.n = n;
     const int sms = device_sm_count();
-    std::map<int, std::vector<int>> by_class;
-    for (int i = 0; i < n; ++i) by_class[plans[i]->m].push_back(i);
+    // one persistent launch per (windows per axis, kernel family): plans whose selected terms are
+    // consecutive use the packed-pair family, the others the scalar family (no padded term groups)
+    std::map<std::pair<int, int>, std::vector<int>> by_class;
+    for (int i = 0; i < n; ++i) {
+        const FilterParams &kp = plans[i]->kp;
+        by_class[{plans[i]->m, kp.k[kp.nr - 1] - kp.k[0] + 1 == kp.nr ? 1 : 0}].push_back(i);
+    }
     L.params.resize(n);
     L.imgs.resize(n);
     L.scratch_off.assign(n, SIZE_MAX);
     size_t scratch = 0;
     std::vector<std::vector<WorkItem>> class_items;
     for (auto &kv : by_class) {
-        const int m = kv.first;
+        const int m = kv.first.first;
+        const bool packed = kv.first.second != 0;
         int rx_max = 0;
         for (int i : kv.second) rx_max = std::max(rx_max, plans[i]->kp.rx);
         // column threads: room for a 128-column tile next to the widest halo
         int ncols = std::min(448, ((2 * rx_max + 128 + 31) / 32) * 32);
-        int nk = batch_class_nk(m, ncols);
+        int nk = batch_class_nk(m, ncols, packed);
         while (nk == 0 && ncols > 2 * rx_max + 32) {
             ncols -= 32;
-            nk = batch_class_nk(m, ncols);
+            nk = batch_class_nk(m, ncols, packed);
         }
         if (nk == 0 || ncols < 2 * rx_max + 8) return fail(BF_ERR_UNSUPPORTED, "batched tile cannot hold this reach");
         std::vector<std::pair<double, WorkItem>> its;
@@ -91,12 +98,13 @@ bf_status build_batch(const bf_plan *const *plans, const bf_image *images, int n
             const bf_plan *p = plans[i];
             const bf_image &im = images[i];
             const FilterParams &kp = p->kp;
-            const int groups = term_groups(kp, nk);
+            const int groups = packed ? term_groups(kp, nk) : (kp.nr + nk - 1) / nk;
             int tw = ((ncols - 2 * kp.rx) / 8) * 8;
             tw = std::min(tw, ((im.width + 7) / 8) * 8);
             const int vspan = kp.vhi - kp.vlo + 1;
             const int th = std::min(im.height, std::max(48, vspan));
-            if (!term_layout(kp, nk, L.params[i]))
+            if (!packed) L.params[i] = kp;
+            else if (!term_layout(kp, nk, L.params[i]))
                 return fail(BF_ERR_UNSUPPORTED, "the plan's terms need more than 128 slots at this class");
             BatchImage &b = L.imgs[i];
             b.in = im.d_in;
@@ -127,6 +135,7 @@ bf_status build_batch(const bf_plan *const *plans, const bf_image *images, int n
         ClassLaunch cl;
         cl.m = m;
         cl.nk = nk;
+        cl.packed = packed;
         cl.ncols = ncols;
         cl.n_items = (int)items.size();
         cl.grid = std::max(1, std::min(cl.n_items, sms * batch_ctas_per_sm(m, nk, ncols)));
@@ -157,7 +166,7 @@ bf_status enqueue_batch(const BatchLayout &L, uint8_t *d_buf, const uint8_t *h_s
     const auto *d_params = reinterpret_cast<const FilterParams *>(d_buf + L.off_params);
     const auto *d_imgs = reinterpret_cast<const BatchImage *>(d_buf + L.off_imgs);
     for (const auto &cl : L.launches) {
-        bf_status st = launch_batch_class(cl.m, cl.nk, cl.ncols, d_imgs, d_params,
+        bf_status st = launch_batch_class(cl.m, cl.nk, cl.packed, cl.ncols, d_imgs, d_params,
                                           reinterpret_cast<const WorkItem *>(d_buf + cl.item_off), cl.n_items,
                                           reinterpret_cast<int *>(d_buf + cl.cursor_off), cl.grid, s);
         if (st != BF_OK) return st;

@@ -1,0 +1,27 @@
+// Kernel class tables of the fused filter: one entry per (windows per axis M, cosine terms per CTA NK),
+// filled by the translation units that instantiate the kernels (kernels_*.cu).
+#pragma once
+
+namespace bfi {
+
+constexpr int kScanThreads = 64;  // two scan warps per CTA
+
+struct KernelClass {
+    int m, nk;
+    const void *fn[2];  // tile kernels without / with the basis ring
+    const void *batch_fn;
+};
+
+// Packed-pair family (terms in consecutive pairs; bf_tile.cuh): kernels_m*.cu.
+extern const KernelClass kClassesM1[];
+extern const KernelClass kClassesM2[];
+extern const KernelClass kClassesM3[];
+extern const KernelClass kClassesM4to6[];
+extern const int kNumClassesM1, kNumClassesM2, kNumClassesM3, kNumClassesM4to6;
+
+// Scalar family (any term set; bf_tile_scalar.cuh): kernels_s_*.cu.
+extern const KernelClass kScalarClassesM1M2[];
+extern const KernelClass kScalarClassesM3to6[];
+extern const int kNumScalarClassesM1M2, kNumScalarClassesM3to6;
+
+}  // namespace bfi

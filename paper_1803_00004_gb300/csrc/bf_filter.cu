@@ -75,27 +75,38 @@ __global__ void bf_finalize_kernel(const float *__restrict__ in, size_t in_pitch
     out[(size_t)y * out_pitch + x] = (den > den_eps) ? num / den + i_lo : in[(size_t)y * in_pitch + x];
 }
 
-// All kernel classes, largest term count first within a window count.
+// All kernel classes of a family, largest term count first within a window count.
 struct ClassList {
-    std::vector<KernelClass> v;
+    std::vector<KernelClass> v[2];  // [packed]
     ClassList() {
-        auto add = [&](const KernelClass *a, int n) { v.insert(v.end(), a, a + n); };
-        add(kClassesM1, kNumClassesM1);
-        add(kClassesM2, kNumClassesM2);
-        add(kClassesM3, kNumClassesM3);
-        add(kClassesM4to6, kNumClassesM4to6);
+        auto add = [&](int f, const KernelClass *a, int n) { v[f].insert(v[f].end(), a, a + n); };
+        add(1, kClassesM1, kNumClassesM1);
+        add(1, kClassesM2, kNumClassesM2);
+        add(1, kClassesM3, kNumClassesM3);
+        add(1, kClassesM4to6, kNumClassesM4to6);
+        add(0, kScalarClassesM1M2, kNumScalarClassesM1M2);
+        add(0, kScalarClassesM3to6, kNumScalarClassesM3to6);
     }
 };
-const std::vector<KernelClass> &classes() {
+const std::vector<KernelClass> &classes(bool packed) {
     static ClassList c;
-    return c.v;
+    return c.v[packed ? 1 : 0];
 }
 
-const void *find_kernel(int m, int nk, bool ring) {
-    for (const auto &c : classes())
+const void *find_kernel(int m, int nk, bool ring, bool packed) {
+    for (const auto &c : classes(packed))
         if (c.m == m && c.nk == nk) return c.fn[ring ? 1 : 0];
     return nullptr;
 }
+
+// Term groups of a launch: packed family, greedy windows of NK consecutive frequencies; scalar family,
+// consecutive slices of NK selected terms.
+int family_groups(const FilterParams &p, int nk, bool packed) {
+    return packed ? term_groups(p, nk) : (p.nr + nk - 1) / nk;
+}
+
+// The selection has gaps (the packed family then pads groups with zero-weight frequencies).
+bool gapped_terms(const FilterParams &p) { return p.k[p.nr - 1] - p.k[0] + 1 != p.nr; }
 
 size_t smem_bytes(int m, int nk, int ncols, int tw, int depth = 2) {
     return sizeof(float) * ((size_t)depth * (m * nk * 4 + 2) * (ncols + 2) + (size_t)depth * nk * 2 * tw);
@@ -115,6 +126,59 @@ int device_sms() {
         return n;
     }();
     return sms;
+}
+
+// Brute-force Eq. (1) with the range kernel read from a table (the look-up-table baseline of Sec. V,
+// Case 2): lut[n] = K_r(n step), n = 0 .. levels - 1, read at the entry nearest to |I(x) - I(y)| (the
+// index rounded to nearest-even in fp32); spatial weights from a (2R + 1)^2 table.  A 32 x 8 block of
+// outputs with its (32 + 2R) x (8 + 2R) input tile, the two tables and the tile in shared memory.
+__global__ void __launch_bounds__(256) bf_bft_kernel(const float *__restrict__ in, size_t in_pitch,
+                                                     float *__restrict__ out, size_t out_pitch, int H, int W,
+                                                     int spatial, float sigma_s, int R, int range, float sigma_r,
+                                                     int levels, float step, float inv_step) {
+    extern __shared__ float sm[];
+    const int sw_n = (2 * R + 1) * (2 * R + 1);
+    const int pw = 32 + 2 * R, ph = 8 + 2 * R;
+    float *lut = sm, *sw = sm + levels, *tile = sw + sw_n;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    for (int n = tid; n < levels; n += 256) {
+        const float t = n * step;
+        lut[n] = range == BF_KERNEL_GAUSSIAN      ? expf(-t * t / (2.f * sigma_r * sigma_r))
+                 : range == BF_KERNEL_EXPONENTIAL ? expf(-t / sigma_r)
+                                                  : (t <= sigma_r ? 1.f : 0.f);
+    }
+    for (int i = tid; i < sw_n; i += 256) {
+        const int dy = i / (2 * R + 1) - R, dx = i % (2 * R + 1) - R;
+        const float r2 = (float)(dx * dx + dy * dy);
+        sw[i] = spatial == BF_KERNEL_BOX           ? 1.f
+                : spatial == BF_KERNEL_EXPONENTIAL ? expf(-sqrtf(r2) / sigma_s)
+                                                   : expf(-r2 / (2.f * sigma_s * sigma_s));
+    }
+    const int xb = blockIdx.x * 32 - R, yb = blockIdx.y * 8 - R;
+    for (int i = tid; i < pw * ph; i += 256) {
+        const int gy = yb + i / pw, gx = xb + i % pw;
+        tile[i] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? __ldg(in + (size_t)gy * in_pitch + gx) : 0.f;
+    }
+    __syncthreads();
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+    if (x >= W || y >= H) return;
+    const float *c = tile + (threadIdx.y + R) * pw + threadIdx.x + R;
+    const float ix = c[0];
+    // neighbours outside the image are excluded (the loop bounds stop at the border)
+    const int dy0 = max(-R, -y), dy1 = min(R, H - 1 - y), dx0 = max(-R, -x), dx1 = min(R, W - 1 - x);
+    float num = 0.f, den = 0.f;
+    for (int dy = dy0; dy <= dy1; ++dy) {
+        const float *row = c + dy * pw;
+        const float *swr = sw + (dy + R) * (2 * R + 1) + R;
+        for (int dx = dx0; dx <= dx1; ++dx) {
+            const float iy = row[dx];
+            const int n = min(__float2int_rn(fabsf(ix - iy) * inv_step), levels - 1);
+            const float wgt = swr[dx] * lut[n];
+            num = fmaf(wgt, iy, num);
+            den += wgt;
+        }
+    }
+    out[(size_t)y * out_pitch + x] = num / den;
 }
 
 __global__ void bf_exact_kernel(const float *__restrict__ in, size_t in_pitch, float *__restrict__ out,
@@ -179,10 +243,13 @@ std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int w
     const int vspan = p.vhi - p.vlo + 1;
     const int wpad = ((width + 7) / 8) * 8;
     std::vector<std::pair<double, TileConfig>> all;
-    for (const auto &cls : classes()) {
+    // the scalar family competes only for gapped selections (otherwise it does the same groups, slower)
+    for (int packed = 1; packed >= (gapped_terms(p) ? 0 : 1); --packed)
+    for (const auto &cls : classes(packed)) {
         if (cls.m != p.m) continue;
-        const int groups = term_groups(p, cls.nk);
-        if (groups * cls.nk > kMaxSlots) continue;
+        const int groups = family_groups(p, cls.nk, packed);
+        if (packed && groups * cls.nk > kMaxSlots) continue;
+        const double term_cost = packed ? 40.0 : 60.0;  // per term and window: the scalar family has no pairing
         // column threads in whole warps; the tile takes what the halo leaves
         for (int ncols = 32; ncols + kScanThreads <= 512; ncols += 32) {
             int tw = ((ncols - 2 * p.rx) / 8) * 8;
@@ -203,7 +270,7 @@ std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int w
                 for (int th : {16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 1024}) {
                     const int the = std::min(th, std::max(height, 1));
                     const long ctas = (long)((width + tw - 1) / tw) * ((height + the - 1) / the) * groups;
-                    const double per_cta = (double)ncols * (the + 0.3 * vspan) * (edge + 40.0 * cls.nk * p.m);
+                    const double per_cta = (double)ncols * (the + 0.3 * vspan) * (edge + term_cost * cls.nk * p.m);
                     const double waves = std::ceil((double)ctas / (sms * cps));
                     const double cost =
                         waves * per_cta * cps + (groups > 1 ? 16.0 * groups * (double)height * width : 0.0);
@@ -216,6 +283,7 @@ std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int w
                     tc.groups = groups;
                     tc.ring = ring;
                     tc.depth = depth;
+                    tc.packed = packed;
                     tc.smem = smem;
                     all.push_back({cost, tc});
                     if (the >= height) break;
@@ -239,8 +307,8 @@ int device_sm_count() { return device_sms(); }
 
 size_t batch_smem_bytes(int m, int nk, int ncols) { return smem_bytes(m, nk, ncols, ncols); }
 
-int batch_class_nk(int m, int ncols) {
-    for (const auto &c : classes())  // classes are listed with the largest term count first
+int batch_class_nk(int m, int ncols, bool packed) {
+    for (const auto &c : classes(packed))  // classes are listed with the largest term count first
         if (c.m == m && batch_smem_bytes(m, c.nk, ncols) <= 220 * 1024) return c.nk;
     return 0;
 }
@@ -254,11 +322,11 @@ int batch_ctas_per_sm(int m, int nk, int ncols) {
     return std::max(1, std::min({by_smem, by_threads, by_regs}));
 }
 
-bf_status launch_batch_class(int m, int nk, int ncols, const BatchImage *d_imgs, const FilterParams *d_params,
+bf_status launch_batch_class(int m, int nk, bool packed, int ncols, const BatchImage *d_imgs, const FilterParams *d_params,
                              const WorkItem *d_items, int n_items, int *d_cursor, int grid, void *stream) {
     if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");
     const void *fn = nullptr;
-    for (const auto &c : classes())
+    for (const auto &c : classes(packed))
         if (c.m == m && c.nk == nk) fn = c.batch_fn;
     if (!fn) return fail(BF_ERR_UNSUPPORTED, "no batched kernel for this class");
     const size_t smem = batch_smem_bytes(m, nk, ncols);
@@ -326,6 +394,7 @@ void fill_info(const TileConfig &tc, int height, int width, int *info) {
     info[8] = tc.ring ? 1 : 0;
     info[9] = tc.depth;
     info[10] = tc.ncols;
+    info[11] = tc.packed;
 }
 
 size_t scratch_bytes(const TileConfig &tc, int height, int width) {
@@ -338,13 +407,14 @@ bf_status launch_filter(const FilterParams &p, int precision, int kahan, const T
     (void)precision;
     (void)kahan;
     if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");
-    const void *fn = find_kernel(p.m, tc.nk, tc.ring != 0);
+    const void *fn = find_kernel(p.m, tc.nk, tc.ring != 0, tc.packed != 0);
     if (!fn || tc.ncols <= 0) return fail(BF_ERR_UNSUPPORTED, "no kernel class for this plan and image");
     if (tc.threads > 512) return fail(BF_ERR_UNSUPPORTED, "horizontal reach too large for one CTA");
     // the tile body needs whole warps of column threads (its two scan warps meet on a 64-thread named
     // barrier) and tile widths in blocks of 8 columns; geometries from a cache file are checked here
     if (tc.ncols % 32 != 0 || tc.threads != tc.ncols + kScanThreads || tc.tw < 8 || tc.tw % 8 != 0 ||
-        tc.tw + 2 * p.rx > tc.ncols || tc.th < 1 || (tc.depth != 2 && tc.depth != 3) || tc.nk < 2 || tc.nk % 2 != 0)
+        tc.tw + 2 * p.rx > tc.ncols || tc.th < 1 || (tc.depth != 2 && tc.depth != 3) || tc.nk < 1 ||
+        (tc.packed && tc.nk % 2 != 0))
         return fail(BF_ERR_INVALID_ARG, "malformed launch geometry");
     if (tc.smem > 227 * 1024) return fail(BF_ERR_UNSUPPORTED, "tile needs more than 227 KB of shared memory");
     if (tc.groups > 1 && !d_scratch) return fail(BF_ERR_INVALID_ARG, "missing scratch for grouped launch");
@@ -354,8 +424,9 @@ bf_status launch_filter(const FilterParams &p, int precision, int kahan, const T
     int tw = tc.tw, th = tc.th, ncols = tc.ncols, H = height, W = width, depth = tc.depth;
     const float *in = d_in;
     float *out = d_out, *part = d_scratch;
-    FilterParams pp;
-    if (!term_layout(p, tc.nk, pp) || pp.nr != tc.groups * tc.nk)
+    FilterParams pp = p;  // scalar family: the selection as the plan holds it
+    if (tc.packed ? !term_layout(p, tc.nk, pp) || pp.nr != tc.groups * tc.nk
+                  : tc.groups != (p.nr + tc.nk - 1) / tc.nk)
         return fail(BF_ERR_INVALID_ARG, "launch geometry does not match the plan's term groups");
     void *args[] = {(void *)&in, (void *)&in_pitch, (void *)&out, (void *)&out_pitch, (void *)&part, (void *)&H,
                     (void *)&W, (void *)&tw, (void *)&th, (void *)&ncols, (void *)&depth, (void *)&pp};
@@ -380,6 +451,24 @@ bf_status launch_exact(const float *d_in, size_t in_pitch, float *d_out, size_t 
                                                              sigma_s, radius, range, sigma_r);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "exact launch");
+    return BF_OK;
+}
+
+bf_status launch_exact_lut(const float *d_in, size_t in_pitch, float *d_out, size_t out_pitch, int height, int width,
+                           int spatial, float sigma_s, int radius, int range, float sigma_r, float data_range,
+                           int levels, void *stream) {
+    if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");
+    const size_t smem = sizeof(float) * ((size_t)levels + (size_t)(2 * radius + 1) * (2 * radius + 1) +
+                                         (size_t)(32 + 2 * radius) * (8 + 2 * radius));
+    cudaError_t e = cudaFuncSetAttribute(bf_bft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    const float inv_step = (float)((levels - 1) / (double)data_range), step = (float)(data_range / (levels - 1));
+    dim3 block(32, 8), grid((width + 31) / 32, (height + 7) / 8);
+    bf_bft_kernel<<<grid, block, smem, (cudaStream_t)stream>>>(d_in, in_pitch, d_out, out_pitch, height, width,
+                                                               spatial, sigma_s, radius, range, sigma_r, levels,
+                                                               step, inv_step);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "look-up-table exact launch");
     return BF_OK;
 }
 

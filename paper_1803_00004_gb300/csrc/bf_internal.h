@@ -55,6 +55,7 @@ struct TileConfig {
     int groups;    // term groups (grid.z); > 1 writes partial planes + finalize
     int ring;      // 1: per-column ring of basis inputs in shared memory
     int depth;     // exchange buffers: 2 (two barriers per row) or 3 (one barrier per row)
+    int packed;    // 1: packed-pair family (consecutive term groups); 0: scalar family (any term set)
     size_t smem;   // dynamic shared memory bytes
 };
 
@@ -91,7 +92,7 @@ int term_groups(const FilterParams &p, int nk);
 bool term_layout(const FilterParams &p, int nk, FilterParams &out);
 
 // Writes the geometry record (kInfoInts ints) of bf_launch_info / bf_autotune.
-constexpr int kInfoInts = 11;
+constexpr int kInfoInts = 12;
 void fill_info(const TileConfig &tc, int height, int width, int *info);
 
 std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int width, int precision, int max_n);
@@ -105,18 +106,21 @@ bf_status launch_filter(const FilterParams &p, int precision, int kahan, const T
 bf_status launch_exact(const float *d_in, size_t in_pitch_elems, float *d_out, size_t out_pitch_elems,
                        int height, int width, int spatial, float sigma_s, int radius, int range, float sigma_r,
                        void *stream);
+bf_status launch_exact_lut(const float *d_in, size_t in_pitch, float *d_out, size_t out_pitch, int height, int width,
+                           int spatial, float sigma_s, int radius, int range, float sigma_r, float data_range,
+                           int levels, void *stream);
 bool debug_consume_launch_failure();
 
 // ---- persistent batched launch (bf_filter.cu) ----
 // Terms per CTA used for kernel class m in batched launches, the shared-memory
 // bytes a launch with `ncols` column threads needs, and the resident CTAs per SM.
-int batch_class_nk(int m, int ncols);
+int batch_class_nk(int m, int ncols, bool packed);
 size_t batch_smem_bytes(int m, int nk, int ncols);
 int batch_ctas_per_sm(int m, int nk, int ncols);
 int device_sm_count();
 // Enqueues the persistent kernel of class (m, nk) over n_items items (cursor: one
 // device int set to 0 before the launch) on `stream`.
-bf_status launch_batch_class(int m, int nk, int ncols, const BatchImage *d_imgs, const FilterParams *d_params,
+bf_status launch_batch_class(int m, int nk, bool packed, int ncols, const BatchImage *d_imgs, const FilterParams *d_params,
                              const WorkItem *d_items, int n_items, int *d_cursor, int grid, void *stream);
 // Batch of images in persistent launches without graph capture (device
 // buffers allocated and freed stream-ordered on `stream`), and the device bytes

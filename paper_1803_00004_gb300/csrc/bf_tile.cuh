@@ -5,11 +5,11 @@
 
 #include <cuda_runtime.h>
 
+#include "bf_classes.h"
 #include "bf_internal.h"
 
 namespace bfi {
 
-constexpr int kScanThreads = 64;  // two scan warps
 
 namespace {
 
@@ -481,23 +481,8 @@ bf_batch_kernel(const BatchImage *__restrict__ imgs, const FilterParams *__restr
 
 }  // namespace
 
-// Kernel classes: windows per axis M and terms per group NK (NK * M <= 16, and
-// no class spills registers).
-struct KernelClass {
-    int m, nk;
-    const void *fn[2];  // tile kernels without / with the basis ring
-    const void *batch_fn;
-};
-
 #define BF_CLASS(M, NK)                                                                                 \
     {M, NK, {(const void *)bf_fused_kernel<NK, M, false>, (const void *)bf_fused_kernel<NK, M, true>},  \
      (const void *)bf_batch_kernel<NK, M>}
-
-// Per-TU class tables (kernels_m*.cu).
-extern const KernelClass kClassesM1[];
-extern const KernelClass kClassesM2[];
-extern const KernelClass kClassesM3[];
-extern const KernelClass kClassesM4to6[];
-extern const int kNumClassesM1, kNumClassesM2, kNumClassesM3, kNumClassesM4to6;
 
 }  // namespace bfi

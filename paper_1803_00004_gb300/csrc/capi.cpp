@@ -194,6 +194,21 @@ bf_status bf_exact(const float *d_in, size_t in_pitch, float *d_out, size_t out_
                         (float)sigma_s, R, range, (float)sigma_r, stream);
 }
 
+bf_status bf_exact_lut(const float *d_in, size_t in_pitch, float *d_out, size_t out_pitch, int height, int width,
+                       int spatial, double sigma_s, int radius, int range, double sigma_r, double data_range,
+                       int levels, void *stream) {
+    bf_status st = check_image(d_in, in_pitch, d_out, out_pitch, height, width);
+    if (st != BF_OK || height == 0 || width == 0) return st;
+    if (!(sigma_s > 0) || !(sigma_r > 0) || radius < 0 || !(data_range > 0) || levels < 2 || levels > 4096)
+        return fail(BF_ERR_INVALID_ARG, "bad look-up-table exact-filter parameters");
+    if (spatial < BF_KERNEL_GAUSSIAN || spatial > BF_KERNEL_BOX) return fail(BF_ERR_INVALID_ARG, "spatial kernel");
+    if (range < BF_KERNEL_GAUSSIAN || range > BF_KERNEL_BOX) return fail(BF_ERR_INVALID_ARG, "range kernel");
+    int R = radius > 0 ? radius : (int)(3.0 * sigma_s + 0.5);
+    if (R > 32) return fail(BF_ERR_UNSUPPORTED, "look-up-table exact filter: radius above 32");
+    return launch_exact_lut(d_in, in_pitch / sizeof(float), d_out, out_pitch / sizeof(float), height, width, spatial,
+                            (float)sigma_s, R, range, (float)sigma_r, (float)data_range, levels, stream);
+}
+
 const char *bf_status_string(bf_status s) {
     switch (s) {
         case BF_OK: return "ok";

@@ -45,9 +45,9 @@ void load_locked() {
     int k[9];
     TileConfig tc;
     unsigned long smem;
-    while (std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %lu", &k[0], &k[1], &k[2], &k[3], &k[4],
+    while (std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %lu", &k[0], &k[1], &k[2], &k[3], &k[4],
                        &k[5], &k[6], &k[7], &k[8], &tc.tw, &tc.th, &tc.ncols, &tc.threads, &tc.nk, &tc.groups,
-                       &tc.ring, &tc.depth, &smem) == 18) {
+                       &tc.ring, &tc.depth, &tc.packed, &smem) == 19) {
         tc.smem = smem;
         g_table[Key{k[0], k[1], k[2], k[3], k[4], k[5], k[6], k[7], k[8]}] = tc;
     }
@@ -59,10 +59,10 @@ void save_locked(const Key &key, const TileConfig &tc) {
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %lu\n", std::get<0>(key), std::get<1>(key),
+    std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %lu\n", std::get<0>(key), std::get<1>(key),
                  std::get<2>(key), std::get<3>(key), std::get<4>(key), std::get<5>(key), std::get<6>(key),
                  std::get<7>(key), std::get<8>(key), tc.tw, tc.th, tc.ncols, tc.threads, tc.nk, tc.groups, tc.ring,
-                 tc.depth, (unsigned long)tc.smem);
+                 tc.depth, tc.packed, (unsigned long)tc.smem);
     std::fclose(f);
 }
 
@@ -85,7 +85,9 @@ TileConfig choose_tile(const FilterParams &p, int height, int width, int precisi
         load_locked();
         auto it = g_table.find(make_key(p, height, width, precision));
         // an entry stays usable only while its term grouping matches this build's layout
-        if (it != g_table.end() && it->second.groups == term_groups(p, it->second.nk)) return it->second;
+        if (it != g_table.end() &&
+            it->second.groups == (it->second.packed ? term_groups(p, it->second.nk) : (p.nr + it->second.nk - 1) / it->second.nk))
+            return it->second;
     }
     return model_tile(p, height, width, precision);
 }
@@ -115,7 +117,7 @@ extern "C" bf_status bf_autotune(const bf_plan *plan, int height, int width, voi
     std::vector<TileConfig> ranked = tile_candidates(plan->kp, height, width, plan->desc.precision, 100000), cands;
     std::map<std::pair<int, int>, int> per_family;
     for (const auto &c : ranked)
-        if (per_family[{c.ring * 4 + c.depth, c.nk}]++ < 4) cands.push_back(c);
+        if (per_family[{c.ring * 4 + c.depth + 8 * c.packed, c.nk}]++ < 4) cands.push_back(c);
     bf_status st = BF_OK;
     float *in = nullptr, *out = nullptr, *scratch = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -216,7 +218,7 @@ extern "C" bf_status bf_set_launch(const bf_plan *plan, int height, int width, c
         fill_info(c, height, width, got);
         // the fields a caller chooses; the rest (threads, launches, bytes) follow from them
         if (got[0] == info[0] && got[1] == info[1] && got[3] == info[3] && got[8] == info[8] && got[9] == info[9] &&
-            got[10] == info[10]) {
+            got[10] == info[10] && got[11] == info[11]) {
             remember_tile(plan->kp, height, width, plan->desc.precision, c);
             return BF_OK;
         }

@@ -118,6 +118,11 @@ def test_plan_create_rejects(kw, status):
 def test_filter_argument_checks_without_gpu():
     p = bf.Plan(device=-1)
     L = bf.lib()
+    # look-up-table brute force: parameters are checked before any device work
+    assert L.bf_exact_lut(4096, 256, 1 << 20, 256, 4, 64, 0, 2.0, 0, 0, 0.1, 1.0, 1, None) == 1    # levels < 2
+    assert L.bf_exact_lut(4096, 256, 1 << 20, 256, 4, 64, 0, 2.0, 0, 0, 0.1, 1.0, 8192, None) == 1  # levels > 4096
+    assert L.bf_exact_lut(4096, 256, 1 << 20, 256, 4, 64, 0, 2.0, 40, 0, 0.1, 1.0, 256, None) == 2  # radius > 32
+    assert L.bf_exact_lut(4096, 256, 1 << 20, 256, 4, 64, 0, 2.0, 0, 0, 0.1, 0.0, 256, None) == 1   # data range
     # overlapping input/output -> invalid argument before any device work
     assert L.bf_filter(p.handle, 4096, 256, 4096 + 128, 256, 4, 64, None) == 1
     # bad pitch
@@ -224,7 +229,7 @@ print(json.dumps(out))
     written, read = json.loads(w.stdout), json.loads(r.stdout)
     assert written == read
     lines = cache.read_text().splitlines()
-    assert len(lines) == 3 and all(len(x.split()) == 18 for x in lines)
+    assert len(lines) == 3 and all(len(x.split()) == 19 for x in lines)
     fresh = json.loads(subprocess.run([sys.executable, "-c", code, "read"], env=dict(os.environ, PYTHONPATH=ROOT),
                                       capture_output=True, text=True, check=True).stdout)
     assert fresh != read                               # without the file: the cost model's choice
@@ -248,10 +253,15 @@ def test_term_groups_cover_the_selection(kw):
                 i += 1
         return groups
 
+    # packed family: greedy windows; scalar family (offered only for gapped selections): slices of NK terms
+    consecutive = k == list(range(k[0], k[0] + len(k)))
     seen = set()
     for c in bf.bf_launch_candidates(plan, 300, 500):
-        assert c["groups"] == greedy(c["nk"]) and c["groups"] * c["nk"] <= 128
-        seen.add(c["nk"])
-    assert seen
-    if k == list(range(len(k))):                       # consecutive selection: ceil(N_r / NK) groups
-        assert all(greedy(nk) == -(-len(k) // nk) for nk in seen)
+        if c["packed"]:
+            assert c["groups"] == greedy(c["nk"]) and c["groups"] * c["nk"] <= 128 and c["nk"] % 2 == 0
+        else:
+            assert not consecutive and c["groups"] == -(-len(k) // c["nk"])
+        seen.add((c["packed"], c["nk"]))
+    assert {f for f, _ in seen} == ({1} if consecutive else {0, 1})
+    if consecutive:                                    # ceil(N_r / NK) groups
+        assert all(greedy(nk) == -(-len(k) // nk) for _, nk in seen)

@@ -208,3 +208,35 @@ def test_kahan_switch_on_long_rows():
         err[k] = float(np.max(np.abs(got - ref)))
     assert err[1] < TOL, err
     assert err[0] < 10 * TOL, err
+
+
+@pytest.mark.parametrize("H,W,kw,levels", [
+    (90, 131, dict(sigma_s=1.0, sigma_r=0.1), 256),
+    (67, 45, dict(sigma_s=2.0, sigma_r=0.05, range=bf.KERNEL_EXPONENTIAL), 1024),
+    (40, 300, dict(sigma_s=1.0, radius=6, sigma_r=0.2, spatial=bf.KERNEL_EXPONENTIAL), 64),
+    (9, 5, dict(sigma_s=3.0, sigma_r=0.1), 256),                       # window larger than the image
+    (33, 70, dict(sigma_s=10.0, radius=32, sigma_r=0.3, range=bf.KERNEL_BOX), 4096),
+])
+def test_exact_lut_matches_oracle(H, W, kw, levels):
+    """The look-up-table brute force against the oracle's same table rule (the entry index is decided in
+    fp32 on both sides)."""
+    img = synth.shapes(H, W, 18, scale=0.1)
+    src = torch.from_numpy(img).cuda()
+    dst = torch.full_like(src, float("nan"))
+    bf.bf_exact_lut(src, dst, levels=levels, **kw)
+    torch.cuda.synchronize()
+    ref = O.exact_bf_lut(img.astype(np.float64), O.Desc(**kw), levels, threads=THREADS)
+    assert np.max(np.abs(dst.cpu().numpy() - ref)) < 1e-5
+
+
+def test_exact_lut_full_size_8bit():
+    """1920x1080 with 8-bit-valued data (k / 255) and a 256-entry table, R = 3: the whole image against the
+    oracle's table rule."""
+    img = (np.round(synth.shapes(1080, 1920, seed=0) * 255) / 255).astype(np.float32)
+    kw = dict(sigma_s=1.0, sigma_r=0.1)
+    src = torch.from_numpy(img).cuda()
+    dst = torch.empty_like(src)
+    bf.bf_exact_lut(src, dst, levels=256, **kw)
+    torch.cuda.synchronize()
+    ref = O.exact_bf_lut(img.astype(np.float64), O.Desc(**kw), 256, threads=THREADS)
+    assert np.max(np.abs(dst.cpu().numpy() - ref)) < 1e-5

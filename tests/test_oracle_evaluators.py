@@ -197,3 +197,26 @@ def test_fast_denominator_is_eq1_denominator():
                 t = I[y, x] - I[y + dy, x + dx]
                 s += p.Ks[-dy + R, -dx + R] * np.sum(p.ak * np.cos(np.pi * p.ks * t / p.P))
     assert abs(den[y, x] - s) < 1e-12
+
+
+# --- the look-up-table brute force (Sec. V, Case 2) -------------------------------------------------------------
+
+@pytest.mark.parametrize("desc", [D(sigma_s=1.5, sigma_r=0.1), D(sigma_s=2.0, sigma_r=0.05, range=O.EXPONENTIAL),
+                                  D(spatial=O.EXPONENTIAL, sigma_s=1.0, sigma_r=0.2), D(sigma_s=1.0, range=O.BOX,
+                                                                                          sigma_r=0.3)])
+def test_lut_exact_on_grid_valued_images(desc):
+    """Values on the table's grid (k / 256 with 257 levels over [0, 1]): every difference is a grid point,
+    so the table holds the kernel's exact values there and the result is O1's."""
+    I = np.round(synth.uniform(19, 26, seed=4).astype(np.float64) * 256) / 256
+    assert np.max(np.abs(O.exact_bf_lut(I, desc, 257) - O.exact_bf(I, desc))) < 1e-15
+
+
+def test_lut_converges_to_exact():
+    """Off-grid data: the nearest entry is within step / 2 of |t|, so each range weight is within
+    max|K_r'| step / 2 of the exact one; the error shrinks with the step."""
+    I = synth.uniform(17, 23, seed=5).astype(np.float64)
+    desc = D(sigma_s=1.5, sigma_r=0.1)
+    errs = [np.max(np.abs(O.exact_bf_lut(I, desc, n) - O.exact_bf(I, desc))) for n in (64, 256, 1024, 1 << 16)]
+    assert all(a > b for a, b in zip(errs, errs[1:]))
+    slope = math.exp(-0.5) / 0.1                  # max |d/dt exp(-t^2 / (2 sigma^2))| = 1 / (sigma sqrt(e))
+    assert errs[-1] < 2 * slope * (1.0 / ((1 << 16) - 1))
