@@ -255,12 +255,14 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = run_e2e(args, bf, plans, img, dev, stream)
 
-    batched = serving = nr_sweep = large = None
+    batched = serving = nr_sweep = large = bft = pre = None
     if not args.no_extras and world == 1:
         batched = run_batched(bf, dev)
         serving = run_serving(bf, dev)
         nr_sweep = run_nr_sweep(bf, dev, src, flush)
         large = run_large(bf, dev, flush)
+        bft = run_bft_crossover(bf, dev, src, flush)
+        pre = run_precompute(bf, dev, src, flush)
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
@@ -279,6 +281,7 @@ def run_ours(args):
                 "bytes_per_px": 8},
         "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
         "batched": batched, "serving": serving, "nr_sweep": nr_sweep, "large_images": large,
+        "bft_crossover": bft, "precompute": pre,
         "e2e": e2e,
     }
     if rank == 0:
@@ -320,22 +323,76 @@ def run_e2e(args, bf, plans, img, dev, stream):
             "d2h_bytes_per_step": 4 * H * W * len(plans)}
 
 
-def timed_launches(bf, plan, src, out, flush, reps):
-    """Mean device time (ms) of bf_filter, events around each launch, L2 flushed before each."""
+def timed_calls(fn, flush, reps):
+    """Mean device time (ms) of fn(), events around each call, L2 flushed before each."""
     import torch
     for _ in range(2):
-        bf.bf_filter(plan, src, out)
+        fn()
     ms = []
     for _ in range(reps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        bf.bf_filter(plan, src, out)
+        fn()
         e1.record()
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
     return float(np.mean(ms))
+
+
+def timed_launches(bf, plan, src, out, flush, reps):
+    """Mean device time (ms) of bf_filter (see timed_calls)."""
+    return timed_calls(lambda: bf.bf_filter(plan, src, out), flush, reps)
+
+
+def run_precompute(bf, dev, src, flush, reps=5):
+    """Sec. V-C, Case 1 on the 1920x1080 image: the window sums of the frequencies k < 32 are computed once
+    (sigma_s = 8, truncation fixed at T_r = 0.9, so P is the same for every sigma_r <= 0.3); each later
+    sigma_r is then filtered from the cache (weighting only) and, for comparison, by the full filter
+    (autotuned).  Device ms of each."""
+    import torch
+    out = torch.empty_like(src)
+    base = dict(sigma_s=8.0, t_r=0.9, ns_terms=NS, nr_terms=NR, device=dev.index)
+    holder = {}
+
+    def build():
+        if "c" in holder:
+            holder["c"].close()
+        holder["c"] = bf.Cache(bf.Plan(sigma_r=0.3, **base), src, kmax=32)
+
+    t_pre = timed_calls(build, flush, 2)
+    cache = holder["c"]
+    rows = []
+    for sr in (0.1, 0.15, 0.2, 0.25, 0.3):
+        p = bf.Plan(sigma_r=sr, **base)
+        t_cached = timed_calls(lambda: cache.filter(p, src, out), flush, reps)
+        bf.bf_autotune(p, H, W)
+        t_full = timed_launches(bf, p, src, out, flush, reps)
+        rows.append({"sigma_r": sr, "cached_ms": round(t_cached, 4), "full_ms": round(t_full, 4)})
+    nbytes = cache.nbytes()
+    cache.close()
+    return {"sigma_s": 8.0, "t_r": 0.9, "kmax": 32, "cache_mib": round(nbytes / 2 ** 20, 1),
+            "precompute_ms": round(t_pre, 3), "by_sigma_r": rows}
+
+
+def run_bft_crossover(bf, dev, src, flush, reps=5):
+    """The brute-force filter with a look-up table (Sec. V, Case 2; 256-entry range table) against the method
+    (autotuned, N_r = 8, N_s = 5) on the 1920x1080 image at small radii R (sigma_s = R / 3, sigma_r = 0.1):
+    Mpixel/s of each.  The brute force costs (2R + 1)^2 taps per pixel; the method's cost is flat in R."""
+    import torch
+    out = torch.empty_like(src)
+    rows = []
+    for R in (1, 2, 3, 4, 6, 9, 12):
+        ss = R / 3.0
+        t_bft = timed_calls(lambda: bf.bf_exact_lut(src, out, levels=256, sigma_s=ss, radius=R, sigma_r=0.1),
+                            flush, reps)
+        p = bf.Plan(sigma_s=ss, radius=R, sigma_r=0.1, nr_terms=NR, ns_terms=NS, device=dev.index)
+        bf.bf_autotune(p, H, W)
+        t_ours = timed_launches(bf, p, src, out, flush, reps)
+        rows.append({"radius": R, "bft_mpix_s": round(H * W / (t_bft * 1e-3) / 1e6, 1),
+                     "method_mpix_s": round(H * W / (t_ours * 1e-3) / 1e6, 1)})
+    return {"sigma_r": 0.1, "levels": 256, "by_radius": rows}
 
 
 def run_nr_sweep(bf, dev, src, flush, reps=5):

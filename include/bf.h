@@ -236,6 +236,45 @@ bf_status bf_launch_candidates(const bf_plan *plan, int height, int width, int m
  * Errors: BF_ERR_INVALID_ARG (no such geometry), BF_ERR_NO_DEVICE. */
 bf_status bf_set_launch(const bf_plan *plan, int height, int width, const int *info);
 
+/* ---------------------------------------------------------------------- */
+/* Pre-computation for later range parameters (Sec. V-C, Case 1)            */
+/* ---------------------------------------------------------------------- */
+
+/* When the image is known before the range parameters, the box sums of the
+ * basis images can be computed once.  They depend only on the cosine
+ * half-period P, the intensity origin and the spatial kernel, not on the
+ * range weights a_k: a fixed truncation t_r (bf_plan_desc.t_r > 0) or the
+ * BF_RANGE_UNTRUNCATED_FULL policy gives plans for different sigma_r the same
+ * P (the paper's predefined T_ri).  The cache holds, per pixel and for every
+ * frequency k < kmax, the four window sums of cos(pi k t) I, sin(pi k t) I,
+ * cos(pi k t), sin(pi k t): 16 x kmax bytes per pixel, allocated by the
+ * library on the plan's device (kmax rounded up to whole term groups). */
+typedef struct bf_cache bf_cache;
+
+/* Runs the fused kernel over the frequencies 0 .. kmax-1 of `plan` on the
+ * height x width image d_in (row pitch in bytes) and returns the cache in
+ * *out (release with bf_cache_destroy).  2 <= kmax <= 128.  Asynchronous on
+ * `stream` after the allocation; *out is NULL on any error.  Errors: BF_ERR_INVALID_ARG, BF_ERR_NO_DEVICE,
+ * BF_ERR_OOM, BF_ERR_UNSUPPORTED, BF_ERR_CUDA. */
+bf_status bf_precompute(const bf_plan *plan, const float *d_in, size_t in_pitch_bytes, int height, int width,
+                        int kmax, void *stream, bf_cache **out);
+
+/* Filters with `plan` from the cache: Eq. (36)'s weighting of the cached sums
+ * by a_k cos/sin(pi k I(x) / P) and the divide; no box filtering.  d_in must
+ * be the image the cache was computed from (I(x) is read from it); d_out is a
+ * separate height x width buffer.  The plan must share the cache's P,
+ * intensity origin and spatial kernel (BF_ERR_INVALID_ARG otherwise), and
+ * select only frequencies below the cache's (BF_ERR_RANGE otherwise).
+ * Asynchronous on `stream`; order it after bf_precompute. */
+bf_status bf_filter_cached(const bf_cache *cache, const bf_plan *plan, const float *d_in, size_t in_pitch_bytes,
+                           float *d_out, size_t out_pitch_bytes, void *stream);
+
+/* Device bytes held by a cache. */
+size_t bf_cache_bytes(const bf_cache *cache);
+
+/* Releases a cache (NULL is a no-op); no work using it may be in flight. */
+void bf_cache_destroy(bf_cache *cache);
+
 /* One image of a batch. */
 typedef struct {
     const float *d_in;

@@ -5,7 +5,7 @@ include/bf.h); this package is its thin Python binding plus the seeded input
 generators in ``synth``.  Importing the package does not load the library; the
 first call does, and raises if it has not been built.
 """
-from ._binding import (BFError, Plan, Server, bf_coeffs, bf_exact, bf_exact_lut, bf_filter, bf_filter_batch,  # noqa: F401
+from ._binding import (BFError, Cache, Plan, Server, bf_coeffs, bf_exact, bf_exact_lut, bf_filter, bf_filter_batch,  # noqa: F401
                        bf_version,
                        bf_launch_info, bf_autotune, bf_launch_candidates, bf_set_launch,
                        bf_debug_fail_launches, desc, lib, LIB_PATH, EXPORTS)

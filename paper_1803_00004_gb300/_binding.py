@@ -63,7 +63,8 @@ EXPORTS = ["bf_plan_desc_default", "bf_plan_create", "bf_plan_destroy", "bf_coef
            "bf_launch_candidates", "bf_set_launch",
            "bf_filter", "bf_filter_noalloc",
            "bf_filter_batch",
-           "bf_exact", "bf_exact_lut", "bf_serve_create", "bf_serve_submit", "bf_serve_poll", "bf_serve_cancel", "bf_serve_destroy",
+           "bf_exact", "bf_exact_lut", "bf_precompute", "bf_filter_cached", "bf_cache_bytes", "bf_cache_destroy",
+           "bf_serve_create", "bf_serve_submit", "bf_serve_poll", "bf_serve_cancel", "bf_serve_destroy",
            "bf_status_string", "bf_last_error", "bf_version", "bf_debug_fail_launches"]
 
 _lib = None
@@ -98,6 +99,12 @@ def lib():
         L.bf_filter_batch.argtypes = [P(vp), P(bf_image), i, vp]
         L.bf_exact.argtypes = [vp, sz, vp, sz, i, i, i, d, i, i, d, vp]
         L.bf_exact_lut.argtypes = [vp, sz, vp, sz, i, i, i, d, i, i, d, d, i, vp]
+        L.bf_precompute.argtypes = [vp, vp, sz, i, i, i, vp, P(vp)]
+        L.bf_filter_cached.argtypes = [vp, vp, vp, sz, vp, sz, vp]
+        L.bf_cache_bytes.argtypes = [vp]
+        L.bf_cache_bytes.restype = sz
+        L.bf_cache_destroy.argtypes = [vp]
+        L.bf_cache_destroy.restype = None
         L.bf_serve_create.argtypes = [P(bf_serve_config), P(vp)]
         L.bf_serve_submit.argtypes = [vp, P(bf_request), P(C.c_uint64)]
         L.bf_serve_poll.argtypes = [vp, C.c_uint64, i, P(bf_result)]
@@ -286,6 +293,36 @@ def bf_exact_lut(src, dst, levels=256, data_range=1.0, spatial=KERNEL_GAUSSIAN, 
     op, opitch, _, _ = _ptr_pitch(dst)
     _check(lib().bf_exact_lut(ip, ipitch, op, opitch, h, w, spatial, sigma_s, radius, range, sigma_r, data_range,
                               levels, _stream_handle(stream)), "bf_exact_lut")
+
+
+class Cache:
+    """Owns a bf_cache* (the pre-computed window sums of one image, Sec. V-C, Case 1)."""
+
+    def __init__(self, plan: "Plan", src, kmax: int, stream=None):
+        ip, ipitch, h, w = _ptr_pitch(src)
+        self.handle = C.c_void_p()
+        _check(lib().bf_precompute(plan.handle, ip, ipitch, h, w, kmax, _stream_handle(stream), C.byref(self.handle)),
+               "bf_precompute")
+
+    def filter(self, plan: "Plan", src, dst, stream=None) -> None:
+        ip, ipitch, _, _ = _ptr_pitch(src)
+        op, opitch, _, _ = _ptr_pitch(dst)
+        _check(lib().bf_filter_cached(self.handle, plan.handle, ip, ipitch, op, opitch, _stream_handle(stream)),
+               "bf_filter_cached")
+
+    def nbytes(self) -> int:
+        return int(lib().bf_cache_bytes(self.handle))
+
+    def close(self) -> None:
+        if self.handle:
+            lib().bf_cache_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def bf_version() -> int:

@@ -6,6 +6,10 @@ namespace bfi {
 
 constexpr int kScanThreads = 64;  // two scan warps per CTA
 
+// Output of a tile: Î (divide and store), a term group's partial numerator / denominator planes, or the
+// window sums of each frequency (the pre-computation cache; packed family only).
+constexpr int kModeFinal = 0, kModePartial = 1, kModeCache = 2;
+
 struct KernelClass {
     int m, nk;
     const void *fn[2];  // tile kernels without / with the basis ring

@@ -403,7 +403,7 @@ size_t scratch_bytes(const TileConfig &tc, int height, int width) {
 
 bf_status launch_filter(const FilterParams &p, int precision, int kahan, const TileConfig &tc, const float *d_in,
                         size_t in_pitch, float *d_out, size_t out_pitch, float *d_scratch, int height, int width,
-                        void *stream) {
+                        void *stream, bool cache_mode) {
     (void)precision;
     (void)kahan;
     if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");
@@ -417,7 +417,8 @@ bf_status launch_filter(const FilterParams &p, int precision, int kahan, const T
         (tc.packed && tc.nk % 2 != 0))
         return fail(BF_ERR_INVALID_ARG, "malformed launch geometry");
     if (tc.smem > 227 * 1024) return fail(BF_ERR_UNSUPPORTED, "tile needs more than 227 KB of shared memory");
-    if (tc.groups > 1 && !d_scratch) return fail(BF_ERR_INVALID_ARG, "missing scratch for grouped launch");
+    if ((tc.groups > 1 || cache_mode) && !d_scratch) return fail(BF_ERR_INVALID_ARG, "missing scratch for grouped launch");
+    if (cache_mode && !tc.packed) return fail(BF_ERR_INVALID_ARG, "the pre-computation runs the packed family");
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc.smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     dim3 grid((width + tc.tw - 1) / tc.tw, (height + tc.th - 1) / tc.th, tc.groups);
@@ -428,11 +429,12 @@ bf_status launch_filter(const FilterParams &p, int precision, int kahan, const T
     if (tc.packed ? !term_layout(p, tc.nk, pp) || pp.nr != tc.groups * tc.nk
                   : tc.groups != (p.nr + tc.nk - 1) / tc.nk)
         return fail(BF_ERR_INVALID_ARG, "launch geometry does not match the plan's term groups");
+    int mode = cache_mode ? kModeCache : tc.groups > 1 ? kModePartial : kModeFinal;
     void *args[] = {(void *)&in, (void *)&in_pitch, (void *)&out, (void *)&out_pitch, (void *)&part, (void *)&H,
-                    (void *)&W, (void *)&tw, (void *)&th, (void *)&ncols, (void *)&depth, (void *)&pp};
+                    (void *)&W, (void *)&tw, (void *)&th, (void *)&ncols, (void *)&depth, (void *)&mode, (void *)&pp};
     e = cudaLaunchKernel(fn, grid, dim3(tc.threads), args, tc.smem, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "filter launch");
-    if (tc.groups > 1) {
+    if (tc.groups > 1 && !cache_mode) {
         if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");
         dim3 fg((width + 255) / 256, height);
         bf_finalize_kernel<<<fg, 256, 0, (cudaStream_t)stream>>>(d_in, in_pitch, d_out, out_pitch, d_scratch, height,

@@ -94,15 +94,17 @@ __device__ __forceinline__ void rot2(float2 &C, float2 &S, float2 cs, float2 ss,
 
 // One tile: output columns [x0, x0 + tw) x rows [y0, y0 + th) of one image,
 // cosine terms [g NK, g NK + NK) of p.  All threads of the CTA call it; it
-// ends on a barrier, so the shared memory can be reused right after.  `grouped`:
-// store partial numerator / denominator planes (part) instead of dividing.
+// ends on a barrier, so the shared memory can be reused right after.  `mode`:
+// kModeFinal divides and stores Î; kModePartial stores this group's numerator
+// and denominator planes (part); kModeCache stores the window sums of every
+// frequency of the group (part = the cache planes [k][4][H][W]).
 //
 // The NK terms are processed as NK / 2 pairs of consecutive terms with the packed pair instructions:
 // pair p holds terms (2p, 2p + 1) of the group in the two lanes of every float2.
 template <int NK, int M, bool RING>
 __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__restrict__ in, size_t in_pitch,
                                           float *__restrict__ out, size_t out_pitch, float *__restrict__ part, int H,
-                                          int W, int x0, int y0, int tw, int th, int ncols, int g, bool grouped,
+                                          int W, int x0, int y0, int tw, int th, int ncols, int g, int mode,
                                           int depth, float *smem) {
     static_assert(NK % 2 == 0, "terms are processed in pairs");
     constexpr int NP = NK / 2;        // term pairs per group
@@ -407,6 +409,8 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
             const int yo = y - lag;
             const int zo = ((j - lag) % depth) * ZC * NP2;
             const float4 *wp = wb0 + ((j - lag) % depth) * NP * tw + xl;
+            const int x = x0 + xl;
+            const size_t plane = (size_t)H * W, px = (size_t)yo * W + x;
             float2 num2 = make_float2(0.f, 0.f), den2 = make_float2(0.f, 0.f);
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
@@ -417,16 +421,24 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
 #pragma unroll
                     for (int q = 1; q < M; ++q) F[t] = add2(F[t], zq[q][zo + (q * 4 + t) * NP + i]);
                 }
+                if (mode == kModeCache) {
+                    // the window sums of frequencies k0 + 2i, k0 + 2i + 1: planes [k][t] of the cache
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        part[((size_t)(k0 + 2 * i) * 4 + t) * plane + px] = F[t].x;
+                        part[((size_t)(k0 + 2 * i + 1) * 4 + t) * plane + px] = F[t].y;
+                    }
+                    continue;
+                }
                 const float4 w = wp[i * tw];
                 const float2 wc = make_float2(w.x, w.y), ws = make_float2(w.z, w.w);
                 num2 = fma2(wc, F[0], fma2(ws, F[1], num2));
                 den2 = fma2(wc, F[2], fma2(ws, F[3], den2));
             }
             const float num = num2.x + num2.y, den = den2.x + den2.y;
-            const int x = x0 + xl;
-            if (grouped) {
-                const size_t plane = (size_t)H * W;
-                float *pp = part + (size_t)(2 * g) * plane + (size_t)yo * W + x;
+            if (mode == kModeCache) {
+            } else if (mode == kModePartial) {
+                float *pp = part + (size_t)(2 * g) * plane + px;
                 pp[0] = num;
                 pp[plane] = den;
             } else {
@@ -444,11 +456,11 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
 template <int NK, int M, bool RING>
 __global__ void __launch_bounds__(512, 1)
 bf_fused_kernel(const float *__restrict__ in, size_t in_pitch, float *__restrict__ out, size_t out_pitch,
-                float *__restrict__ part, int H, int W, int tw, int th, int ncols, int depth,
+                float *__restrict__ part, int H, int W, int tw, int th, int ncols, int depth, int mode,
                 const __grid_constant__ FilterParams p) {
     extern __shared__ __align__(16) float smem[];
     tile_body<NK, M, RING>(p, in, in_pitch, out, out_pitch, part, H, W, blockIdx.x * tw, blockIdx.y * th, tw, th, ncols,
-                           blockIdx.z, gridDim.z > 1, depth, smem);
+                           blockIdx.z, mode, depth, smem);
 }
 
 // Persistent batched form: each CTA repeatedly takes the next work item from
@@ -474,7 +486,7 @@ bf_batch_kernel(const BatchImage *__restrict__ imgs, const FilterParams *__restr
         for (int i = threadIdx.x; i < (int)(sizeof(FilterParams) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
         __syncthreads();
         tile_body<NK, M, false>(sp, im.in, im.in_pitch, im.out, im.out_pitch, im.part, im.H, im.W, w.x0, w.y0, w.tw,
-                                w.th, ncols, w.g, im.groups > 1, 2, smem);
+                                w.th, ncols, w.g, im.groups > 1 ? kModePartial : kModeFinal, 2, smem);
     }
 }
 

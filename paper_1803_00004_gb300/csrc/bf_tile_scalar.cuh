@@ -378,11 +378,11 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
 template <int NK, int M, bool RING>
 __global__ void __launch_bounds__(512, 1)
 bf_fused_scalar_kernel(const float *__restrict__ in, size_t in_pitch, float *__restrict__ out, size_t out_pitch,
-                float *__restrict__ part, int H, int W, int tw, int th, int ncols, int depth,
+                float *__restrict__ part, int H, int W, int tw, int th, int ncols, int depth, int mode,
                 const __grid_constant__ FilterParams p) {
     extern __shared__ __align__(16) float smem[];
     tile_body<NK, M, RING>(p, in, in_pitch, out, out_pitch, part, H, W, blockIdx.x * tw, blockIdx.y * th, tw, th, ncols,
-                           blockIdx.z, gridDim.z > 1, depth, smem);
+                           blockIdx.z, mode == kModePartial, depth, smem);
 }
 
 // Persistent batched form: each CTA repeatedly takes the next work item from

@@ -265,3 +265,17 @@ def test_term_groups_cover_the_selection(kw):
     assert {f for f, _ in seen} == ({1} if consecutive else {0, 1})
     if consecutive:                                    # ceil(N_r / NK) groups
         assert all(greedy(nk) == -(-len(k) // nk) for _, nk in seen)
+
+
+def test_precompute_argument_checks_without_gpu():
+    L = bf.lib()
+    out = C.c_void_p(123)
+    host = bf.Plan(device=-1, t_r=0.6)
+    assert L.bf_precompute(host.handle, 4096, 256, 4, 64, 1, None, C.byref(out)) == 1      # kmax < 2
+    assert out.value is None
+    assert L.bf_precompute(host.handle, 4096, 256, 4, 64, 200, None, C.byref(out)) == 1    # kmax > 128
+    assert L.bf_precompute(host.handle, 4096, 100, 4, 64, 16, None, C.byref(out)) == 1     # pitch < width * 4
+    assert L.bf_precompute(host.handle, 4096, 256, 4, 64, 16, None, C.byref(out)) == 9     # host-only plan
+    assert L.bf_filter_cached(None, host.handle, 4096, 256, 1 << 20, 256, None) == 1
+    L.bf_cache_destroy(None)                                                                # no-op
+    assert L.bf_cache_bytes(None) == 0
