@@ -100,7 +100,8 @@ bf_status bf_precompute(const bf_plan *plan, const float *d_in, size_t in_pitch,
         pv.k[i] = i;
         pv.a[i] = 1.f;
     }
-    TileConfig tc = choose_tile(pv, height, width, plan->desc.precision);
+    // the cost model's packed-family geometry (consecutive frequencies: every candidate is packed)
+    TileConfig tc = model_tile(pv, height, width, plan->desc.precision);
     bf_cache *c = nullptr;
     if (tc.ncols == 0 || !tc.packed) st = fail(BF_ERR_UNSUPPORTED, "no launch geometry for the pre-computation");
     if (st == BF_OK) {

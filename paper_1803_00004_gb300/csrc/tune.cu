@@ -20,7 +20,7 @@
 namespace bfi {
 namespace {
 
-using Key = std::tuple<int, int, int, int, int, int, int, int, int>;
+using Key = std::tuple<int, int, int, int, int, int, int, int, int, int>;  // ..., gapped term selection
 
 std::mutex g_mu;
 std::map<Key, TileConfig> g_table;
@@ -32,7 +32,8 @@ Key make_key(const FilterParams &p, int h, int w, int precision) {
         cudaGetLastError();
         dev = -1;
     }
-    return Key{dev, p.m, p.nr, p.rx, p.vlo, p.vhi, h, w, precision};
+    const int gapped = p.k[p.nr - 1] - p.k[0] + 1 != p.nr ? 1 : 0;  // the families on offer differ
+    return Key{dev, p.m, p.nr, p.rx, p.vlo, p.vhi, h, w, precision, gapped};
 }
 
 void load_locked() {
@@ -42,14 +43,14 @@ void load_locked() {
     if (!path) return;
     FILE *f = std::fopen(path, "r");
     if (!f) return;
-    int k[9];
+    int k[10];
     TileConfig tc;
     unsigned long smem;
-    while (std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %lu", &k[0], &k[1], &k[2], &k[3], &k[4],
-                       &k[5], &k[6], &k[7], &k[8], &tc.tw, &tc.th, &tc.ncols, &tc.threads, &tc.nk, &tc.groups,
-                       &tc.ring, &tc.depth, &tc.packed, &smem) == 19) {
+    while (std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %lu", &k[0], &k[1], &k[2], &k[3], &k[4],
+                       &k[5], &k[6], &k[7], &k[8], &k[9], &tc.tw, &tc.th, &tc.ncols, &tc.threads, &tc.nk, &tc.groups,
+                       &tc.ring, &tc.depth, &tc.packed, &smem) == 20) {
         tc.smem = smem;
-        g_table[Key{k[0], k[1], k[2], k[3], k[4], k[5], k[6], k[7], k[8]}] = tc;
+        g_table[Key{k[0], k[1], k[2], k[3], k[4], k[5], k[6], k[7], k[8], k[9]}] = tc;
     }
     std::fclose(f);
 }
@@ -59,9 +60,9 @@ void save_locked(const Key &key, const TileConfig &tc) {
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %lu\n", std::get<0>(key), std::get<1>(key),
+    std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %lu\n", std::get<0>(key), std::get<1>(key),
                  std::get<2>(key), std::get<3>(key), std::get<4>(key), std::get<5>(key), std::get<6>(key),
-                 std::get<7>(key), std::get<8>(key), tc.tw, tc.th, tc.ncols, tc.threads, tc.nk, tc.groups, tc.ring,
+                 std::get<7>(key), std::get<8>(key), std::get<9>(key), tc.tw, tc.th, tc.ncols, tc.threads, tc.nk, tc.groups, tc.ring,
                  tc.depth, tc.packed, (unsigned long)tc.smem);
     std::fclose(f);
 }

@@ -229,7 +229,7 @@ print(json.dumps(out))
     written, read = json.loads(w.stdout), json.loads(r.stdout)
     assert written == read
     lines = cache.read_text().splitlines()
-    assert len(lines) == 3 and all(len(x.split()) == 19 for x in lines)
+    assert len(lines) == 3 and all(len(x.split()) == 20 for x in lines)
     fresh = json.loads(subprocess.run([sys.executable, "-c", code, "read"], env=dict(os.environ, PYTHONPATH=ROOT),
                                       capture_output=True, text=True, check=True).stdout)
     assert fresh != read                               # without the file: the cost model's choice
