@@ -363,15 +363,26 @@ def run_precompute(bf, dev, src, flush, reps=5):
 
     t_pre = timed_calls(build, flush, 2)
     cache = holder["c"]
+    c16 = bf.Cache(bf.Plan(sigma_r=0.3, **base), src, kmax=32, precision=bf.PREC_FP16)
+    ex = torch.empty_like(src)
+    o16 = torch.empty_like(src)
     rows = []
     for sr in (0.1, 0.15, 0.2, 0.25, 0.3):
         p = bf.Plan(sigma_r=sr, **base)
         t_cached = timed_calls(lambda: cache.filter(p, src, out), flush, reps)
+        t_c16 = timed_calls(lambda: c16.filter(p, src, o16), flush, reps)
         bf.bf_autotune(p, H, W)
         t_full = timed_launches(bf, p, src, out, flush, reps)
-        rows.append({"sigma_r": sr, "cached_ms": round(t_cached, 4), "full_ms": round(t_full, 4)})
+        bf.bf_exact(src, ex, sigma_s=8.0, sigma_r=sr)
+        torch.cuda.synchronize()
+        d16 = (o16.double() - out.double())
+        mse = torch.mean((o16.double() - ex.double()) ** 2).item()
+        rows.append({"sigma_r": sr, "cached_ms": round(t_cached, 4), "cached_fp16_ms": round(t_c16, 4),
+                     "full_ms": round(t_full, 4), "fp16_max_abs_vs_fp32": round(torch.max(torch.abs(d16)).item(), 6),
+                     "fp16_psnr_db_vs_exact": round(10 * np.log10(1.0 / mse), 2)})
     nbytes = cache.nbytes()
     cache.close()
+    c16.close()
     return {"sigma_s": 8.0, "t_r": 0.9, "kmax": 32, "cache_mib": round(nbytes / 2 ** 20, 1),
             "precompute_ms": round(t_pre, 3), "by_sigma_r": rows}
 

@@ -78,16 +78,21 @@ typedef enum {
     BF_RANGE_PAPER_3D = 2
 } bf_range_policy;
 
-/* Arithmetic of the filter.  The fused kernel never stores a basis image (in
- * HBM or shared memory): basis values live in registers at the rows where they
- * enter or leave a window, so 16-bit storage has nothing to shrink, and the
- * kernel is bound by fp32 issue, which 16-bit storage does not relieve.  The
- * 16-bit modes are therefore rejected: bf_plan_create returns
- * BF_ERR_UNSUPPORTED for them. */
+/* Storage precision.  The fused filter computes and exchanges everything in
+ * fp32 and stores no basis image (in HBM or shared memory): basis values live
+ * in registers at the rows where they enter or leave a window, and the kernel
+ * is bound by fp32 issue, so it has nothing to store in 16 bits.  Plans are
+ * therefore fp32 (bf_plan_create rejects the 16-bit values with
+ * BF_ERR_UNSUPPORTED).  The one stored intermediate is the pre-computation
+ * cache of bf_precompute (Sec. V-C, Case 1): its window sums may be stored as
+ * fp16 or bf16 (rounded once from the fp32 sums), halving the cache and the
+ * traffic of bf_filter_cached, with a relative error of at most u = 2^-11
+ * (fp16) or 2^-8 (bf16) per sum, so |delta I^| <= 2 u sum|a_k| mass (1 + |I^|)
+ * / |den| (mass = sum |K~_s| over the window). */
 typedef enum {
-    BF_PREC_FP32 = 0,           /* all arithmetic and on-chip exchange in fp32 */
-    BF_PREC_BF16_EXCHANGE = 1,  /* window sums exchanged as bf16: not built (BF_ERR_UNSUPPORTED) */
-    BF_PREC_FP16_EXCHANGE = 2   /* window sums exchanged as fp16: not built (BF_ERR_UNSUPPORTED) */
+    BF_PREC_FP32 = 0,  /* fp32 */
+    BF_PREC_BF16 = 1,  /* bf16 storage of the pre-computation cache */
+    BF_PREC_FP16 = 2   /* fp16 storage of the pre-computation cache */
 } bf_precision;
 
 /* Plan parameters (Sec. IV-A..C).  Fill with bf_plan_desc_default() first. */
@@ -253,11 +258,13 @@ typedef struct bf_cache bf_cache;
 
 /* Runs the fused kernel over the frequencies 0 .. kmax-1 of `plan` on the
  * height x width image d_in (row pitch in bytes) and returns the cache in
- * *out (release with bf_cache_destroy).  2 <= kmax <= 128.  Asynchronous on
+ * *out (release with bf_cache_destroy).  2 <= kmax <= 128.  `precision`
+ * (bf_precision) is the storage of the sums: fp32 (16 x kmax bytes per pixel),
+ * or fp16 / bf16 (8 x kmax bytes per pixel, error bound above).  Asynchronous on
  * `stream` after the allocation; *out is NULL on any error.  Errors: BF_ERR_INVALID_ARG, BF_ERR_NO_DEVICE,
  * BF_ERR_OOM, BF_ERR_UNSUPPORTED, BF_ERR_CUDA. */
 bf_status bf_precompute(const bf_plan *plan, const float *d_in, size_t in_pitch_bytes, int height, int width,
-                        int kmax, void *stream, bf_cache **out);
+                        int kmax, int precision, void *stream, bf_cache **out);
 
 /* Filters with `plan` from the cache: Eq. (36)'s weighting of the cached sums
  * by a_k cos/sin(pi k I(x) / P) and the divide; no box filtering.  d_in must

@@ -20,7 +20,7 @@ ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA, ERR_ADMISSION = 1, 2, 3, 4,
 ERR_TIMEOUT, ERR_DEVICE_TIMEOUT, ERR_RANGE, ERR_NO_DEVICE, ERR_NOT_FOUND, ERR_CANCELLED = 6, 7, 8, 9, 10, 11
 KERNEL_GAUSSIAN, KERNEL_EXPONENTIAL, KERNEL_BOX = 0, 1, 2
 RANGE_TRUNCATED_MIN_PERIOD, RANGE_UNTRUNCATED_FULL, RANGE_PAPER_3D = 0, 1, 2
-PREC_FP32, PREC_BF16_EXCHANGE, PREC_FP16_EXCHANGE = 0, 1, 2
+PREC_FP32, PREC_BF16, PREC_FP16 = 0, 1, 2
 
 
 class bf_plan_desc(C.Structure):
@@ -99,7 +99,7 @@ def lib():
         L.bf_filter_batch.argtypes = [P(vp), P(bf_image), i, vp]
         L.bf_exact.argtypes = [vp, sz, vp, sz, i, i, i, d, i, i, d, vp]
         L.bf_exact_lut.argtypes = [vp, sz, vp, sz, i, i, i, d, i, i, d, d, i, vp]
-        L.bf_precompute.argtypes = [vp, vp, sz, i, i, i, vp, P(vp)]
+        L.bf_precompute.argtypes = [vp, vp, sz, i, i, i, i, vp, P(vp)]
         L.bf_filter_cached.argtypes = [vp, vp, vp, sz, vp, sz, vp]
         L.bf_cache_bytes.argtypes = [vp]
         L.bf_cache_bytes.restype = sz
@@ -298,11 +298,11 @@ def bf_exact_lut(src, dst, levels=256, data_range=1.0, spatial=KERNEL_GAUSSIAN, 
 class Cache:
     """Owns a bf_cache* (the pre-computed window sums of one image, Sec. V-C, Case 1)."""
 
-    def __init__(self, plan: "Plan", src, kmax: int, stream=None):
+    def __init__(self, plan: "Plan", src, kmax: int, precision: int = 0, stream=None):
         ip, ipitch, h, w = _ptr_pitch(src)
         self.handle = C.c_void_p()
-        _check(lib().bf_precompute(plan.handle, ip, ipitch, h, w, kmax, _stream_handle(stream), C.byref(self.handle)),
-               "bf_precompute")
+        _check(lib().bf_precompute(plan.handle, ip, ipitch, h, w, kmax, precision, _stream_handle(stream),
+                                   C.byref(self.handle)), "bf_precompute")
 
     def filter(self, plan: "Plan", src, dst, stream=None) -> None:
         ip, ipitch, _, _ = _ptr_pitch(src)

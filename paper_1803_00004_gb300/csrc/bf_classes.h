@@ -8,7 +8,8 @@ constexpr int kScanThreads = 64;  // two scan warps per CTA
 
 // Output of a tile: Î (divide and store), a term group's partial numerator / denominator planes, or the
 // window sums of each frequency (the pre-computation cache; packed family only).
-constexpr int kModeFinal = 0, kModePartial = 1, kModeCache = 2;
+// The cache modes store the sums as fp32, fp16 or bf16.
+constexpr int kModeFinal = 0, kModePartial = 1, kModeCache = 2, kModeCacheF16 = 3, kModeCacheBF16 = 4;
 
 struct KernelClass {
     int m, nk;

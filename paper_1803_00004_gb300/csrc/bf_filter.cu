@@ -403,7 +403,7 @@ size_t scratch_bytes(const TileConfig &tc, int height, int width) {
 
 bf_status launch_filter(const FilterParams &p, int precision, int kahan, const TileConfig &tc, const float *d_in,
                         size_t in_pitch, float *d_out, size_t out_pitch, float *d_scratch, int height, int width,
-                        void *stream, bool cache_mode) {
+                        void *stream, int cache_mode) {
     (void)precision;
     (void)kahan;
     if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");
@@ -429,7 +429,7 @@ bf_status launch_filter(const FilterParams &p, int precision, int kahan, const T
     if (tc.packed ? !term_layout(p, tc.nk, pp) || pp.nr != tc.groups * tc.nk
                   : tc.groups != (p.nr + tc.nk - 1) / tc.nk)
         return fail(BF_ERR_INVALID_ARG, "launch geometry does not match the plan's term groups");
-    int mode = cache_mode ? kModeCache : tc.groups > 1 ? kModePartial : kModeFinal;
+    int mode = cache_mode ? cache_mode : tc.groups > 1 ? kModePartial : kModeFinal;
     void *args[] = {(void *)&in, (void *)&in_pitch, (void *)&out, (void *)&out_pitch, (void *)&part, (void *)&H,
                     (void *)&W, (void *)&tw, (void *)&th, (void *)&ncols, (void *)&depth, (void *)&mode, (void *)&pp};
     e = cudaLaunchKernel(fn, grid, dim3(tc.threads), args, tc.smem, (cudaStream_t)stream);

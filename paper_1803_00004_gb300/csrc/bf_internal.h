@@ -102,7 +102,7 @@ void remember_tile(const FilterParams &p, int height, int width, int precision, 
 size_t scratch_bytes(const TileConfig &tc, int height, int width);
 bf_status launch_filter(const FilterParams &p, int precision, int kahan, const TileConfig &tc, const float *d_in,
                         size_t in_pitch_elems, float *d_out, size_t out_pitch_elems, float *d_scratch, int height,
-                        int width, void *stream, bool cache_mode = false);
+                        int width, void *stream, int cache_mode = 0);  // 0, or kModeCache*
 bf_status launch_exact(const float *d_in, size_t in_pitch_elems, float *d_out, size_t out_pitch_elems,
                        int height, int width, int spatial, float sigma_s, int radius, int range, float sigma_r,
                        void *stream);

@@ -3,6 +3,8 @@
 // that they compile in parallel.  See bf_filter.cu for the algorithm.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "bf_classes.h"
@@ -96,8 +98,9 @@ __device__ __forceinline__ void rot2(float2 &C, float2 &S, float2 cs, float2 ss,
 // cosine terms [g NK, g NK + NK) of p.  All threads of the CTA call it; it
 // ends on a barrier, so the shared memory can be reused right after.  `mode`:
 // kModeFinal divides and stores Î; kModePartial stores this group's numerator
-// and denominator planes (part); kModeCache stores the window sums of every
-// frequency of the group (part = the cache planes [k][4][H][W]).
+// and denominator planes (part); kModeCache / kModeCacheF16 / kModeCacheBF16
+// store the window sums of every frequency of the group (part = the cache
+// planes [k][4][H][W], of fp32 / fp16 / bf16).
 //
 // The NK terms are processed as NK / 2 pairs of consecutive terms with the packed pair instructions:
 // pair p holds terms (2p, 2p + 1) of the group in the two lanes of every float2.
@@ -421,12 +424,25 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
 #pragma unroll
                     for (int q = 1; q < M; ++q) F[t] = add2(F[t], zq[q][zo + (q * 4 + t) * NP + i]);
                 }
-                if (mode == kModeCache) {
-                    // the window sums of frequencies k0 + 2i, k0 + 2i + 1: planes [k][t] of the cache
+                if (mode >= kModeCache) {
+                    // the window sums of frequencies k0 + 2i, k0 + 2i + 1: planes [k][t] of the cache, stored as
+                    // fp32, or rounded once to fp16 / bf16
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
-                        part[((size_t)(k0 + 2 * i) * 4 + t) * plane + px] = F[t].x;
-                        part[((size_t)(k0 + 2 * i + 1) * 4 + t) * plane + px] = F[t].y;
+                        const size_t ia = ((size_t)(k0 + 2 * i) * 4 + t) * plane + px;
+                        const size_t ib = ((size_t)(k0 + 2 * i + 1) * 4 + t) * plane + px;
+                        if (mode == kModeCache) {
+                            part[ia] = F[t].x;
+                            part[ib] = F[t].y;
+                        } else if (mode == kModeCacheF16) {
+                            __half *h = reinterpret_cast<__half *>(part);
+                            h[ia] = __float2half_rn(F[t].x);
+                            h[ib] = __float2half_rn(F[t].y);
+                        } else {
+                            __nv_bfloat16 *h = reinterpret_cast<__nv_bfloat16 *>(part);
+                            h[ia] = __float2bfloat16_rn(F[t].x);
+                            h[ib] = __float2bfloat16_rn(F[t].y);
+                        }
                     }
                     continue;
                 }
@@ -436,7 +452,7 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
                 den2 = fma2(wc, F[2], fma2(ws, F[3], den2));
             }
             const float num = num2.x + num2.y, den = den2.x + den2.y;
-            if (mode == kModeCache) {
+            if (mode >= kModeCache) {
             } else if (mode == kModePartial) {
                 float *pp = part + (size_t)(2 * g) * plane + px;
                 pp[0] = num;

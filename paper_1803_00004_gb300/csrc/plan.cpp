@@ -329,11 +329,11 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
         return fail(BF_ERR_UNSUPPORTED, "BF_RANGE_PAPER_3D (z-binned range box) is not implemented");
     if (d.policy != BF_RANGE_TRUNCATED_MIN_PERIOD && d.policy != BF_RANGE_UNTRUNCATED_FULL)
         return fail(BF_ERR_INVALID_ARG, "unknown range policy");
-    if (d.precision < BF_PREC_FP32 || d.precision > BF_PREC_FP16_EXCHANGE)
+    if (d.precision < BF_PREC_FP32 || d.precision > BF_PREC_FP16)
         return fail(BF_ERR_INVALID_ARG, "unknown precision");
     if (d.precision != BF_PREC_FP32)
-        return fail(BF_ERR_UNSUPPORTED, "16-bit exchange is not built: the kernel stores no basis image and is bound by "
-                                        "fp32 issue, which 16-bit storage does not relieve");
+        return fail(BF_ERR_UNSUPPORTED, "plans are fp32 (the fused kernel stores no basis image); 16-bit storage "
+                                        "applies to the pre-computation cache (bf_precompute)");
 
     p.desc = d;
     const double dI = (double)d.i_hi - (double)d.i_lo;

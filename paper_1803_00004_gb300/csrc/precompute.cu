@@ -8,6 +8,8 @@
 // bf_filter_cached then filters with any plan sharing P and the spatial
 // kernel by weighting those sums with its a_k cos/sin(pi k I(x) / P): one read
 // of 16 bytes per selected term per pixel, no box filtering.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -20,7 +22,8 @@ struct bf_cache {
     bfi::FilterParams basis;  // the plan's parameters the sums were computed with
     int kslots = 0;           // frequencies 0 .. kslots - 1 are stored
     int height = 0, width = 0, device = 0;
-    float *planes = nullptr;  // [kslots][4][height][width]: sums of cos I, sin I, cos, sin
+    int precision = 0;        // bf_precision of the stored sums
+    float *planes = nullptr;  // [kslots][4][height][width]: sums of cos I, sin I, cos, sin (fp32, fp16 or bf16)
     size_t bytes = 0;
 };
 
@@ -30,8 +33,13 @@ namespace {
 // Weighting of the cached sums (Eq. (36)): for each selected term k, (cos, sin)(pi k t) at the centre pixel
 // (t = (I(x) - i_lo) / P carried as two floats, sincospi corrected to first order in the low part), then
 // num / den.  Guard as the fused kernel: den <= den_eps -> I(x).
+__device__ __forceinline__ float load_sum(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float load_sum(const __half *p) { return __half2float(*p); }
+__device__ __forceinline__ float load_sum(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+
+template <typename T>
 __global__ void bf_cached_kernel(const float *__restrict__ in, size_t in_pitch, float *__restrict__ out,
-                                 size_t out_pitch, const float *__restrict__ planes, int H, int W,
+                                 size_t out_pitch, const T *__restrict__ planes, int H, int W,
                                  const __grid_constant__ FilterParams p) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= W || y >= H) return;
@@ -50,10 +58,10 @@ __global__ void bf_cached_kernel(const float *__restrict__ in, size_t in_pitch, 
         sincospif(kh, &s, &c);
         const float d = kPiF * kl;
         const float ck = fmaf(-d, s, c), sk = fmaf(d, c, s);
-        const float *f = planes + (size_t)p.k[j] * 4 * plane + px;
+        const T *f = planes + (size_t)p.k[j] * 4 * plane + px;
         const float a = p.a[j];
-        num = fmaf(a, fmaf(ck, __ldg(f), sk * __ldg(f + plane)), num);
-        den = fmaf(a, fmaf(ck, __ldg(f + 2 * plane), sk * __ldg(f + 3 * plane)), den);
+        num = fmaf(a, fmaf(ck, load_sum(f), sk * load_sum(f + plane)), num);
+        den = fmaf(a, fmaf(ck, load_sum(f + 2 * plane), sk * load_sum(f + 3 * plane)), den);
     }
     out[(size_t)y * out_pitch + x] = den > p.den_eps ? num / den + p.i_lo : ix;
 }
@@ -80,9 +88,10 @@ using namespace bfi;
 extern "C" {
 
 bf_status bf_precompute(const bf_plan *plan, const float *d_in, size_t in_pitch, int height, int width, int kmax,
-                        void *stream, bf_cache **out) {
+                        int precision, void *stream, bf_cache **out) {
     if (out) *out = nullptr;
-    if (!plan || !out || kmax < 2 || kmax > kMaxSlots) return fail(BF_ERR_INVALID_ARG, "bad pre-computation arguments");
+    if (!plan || !out || kmax < 2 || kmax > kMaxSlots || precision < BF_PREC_FP32 || precision > BF_PREC_FP16)
+        return fail(BF_ERR_INVALID_ARG, "bad pre-computation arguments");
     if (height < 1 || width < 1) return fail(BF_ERR_INVALID_ARG, "empty image");
     if (!d_in || in_pitch % sizeof(float) || in_pitch < (size_t)width * sizeof(float))
         return fail(BF_ERR_INVALID_ARG, "NULL input or bad pitch");
@@ -111,7 +120,8 @@ bf_status bf_precompute(const bf_plan *plan, const float *d_in, size_t in_pitch,
         c->height = height;
         c->width = width;
         c->device = plan->desc.device;
-        c->bytes = sizeof(float) * 4 * (size_t)c->kslots * height * width;
+        c->precision = precision;
+        c->bytes = (precision == BF_PREC_FP32 ? 4 : 2) * 4 * (size_t)c->kslots * height * width;
         if (cudaMalloc((void **)&c->planes, c->bytes) != cudaSuccess) {
             cudaGetLastError();
             st = fail(BF_ERR_OOM, "pre-computation cache (" + std::to_string(c->bytes >> 20) + " MiB)");
@@ -119,7 +129,10 @@ bf_status bf_precompute(const bf_plan *plan, const float *d_in, size_t in_pitch,
     }
     if (st == BF_OK)
         st = launch_filter(pv, plan->desc.precision, plan->desc.kahan, tc, d_in, in_pitch / sizeof(float), nullptr, 0,
-                           c->planes, height, width, stream, true);
+                           c->planes, height, width, stream,
+                           precision == BF_PREC_FP16   ? kModeCacheF16
+                           : precision == BF_PREC_BF16 ? kModeCacheBF16
+                                                       : kModeCache);
     if (st == BF_OK) {
         *out = c;
     } else if (c) {
@@ -149,9 +162,18 @@ bf_status bf_filter_cached(const bf_cache *cache, const bf_plan *plan, const flo
         st = fail(BF_ERR_CUDA, "injected launch failure (test hook)");
     } else {
         dim3 grid((cache->width + 255) / 256, cache->height);
-        bf_cached_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(d_in, in_pitch / sizeof(float), d_out,
-                                                                 out_pitch / sizeof(float), cache->planes,
-                                                                 cache->height, cache->width, plan->kp);
+        const size_t ip = in_pitch / sizeof(float), op = out_pitch / sizeof(float);
+        cudaStream_t s = (cudaStream_t)stream;
+        if (cache->precision == BF_PREC_FP16)
+            bf_cached_kernel<<<grid, 256, 0, s>>>(d_in, ip, d_out, op, reinterpret_cast<const __half *>(cache->planes),
+                                                  cache->height, cache->width, plan->kp);
+        else if (cache->precision == BF_PREC_BF16)
+            bf_cached_kernel<<<grid, 256, 0, s>>>(d_in, ip, d_out, op,
+                                                  reinterpret_cast<const __nv_bfloat16 *>(cache->planes), cache->height,
+                                                  cache->width, plan->kp);
+        else
+            bf_cached_kernel<<<grid, 256, 0, s>>>(d_in, ip, d_out, op, cache->planes, cache->height, cache->width,
+                                                  plan->kp);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) st = fail(BF_ERR_CUDA, std::string("cached filter launch: ") + cudaGetErrorString(e));
     }

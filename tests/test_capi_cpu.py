@@ -107,7 +107,7 @@ def test_paper_five_terms_compile_to_two_nested_windows():
     (dict(sigma_s=0.0), 1), (dict(sigma_r=-1.0), 1), (dict(ns_terms=0), 1), (dict(nr_terms=0), 1),
     (dict(i_lo=1.0, i_hi=1.0), 1), (dict(policy=bf.RANGE_PAPER_3D), 2),
     (dict(spatial=bf.KERNEL_EXPONENTIAL, sigma_s=100.0), 2),
-    (dict(spatial=7), 1), (dict(precision=9), 1), (dict(radius=-2), 1), (dict(precision=1), 2), (dict(precision=2), 2),
+    (dict(spatial=7), 1), (dict(precision=9), 1), (dict(radius=-2), 1), (dict(precision=bf.PREC_BF16), 2), (dict(precision=bf.PREC_FP16), 2),
 ])
 def test_plan_create_rejects(kw, status):
     with pytest.raises(bf.BFError) as ei:
@@ -271,11 +271,12 @@ def test_precompute_argument_checks_without_gpu():
     L = bf.lib()
     out = C.c_void_p(123)
     host = bf.Plan(device=-1, t_r=0.6)
-    assert L.bf_precompute(host.handle, 4096, 256, 4, 64, 1, None, C.byref(out)) == 1      # kmax < 2
+    assert L.bf_precompute(host.handle, 4096, 256, 4, 64, 1, 0, None, C.byref(out)) == 1      # kmax < 2
     assert out.value is None
-    assert L.bf_precompute(host.handle, 4096, 256, 4, 64, 200, None, C.byref(out)) == 1    # kmax > 128
-    assert L.bf_precompute(host.handle, 4096, 100, 4, 64, 16, None, C.byref(out)) == 1     # pitch < width * 4
-    assert L.bf_precompute(host.handle, 4096, 256, 4, 64, 16, None, C.byref(out)) == 9     # host-only plan
+    assert L.bf_precompute(host.handle, 4096, 256, 4, 64, 200, 0, None, C.byref(out)) == 1    # kmax > 128
+    assert L.bf_precompute(host.handle, 4096, 100, 4, 64, 16, 0, None, C.byref(out)) == 1     # pitch < width * 4
+    assert L.bf_precompute(host.handle, 4096, 256, 4, 64, 16, 3, None, C.byref(out)) == 1     # unknown precision
+    assert L.bf_precompute(host.handle, 4096, 256, 4, 64, 16, 0, None, C.byref(out)) == 9     # host-only plan
     assert L.bf_filter_cached(None, host.handle, 4096, 256, 1 << 20, 256, None) == 1
     L.bf_cache_destroy(None)                                                                # no-op
     assert L.bf_cache_bytes(None) == 0

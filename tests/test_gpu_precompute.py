@@ -66,3 +66,32 @@ def test_cached_filter_rejects_other_basis_and_missing_frequencies():
         cache.filter(bf.Plan(device=0, sigma_s=4.0, t_r=0.6, sigma_r=0.05, nr_terms=16), src, dst)
     assert ei.value.status == 8
     cache.close()
+
+
+@pytest.mark.parametrize("precision,u", [(bf.PREC_FP16, 2.0 ** -11), (bf.PREC_BF16, 2.0 ** -8)])
+def test_16bit_cache_within_its_rounding_bound(precision, u):
+    """Sums stored in 16 bits carry a relative error of at most u each (one round-to-nearest of the fp32
+    sum), so num and den are each off by at most u sum|a_k| (|F_cI| + |F_sI|) <= 2 u sum|a_k| mass, and
+    |delta I^| <= 2 u sum|a_k| mass (1 + |I^|) / |den|.  Checked per pixel against the fp64 oracle (plus the
+    fp32 bar); the cache is half the size of the fp32 one."""
+    from scipy import ndimage
+    img = synth.shapes(200, 280, 53, scale=0.2)
+    src = torch.from_numpy(img).cuda()
+    base = dict(sigma_s=4.0, t_r=0.6)
+    c32 = bf.Cache(bf.Plan(device=0, sigma_r=0.2, **base), src, kmax=16)
+    c16 = bf.Cache(bf.Plan(device=0, sigma_r=0.2, **base), src, kmax=16, precision=precision)
+    assert c16.nbytes() * 2 == c32.nbytes()
+    for sr in (0.1, 0.2):
+        kw = dict(base, sigma_r=sr)
+        plan = bf.Plan(device=0, **kw)
+        got = torch.full_like(src, float("nan"))
+        c16.filter(plan, src, got)
+        torch.cuda.synchronize()
+        ref, _, den = O.approx_fast(img.astype(np.float64), O.Desc(**kw), threads=16, return_den=True)
+        p = O.plan_info(O.Desc(**kw))
+        mass = ndimage.correlate(np.ones(img.shape), np.abs(p.Ks[::-1, ::-1]), mode="constant", cval=0.0)
+        bound = TOL + 2 * u * np.sum(np.abs(p.ak)) * mass * (1 + np.abs(ref)) / np.abs(den)
+        err = np.abs(got.cpu().numpy() - ref)
+        assert np.all(err <= bound), (precision, sr, float(np.max(err / bound)))
+    c16.close()
+    c32.close()
