@@ -108,12 +108,27 @@ int family_groups(const FilterParams &p, int nk, bool packed) {
 // The selection has gaps (the packed family then pads groups with zero-weight frequencies).
 bool gapped_terms(const FilterParams &p) { return p.k[p.nr - 1] - p.k[0] + 1 != p.nr; }
 
-size_t smem_bytes(int m, int nk, int ncols, int tw, int depth = 2) {
-    return sizeof(float) * ((size_t)depth * (m * nk * 4 + 2) * (ncols + 2) + (size_t)depth * nk * 2 * tw);
+// Shared memory of a tile: the exchange, the output weights (not with the packed family's ring, which
+// recomputes them from the ring) and the ring.
+size_t smem_bytes(int m, int nk, int ncols, int tw, int depth = 2, bool weights = true) {
+    return sizeof(float) * ((size_t)depth * (m * nk * 4 + 2) * (ncols + 2) + (weights ? (size_t)depth * nk * 2 * tw : 0));
 }
 
-size_t ring_bytes(const FilterParams &p, int ncols) {
-    return sizeof(float) * 6 * (size_t)(p.vhi - p.vlo + 2) * ncols;
+// The ring: (v, cos, sin of the base angle, pad) per row and column, plus the anchor (cos, sin)(pi k0 t) when
+// some term group starts at k0 >= 2 (the scalar family always keeps it).
+size_t ring_bytes(const FilterParams &p, int ncols, bool anchor = true) {
+    return (16 + (anchor ? 8 : 0)) * (size_t)(p.vhi - p.vlo + 2) * ncols;
+}
+
+// Some group of the launch's term layout starts at frequency 2 or more.
+bool groups_need_anchor(const FilterParams &p, int nk, bool packed) {
+    if (!packed) return true;
+    for (int i = 0; i < p.nr;) {
+        const int k0 = p.k[i];
+        if (k0 >= 2) return true;
+        while (i < p.nr && p.k[i] < k0 + nk) ++i;
+    }
+    return false;
 }
 
 int device_sms() {
@@ -260,7 +275,11 @@ std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int w
                 const int ring = variant & 1, depth = 2 + (variant >> 1);
                 // the ring serves the output row too, so it must lie inside the window span
                 if (ring && !(p.vlo <= 0 && p.vhi >= 0)) continue;
-                const size_t smem = smem_bytes(p.m, cls.nk, ncols, tw, depth) + (ring ? ring_bytes(p, ncols) : 0);
+                // the packed ring's output phase reads row y - lag back from the ring: lag <= 1 - vlo
+                if (ring && packed && depth - 1 > 1 - p.vlo) continue;
+                const bool pring = ring && packed;
+                const size_t smem = smem_bytes(p.m, cls.nk, ncols, tw, depth, !pring) +
+                                    (ring ? ring_bytes(p, ncols, groups_need_anchor(p, cls.nk, packed)) : 0);
                 if (smem > 227 * 1024) continue;
                 const int by_smem = (int)((228 * 1024) / (smem + 1024));
                 const int by_threads = 2048 / (ncols + kScanThreads);

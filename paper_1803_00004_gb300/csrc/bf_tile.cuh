@@ -127,9 +127,11 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
     // [depth][NP][tw] float4: a_k cos, a_k' cos, a_k sin, a_k' sin of a term pair at the output row
     float4 *wb0 = reinterpret_cast<float4 *>(smem + depth * ZC * NRP);
     // RING: per column, the basis inputs of the last D rows, so each row's load and sincospi happen once
-    // instead of at every window edge: (v, cos pi t, sin pi t) in ringA, (cos, sin)(pi k0 t) in ringB
+    // instead of at every window edge: (v, cos pi t, sin pi t) in ringA, (cos, sin)(pi k0 t) in ringB (only
+    // touched, and only allocated, for groups whose first frequency k0 is 2 or more)
     const int D = p.vhi - p.vlo + 2;
-    float4 *ringA = reinterpret_cast<float4 *>(wb0 + depth * NP * tw);  // [D][ncols]
+    // (with RING the output weights are recomputed from the ring and wb0 is not allocated)
+    float4 *ringA = reinterpret_cast<float4 *>(smem + depth * ZC * NRP) + (RING ? 0 : depth * NP * tw);  // [D][ncols]
     float2 *ringB = reinterpret_cast<float2 *>(ringA + (RING ? D * ncols : 0));  // [D][ncols]
     const int halo = p.rx;
 
@@ -193,7 +195,7 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
             if (RING) {
                 const int sl = pos_mod(row, D) * ncols + tid;
                 ringA[sl] = make_float4(v, c1, s1, 0.f);
-                ringB[sl] = make_float2(c0, s0);
+                if (k0 >= 2) ringB[sl] = make_float2(c0, s0);
             }
             const float2 v2 = pair(v);
             float2 C, S, cs, ss, nss;
@@ -258,7 +260,7 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
                     basis_start(vr, p.inv_p, p.inv_p_lo, k0, colv, a, b, c, s);
                     const int sl = ring_slot(ys, p.vhi, D) * ncols + tid;
                     ringA[sl] = make_float4(vr, a, b, 0.f);
-                    ringB[sl] = make_float2(c, s);
+                    if (k0 >= 2) ringB[sl] = make_float2(c, s);
                 }
             }
             float2 *zb = reinterpret_cast<float2 *>(zb0 + ((j % depth) * ZC + tid + 1) * NRP);
@@ -266,6 +268,7 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
             // one edge at a time: its term pairs update the sums of its window (only one edge's state is live)
 #pragma unroll
             for (int e = 0; e < NE; ++e) {
+                if (RING && e == 2 * M) continue;  // RING: the output phase rebuilds the output row's basis
                 const int off = edge_off(e);
                 const int row = y + off;
                 // at j == 0 the sums already hold row y0: only the output-row edge is live
@@ -312,7 +315,7 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
                             V[i][2][r] = sub2(V[i][2][r], C);
                             V[i][3][r] = sub2(V[i][3][r], S);
                         }
-                    } else if (is_out) {
+                    } else if (!RING && is_out) {
                         const float2 a2 = make_float2(aa[2 * i], aa[2 * i + 1]);
                         const float2 ca = mul2(a2, C), sa = mul2(a2, S);
                         wb[i * tw + xl] = make_float4(ca.x, ca.y, sa.x, sa.y);
@@ -415,6 +418,23 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
             const int x = x0 + xl;
             const size_t plane = (size_t)H * W, px = (size_t)yo * W + x;
             float2 num2 = make_float2(0.f, 0.f), den2 = make_float2(0.f, 0.f);
+            // RING: (cos, sin) of the output row's term pairs from this column's ring entry (row yo is still in
+            // the ring: it holds rows y + vlo - 1 .. y + vhi, and lag <= 1 - vlo)
+            float2 Co = make_float2(0.f, 0.f), So = Co, cso = Co, sso = Co, nsso = Co;
+            if (RING) {
+                const int sl = ring_slot(ys, -lag, D) * ncols + tid;
+                const float4 A = ringA[sl];
+                float c0 = 1.f, s0 = 0.f;
+                if (k0 == 1) {
+                    c0 = A.y;
+                    s0 = A.z;
+                } else if (k0 >= 2) {
+                    const float2 B = ringB[sl];
+                    c0 = B.x;
+                    s0 = B.y;
+                }
+                start_pair(A.y, A.z, c0, s0, Co, So, cso, sso, nsso);
+            }
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
                 float2 F[4];
@@ -446,8 +466,17 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
                     }
                     continue;
                 }
-                const float4 w = wp[i * tw];
-                const float2 wc = make_float2(w.x, w.y), ws = make_float2(w.z, w.w);
+                float2 wc, ws;
+                if (RING) {
+                    if (i > 0) rot2(Co, So, cso, sso, nsso);
+                    const float2 a2 = make_float2(aa[2 * i], aa[2 * i + 1]);
+                    wc = mul2(a2, Co);
+                    ws = mul2(a2, So);
+                } else {
+                    const float4 w = wp[i * tw];
+                    wc = make_float2(w.x, w.y);
+                    ws = make_float2(w.z, w.w);
+                }
                 num2 = fma2(wc, F[0], fma2(ws, F[1], num2));
                 den2 = fma2(wc, F[2], fma2(ws, F[3], den2));
             }
