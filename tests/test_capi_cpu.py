@@ -280,3 +280,51 @@ def test_precompute_argument_checks_without_gpu():
     assert L.bf_filter_cached(None, host.handle, 4096, 256, 1 << 20, 256, None) == 1
     L.bf_cache_destroy(None)                                                                # no-op
     assert L.bf_cache_bytes(None) == 0
+
+
+def _random_descs(n, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        spatial = int(rng.choice([bf.KERNEL_GAUSSIAN, bf.KERNEL_BOX, bf.KERNEL_EXPONENTIAL]))
+        kw = dict(spatial=spatial, sigma_s=float(rng.uniform(0.6, 12.0)), ns_terms=int(rng.choice([1, 2, 3, 5, 9, 13, 25])),
+                  range=int(rng.integers(0, 3)), sigma_r=float(rng.uniform(0.03, 0.5)),
+                  nr_terms=int(rng.integers(1, 17)), policy=int(rng.choice([bf.RANGE_TRUNCATED_MIN_PERIOD,
+                                                                             bf.RANGE_UNTRUNCATED_FULL])))
+        if rng.random() < 0.3:
+            kw["radius"] = int(rng.integers(1, 20))
+        if spatial == bf.KERNEL_EXPONENTIAL:  # the oracle's 2-D quadrature grows with 4^J: keep R <= 12
+            kw["sigma_s"] = min(kw["sigma_s"], 4.0)
+            kw["radius"] = min(kw.get("radius", 12), 12)
+        out.append(kw)
+    return out
+
+
+@pytest.mark.parametrize("kw", _random_descs(40, 7))
+def test_random_plans_match_oracle(kw):
+    """Seeded random descriptors: the product's plan (selections, coefficients, kernel table, windows) equals
+    the oracle's, or both reject it; the compiled windows reproduce the kernel."""
+    try:
+        o = O.plan_info(_odesc(kw))
+    except ValueError:
+        o = None
+    try:
+        p = bf.Plan(device=-1, **kw)
+    except bf.BFError as e:
+        # the product may reject what the oracle evaluates (more than 6 box windows per axis, more than 64
+        # terms), never the other way round
+        assert e.status == 2, (kw, e)
+        return
+    assert o is not None, kw
+    c = p.coeffs()
+    order = np.argsort(o.ks)
+    assert list(c["k"]) == list(o.ks[order]), kw
+    assert np.max(np.abs(np.array(c["a"]) - o.ak[order])) < 1e-13
+    assert [list(t) for t in c["haar_terms"]] == [list(t) for t in o.terms]
+    assert np.max(np.abs(np.array(c["kernel"]) - o.Ks)) < 1e-13 * max(1.0, np.max(np.abs(o.Ks)))
+    R, K = c["radius"], np.array(c["kernel"])
+    rec = np.zeros_like(K)
+    for v, (v0, v1) in enumerate(c["vwin"]):
+        for h, (u0, u1) in enumerate(c["hwin"]):
+            rec[v0 + R:v1 + R + 1, u0 + R:u1 + R + 1] += c["wcoef"][v][h]
+    assert np.max(np.abs(rec - K[::-1, ::-1])) < 1e-12 * max(1.0, np.max(np.abs(K)))

@@ -1,0 +1,85 @@
+"""Seeded random plans on random ragged images against the oracle: kernels, bandwidths, N_s, N_r, policies,
+radii and image sizes drawn at random, each filtered in the default launch geometry and in a randomly chosen
+candidate geometry (any family: packed or scalar, ring or not, exchange depth, terms per CTA).  Needs a GPU."""
+import numpy as np
+import pytest
+
+import paper_1803_00004_gb300 as bf
+from paper_1803_00004_gb300 import synth
+from oracle import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1803_00004_gb300 import _build
+    _build.build()
+
+
+def _cases(n, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < n:
+        spatial = int(rng.choice([bf.KERNEL_GAUSSIAN, bf.KERNEL_BOX, bf.KERNEL_EXPONENTIAL]))
+        kw = dict(spatial=spatial, sigma_s=float(rng.uniform(0.6, 6.0 if spatial == bf.KERNEL_EXPONENTIAL else 14.0)),
+                  ns_terms=int(rng.choice([1, 2, 3, 5, 9, 13])), range=int(rng.integers(0, 3)),
+                  sigma_r=float(rng.uniform(0.04, 0.5)), nr_terms=int(rng.integers(1, 17)),
+                  policy=int(rng.choice([bf.RANGE_TRUNCATED_MIN_PERIOD, bf.RANGE_UNTRUNCATED_FULL])))
+        try:
+            bf.Plan(device=-1, **kw)
+        except bf.BFError:
+            continue
+        H, W = int(rng.integers(1, 260)), int(rng.integers(1, 420))
+        gen = int(rng.integers(0, 3))
+        seed_img = int(rng.integers(0, 1 << 30))
+        out.append((H, W, gen, seed_img, int(rng.integers(0, 1 << 30)), kw))
+    return out
+
+
+def _image(H, W, gen, seed):
+    if gen == 0:
+        return synth.shapes(H, W, seed, scale=max(H, W) / 1080.0)
+    if gen == 1:
+        return synth.blocks(H, W, seed)
+    return synth.uniform(H, W, seed)
+
+
+@pytest.mark.parametrize("H,W,gen,seed_img,seed_geo,kw", _cases(30, 2026))
+def test_random_plan_and_geometry_match_oracle(H, W, gen, seed_img, seed_geo, kw):
+    from scipy import ndimage
+    img = _image(H, W, gen, seed_img)
+    plan = bf.Plan(device=0, **kw)
+    # Random plans are often crude (one or two range terms, Gibbs-heavy box kernels) with denominators near
+    # cancellation at some pixels, so every pixel is held to the fp32 bar plus the fp32 rounding of the sums
+    # (~2e-7 relative) amplified by sum|a_k| mass / |den|: 1e-5 + 2e-7 sum|a_k| (1 + |I^|) mass / |den|.
+    # Pixels within 10x of the denominator guard are excluded (fp32 and fp64 may decide the guard
+    # differently there).
+    ref, _, den = O.approx_fast(img.astype(np.float64), O.Desc(**kw), threads=16, return_den=True)
+    p = O.plan_info(O.Desc(**kw))
+    mass = ndimage.correlate(np.ones(img.shape), np.abs(p.Ks[::-1, ::-1]), mode="constant", cval=0.0)
+    ratio = np.abs(den) / mass
+    bound = TOL + 2e-7 * np.sum(np.abs(p.ak)) * (1 + np.abs(ref)) / np.maximum(ratio, 1e-12)
+    check = np.abs(den) > 10 * p.den_eps
+    src = torch.from_numpy(img).cuda()
+    default = bf.bf_launch_info(plan, H, W)
+    cands = bf.bf_launch_candidates(plan, H, W)
+    pick = cands[np.random.default_rng(seed_geo).integers(0, len(cands))]
+    for geo in (None, pick):
+        if geo is not None:
+            bf.bf_set_launch(plan, H, W, geo)
+        dst = torch.full_like(src, float("nan"))
+        try:
+            bf.bf_filter(plan, src, dst)
+            torch.cuda.synchronize()
+        finally:
+            if geo is not None:
+                bf.bf_set_launch(plan, H, W, default)
+        got = dst.cpu().numpy().astype(np.float64)
+        err = np.abs(got - ref)
+        assert np.all(err[check] <= bound[check]), (kw, geo, float(np.max(err[check] / bound[check])))
