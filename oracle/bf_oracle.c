@@ -27,7 +27,11 @@
  *     Eqs. (30) and (33) (the definition of the approximation);
  *   - O3 the paper's fast algorithm, Eqs. (34)-(36): basis images, signed
  *     2-D boxes from App. A / Eq. (37), box sums by 2-D summed-area tables
- *     (Eqs. (24)-(26)), weighting by cos/sin at I(x), divide.
+ *     (Eqs. (24)-(26)), weighting by cos/sin at I(x), divide;
+ *   - O2-3D / O3-3D the 3-D form of Sec. IV-D: cosine half-period P = T_r and
+ *     the range box applied by dimension promotion (Eq. (2)) over Z intensity
+ *     slices; O3-3D takes per-slice 2-D box sums (Eq. (28)) and sums them over
+ *     the slice window along z (Eq. (29)).
  *
  * Readings of points the paper leaves open (all listed in the design doc):
  *   - square spatial window |y-x|_inf <= R, R = round(3 sigma_s) by default,
@@ -44,7 +48,10 @@
  *     range box of Eq. (33) is identically 1 on the data (Case 1 of Sec. V-C,
  *     "extend the truncated region"); k = 0 is a candidate;
  *   - pixels outside the image are excluded (zero padding, num and den);
- *   - den <= 1e-6 * (sum |K~_s|)(sum |a_k|) -> output I(x) and count it.
+ *   - den <= 1e-6 * (sum |K~_s|)(sum |a_k|) -> output I(x) and count it;
+ *   - 3-D form: Z levels n dI / (Z - 1) on [0, dI]; a pixel's slice is its
+ *     nearest level, decided in fp32; the window along z is R_z =
+ *     floor(T_r (Z - 1) / dI) slices each side; the basis uses I(y) itself.
  *
  * Parity pinned by tests/test_oracle_*.py; see the design doc for the pin list.
  */
@@ -67,6 +74,7 @@
 /* range policies */
 #define ORC_TRUNCATED_MIN_PERIOD 0
 #define ORC_UNTRUNCATED_FULL 1
+#define ORC_PAPER_3D 2        /* P = T_r; the range box is applied over intensity bins (the 3-D form) */
 #define ORC_PAPER_TRUNCATED 3 /* P = T_r exactly (the paper's own series, used for Table VII) */
 
 static const double ORC_PI = 3.14159265358979323846;
@@ -105,7 +113,7 @@ double orc_default_tr(int kind, double sigma_r)
 double orc_period(int policy, double t_r, double data_range)
 {
     if (policy == ORC_UNTRUNCATED_FULL) return data_range;
-    if (policy == ORC_PAPER_TRUNCATED) return t_r;
+    if (policy == ORC_PAPER_TRUNCATED || policy == ORC_PAPER_3D) return t_r;
     double p = 0.5 * (data_range + t_r);
     return p > t_r ? p : t_r;
 }
@@ -784,6 +792,26 @@ static double sat_rect(const double *S, int H, int W, int x0, int x1, int y0, in
 
 typedef struct { int x0, x1, y0, y1; double c; } dbox;
 
+/* The signed discrete boxes of Eq. (37) for the plan's selected Haar terms: products of the 1-D piece
+ * ranges (at most 16 per term).  Returns the count. */
+static int plan_boxes(const orc_plan *p, dbox *boxes)
+{
+    int nb = 0;
+    for (int i = 0; i < p->ns; i++) {
+        drange rx[4], ry[4];
+        int nx = haar_ranges(p->sl1[i], p->sk1[i], p->Ts, rx);
+        int ny = haar_ranges(p->sl2[i], p->sk2[i], p->Ts, ry);
+        for (int a = 0; a < nx; a++)
+            for (int b = 0; b < ny; b++) {
+                if (rx[a].lo > rx[a].hi || ry[b].lo > ry[b].hi) continue;
+                dbox *e = &boxes[nb++];
+                e->x0 = rx[a].lo; e->x1 = rx[a].hi; e->y0 = ry[b].lo; e->y1 = ry[b].hi;
+                e->c = p->sc[i] * rx[a].w * ry[b].w;
+            }
+    }
+    return nb;
+}
+
 int orc_approx_fast(const double *I, int H, int W,
                     int skind, double sigma_s, int radius, int ns_terms,
                     int rkind, double sigma_r, double t_r, int nr_terms, int policy, double data_range,
@@ -798,19 +826,7 @@ int orc_approx_fast(const double *I, int H, int W,
 
     /* signed discrete boxes of Eq. (37): products of the 1-D piece ranges */
     dbox *boxes = malloc(sizeof(dbox) * 16 * p.ns);
-    int nb = 0;
-    for (int i = 0; i < p.ns; i++) {
-        drange rx[4], ry[4];
-        int nx = haar_ranges(p.sl1[i], p.sk1[i], p.Ts, rx);
-        int ny = haar_ranges(p.sl2[i], p.sk2[i], p.Ts, ry);
-        for (int a = 0; a < nx; a++)
-            for (int b = 0; b < ny; b++) {
-                if (rx[a].lo > rx[a].hi || ry[b].lo > ry[b].hi) continue;
-                dbox *e = &boxes[nb++];
-                e->x0 = rx[a].lo; e->x1 = rx[a].hi; e->y0 = ry[b].lo; e->y1 = ry[b].hi;
-                e->c = p.sc[i] * rx[a].w * ry[b].w;
-            }
-    }
+    int nb = boxes ? plan_boxes(&p, boxes) : 0;
 
     double *num = calloc(np, sizeof(double)), *den = calloc(np, sizeof(double));
     double *g = malloc(sizeof(double) * np * 4);
@@ -873,6 +889,164 @@ int orc_box_count(int skind, double sigma_s, int radius, int ns_terms,
     }
     plan_free(&p);
     return nb;
+}
+
+/* ------------------------------------------------------------------ */
+/* The 3-D form (Sec. IV-D): P = T_r, the range box applied by          */
+/* dimension promotion (Eq. (2)) over intensity bins z                  */
+/* ------------------------------------------------------------------ */
+
+/* The z axis: the data range [0, dI] sampled at Z levels n dI / (Z - 1), n = 0 .. Z - 1 (for 8-bit data,
+ * Z = 256 and the levels are the 256 intensities of Sec. II-B).  A pixel sits in the slice of its nearest
+ * level.  The decision is taken in fp32, as the images are fp32: n = rint(I * s), s = fl32((Z - 1) / dI),
+ * ties to even, clamped to [0, Z - 1]. */
+static float z_scale(int Z, double data_range) { return (float)((Z - 1) / data_range); }
+
+static int z_bin(double I, float s, int Z)
+{
+    float t = nearbyintf((float)I * s);
+    if (!(t > 0.0f)) return 0;
+    if (t > (float)(Z - 1)) return Z - 1;
+    return (int)t;
+}
+
+/* The window along z: slices within R_z = floor(T_r (Z - 1) / dI) of the centre pixel's slice, i.e. the
+ * levels inside [I(x) - T_r, I(x) + T_r] (Eq. (35)) for on-grid data.  The 1e-9 absorbs the rounding of
+ * T_r (Z - 1) / dI when T_r is a whole number of levels. */
+static int z_radius(double Tr, int Z, double data_range) { return (int)floor(Tr * (Z - 1) / data_range + 1e-9); }
+
+/* O2-3D: the definition.  Eq. (1) with K~_s (Eq. (30)), the cosine series of period 2 T_r (Eq. (33) with
+ * P = T_r) and the range box over slices: neighbour y counts for centre x iff |n(y) - n(x)| <= R_z. */
+int orc_approx3d_direct(const double *I, int H, int W,
+                        int skind, double sigma_s, int radius, int ns_terms,
+                        int rkind, double sigma_r, double t_r, int nr_terms, int policy, double data_range,
+                        int zbins, double *out, int *ndegen, int nthreads)
+{
+    if (!I || !out || H < 0 || W < 0 || policy != ORC_PAPER_3D || zbins < 2 || !(data_range > 0)) return ORC_EINVAL;
+    orc_plan p;
+    int st = plan_build(&p, skind, sigma_s, radius, ns_terms, rkind, sigma_r, t_r, nr_terms, policy, data_range);
+    if (st) { plan_free(&p); return st; }
+    const int R = p.R, w = 2 * R + 1, Z = zbins, Rz = z_radius(p.Tr, Z, data_range);
+    const float zs = z_scale(Z, data_range);
+    int degen = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+:degen) num_threads(nthreads > 0 ? nthreads : 1)
+    for (int y = 0; y < H; y++) {
+        for (int x = 0; x < W; x++) {
+            double ix = I[(size_t)y * W + x], num = 0.0, den = 0.0;
+            int nx = z_bin(ix, zs, Z);
+            for (int dy = -R; dy <= R; dy++) {
+                int yy = y + dy;
+                if (yy < 0 || yy >= H) continue;
+                for (int dx = -R; dx <= R; dx++) {
+                    int xx = x + dx;
+                    if (xx < 0 || xx >= W) continue;
+                    double iy = I[(size_t)yy * W + xx];
+                    if (abs(z_bin(iy, zs, Z) - nx) > Rz) continue;
+                    double ks = p.Ks[(-dy + R) * w + (-dx + R)];
+                    if (ks == 0.0) continue;
+                    double kr = 0.0, t = ix - iy;
+                    for (int i = 0; i < p.nr; i++) kr += p.ak[i] * cos(ORC_PI * p.ks[i] * t / p.P);
+                    num += ks * kr * iy;
+                    den += ks * kr;
+                }
+            }
+            if (den <= p.den_eps) { out[(size_t)y * W + x] = ix; degen++; }
+            else out[(size_t)y * W + x] = num / den;
+        }
+    }
+    if (ndegen) *ndegen = degen;
+    plan_free(&p);
+    return ORC_OK;
+}
+
+/* O3-3D: the paper's steps.  For each term k the auxiliary images of Eq. (35) are one-hot in z:
+ * F(y, z) = g(y) [n(y) = z] for the four basis images g of Eq. (34).  For every slice z the 2-D box sums
+ * of the signed boxes (Eq. (37)) come from 2-D summed-area tables of the slice (Eq. (28)); the sum over
+ * the window [n(x) - R_z, n(x) + R_z] along z (Eq. (29)) is accumulated slice by slice at the pixels
+ * whose window holds z (the sliding-window form of the 1-D table along z, Sec. V).  The window sums are
+ * then weighted by a_k cos / sin at I(x) (Eq. (36)) and divided.  Slices no pixel falls in contribute
+ * zero and are skipped. */
+int orc_approx3d_fast(const double *I, int H, int W,
+                      int skind, double sigma_s, int radius, int ns_terms,
+                      int rkind, double sigma_r, double t_r, int nr_terms, int policy, double data_range,
+                      int zbins, double *out, int *ndegen, int nthreads, double *den_out)
+{
+    if (!I || !out || H < 0 || W < 0 || policy != ORC_PAPER_3D || zbins < 2 || !(data_range > 0)) return ORC_EINVAL;
+    orc_plan p;
+    int st = plan_build(&p, skind, sigma_s, radius, ns_terms, rkind, sigma_r, t_r, nr_terms, policy, data_range);
+    if (st) { plan_free(&p); return st; }
+    size_t np = (size_t)H * W;
+    if (np == 0) { if (ndegen) *ndegen = 0; plan_free(&p); return ORC_OK; }
+    const int Z = zbins, Rz = z_radius(p.Tr, Z, data_range);
+    const float zs = z_scale(Z, data_range);
+
+    dbox *boxes = malloc(sizeof(dbox) * 16 * p.ns);
+    int nb = boxes ? plan_boxes(&p, boxes) : 0;
+    double *num = calloc(np, sizeof(double)), *den = calloc(np, sizeof(double));
+    double *g = malloc(sizeof(double) * np * 4);
+    double *S = malloc(sizeof(double) * (size_t)(H + 1) * (W + 1) * 4);
+    double *F = malloc(sizeof(double) * np * 4);
+    double *cb = malloc(sizeof(double) * np), *sb = malloc(sizeof(double) * np);
+    int *nz = malloc(sizeof(int) * np), *occupied = calloc((size_t)Z, sizeof(int));
+    if (!num || !den || !g || !S || !F || !cb || !sb || !boxes || !nz || !occupied) {
+        free(num); free(den); free(g); free(S); free(F); free(cb); free(sb); free(boxes); free(nz); free(occupied);
+        plan_free(&p);
+        return ORC_ECAP;
+    }
+    for (size_t i = 0; i < np; i++) { nz[i] = z_bin(I[i], zs, Z); occupied[nz[i]] = 1; }
+    int nt = nthreads > 0 ? nthreads : 1;
+    for (int r = 0; r < p.nr; r++) {
+        double wk = ORC_PI * p.ks[r] / p.P, ak = p.ak[r];
+        for (size_t i = 0; i < np; i++) { cb[i] = cos(wk * I[i]); sb[i] = sin(wk * I[i]); }
+        memset(F, 0, sizeof(double) * np * 4);
+        for (int z = 0; z < Z; z++) {
+            if (!occupied[z]) continue;
+            /* slice z of the auxiliary images: the basis images where n(y) = z, zero elsewhere */
+            for (size_t i = 0; i < np; i++) {
+                int on = nz[i] == z;
+                g[i] = on ? cb[i] * I[i] : 0.0; g[np + i] = on ? sb[i] * I[i] : 0.0;
+                g[2 * np + i] = on ? cb[i] : 0.0; g[3 * np + i] = on ? sb[i] : 0.0;
+            }
+#pragma omp parallel for num_threads(nt)
+            for (int q = 0; q < 4; q++) sat_build(g + q * np, H, W, S + (size_t)q * (H + 1) * (W + 1));
+#pragma omp parallel for schedule(static) num_threads(nt)
+            for (int y = 0; y < H; y++)
+                for (int x = 0; x < W; x++) {
+                    size_t i = (size_t)y * W + x;
+                    if (abs(nz[i] - z) > Rz) continue;
+                    for (int b = 0; b < nb; b++) {
+                        const dbox *e = &boxes[b];
+                        for (int q = 0; q < 4; q++)
+                            F[q * np + i] += e->c * sat_rect(S + (size_t)q * (H + 1) * (W + 1), H, W, x + e->x0,
+                                                             x + e->x1, y + e->y0, y + e->y1);
+                    }
+                }
+        }
+        for (size_t i = 0; i < np; i++) {
+            num[i] += ak * (cb[i] * F[i] + sb[i] * F[np + i]);
+            den[i] += ak * (cb[i] * F[2 * np + i] + sb[i] * F[3 * np + i]);
+        }
+    }
+    int degen = 0;
+    for (size_t i = 0; i < np; i++) {
+        if (den[i] <= p.den_eps) { out[i] = I[i]; degen++; }
+        else out[i] = num[i] / den[i];
+        if (den_out) den_out[i] = den[i];
+    }
+    if (ndegen) *ndegen = degen;
+    free(num); free(den); free(g); free(S); free(F); free(cb); free(sb); free(boxes); free(nz); free(occupied);
+    plan_free(&p);
+    return ORC_OK;
+}
+
+/* The z axis of a plan (for the tests): R_z and the fp32 bin of each listed intensity. */
+int orc_z_bins(double t_r_resolved, int zbins, double data_range, const double *I, int n, int *bins_out, int *rz_out)
+{
+    if (zbins < 2 || !(data_range > 0) || n < 0) return ORC_EINVAL;
+    const float zs = z_scale(zbins, data_range);
+    for (int i = 0; i < n; i++) bins_out[i] = z_bin(I[i], zs, zbins);
+    if (rz_out) *rz_out = z_radius(t_r_resolved, zbins, data_range);
+    return ORC_OK;
 }
 
 int orc_max_threads(void)

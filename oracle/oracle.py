@@ -8,6 +8,8 @@ exposes numpy-level functions:
 * ``exact_bf``       -- O1, Eq. (1) by brute force;
 * ``approx_direct``  -- O2, Eq. (1) with the approximated kernels (Eqs. (30), (33));
 * ``approx_fast``    -- O3, the paper's algorithm (Eqs. (34)-(36), App. A boxes);
+* ``approx3d_direct`` / ``approx3d_fast`` -- O2 / O3 of the 3-D form (Sec. IV-D: P = T_r, the range box
+  applied over Z intensity slices by dimension promotion, Eqs. (2), (28)-(29), (35)-(36));
 * ``range_coeffs``, ``haar1d``, ``plan_info`` -- coefficient and selection steps.
 
 Every function follows the paper step by step; the C file header lists the
@@ -28,7 +30,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liborc.so")
 
 GAUSSIAN, EXPONENTIAL, BOX = 0, 1, 2
-TRUNCATED_MIN_PERIOD, UNTRUNCATED_FULL, PAPER_TRUNCATED = 0, 1, 3
+TRUNCATED_MIN_PERIOD, UNTRUNCATED_FULL, PAPER_3D, PAPER_TRUNCATED = 0, 1, 2, 3
 
 _lib = None
 
@@ -71,6 +73,9 @@ def _load():
         lib.orc_rect_int_exp.argtypes = [d, d, d, d, d]
         lib.orc_rect_int_exp.restype = d
         lib.orc_haar2d_exp.argtypes = [d, d, i, pd, i]
+        lib.orc_approx3d_direct.argtypes = [pd, i, i, i, d, i, i, i, d, d, i, i, d, i, pd, pi, i]
+        lib.orc_approx3d_fast.argtypes = [pd, i, i, i, d, i, i, i, d, d, i, i, d, i, pd, pi, i, pd]
+        lib.orc_z_bins.argtypes = [d, i, d, pd, i, pi, pi]
         _lib = lib
     return _lib
 
@@ -288,3 +293,42 @@ def approx_direct_at(I, desc: Desc, pts, threads: int = 1) -> np.ndarray:
 
 def box_count(desc: Desc) -> int:
     return int(_load().orc_box_count(*desc.args()))
+
+
+def approx3d_direct(I, desc: Desc, zbins: int = 256, threads: int = 1):
+    """O2-3D (desc.policy must be PAPER_3D): returns (output, guard count)."""
+    I = _img(I)
+    H, W = I.shape
+    out = np.zeros((H, W))
+    nd = np.zeros(1, dtype=np.int32)
+    st = _load().orc_approx3d_direct(_dp(I), H, W, *desc.args(), zbins, _dp(out), _ip(nd), threads)
+    if st:
+        raise ValueError("orc_approx3d_direct status %d" % st)
+    return out, int(nd[0])
+
+
+def approx3d_fast(I, desc: Desc, zbins: int = 256, threads: int = 1, return_den: bool = False):
+    """O3-3D (desc.policy must be PAPER_3D): returns (output, guard count)[, denominator]."""
+    I = _img(I)
+    H, W = I.shape
+    out = np.zeros((H, W))
+    den = np.zeros((H, W)) if return_den else None
+    nd = np.zeros(1, dtype=np.int32)
+    st = _load().orc_approx3d_fast(_dp(I), H, W, *desc.args(), zbins, _dp(out), _ip(nd), threads,
+                                   _dp(den) if return_den else None)
+    if st:
+        raise ValueError("orc_approx3d_fast status %d" % st)
+    if return_den:
+        return out, int(nd[0]), den
+    return out, int(nd[0])
+
+
+def z_bins(I, t_r: float, zbins: int = 256, data_range: float = 1.0):
+    """(slice index of each intensity, R_z) on the z axis of the 3-D form; t_r already resolved."""
+    v = np.ascontiguousarray(np.ravel(I), dtype=np.float64)
+    out = np.zeros(len(v), dtype=np.int32)
+    rz = np.zeros(1, dtype=np.int32)
+    st = _load().orc_z_bins(t_r, zbins, data_range, _dp(v), len(v), _ip(out), _ip(rz))
+    if st:
+        raise ValueError("orc_z_bins status %d" % st)
+    return out.reshape(np.shape(I)), int(rz[0])
