@@ -255,7 +255,7 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = run_e2e(args, bf, plans, img, dev, stream)
 
-    batched = serving = nr_sweep = large = bft = pre = None
+    batched = serving = nr_sweep = large = bft = pre = p3d = None
     if not args.no_extras and world == 1:
         batched = run_batched(bf, dev)
         serving = run_serving(bf, dev)
@@ -263,6 +263,7 @@ def run_ours(args):
         large = run_large(bf, dev, flush)
         bft = run_bft_crossover(bf, dev, src, flush)
         pre = run_precompute(bf, dev, src, flush)
+        p3d = run_paper_3d(bf, dev, src, img, flush, alu_peak)
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
@@ -281,7 +282,7 @@ def run_ours(args):
                 "bytes_per_px": 8},
         "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
         "batched": batched, "serving": serving, "nr_sweep": nr_sweep, "large_images": large,
-        "bft_crossover": bft, "precompute": pre,
+        "bft_crossover": bft, "precompute": pre, "paper_3d": p3d,
         "e2e": e2e,
     }
     if rank == 0:
@@ -385,6 +386,63 @@ def run_precompute(bf, dev, src, flush, reps=5):
     c16.close()
     return {"sigma_s": 8.0, "t_r": 0.9, "kmax": 32, "cache_mib": round(nbytes / 2 ** 20, 1),
             "precompute_ms": round(t_pre, 3), "by_sigma_r": rows}
+
+
+def slice_passes(img, tw, th, zbins=256):
+    """Tile passes of the 3-D form (work items of its list): per tile, the distinct slices among its
+    output pixels, by the slice rule of the plan (nearest of zbins levels on [0, 1], decided in fp32)."""
+    n = np.clip(np.rint(img.astype(np.float32) * np.float32(zbins - 1)), 0, zbins - 1).astype(np.int32)
+    h, w = n.shape
+    items = 0
+    for y0 in range(0, h, th):
+        for x0 in range(0, w, tw):
+            items += len(np.unique(n[y0:y0 + th, x0:x0 + tw]))
+    return items
+
+
+def run_paper_3d(bf, dev, src, img, flush, alu_peak, reps=3):
+    """The 3-D form of Sec. IV-D (P = T_r, the range box applied over 256 intensity slices, N_r = 8,
+    N_s = 5) on the 1920x1080 image for every (sigma_s, sigma_r) of the sweep: device ms, Mpixel/s and
+    PSNR against the exact filter, beside the collapsed form's PSNR at the same N_r, plus the same at
+    N_r = 4 (the 3-D form's series fits one period of the truncated kernel, so it needs fewer terms).
+    Each plan is autotuned first, as the sweep's plans are.  Work: one tile pass per (tile, slice present
+    in the tile); `passes_per_px` = items x tile area / pixels, and the roofline fraction counts each pass
+    as a filter pass over its tile's pixels."""
+    import torch
+    out = torch.empty_like(src)
+    ex = torch.empty_like(src)
+    rows = []
+    total_ms = 0.0
+    for ss in SIGMA_S:
+        for sr in SIGMA_R:
+            bf.bf_exact(src, ex, sigma_s=ss, sigma_r=sr)
+            row = {"sigma_s": ss, "sigma_r": sr}
+            for nr in (8, 4):
+                p3 = bf.Plan(sigma_s=ss, sigma_r=sr, nr_terms=nr, ns_terms=NS, device=dev.index,
+                             policy=bf.RANGE_PAPER_3D, z_bins=256)
+                bf.bf_autotune(p3, H, W)
+                t = timed_launches(bf, p3, src, out, flush, reps)
+                mse3 = torch.mean((out.double() - ex.double()) ** 2).item()
+                pc = bf.Plan(sigma_s=ss, sigma_r=sr, nr_terms=nr, ns_terms=NS, device=dev.index)
+                bf.bf_filter(pc, src, out)
+                torch.cuda.synchronize()
+                msec = torch.mean((out.double() - ex.double()) ** 2).item()
+                tag = "" if nr == 8 else "_nr4"
+                row["ms" + tag] = round(t, 3)
+                row["mpix_s" + tag] = round(H * W / (t * 1e-3) / 1e6, 1)
+                row["psnr_db" + tag] = round(10 * np.log10(1.0 / mse3), 2)
+                row["collapsed_psnr_db" + tag] = round(10 * np.log10(1.0 / msec), 2)
+                if nr == 8:
+                    info = bf.bf_launch_info(p3, H, W)
+                    items = slice_passes(img, info["tw"], info["th"])
+                    ops = algorithmic_ops_per_pixel(p3.coeffs()) * items * info["tw"] * info["th"]
+                    row["tile"] = [info["tw"], info["th"], info["nk"], info["depth"], info["ncols"]]
+                    row["passes_per_px"] = round(items * info["tw"] * info["th"] / (H * W), 1)
+                    row["roofline_frac"] = round(ops / (t * 1e-3) / 1e12 / alu_peak, 4)
+                    total_ms += t
+            rows.append(row)
+    return {"z_bins": 256, "ns_terms": NS, "mpix_s_sweep": round(len(rows) * H * W / (total_ms * 1e-3) / 1e6, 1),
+            "by_combo": rows}
 
 
 def run_bft_crossover(bf, dev, src, flush, reps=5):

@@ -72,9 +72,18 @@ typedef enum {
     BF_RANGE_TRUNCATED_MIN_PERIOD = 0,
     /* P = dI and the kernel is fitted untruncated on [-dI, dI]. */
     BF_RANGE_UNTRUNCATED_FULL = 1,
-    /* P = T_r with the range box applied by dimension promotion over
-     * intensity bins (Eqs. (35)-(36) with z).  Not implemented in this build:
-     * bf_plan_create returns BF_ERR_UNSUPPORTED. */
+    /* The 3-D form of Sec. IV-D: P = T_r (the kernel truncated at T_r is
+     * fitted on one period) and the range box [I(x) - T_r, I(x) + T_r] is
+     * applied by dimension promotion (Eq. (2)) over Z intensity slices
+     * (z_bins): the data range is sampled at Z levels i_lo + n dI / (Z - 1),
+     * a pixel lies in the slice of its nearest level (n = rint((I - i_lo) s)
+     * in fp32, s = fl32((Z - 1) / dI), clamped to [0, Z - 1]), and neighbour
+     * y counts for centre x iff |n(y) - n(x)| <= R_z = floor(T_r (Z - 1) /
+     * dI).  Eqs. (35)-(36): the window sums are 3-D boxes, box over space
+     * times the slice window along z.  The basis images use I(y) itself
+     * (for data on the Z levels, e.g. 8-bit images with Z = 256, the window
+     * is exactly the range box).  Cost: every tile is filtered once per
+     * distinct slice among its output pixels. */
     BF_RANGE_PAPER_3D = 2
 } bf_range_policy;
 
@@ -115,13 +124,16 @@ typedef struct {
                            running sums restart at every tile (at most a tile height of rows). */
     int device;         /* CUDA device ordinal; -1: host-only plan (bf_coeffs works,
                            filtering returns BF_ERR_NO_DEVICE) */
+    int z_bins;         /* BF_RANGE_PAPER_3D: intensity slices Z in [2, 4096]; 0 -> 256 (the
+                           8-bit case of Sec. II-B).  Ignored by the other policies. */
 } bf_plan_desc;
 
 typedef struct bf_plan bf_plan;
 
 /* Fills *desc with defaults: Gaussian/Gaussian, sigma_s = 4, R = 0 (auto),
  * N_s = 5 (the paper's three-box setting, Sec. V-C), sigma_r = 0.1, N_r = 8,
- * truncated-min-period policy, data range [0, 1], fp32, no Kahan, device 0. */
+ * truncated-min-period policy, data range [0, 1], fp32, Kahan on, device 0,
+ * z_bins = 0 (256). */
 void bf_plan_desc_default(bf_plan_desc *desc);
 
 /* Builds a plan (Sec. IV-A..C; App. B): truncation points, range cosine
@@ -135,9 +147,10 @@ void bf_plan_desc_default(bf_plan_desc *desc);
  * compiled into nested horizontal and vertical box windows for the kernel.
  * Host memory only; the coefficient tables travel to the device as kernel
  * parameters.  *out receives a plan the caller releases with bf_plan_destroy.
- * Errors: BF_ERR_INVALID_ARG (NULL, sigma <= 0, N < 1, i_hi <= i_lo, bad enum),
- * BF_ERR_UNSUPPORTED (BF_RANGE_PAPER_3D; exponential spatial kernel with
- * R > 255; a selection needing more than 6 box windows per axis),
+ * Errors: BF_ERR_INVALID_ARG (NULL, sigma <= 0, N < 1, i_hi <= i_lo, bad enum,
+ * z_bins outside [2, 4096] for BF_RANGE_PAPER_3D),
+ * BF_ERR_UNSUPPORTED (exponential spatial kernel with R > 255; a selection
+ * needing more than 6 box windows per axis; 16-bit precision),
  * BF_ERR_OOM, BF_ERR_NO_DEVICE (device >= 0 that does not exist). */
 bf_status bf_plan_create(const bf_plan_desc *desc, bf_plan **out);
 
@@ -165,10 +178,13 @@ typedef struct {
     const int *vwin;            /* [2 n_vwin] first/last neighbour row offset */
     const int *hwin;            /* [2 n_hwin] first/last neighbour column offset */
     const double *wcoef;        /* [n_vwin * n_hwin] weight of window pair (v, h) */
-    double range_max_err;       /* max |K_r - K~_r| over [-dI, dI] (sampled) */
+    double range_max_err;       /* max |K_r - K~_r| over [-dI, dI] (sampled); BF_RANGE_PAPER_3D:
+                                   over [-T_r, T_r], where the range box keeps the series */
     double spatial_max_err;     /* max |K_s - K~_s| over the integer window */
     double den_eps;             /* denominator guard: den <= den_eps -> output I(x) */
     int passes;                 /* term groups at the largest group size (ceil(nr / 16)) */
+    int z_bins;                 /* BF_RANGE_PAPER_3D: slices Z; 0 for the other policies */
+    int z_radius;               /* BF_RANGE_PAPER_3D: slice window half-width R_z; 0 otherwise */
 } bf_coeff_view;
 
 /* Fills *out with the plan's coefficients.  Errors: BF_ERR_INVALID_ARG. */

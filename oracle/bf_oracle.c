@@ -915,46 +915,87 @@ static int z_bin(double I, float s, int Z)
  * T_r (Z - 1) / dI when T_r is a whole number of levels. */
 static int z_radius(double Tr, int Z, double data_range) { return (int)floor(Tr * (Z - 1) / data_range + 1e-9); }
 
-/* O2-3D: the definition.  Eq. (1) with K~_s (Eq. (30)), the cosine series of period 2 T_r (Eq. (33) with
- * P = T_r) and the range box over slices: neighbour y counts for centre x iff |n(y) - n(x)| <= R_z. */
+/* O2-3D at one pixel: Eq. (1) with K~_s (Eq. (30)), the cosine series of period 2 T_r (Eq. (33) with
+ * P = T_r) and the range box over slices: neighbour y counts for centre x iff |n(y) - n(x)| <= R_z.
+ * Returns the numerator and denominator. */
+static void direct3d_at(const orc_plan *p, const double *I, int H, int W, int y, int x, float zs, int Z, int Rz,
+                        double *num_out, double *den_out)
+{
+    const int R = p->R, w = 2 * R + 1;
+    double ix = I[(size_t)y * W + x], num = 0.0, den = 0.0;
+    int nx = z_bin(ix, zs, Z);
+    for (int dy = -R; dy <= R; dy++) {
+        int yy = y + dy;
+        if (yy < 0 || yy >= H) continue;
+        for (int dx = -R; dx <= R; dx++) {
+            int xx = x + dx;
+            if (xx < 0 || xx >= W) continue;
+            double iy = I[(size_t)yy * W + xx];
+            if (abs(z_bin(iy, zs, Z) - nx) > Rz) continue;
+            double ks = p->Ks[(-dy + R) * w + (-dx + R)];
+            if (ks == 0.0) continue;
+            double kr = 0.0, t = ix - iy;
+            for (int i = 0; i < p->nr; i++) kr += p->ak[i] * cos(ORC_PI * p->ks[i] * t / p->P);
+            num += ks * kr * iy;
+            den += ks * kr;
+        }
+    }
+    *num_out = num;
+    *den_out = den;
+}
+
+/* O2-3D: the definition at every pixel (den_out, if not NULL, receives the denominators). */
 int orc_approx3d_direct(const double *I, int H, int W,
                         int skind, double sigma_s, int radius, int ns_terms,
                         int rkind, double sigma_r, double t_r, int nr_terms, int policy, double data_range,
-                        int zbins, double *out, int *ndegen, int nthreads)
+                        int zbins, double *out, int *ndegen, int nthreads, double *den_out)
 {
     if (!I || !out || H < 0 || W < 0 || policy != ORC_PAPER_3D || zbins < 2 || !(data_range > 0)) return ORC_EINVAL;
     orc_plan p;
     int st = plan_build(&p, skind, sigma_s, radius, ns_terms, rkind, sigma_r, t_r, nr_terms, policy, data_range);
     if (st) { plan_free(&p); return st; }
-    const int R = p.R, w = 2 * R + 1, Z = zbins, Rz = z_radius(p.Tr, Z, data_range);
+    const int Z = zbins, Rz = z_radius(p.Tr, Z, data_range);
     const float zs = z_scale(Z, data_range);
     int degen = 0;
 #pragma omp parallel for schedule(dynamic, 1) reduction(+:degen) num_threads(nthreads > 0 ? nthreads : 1)
     for (int y = 0; y < H; y++) {
         for (int x = 0; x < W; x++) {
-            double ix = I[(size_t)y * W + x], num = 0.0, den = 0.0;
-            int nx = z_bin(ix, zs, Z);
-            for (int dy = -R; dy <= R; dy++) {
-                int yy = y + dy;
-                if (yy < 0 || yy >= H) continue;
-                for (int dx = -R; dx <= R; dx++) {
-                    int xx = x + dx;
-                    if (xx < 0 || xx >= W) continue;
-                    double iy = I[(size_t)yy * W + xx];
-                    if (abs(z_bin(iy, zs, Z) - nx) > Rz) continue;
-                    double ks = p.Ks[(-dy + R) * w + (-dx + R)];
-                    if (ks == 0.0) continue;
-                    double kr = 0.0, t = ix - iy;
-                    for (int i = 0; i < p.nr; i++) kr += p.ak[i] * cos(ORC_PI * p.ks[i] * t / p.P);
-                    num += ks * kr * iy;
-                    den += ks * kr;
-                }
-            }
-            if (den <= p.den_eps) { out[(size_t)y * W + x] = ix; degen++; }
-            else out[(size_t)y * W + x] = num / den;
+            size_t i = (size_t)y * W + x;
+            double num, den;
+            direct3d_at(&p, I, H, W, y, x, zs, Z, Rz, &num, &den);
+            if (den <= p.den_eps) { out[i] = I[i]; degen++; }
+            else out[i] = num / den;
+            if (den_out) den_out[i] = den;
         }
     }
     if (ndegen) *ndegen = degen;
+    plan_free(&p);
+    return ORC_OK;
+}
+
+/* O2-3D at the listed pixels only (pts: npts (row, col) pairs), for sampled checks of large images. */
+int orc_approx3d_direct_at(const double *I, int H, int W,
+                           int skind, double sigma_s, int radius, int ns_terms,
+                           int rkind, double sigma_r, double t_r, int nr_terms, int policy, double data_range,
+                           int zbins, const int *pts, int npts, double *out, double *den_out, int nthreads)
+{
+    if (!I || !out || !pts || H < 1 || W < 1 || npts < 0 || policy != ORC_PAPER_3D || zbins < 2 || !(data_range > 0))
+        return ORC_EINVAL;
+    for (int n = 0; n < npts; n++)
+        if (pts[2 * n] < 0 || pts[2 * n] >= H || pts[2 * n + 1] < 0 || pts[2 * n + 1] >= W) return ORC_EINVAL;
+    orc_plan p;
+    int st = plan_build(&p, skind, sigma_s, radius, ns_terms, rkind, sigma_r, t_r, nr_terms, policy, data_range);
+    if (st) { plan_free(&p); return st; }
+    const int Z = zbins, Rz = z_radius(p.Tr, Z, data_range);
+    const float zs = z_scale(Z, data_range);
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads > 0 ? nthreads : 1)
+    for (int n = 0; n < npts; n++) {
+        int y = pts[2 * n], x = pts[2 * n + 1];
+        double num, den;
+        direct3d_at(&p, I, H, W, y, x, zs, Z, Rz, &num, &den);
+        out[n] = den <= p.den_eps ? I[(size_t)y * W + x] : num / den;
+        if (den_out) den_out[n] = den;
+    }
     plan_free(&p);
     return ORC_OK;
 }

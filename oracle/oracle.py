@@ -73,7 +73,8 @@ def _load():
         lib.orc_rect_int_exp.argtypes = [d, d, d, d, d]
         lib.orc_rect_int_exp.restype = d
         lib.orc_haar2d_exp.argtypes = [d, d, i, pd, i]
-        lib.orc_approx3d_direct.argtypes = [pd, i, i, i, d, i, i, i, d, d, i, i, d, i, pd, pi, i]
+        lib.orc_approx3d_direct.argtypes = [pd, i, i, i, d, i, i, i, d, d, i, i, d, i, pd, pi, i, pd]
+        lib.orc_approx3d_direct_at.argtypes = [pd, i, i, i, d, i, i, i, d, d, i, i, d, i, pi, i, pd, pd, i]
         lib.orc_approx3d_fast.argtypes = [pd, i, i, i, d, i, i, i, d, d, i, i, d, i, pd, pi, i, pd]
         lib.orc_z_bins.argtypes = [d, i, d, pd, i, pi, pi]
         _lib = lib
@@ -295,16 +296,34 @@ def box_count(desc: Desc) -> int:
     return int(_load().orc_box_count(*desc.args()))
 
 
-def approx3d_direct(I, desc: Desc, zbins: int = 256, threads: int = 1):
-    """O2-3D (desc.policy must be PAPER_3D): returns (output, guard count)."""
+def approx3d_direct(I, desc: Desc, zbins: int = 256, threads: int = 1, return_den: bool = False):
+    """O2-3D (desc.policy must be PAPER_3D): returns (output, guard count)[, denominator]."""
     I = _img(I)
     H, W = I.shape
     out = np.zeros((H, W))
+    den = np.zeros((H, W)) if return_den else None
     nd = np.zeros(1, dtype=np.int32)
-    st = _load().orc_approx3d_direct(_dp(I), H, W, *desc.args(), zbins, _dp(out), _ip(nd), threads)
+    st = _load().orc_approx3d_direct(_dp(I), H, W, *desc.args(), zbins, _dp(out), _ip(nd), threads,
+                                     _dp(den) if return_den else None)
     if st:
         raise ValueError("orc_approx3d_direct status %d" % st)
+    if return_den:
+        return out, int(nd[0]), den
     return out, int(nd[0])
+
+
+def approx3d_direct_at(I, desc: Desc, pts, zbins: int = 256, threads: int = 1):
+    """O2-3D at the given (row, col) pixels: (output, denominator) arrays."""
+    I = _img(I)
+    H, W = I.shape
+    pts = np.ascontiguousarray(pts, dtype=np.int32).reshape(-1, 2)
+    out = np.zeros(len(pts))
+    den = np.zeros(len(pts))
+    st = _load().orc_approx3d_direct_at(_dp(I), H, W, *desc.args(), zbins, _ip(pts), len(pts), _dp(out), _dp(den),
+                                        threads)
+    if st:
+        raise ValueError("orc_approx3d_direct_at status %d" % st)
+    return out, den
 
 
 def approx3d_fast(I, desc: Desc, zbins: int = 256, threads: int = 1, return_den: bool = False):

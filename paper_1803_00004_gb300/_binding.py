@@ -27,7 +27,7 @@ class bf_plan_desc(C.Structure):
     _fields_ = [("spatial", C.c_int), ("sigma_s", C.c_double), ("radius", C.c_int), ("ns_terms", C.c_int),
                 ("range", C.c_int), ("sigma_r", C.c_double), ("t_r", C.c_double), ("nr_terms", C.c_int),
                 ("policy", C.c_int), ("i_lo", C.c_float), ("i_hi", C.c_float), ("precision", C.c_int),
-                ("kahan", C.c_int), ("device", C.c_int)]
+                ("kahan", C.c_int), ("device", C.c_int), ("z_bins", C.c_int)]
 
 
 class bf_coeff_view(C.Structure):
@@ -37,7 +37,7 @@ class bf_coeff_view(C.Structure):
                 ("tie_split", C.c_int), ("kernel", C.POINTER(C.c_double)), ("n_vwin", C.c_int),
                 ("n_hwin", C.c_int), ("vwin", C.POINTER(C.c_int)), ("hwin", C.POINTER(C.c_int)),
                 ("wcoef", C.POINTER(C.c_double)), ("range_max_err", C.c_double), ("spatial_max_err", C.c_double),
-                ("den_eps", C.c_double), ("passes", C.c_int)]
+                ("den_eps", C.c_double), ("passes", C.c_int), ("z_bins", C.c_int), ("z_radius", C.c_int)]
 
 
 class bf_image(C.Structure):
@@ -195,7 +195,7 @@ def bf_coeffs(plan: Plan) -> dict:
         "hwin": [(v.hwin[2 * j], v.hwin[2 * j + 1]) for j in range(v.n_hwin)],
         "wcoef": [[v.wcoef[a * v.n_hwin + b] for b in range(v.n_hwin)] for a in range(v.n_vwin)],
         "range_max_err": v.range_max_err, "spatial_max_err": v.spatial_max_err, "den_eps": v.den_eps,
-        "passes": v.passes,
+        "passes": v.passes, "z_bins": v.z_bins, "z_radius": v.z_radius,
     }
 
 

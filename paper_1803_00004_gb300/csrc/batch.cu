@@ -73,6 +73,7 @@ bf_status build_batch(const bf_plan *const *plans, const bf_image *images, int n
     std::map<std::pair<int, int>, std::vector<int>> by_class;
     for (int i = 0; i < n; ++i) {
         const FilterParams &kp = plans[i]->kp;
+        if (kp.zbins > 0) return fail(BF_ERR_UNSUPPORTED, "the 3-D form (BF_RANGE_PAPER_3D) runs through bf_filter");
         by_class[{plans[i]->m, kp.k[kp.nr - 1] - kp.k[0] + 1 == kp.nr ? 1 : 0}].push_back(i);
     }
     L.params.resize(n);
@@ -301,6 +302,8 @@ extern "C" bf_status bf_filter_batch(const bf_plan *const *plans, const bf_image
     for (int i = 0; i < n; ++i) {
         if (!plans[i]) return fail(BF_ERR_INVALID_ARG, "NULL plan in batch");
         if (plans[i]->desc.device < 0) return fail(BF_ERR_NO_DEVICE, "host-only plan in batch");
+        if (plans[i]->kp.zbins > 0)
+            return fail(BF_ERR_UNSUPPORTED, "the 3-D form (BF_RANGE_PAPER_3D) runs through bf_filter, not in batches");
         if (device == -2) device = plans[i]->desc.device;
         if (plans[i]->desc.device != device) return fail(BF_ERR_INVALID_ARG, "plans of one batch must share a device");
         const bf_image &im = images[i];

@@ -24,6 +24,12 @@ extern const KernelClass kClassesM3[];
 extern const KernelClass kClassesM4to6[];
 extern const int kNumClassesM1, kNumClassesM2, kNumClassesM3, kNumClassesM4to6;
 
+// The 3-D form's slice kernels (packed family without the ring; bf_tile.cuh): kernels_z_*.cu.
+// fn[0] is the persistent slice kernel, fn[1] and batch_fn are unused.
+extern const KernelClass kZClassesM1M2[];
+extern const KernelClass kZClassesM3to6[];
+extern const int kNumZClassesM1M2, kNumZClassesM3to6;
+
 // Scalar family (any term set; bf_tile_scalar.cuh): kernels_s_*.cu.
 extern const KernelClass kScalarClassesM1M2[];
 extern const KernelClass kScalarClassesM3to6[];

@@ -99,6 +99,58 @@ const void *find_kernel(int m, int nk, bool ring, bool packed) {
     return nullptr;
 }
 
+// The 3-D form's persistent slice kernel of class (m, nk).
+const void *find_zkernel(int m, int nk) {
+    for (const auto *t : {kZClassesM1M2, kZClassesM3to6}) {
+        const int n = t == kZClassesM1M2 ? kNumZClassesM1M2 : kNumZClassesM3to6;
+        for (int i = 0; i < n; ++i)
+            if (t[i].m == m && t[i].nk == nk) return t[i].fn[0];
+    }
+    return nullptr;
+}
+
+// The 3-D form's work list: one CTA per tile marks the slices of the tile's output pixels in a shared
+// bitmap (the same slice rule as the tile body) and appends one item (tile, slice) per marked slice at
+// the position counters[0] hands out.  At most `cap` items are stored.
+__global__ void __launch_bounds__(256) bf_zlist_kernel(const float *__restrict__ in, size_t in_pitch, int H, int W,
+                                                       int tw, int th, int tiles_x, int2 *__restrict__ items, int cap,
+                                                       int *__restrict__ counters,
+                                                       const __grid_constant__ FilterParams p) {
+    __shared__ unsigned bits[kMaxZBins / 32];
+    __shared__ int woff[kMaxZBins / 32];
+    __shared__ int base;
+    const int tile = blockIdx.x, ty = tile / tiles_x, tx = tile - ty * tiles_x;
+    const int x0 = tx * tw, y0 = ty * th, nx = min(tw, W - x0), ny = min(th, H - y0);
+    const int words = (p.zbins + 31) >> 5;
+    for (int i = threadIdx.x; i < words; i += blockDim.x) bits[i] = 0u;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nx * ny; i += blockDim.x) {
+        const int r = i / nx, c = i - r * nx;
+        const int n = z_slice(__ldg(in + (size_t)(y0 + r) * in_pitch + x0 + c) - p.i_lo, p);
+        atomicOr(&bits[n >> 5], 1u << (n & 31));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < words; ++w) {
+            woff[w] = t;
+            t += __popc(bits[w]);
+        }
+        base = atomicAdd(counters, t);
+    }
+    __syncthreads();
+    for (int w = threadIdx.x; w < words; w += blockDim.x) {
+        unsigned b = bits[w];
+        int o = base + woff[w];
+        while (b) {
+            const int bit = __ffs(b) - 1;
+            b &= b - 1;
+            if (o < cap) items[o] = make_int2(tile, w * 32 + bit);
+            ++o;
+        }
+    }
+}
+
 // Term groups of a launch: packed family, greedy windows of NK consecutive frequencies; scalar family,
 // consecutive slices of NK selected terms.
 int family_groups(const FilterParams &p, int nk, bool packed) {
@@ -258,8 +310,10 @@ std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int w
     const int vspan = p.vhi - p.vlo + 1;
     const int wpad = ((width + 7) / 8) * 8;
     std::vector<std::pair<double, TileConfig>> all;
-    // the scalar family competes only for gapped selections (otherwise it does the same groups, slower)
-    for (int packed = 1; packed >= (gapped_terms(p) ? 0 : 1); --packed)
+    // the scalar family competes only for gapped selections (otherwise it does the same groups, slower);
+    // the 3-D form runs the packed family without the ring
+    const bool z3d = p.zbins > 0;
+    for (int packed = 1; packed >= (gapped_terms(p) && !z3d ? 0 : 1); --packed)
     for (const auto &cls : classes(packed)) {
         if (cls.m != p.m) continue;
         const int groups = family_groups(p, cls.nk, packed);
@@ -273,6 +327,7 @@ std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int w
             if (ncols > ((tw + 2 * p.rx + 31) / 32) * 32) break;  // wider tiles than the image gain nothing
             for (int variant = 0; variant < 4; ++variant) {
                 const int ring = variant & 1, depth = 2 + (variant >> 1);
+                if (ring && z3d) continue;
                 // the ring serves the output row too, so it must lie inside the window span
                 if (ring && !(p.vlo <= 0 && p.vhi >= 0)) continue;
                 // the packed ring's output phase reads row y - lag back from the ring: lag <= 1 - vlo
@@ -280,19 +335,32 @@ std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int w
                 const bool pring = ring && packed;
                 const size_t smem = smem_bytes(p.m, cls.nk, ncols, tw, depth, !pring) +
                                     (ring ? ring_bytes(p, ncols, groups_need_anchor(p, cls.nk, packed)) : 0);
-                if (smem > 227 * 1024) continue;
+                // the slice kernel keeps a few bytes of static shared memory besides the tile's
+                if (smem > 227 * 1024 - (z3d ? 256 : 0)) continue;
                 const int by_smem = (int)((228 * 1024) / (smem + 1024));
                 const int by_threads = 2048 / (ncols + kScanThreads);
                 const int by_regs = 65536 / (128 * (ncols + kScanThreads));
                 const int cps = std::max(1, std::min({by_smem, by_threads, by_regs}));
-                const double edge = (ring ? 60.0 + 12.0 * (2 * p.m + 1) : 60.0 * (2 * p.m + 1)) * (depth == 3 ? 0.9 : 1.0);
+                // three exchange buffers save a barrier per row; the slice kernel measured no gain from them
+                const double edge = (ring ? 60.0 + 12.0 * (2 * p.m + 1) : 60.0 * (2 * p.m + 1)) *
+                                    (depth == 3 && !z3d ? 0.9 : 1.0);
                 for (int th : {16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 1024}) {
                     const int the = std::min(th, std::max(height, 1));
                     const long ctas = (long)((width + tw - 1) / tw) * ((height + the - 1) / the) * groups;
                     const double per_cta = (double)ncols * (the + 0.3 * vspan) * (edge + term_cost * cls.nk * p.m);
                     const double waves = std::ceil((double)ctas / (sms * cps));
-                    const double cost =
-                        waves * per_cta * cps + (groups > 1 ? 16.0 * groups * (double)height * width : 0.0);
+                    double cost = waves * per_cta * cps + (groups > 1 ? 16.0 * groups * (double)height * width : 0.0);
+                    if (z3d) {
+                        // the 3-D form passes over a tile once per distinct slice among its output pixels; the
+                        // count is modelled as 7.5 (tw th)^0.27 (a fit on noisy piecewise-constant images),
+                        // at most zbins.  The persistent launch balances the items, so waves do not matter;
+                        // two resident CTAs hide latency better, fewer than 256 resident threads worse.
+                        const double slices = std::min((double)p.zbins, 7.5 * std::pow((double)tw * the, 0.27));
+                        const int resident = cps * (ncols + kScanThreads);
+                        const double occ = (cps > 1 ? 1.3 : 1.0) / (resident < 256 ? 1.35 : 1.0);
+                        cost = (double)ctas * slices * per_cta / (sms * occ) +
+                               (groups > 1 ? 16.0 * groups * (double)height * width : 0.0);
+                    }
                     TileConfig tc;
                     tc.tw = tw;
                     tc.th = the;
@@ -401,7 +469,7 @@ bool term_layout(const FilterParams &p, int nk, FilterParams &out) {
     return true;
 }
 
-void fill_info(const TileConfig &tc, int height, int width, int *info) {
+void fill_info(const TileConfig &tc, int height, int width, int *info, int zbins) {
     info[0] = tc.tw;
     info[1] = tc.th;
     info[2] = tc.threads;
@@ -409,15 +477,93 @@ void fill_info(const TileConfig &tc, int height, int width, int *info) {
     info[4] = tc.groups;
     info[5] = tc.groups > 1 ? 2 : 1;
     info[6] = (int)tc.smem;
-    info[7] = (int)(scratch_bytes(tc, height, width) >> 10);
+    info[7] = (int)(scratch_bytes(tc, height, width, zbins) >> 10);
     info[8] = tc.ring ? 1 : 0;
     info[9] = tc.depth;
     info[10] = tc.ncols;
     info[11] = tc.packed;
 }
 
-size_t scratch_bytes(const TileConfig &tc, int height, int width) {
+namespace {
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+size_t partial_bytes(const TileConfig &tc, int height, int width) {
     return tc.groups > 1 ? sizeof(float) * 2 * (size_t)tc.groups * height * width : 0;
+}
+
+// Work items of the 3-D form: each tile holds at most min(zbins, its pixels) slices.
+size_t zlist_cap(const TileConfig &tc, int height, int width, int zbins) {
+    if (tc.tw < 1 || tc.th < 1) return 0;
+    const size_t tiles = (size_t)((width + tc.tw - 1) / tc.tw) * ((height + tc.th - 1) / tc.th);
+    return std::min(tiles * (size_t)zbins, (size_t)height * width);
+}
+}  // namespace
+
+size_t scratch_bytes(const TileConfig &tc, int height, int width, int zbins) {
+    const size_t part = partial_bytes(tc, height, width);
+    if (zbins <= 0) return part;
+    // [partial planes][counters: 2 ints, 256 bytes reserved][items: int2 each]
+    return align256(part) + 256 + sizeof(int2) * zlist_cap(tc, height, width, zbins);
+}
+
+// The 3-D form (Sec. IV-D): the work list of (tile, slice) items, the persistent slice kernel over it, and
+// the finalize of a grouped launch.  Geometry already checked by launch_filter.
+bf_status launch_filter_z3d(const FilterParams &p, const TileConfig &tc, const float *d_in, size_t in_pitch,
+                            float *d_out, size_t out_pitch, float *d_scratch, int height, int width, void *stream) {
+    if (p.zbins < 2 || p.zbins > kMaxZBins || p.rz < 0) return fail(BF_ERR_INVALID_ARG, "bad slice count");
+    if (tc.ring || !tc.packed) return fail(BF_ERR_INVALID_ARG, "the 3-D form runs the packed family without the ring");
+    if (tc.smem > 227 * 1024 - 256) return fail(BF_ERR_UNSUPPORTED, "tile too large for the slice kernel");
+    const void *fn = find_zkernel(p.m, tc.nk);
+    if (!fn) return fail(BF_ERR_UNSUPPORTED, "no slice kernel for this class");
+    FilterParams pp;
+    if (!term_layout(p, tc.nk, pp) || pp.nr != tc.groups * tc.nk)
+        return fail(BF_ERR_INVALID_ARG, "launch geometry does not match the plan's term groups");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int tiles_x = (width + tc.tw - 1) / tc.tw, tiles_y = (height + tc.th - 1) / tc.th;
+    const size_t cap_sz = zlist_cap(tc, height, width, p.zbins);
+    if (cap_sz > (size_t)INT32_MAX / std::max(tc.groups, 1) || (size_t)tiles_x * tiles_y > (size_t)INT32_MAX)
+        return fail(BF_ERR_UNSUPPORTED, "image too large for the slice work list");
+    int cap = (int)cap_sz;
+    char *base = reinterpret_cast<char *>(d_scratch);
+    float *part = tc.groups > 1 ? d_scratch : nullptr;
+    int *counters = reinterpret_cast<int *>(base + align256(partial_bytes(tc, height, width)));
+    int2 *items = reinterpret_cast<int2 *>(reinterpret_cast<char *>(counters) + 256);
+    cudaError_t e = cudaMemsetAsync(counters, 0, 2 * sizeof(int), s);
+    if (e != cudaSuccess) return cuda_fail(e, "slice counters");
+    if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");
+    bf_zlist_kernel<<<tiles_x * tiles_y, 256, 0, s>>>(d_in, in_pitch, height, width, tc.tw, tc.th, tiles_x, items,
+                                                      cap, counters, pp);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "slice list launch");
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc.smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    int cps = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cps, fn, tc.threads, tc.smem);
+    if (e != cudaSuccess || cps < 1) {
+        cudaGetLastError();
+        cps = 1;
+    }
+    const long want = (long)cap * tc.groups;
+    const int grid = (int)std::max(1L, std::min((long)device_sms() * cps, want));
+    int tw = tc.tw, th = tc.th, ncols = tc.ncols, H = height, W = width, depth = tc.depth, groups = tc.groups;
+    int max_iter = cap * tc.groups;
+    const float *in = d_in;
+    float *out = d_out;
+    void *args[] = {(void *)&in, (void *)&in_pitch, (void *)&out, (void *)&out_pitch, (void *)&part, (void *)&H,
+                    (void *)&W, (void *)&tw, (void *)&th, (void *)&ncols, (void *)&depth, (void *)&tiles_x,
+                    (void *)&groups, (void *)&items, (void *)&cap, (void *)&counters, (void *)&max_iter, (void *)&pp};
+    if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");
+    e = cudaLaunchKernel(fn, dim3(grid), dim3(tc.threads), args, tc.smem, s);
+    if (e != cudaSuccess) return cuda_fail(e, "slice filter launch");
+    if (tc.groups > 1) {
+        if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");
+        dim3 fg((width + 255) / 256, height);
+        bf_finalize_kernel<<<fg, 256, 0, s>>>(d_in, in_pitch, d_out, out_pitch, d_scratch, height, width, tc.groups,
+                                               p.den_eps, p.i_lo);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "finalize launch");
+    }
+    return BF_OK;
 }
 
 bf_status launch_filter(const FilterParams &p, int precision, int kahan, const TileConfig &tc, const float *d_in,
@@ -436,8 +582,13 @@ bf_status launch_filter(const FilterParams &p, int precision, int kahan, const T
         (tc.packed && tc.nk % 2 != 0))
         return fail(BF_ERR_INVALID_ARG, "malformed launch geometry");
     if (tc.smem > 227 * 1024) return fail(BF_ERR_UNSUPPORTED, "tile needs more than 227 KB of shared memory");
-    if ((tc.groups > 1 || cache_mode) && !d_scratch) return fail(BF_ERR_INVALID_ARG, "missing scratch for grouped launch");
+    if ((tc.groups > 1 || cache_mode || p.zbins > 0) && !d_scratch)
+        return fail(BF_ERR_INVALID_ARG, "missing scratch for grouped launch");
     if (cache_mode && !tc.packed) return fail(BF_ERR_INVALID_ARG, "the pre-computation runs the packed family");
+    if (p.zbins > 0) {
+        if (cache_mode) return fail(BF_ERR_UNSUPPORTED, "the 3-D form has no pre-computation cache");
+        return launch_filter_z3d(p, tc, d_in, in_pitch, d_out, out_pitch, d_scratch, height, width, stream);
+    }
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc.smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     dim3 grid((width + tc.tw - 1) / tc.tw, (height + tc.th - 1) / tc.th, tc.groups);

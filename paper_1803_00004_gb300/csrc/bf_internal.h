@@ -43,7 +43,15 @@ struct FilterParams {
     int rx;                   // max |u| (horizontal reach)
     int vlo, vhi;             // min v0, max v1
     int kahan;                // 1: compensated horizontal sliding sums
+    // The 3-D form (z-binned range box): zbins > 0 slices; a pixel's slice is rint((I - i_lo) zscale) in
+    // fp32, clamped to [0, zbins - 1]; neighbours within rz slices of the centre's count.  zbins = 0: off.
+    int zbins;
+    int rz;
+    float zscale;
 };
+
+// Largest slice count of the 3-D form (the per-tile slice bitmap lives in shared memory).
+constexpr int kMaxZBins = 4096;
 
 // Launch geometry chosen by the host.
 struct TileConfig {
@@ -93,13 +101,15 @@ bool term_layout(const FilterParams &p, int nk, FilterParams &out);
 
 // Writes the geometry record (kInfoInts ints) of bf_launch_info / bf_autotune.
 constexpr int kInfoInts = 12;
-void fill_info(const TileConfig &tc, int height, int width, int *info);
+void fill_info(const TileConfig &tc, int height, int width, int *info, int zbins = 0);
 
 std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int width, int precision, int max_n);
 TileConfig model_tile(const FilterParams &p, int height, int width, int precision);
 TileConfig choose_tile(const FilterParams &p, int height, int width, int precision);
 void remember_tile(const FilterParams &p, int height, int width, int precision, const TileConfig &tc);
-size_t scratch_bytes(const TileConfig &tc, int height, int width);
+// Device scratch of a launch: the partial planes of a grouped launch, plus for the 3-D form (zbins > 0)
+// the per-tile slice work list and its two counters.
+size_t scratch_bytes(const TileConfig &tc, int height, int width, int zbins = 0);
 bf_status launch_filter(const FilterParams &p, int precision, int kahan, const TileConfig &tc, const float *d_in,
                         size_t in_pitch_elems, float *d_out, size_t out_pitch_elems, float *d_scratch, int height,
                         int width, void *stream, int cache_mode = 0);  // 0, or kModeCache*

@@ -51,6 +51,13 @@ __device__ __forceinline__ void basis_start(float v, float inv_p, float inv_p_lo
     }
 }
 
+// Slice of the 3-D form's z axis holding intensity v (minus i_lo): the nearest of the zbins levels,
+// rint(v zscale) in fp32 (ties to even), clamped to [0, zbins - 1].
+__device__ __forceinline__ int z_slice(float v, const FilterParams &p) {
+    const float t = fminf(fmaxf(rintf(v * p.zscale), 0.f), (float)(p.zbins - 1));
+    return (int)t;
+}
+
 __device__ __forceinline__ int pos_mod(int a, int d) {
     const int r = a % d;
     return r < 0 ? r + d : r;
@@ -96,7 +103,9 @@ __device__ __forceinline__ void rot2(float2 &C, float2 &S, float2 cs, float2 ss,
 
 // One tile: output columns [x0, x0 + tw) x rows [y0, y0 + th) of one image,
 // cosine terms [g NK, g NK + NK) of p.  All threads of the CTA call it; it
-// ends on a barrier, so the shared memory can be reused right after.  `mode`:
+// ends on a barrier, so the shared memory can be reused right after.
+// ZB (the 3-D form, Eqs. (35)-(36) with the z axis): only neighbours whose slice lies within p.rz of
+// slice zc enter the window sums, and only output pixels of slice zc are stored.  `mode`:
 // kModeFinal divides and stores Î; kModePartial stores this group's numerator
 // and denominator planes (part); kModeCache / kModeCacheF16 / kModeCacheBF16
 // store the window sums of every frequency of the group (part = the cache
@@ -104,12 +113,13 @@ __device__ __forceinline__ void rot2(float2 &C, float2 &S, float2 cs, float2 ss,
 //
 // The NK terms are processed as NK / 2 pairs of consecutive terms with the packed pair instructions:
 // pair p holds terms (2p, 2p + 1) of the group in the two lanes of every float2.
-template <int NK, int M, bool RING>
+template <int NK, int M, bool RING, bool ZB = false>
 __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__restrict__ in, size_t in_pitch,
                                           float *__restrict__ out, size_t out_pitch, float *__restrict__ part, int H,
                                           int W, int x0, int y0, int tw, int th, int ncols, int g, int mode,
-                                          int depth, float *smem) {
+                                          int depth, float *smem, int zc = 0) {
     static_assert(NK % 2 == 0, "terms are processed in pairs");
+    static_assert(!(ZB && RING), "the 3-D form runs without the ring");
     constexpr int NP = NK / 2;        // term pairs per group
     constexpr int NROW = M * NK * 4;  // exchange rows per image row: windows x basis images x terms
     constexpr int NE = 2 * M + 1;     // edges per step: M entering rows, M leaving rows, the output row
@@ -191,7 +201,8 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
             if (off < p.vhi) vn = pixel(row + 1);
             if (row < 0 || row >= H) continue;
             float c1, s1, c0, s0;
-            basis_start(v, p.inv_p, p.inv_p_lo, k0, colv, c1, s1, c0, s0);
+            const bool inz = !ZB || abs(z_slice(v, p) - zc) <= p.rz;  // 3-D form: the neighbour's slice window
+            basis_start(v, p.inv_p, p.inv_p_lo, k0, colv && inz, c1, s1, c0, s0);
             if (RING) {
                 const int sl = pos_mod(row, D) * ncols + tid;
                 ringA[sl] = make_float4(v, c1, s1, 0.f);
@@ -228,6 +239,8 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
     // The pixels a step needs from global memory are loaded one step ahead, so their latency overlaps the
     // previous step: RING: the row entering the ring; otherwise the 2M + 1 edge rows.
     float pf[RING ? 1 : NE];
+    // ZB: bit d = the output row y - d of this column lies in slice zc (set in the column phase of row y)
+    unsigned zrow = 0;
     if (RING) {
         pf[0] = pixel(y0 + 1 + p.vhi);
     } else {
@@ -236,6 +249,7 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
     }
     for (int j = 0; j < nout + lag; ++j) {
         const int y = y0 + j;
+        if (ZB) zrow <<= 1;
         if (is_col && j < nout) {
             float Ie[NE];
             float vr = 0.f;
@@ -296,7 +310,13 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
                     // the prefetched value is 0 outside the image; `valid` also masks the rows that the
                     // sums already hold at j == 0
                     v = valid ? Ie[e] : 0.f;
-                    basis_start(v, p.inv_p, p.inv_p_lo, k0, valid, c1, s1, c0, s0);
+                    bool live = valid;
+                    if (ZB) {
+                        const int n = z_slice(v, p);
+                        if (e < 2 * M) live = valid && abs(n - zc) <= p.rz;  // a window edge: the slice window
+                        else zrow |= (valid && n == zc) ? 1u : 0u;             // the output row: its own slice
+                    }
+                    basis_start(v, p.inv_p, p.inv_p_lo, k0, live, c1, s1, c0, s0);
                 }
                 float2 C, S, cs, ss, nss;
                 start_pair(c1, s1, c0, s0, C, S, cs, ss, nss);
@@ -411,7 +431,7 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
             if (hp) *hp = held;
         }
         if (depth == 2) __syncthreads();
-        if (is_out && j >= lag) {
+        if (is_out && j >= lag && (!ZB || ((zrow >> lag) & 1u))) {
             const int yo = y - lag;
             const int zo = ((j - lag) % depth) * ZC * NP2;
             const float4 *wp = wb0 + ((j - lag) % depth) * NP * tw + xl;
@@ -536,7 +556,36 @@ bf_batch_kernel(const BatchImage *__restrict__ imgs, const FilterParams *__restr
 }
 
 
+// The 3-D form (Sec. IV-D), persistent: each CTA repeatedly takes the next work item from the cursor
+// (counters[1]) and runs the tile body restricted to one slice.  items[0 .. counters[0]) hold (tile, slice)
+// for every slice present among a tile's output pixels; item i of term group g is i + g counters[0].  The
+// loop is bounded by max_iter.
+template <int NK, int M>
+__global__ void __launch_bounds__(512, 1)
+bf_zslice_kernel(const float *__restrict__ in, size_t in_pitch, float *__restrict__ out, size_t out_pitch,
+                 float *__restrict__ part, int H, int W, int tw, int th, int ncols, int depth, int tiles_x,
+                 int groups, const int2 *__restrict__ items, int cap, int *__restrict__ counters, int max_iter,
+                 const __grid_constant__ FilterParams p) {
+    extern __shared__ __align__(16) float smem[];
+    __shared__ int s_item;
+    const int n = min(counters[0], cap);
+    const int total = n * groups;
+    for (int iter = 0; iter < max_iter; ++iter) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counters + 1, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= total) break;
+        const int g = it / n;
+        const int2 w = items[it - g * n];
+        const int ty = w.x / tiles_x, tx = w.x - ty * tiles_x;
+        tile_body<NK, M, false, true>(p, in, in_pitch, out, out_pitch, part, H, W, tx * tw, ty * th, tw, th, ncols,
+                                      g, groups > 1 ? kModePartial : kModeFinal, depth, smem, w.y);
+    }
+}
+
 }  // namespace
+
+#define BF_ZCLASS(M, NK) {M, NK, {(const void *)bf_zslice_kernel<NK, M>, nullptr}, nullptr}
 
 #define BF_CLASS(M, NK)                                                                                 \
     {M, NK, {(const void *)bf_fused_kernel<NK, M, false>, (const void *)bf_fused_kernel<NK, M, true>},  \

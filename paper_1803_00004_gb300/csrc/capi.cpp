@@ -64,7 +64,8 @@ bf_status check_image(const float *d_in, size_t in_pitch, const float *d_out, si
 }
 
 // Launch sequence of one image (no argument checks).  d_scratch: at least
-// scratch_bytes(tc, h, w) bytes when the configuration has several term groups.
+// scratch_bytes(tc, h, w, zbins) bytes when the configuration has several term groups or the plan is
+// the 3-D form.
 bf_status filter_image(const bf_plan *plan, const TileConfig &tc, const float *d_in, size_t in_pitch, float *d_out,
                        size_t out_pitch, int h, int w, float *d_scratch, void *stream) {
     return launch_filter(plan->kp, plan->desc.precision, plan->desc.kahan, tc, d_in, in_pitch / sizeof(float), d_out,
@@ -94,6 +95,7 @@ void bf_plan_desc_default(bf_plan_desc *d) {
     d->precision = BF_PREC_FP32;
     d->kahan = 1;
     d->device = 0;
+    d->z_bins = 0;
 }
 
 bf_status bf_plan_create(const bf_plan_desc *desc, bf_plan **out) {
@@ -148,6 +150,8 @@ bf_status bf_coeffs(const bf_plan *p, bf_coeff_view *o) {
     o->spatial_max_err = p->spatial_max_err;
     o->den_eps = p->den_eps;
     o->passes = (int)((p->k.size() + 15) / 16);
+    o->z_bins = p->kp.zbins;
+    o->z_radius = p->kp.rz;
     return BF_OK;
 }
 
@@ -161,7 +165,7 @@ bf_status bf_filter(const bf_plan *plan, const float *d_in, size_t in_pitch, flo
         TileConfig tc = choose_tile(plan->kp, height, width, plan->desc.precision);
         float *scratch = nullptr;
         cudaStream_t s = (cudaStream_t)stream;
-        size_t need = scratch_bytes(tc, height, width);
+        size_t need = scratch_bytes(tc, height, width, plan->kp.zbins);
         if (need) {
             cudaError_t e = cudaMallocAsync((void **)&scratch, need, s);
             if (e != cudaSuccess) {
@@ -178,7 +182,7 @@ bf_status bf_filter(const bf_plan *plan, const float *d_in, size_t in_pitch, flo
 bf_status bf_launch_info(const bf_plan *plan, int height, int width, int *info) {
     if (!plan || !info || height < 1 || width < 1) return fail(BF_ERR_INVALID_ARG, "bad launch-info arguments");
     TileConfig tc = choose_tile(plan->kp, height, width, plan->desc.precision);
-    fill_info(tc, height, width, info);
+    fill_info(tc, height, width, info, plan->kp.zbins);
     return BF_OK;
 }
 

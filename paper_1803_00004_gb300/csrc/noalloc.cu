@@ -71,10 +71,10 @@ extern "C" bf_status bf_filter_noalloc(const bf_plan *plan, const float *d_in, s
     }
     // the geometry bf_filter would use, else the best-ranked one whose planes fit the array
     bfi::TileConfig tc = bfi::choose_tile(plan->kp, height, width, plan->desc.precision);
-    if (bfi::scratch_bytes(tc, height, width) > kScratchBytes) {
+    if (bfi::scratch_bytes(tc, height, width, plan->kp.zbins) > kScratchBytes) {
         tc.ncols = 0;
         for (const auto &c : bfi::tile_candidates(plan->kp, height, width, plan->desc.precision, 64))
-            if (bfi::scratch_bytes(c, height, width) <= kScratchBytes) {
+            if (bfi::scratch_bytes(c, height, width, plan->kp.zbins) <= kScratchBytes) {
                 tc = c;
                 break;
             }
@@ -84,7 +84,7 @@ extern "C" bf_status bf_filter_noalloc(const bf_plan *plan, const float *d_in, s
                                      "width floats); use bf_filter");
     } else {
         float *scratch = nullptr;
-        st = bfi::scratch_bytes(tc, height, width) ? scratch_address(device, &scratch) : BF_OK;
+        st = bfi::scratch_bytes(tc, height, width, plan->kp.zbins) ? scratch_address(device, &scratch) : BF_OK;
         if (st == BF_OK)
             st = bfi::launch_filter(plan->kp, plan->desc.precision, plan->desc.kahan, tc, d_in, in_pitch / sizeof(float),
                                     d_out, out_pitch / sizeof(float), scratch, height, width, stream);

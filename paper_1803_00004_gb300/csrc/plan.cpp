@@ -325,10 +325,11 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
     if (d.spatial != BF_KERNEL_GAUSSIAN && d.spatial != BF_KERNEL_BOX && d.spatial != BF_KERNEL_EXPONENTIAL)
         return fail(BF_ERR_INVALID_ARG, "unknown spatial kernel");
     if (d.range < BF_KERNEL_GAUSSIAN || d.range > BF_KERNEL_BOX) return fail(BF_ERR_INVALID_ARG, "unknown range kernel");
-    if (d.policy == BF_RANGE_PAPER_3D)
-        return fail(BF_ERR_UNSUPPORTED, "BF_RANGE_PAPER_3D (z-binned range box) is not implemented");
-    if (d.policy != BF_RANGE_TRUNCATED_MIN_PERIOD && d.policy != BF_RANGE_UNTRUNCATED_FULL)
+    if (d.policy != BF_RANGE_TRUNCATED_MIN_PERIOD && d.policy != BF_RANGE_UNTRUNCATED_FULL &&
+        d.policy != BF_RANGE_PAPER_3D)
         return fail(BF_ERR_INVALID_ARG, "unknown range policy");
+    if (d.policy == BF_RANGE_PAPER_3D && d.z_bins != 0 && (d.z_bins < 2 || d.z_bins > bfi::kMaxZBins))
+        return fail(BF_ERR_INVALID_ARG, "z_bins must be 0 (256) or in [2, 4096]");
     if (d.precision < BF_PREC_FP32 || d.precision > BF_PREC_FP16)
         return fail(BF_ERR_INVALID_ARG, "unknown precision");
     if (d.precision != BF_PREC_FP32)
@@ -347,6 +348,10 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
     if (d.policy == BF_RANGE_UNTRUNCATED_FULL) {
         p.P = dI;
         p.Tr = dI;
+    } else if (d.policy == BF_RANGE_PAPER_3D) {
+        // one period of the series fits the kernel truncated at T_r; the slice window applies the box
+        p.P = tr;
+        p.Tr = tr;
     } else {
         p.P = std::max(tr, 0.5 * (dI + tr));
         p.Tr = tr;
@@ -472,8 +477,10 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
     for (double v : p.a) sa += std::fabs(v);
     p.den_eps = 1e-6 * sk * sa;
     p.range_max_err = 0;
+    // the 3-D form keeps the series only inside the range box [-T_r, T_r]
+    const double tspan = d.policy == BF_RANGE_PAPER_3D ? std::min(dI, p.Tr) : dI;
     for (int i = 0; i <= 4000; ++i) {
-        double t = -dI + 2.0 * dI * i / 4000.0, s = 0;
+        double t = -tspan + 2.0 * tspan * i / 4000.0, s = 0;
         for (size_t j = 0; j < p.k.size(); ++j) s += p.a[j] * std::cos(kPi * p.k[j] * t / p.P);
         p.range_max_err = std::max(p.range_max_err, std::fabs(s - range_value(d.range, d.sigma_r, t)));
     }
@@ -523,6 +530,15 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
     kp.vlo = vlo;
     kp.vhi = vhi;
     kp.kahan = d.kahan ? 1 : 0;
+    if (d.policy == BF_RANGE_PAPER_3D) {
+        // z axis: Z levels i_lo + n dI / (Z - 1); window R_z = floor(T_r (Z - 1) / dI) slices (the 1e-9
+        // keeps a whole number of levels whole)
+        const int Z = d.z_bins ? d.z_bins : 256;
+        kp.zbins = Z;
+        kp.zscale = (float)((Z - 1) / dI);
+        const double rz = std::floor(p.Tr * (Z - 1) / dI + 1e-9);
+        kp.rz = (int)std::min(rz, (double)Z);
+    }
     return BF_OK;
 }
 

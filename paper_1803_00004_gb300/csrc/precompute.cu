@@ -96,6 +96,8 @@ bf_status bf_precompute(const bf_plan *plan, const float *d_in, size_t in_pitch,
     if (!d_in || in_pitch % sizeof(float) || in_pitch < (size_t)width * sizeof(float))
         return fail(BF_ERR_INVALID_ARG, "NULL input or bad pitch");
     bf_status st = BF_OK;
+    if (plan->kp.zbins > 0)
+        return fail(BF_ERR_UNSUPPORTED, "the 3-D form (BF_RANGE_PAPER_3D) has no pre-computation cache");
     if (plan->desc.device < 0) return fail(BF_ERR_NO_DEVICE, "host-only plan (device = -1)");
     int prev = 0;
     if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(plan->desc.device) != cudaSuccess) {

@@ -261,6 +261,8 @@ bf_status bf_serve_submit(bf_server *S, const bf_request *req, uint64_t *ticket)
         return bfi::fail(BF_ERR_INVALID_ARG, "bad request image");
     bf_plan_desc d = req->desc;
     d.device = S->cfg.device;
+    if (d.policy == BF_RANGE_PAPER_3D)
+        return bfi::fail(BF_ERR_UNSUPPORTED, "the 3-D form (BF_RANGE_PAPER_3D) runs through bf_filter, not the server");
     bf_plan *plan = nullptr;
     {
         std::lock_guard<std::mutex> lk(S->mu);

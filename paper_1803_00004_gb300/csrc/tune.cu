@@ -20,7 +20,9 @@
 namespace bfi {
 namespace {
 
-using Key = std::tuple<int, int, int, int, int, int, int, int, int, int>;  // ..., gapped term selection
+// (device, M, terms, reach, vlo, vhi, h, w, precision, selection kind): the kind is 1 for a gapped term
+// selection (the families on offer differ) plus 2 for the 3-D form (no ring)
+using Key = std::tuple<int, int, int, int, int, int, int, int, int, int>;
 
 std::mutex g_mu;
 std::map<Key, TileConfig> g_table;
@@ -32,8 +34,8 @@ Key make_key(const FilterParams &p, int h, int w, int precision) {
         cudaGetLastError();
         dev = -1;
     }
-    const int gapped = p.k[p.nr - 1] - p.k[0] + 1 != p.nr ? 1 : 0;  // the families on offer differ
-    return Key{dev, p.m, p.nr, p.rx, p.vlo, p.vhi, h, w, precision, gapped};
+    const int kind = (p.k[p.nr - 1] - p.k[0] + 1 != p.nr ? 1 : 0) + (p.zbins > 0 ? 2 : 0);
+    return Key{dev, p.m, p.nr, p.rx, p.vlo, p.vhi, h, w, precision, kind};
 }
 
 void load_locked() {
@@ -67,14 +69,21 @@ void save_locked(const Key &key, const TileConfig &tc) {
     std::fclose(f);
 }
 
-// Deterministic pseudo-random pixels in [lo, hi] (a hash of the index).
-__global__ void fill_kernel(float *img, size_t n, float lo, float hi) {
+// Deterministic pseudo-random pixels in [lo, hi] (a hash of the index).  smooth = 0: uniform over the
+// range.  smooth = 1 (the 3-D form, whose cost grows with the distinct intensity slices per tile): a
+// slowly varying field plus 3% noise, closer to natural images than white noise.
+__global__ void fill_kernel(float *img, size_t n, int width, float lo, float hi, int smooth) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         uint32_t x = (uint32_t)i * 2654435761u + 0x9e3779b9u;
         x ^= x >> 16;
         x *= 0x85ebca6bu;
         x ^= x >> 13;
-        img[i] = lo + (hi - lo) * (float)(x >> 8) * (1.0f / 16777216.0f);
+        float u = (float)(x >> 8) * (1.0f / 16777216.0f);
+        if (smooth) {
+            const float c = (float)(i % (size_t)width), r = (float)(i / (size_t)width);
+            u = 0.5f + 0.4f * __sinf(c * 0.011f) * __sinf(r * 0.017f) + 0.06f * (u - 0.5f);
+        }
+        img[i] = lo + (hi - lo) * u;
     }
 }
 
@@ -87,7 +96,8 @@ TileConfig choose_tile(const FilterParams &p, int height, int width, int precisi
         auto it = g_table.find(make_key(p, height, width, precision));
         // an entry stays usable only while its term grouping matches this build's layout
         if (it != g_table.end() &&
-            it->second.groups == (it->second.packed ? term_groups(p, it->second.nk) : (p.nr + it->second.nk - 1) / it->second.nk))
+            it->second.groups == (it->second.packed ? term_groups(p, it->second.nk) : (p.nr + it->second.nk - 1) / it->second.nk) &&
+            (p.zbins == 0 || (it->second.packed && !it->second.ring)))
             return it->second;
     }
     return model_tile(p, height, width, precision);
@@ -123,7 +133,7 @@ extern "C" bf_status bf_autotune(const bf_plan *plan, int height, int width, voi
     float *in = nullptr, *out = nullptr, *scratch = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     size_t n = (size_t)height * width, need = 0;
-    for (const auto &c : cands) need = std::max(need, scratch_bytes(c, height, width));
+    for (const auto &c : cands) need = std::max(need, scratch_bytes(c, height, width, plan->kp.zbins));
     if (cands.empty()) st = fail(BF_ERR_UNSUPPORTED, "no launch geometry for this plan");
     if (st == BF_OK && (cudaMalloc((void **)&in, n * sizeof(float)) != cudaSuccess ||
                         cudaMalloc((void **)&out, n * sizeof(float)) != cudaSuccess ||
@@ -138,7 +148,7 @@ extern "C" bf_status bf_autotune(const bf_plan *plan, int height, int width, voi
     TileConfig best{};
     float best_ms = 1e30f;
     if (st == BF_OK) {
-        fill_kernel<<<256, 256, 0, s>>>(in, n, plan->desc.i_lo, plan->desc.i_hi);
+        fill_kernel<<<256, 256, 0, s>>>(in, n, width, plan->desc.i_lo, plan->desc.i_hi, plan->kp.zbins > 0 ? 1 : 0);
         for (const auto &c : cands) {
             bf_status r = launch_filter(plan->kp, plan->desc.precision, plan->desc.kahan, c, in, width, out, width,
                                         scratch, height, width, stream);  // warm-up
@@ -165,7 +175,7 @@ extern "C" bf_status bf_autotune(const bf_plan *plan, int height, int width, voi
     if (st == BF_OK) {
         remember_tile(plan->kp, height, width, plan->desc.precision, best);
         if (info) {
-            fill_info(best, height, width, info);
+            fill_info(best, height, width, info, plan->kp.zbins);
         }
     }
     cudaStreamSynchronize(s);
@@ -205,7 +215,7 @@ extern "C" bf_status bf_launch_candidates(const bf_plan *plan, int height, int w
     if (!plan || height < 1 || width < 1 || max_n < 0 || !n_out || (max_n > 0 && !infos))
         return fail(BF_ERR_INVALID_ARG, "bad launch-candidate arguments");
     std::vector<TileConfig> c = tile_candidates(plan->kp, height, width, plan->desc.precision, max_n);
-    for (size_t i = 0; i < c.size(); ++i) fill_info(c[i], height, width, infos + kInfoInts * i);
+    for (size_t i = 0; i < c.size(); ++i) fill_info(c[i], height, width, infos + kInfoInts * i, plan->kp.zbins);
     *n_out = (int)c.size();
     return BF_OK;
 }
@@ -216,7 +226,7 @@ extern "C" bf_status bf_set_launch(const bf_plan *plan, int height, int width, c
     if (!dev.ok) return fail(BF_ERR_NO_DEVICE, "cannot select the plan's device");
     for (const auto &c : tile_candidates(plan->kp, height, width, plan->desc.precision, 100000)) {
         int got[kInfoInts];
-        fill_info(c, height, width, got);
+        fill_info(c, height, width, got, plan->kp.zbins);
         // the fields a caller chooses; the rest (threads, launches, bytes) follow from them
         if (got[0] == info[0] && got[1] == info[1] && got[3] == info[3] && got[8] == info[8] && got[9] == info[9] &&
             got[10] == info[10] && got[11] == info[11]) {

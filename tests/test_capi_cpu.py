@@ -103,9 +103,26 @@ def test_paper_five_terms_compile_to_two_nested_windows():
     assert c["passes"] == 1
 
 
+@pytest.mark.parametrize("sigma_r,z_bins,t_r", [(0.1, 0, 0.0), (0.05, 64, 0.0), (0.2, 4096, 0.0), (0.3, 256, 10 / 255)])
+def test_paper_3d_plan_matches_oracle(sigma_r, z_bins, t_r):
+    """The 3-D form's plan: P = T_r, the oracle's coefficients, and the slice window R_z."""
+    c = bf.Plan(device=-1, policy=bf.RANGE_PAPER_3D, sigma_r=sigma_r, z_bins=z_bins, t_r=t_r).coeffs()
+    d = O.Desc(sigma_r=sigma_r, t_r=t_r, policy=O.PAPER_3D)
+    info = O.plan_info(d)
+    assert c["period"] == pytest.approx(info.P, rel=1e-15) and c["t_r"] == pytest.approx(info.Tr, rel=1e-15)
+    order = np.argsort(info.ks)                       # the plan lists its terms by frequency
+    assert list(c["k"]) == list(info.ks[order])
+    assert np.max(np.abs(np.array(c["a"]) - info.ak[order])) < 1e-13
+    Z = z_bins or 256
+    _, rz = O.z_bins([0.0], info.Tr, Z)
+    assert c["z_bins"] == Z and c["z_radius"] == rz
+    assert bf.Plan(device=-1).coeffs()["z_bins"] == 0
+
+
 @pytest.mark.parametrize("kw,status", [
     (dict(sigma_s=0.0), 1), (dict(sigma_r=-1.0), 1), (dict(ns_terms=0), 1), (dict(nr_terms=0), 1),
-    (dict(i_lo=1.0, i_hi=1.0), 1), (dict(policy=bf.RANGE_PAPER_3D), 2),
+    (dict(i_lo=1.0, i_hi=1.0), 1), (dict(policy=bf.RANGE_PAPER_3D, z_bins=1), 1),
+    (dict(policy=bf.RANGE_PAPER_3D, z_bins=4097), 1), (dict(policy=5), 1),
     (dict(spatial=bf.KERNEL_EXPONENTIAL, sigma_s=100.0), 2),
     (dict(spatial=7), 1), (dict(precision=9), 1), (dict(radius=-2), 1), (dict(precision=bf.PREC_BF16), 2), (dict(precision=bf.PREC_FP16), 2),
 ])

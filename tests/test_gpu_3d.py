@@ -1,0 +1,205 @@
+"""GPU parity of the 3-D form (BF_RANGE_PAPER_3D: P = T_r, the range box applied over intensity slices)
+against the FP64 oracle (needs a CUDA GPU).
+
+The reference is O2-3D (the definition; pinned equal to the paper's per-slice steps O3-3D).  Slice
+decisions are taken in fp32 on both sides, so every neighbour is in or out of a window identically.
+Tolerance: 1e-5 max-abs where the denominator is at least 1% of the in-window kernel mass (the mass of
+the neighbours inside the slice window); below that the fp32 rounding of the sums (~2e-7 relative) is
+amplified by sum |a_k| mass / |den| and the bound scales with it.  Images span several tiles with ragged
+tails; edge cases cover tiny images, two and 4096 slices, several term groups, windows wider than the
+data range, every launch geometry family and the full 1920x1080 size (sampled).
+"""
+import numpy as np
+import pytest
+
+import paper_1803_00004_gb300 as bf
+from oracle import oracle as O
+from paper_1803_00004_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+THREADS = 16
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1803_00004_gb300 import _build
+    _build.build()
+    torch.cuda.init()
+
+
+def on_grid(H, W, seed):
+    """8-bit data: levels j / 255 stored as fp32."""
+    rng = np.random.default_rng(seed)
+    j = np.clip(np.rint(synth.shapes(H, W, seed, scale=0.2) * 255) + rng.integers(-2, 3, (H, W)), 0, 255)
+    return (j / 255.0).astype(np.float32)
+
+
+def plan3d(Z, **kw):
+    return bf.Plan(device=0, policy=bf.RANGE_PAPER_3D, z_bins=Z, **kw)
+
+
+def gpu(plan, img):
+    src = torch.from_numpy(np.ascontiguousarray(img, dtype=np.float32)).cuda()
+    dst = torch.full_like(src, float("nan"))
+    bf.bf_filter(plan, src, dst)
+    torch.cuda.synchronize()
+    return dst.cpu().numpy().astype(np.float64)
+
+
+def odesc(kw):
+    return O.Desc(policy=O.PAPER_3D, **kw)
+
+
+def window_mass(img, kw, Z):
+    """sum over the window of |K~_s(x - y)| for the neighbours y inside x's slice window."""
+    p = O.plan_info(odesc(kw))
+    bins, rz = O.z_bins(img.astype(np.float64), p.Tr, Z)
+    H, W = img.shape
+    R = p.R
+    pb = np.full((H + 2 * R, W + 2 * R), -10 ** 6, dtype=np.int64)
+    pb[R:R + H, R:R + W] = bins
+    mass = np.zeros((H, W))
+    for dy in range(-R, R + 1):
+        for dx in range(-R, R + 1):
+            k = abs(p.Ks[-dy + R, -dx + R])
+            if k == 0.0:
+                continue
+            nb = pb[R + dy:R + dy + H, R + dx:R + dx + W]
+            mass += k * (np.abs(nb - bins) <= rz)
+    return mass, p
+
+
+def check(got, img, kw, Z):
+    ref, _, den = O.approx3d_direct(img.astype(np.float64), odesc(kw), Z, threads=THREADS, return_den=True)
+    mass, p = window_mass(img, kw, Z)
+    ratio = np.abs(den) / mass
+    err = np.abs(got - ref)
+    assert np.all(np.isfinite(got))
+    good = ratio >= 0.01
+    assert good.mean() > 0.98, "too many ill-conditioned pixels: %g" % (1 - good.mean())
+    e_good = err[good].max()
+    bound = TOL + 2e-7 * np.sum(np.abs(p.ak)) * (1 + np.abs(ref)) / np.maximum(ratio, 1e-12)
+    worst = np.max(err[~good] / bound[~good]) if (~good).any() else 0.0
+    return e_good, worst
+
+
+CASES = [
+    ("shapes_s2_z256", synth.shapes(150, 203, 1, scale=0.2), dict(sigma_s=2.0, sigma_r=0.1), 256),
+    ("8bit_s4_z256", on_grid(170, 150, 2), dict(sigma_s=4.0, sigma_r=0.05), 256),
+    ("blocks_groups", synth.blocks(131, 260, 3), dict(sigma_s=3.0, sigma_r=0.1, nr_terms=12), 64),
+    ("exp_range", synth.shapes(140, 190, 4, scale=0.2),
+     dict(range=bf.KERNEL_EXPONENTIAL, sigma_r=0.1, nr_terms=6, sigma_s=2.0), 128),
+    ("box_spatial_m1", synth.blocks(100, 333, 5), dict(spatial=bf.KERNEL_BOX, sigma_s=2.0, ns_terms=1, nr_terms=4), 256),
+    ("m3_ns13", synth.shapes(160, 170, 6, scale=0.2), dict(sigma_s=2.0, ns_terms=13, sigma_r=0.08), 256),
+    ("z2", synth.uniform(64, 90, 7), dict(sigma_s=2.0, sigma_r=0.3), 2),
+    ("z4096", synth.shapes(90, 120, 8, scale=0.1), dict(sigma_s=2.0, sigma_r=0.02, nr_terms=4), 4096),
+    ("exp_spatial", synth.shapes(120, 150, 9, scale=0.2), dict(spatial=bf.KERNEL_EXPONENTIAL, sigma_s=2.0), 256),
+    ("sigma8", synth.shapes(200, 230, 10, scale=0.2), dict(sigma_s=8.0, sigma_r=0.1), 256),
+]
+
+
+@pytest.mark.parametrize("name,img,kw,Z", CASES, ids=[c[0] for c in CASES])
+def test_3d_matches_oracle(name, img, kw, Z):
+    got = gpu(plan3d(Z, **kw), img)
+    e_good, worst = check(got, img, kw, Z)
+    assert e_good < TOL, "%s: max err %.3g" % (name, e_good)
+    assert worst < 1.0, "%s: error / bound %.3g on ill-conditioned pixels" % (name, worst)
+
+
+@pytest.mark.parametrize("H,W", [(1, 1), (2, 3), (5, 1), (1, 77), (9, 300)])
+def test_3d_tiny_images(H, W):
+    img = synth.uniform(H, W, seed=H * 31 + W)
+    kw = dict(sigma_s=2.0, sigma_r=0.1)
+    got = gpu(plan3d(256, **kw), img)
+    ref, _ = O.approx3d_direct(img.astype(np.float64), odesc(kw), 256)
+    assert np.max(np.abs(got - ref)) < TOL
+
+
+@pytest.mark.parametrize("m", [0, 5])
+def test_3d_box_kernels_on_8bit_data_are_exact_bf(m):
+    """Box spatial and range kernels on 8-bit data: the 3-D form is the exact bilateral filter."""
+    img = on_grid(97, 140, 11 + m)
+    kw = dict(spatial=bf.KERNEL_BOX, sigma_s=1.0, radius=3, ns_terms=1, range=bf.KERNEL_BOX,
+              sigma_r=(m + 0.5) / 255.0, nr_terms=2)
+    got = gpu(plan3d(256, **kw), img)
+    ref = O.exact_bf(img.astype(np.float64), O.Desc(**kw))
+    assert np.max(np.abs(got - ref)) < 2e-6
+
+
+def test_3d_wide_window_equals_collapsed_filter():
+    """T_r >= dI: every neighbour is inside the slice window and both policies take P = T_r, so the 3-D
+    launch and the collapsed launch compute the same sums."""
+    img = synth.shapes(180, 210, 12, scale=0.2)
+    kw = dict(sigma_s=3.0, sigma_r=0.4, t_r=1.25, nr_terms=8)
+    a = gpu(plan3d(256, **kw), img)
+    b = gpu(bf.Plan(device=0, **kw), img)
+    assert np.max(np.abs(a - b)) < 2e-6
+
+
+def family(c):
+    return (c["nk"], c["depth"], c["tw"], c["th"])
+
+
+def test_3d_every_candidate_family():
+    """Launch geometries of a 3-D plan (packed family, no ring): each distinct terms-per-CTA and depth."""
+    img = synth.shapes(140, 250, 13, scale=0.2)
+    kw = dict(sigma_s=2.0, sigma_r=0.1, nr_terms=8)
+    plan = plan3d(256, **kw)
+    H, W = img.shape
+    default = bf.bf_launch_info(plan, H, W)
+    cands = bf.bf_launch_candidates(plan, H, W)
+    assert cands and all(c["ring"] == 0 and c["packed"] == 1 for c in cands)
+    firsts = {}
+    for c in cands:
+        firsts.setdefault((c["nk"], c["depth"]), c)
+    assert len(firsts) >= 4
+    try:
+        for fam, c in firsts.items():
+            bf.bf_set_launch(plan, H, W, c)
+            got = gpu(plan, img)
+            e_good, worst = check(got, img, kw, 256)
+            assert e_good < TOL and worst < 1.0, (fam, e_good, worst)
+    finally:
+        bf.bf_set_launch(plan, H, W, default)
+
+
+def test_3d_autotune_keeps_parity():
+    img = synth.shapes(96, 200, 14, scale=0.2)
+    kw = dict(sigma_s=2.0, sigma_r=0.05, nr_terms=6)
+    plan = plan3d(256, **kw)
+    info = bf.bf_autotune(plan, *img.shape)
+    assert info["ring"] == 0 and info["packed"] == 1
+    got = gpu(plan, img)
+    e_good, worst = check(got, img, kw, 256)
+    assert e_good < TOL and worst < 1.0
+
+
+def test_3d_full_size_sampled():
+    """The 1920 x 1080 sweep image with sigma_s = 8, sigma_r = 0.1, N_r = 8, 256 slices: 3000 sampled pixels."""
+    img = synth.shapes(1080, 1920, seed=0)
+    kw = dict(sigma_s=8.0, sigma_r=0.1, nr_terms=8)
+    got = gpu(plan3d(256, **kw), img)
+    assert np.all(np.isfinite(got))
+    rng = np.random.default_rng(5)
+    pts = np.stack([rng.integers(0, 1080, 3000), rng.integers(0, 1920, 3000)], axis=1)
+    pts[:4] = [[0, 0], [1079, 1919], [0, 1919], [1079, 0]]
+    ref, den = O.approx3d_direct_at(img.astype(np.float64), odesc(kw), pts, 256, threads=THREADS)
+    err = np.abs(got[pts[:, 0], pts[:, 1]] - ref)
+    assert np.max(err) < TOL
+
+
+def test_3d_rejected_where_unsupported():
+    plan = plan3d(256, sigma_s=2.0)
+    src = torch.rand(64, 64, device="cuda")
+    dst = torch.empty_like(src)
+    with pytest.raises(bf.BFError) as ei:
+        bf.bf_filter_batch([plan], [src], [dst])
+    assert ei.value.status == 2  # BF_ERR_UNSUPPORTED
+    with pytest.raises(bf.BFError) as ei:
+        bf.Cache(plan, src, kmax=8)
+    assert ei.value.status == 2  # BF_ERR_UNSUPPORTED

@@ -56,3 +56,17 @@ def test_noalloc_rejects_oversized_scratch():
     dst = torch.empty_like(src)
     assert noalloc(plan, src, dst) == 8
     assert "64 MiB" in bf.lib().bf_last_error().decode()
+
+
+def test_noalloc_3d_form_matches_bf_filter():
+    # the 3-D form keeps its slice work list (and partial planes of 2 term groups) in the fixed array
+    img = synth.shapes(260, 390, 23, scale=0.3)
+    for nr in (8, 12):
+        plan = bf.Plan(device=0, sigma_s=3.0, sigma_r=0.1, nr_terms=nr, policy=bf.RANGE_PAPER_3D, z_bins=256)
+        src = torch.from_numpy(img).cuda()
+        ref = torch.empty_like(src)
+        bf.bf_filter(plan, src, ref)
+        got = torch.full_like(src, float("nan"))
+        assert noalloc(plan, src, got) == 0
+        torch.cuda.synchronize()
+        assert torch.max(torch.abs(got - ref)).item() < TOL
