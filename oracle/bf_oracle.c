@@ -31,7 +31,10 @@
  *   - O2-3D / O3-3D the 3-D form of Sec. IV-D: cosine half-period P = T_r and
  *     the range box applied by dimension promotion (Eq. (2)) over Z intensity
  *     slices; O3-3D takes per-slice 2-D box sums (Eq. (28)) and sums them over
- *     the slice window along z (Eq. (29)).
+ *     the slice window along z (Eq. (29));
+ *   - the same with a Haar series in range: the truncated range kernel's best
+ *     N-term Haar expansion (Eqs. (17)-(20), (11)) on the slice axis, each term
+ *     a pair of boxes along z evaluated through a running sum over slices.
  *
  * Readings of points the paper leaves open (all listed in the design doc):
  *   - square spatial window |y-x|_inf <= R, R = round(3 sigma_s) by default,
@@ -51,7 +54,10 @@
  *   - den <= 1e-6 * (sum |K~_s|)(sum |a_k|) -> output I(x) and count it;
  *   - 3-D form: Z levels n dI / (Z - 1) on [0, dI]; a pixel's slice is its
  *     nearest level, decided in fp32; the window along z is R_z =
- *     floor(T_r (Z - 1) / dI) slices each side; the basis uses I(y) itself.
+ *     floor(T_r (Z - 1) / dI) slices each side; the basis uses I(y) itself;
+ *   - Haar series in range: domain [-T_z, T_z], T_z = R_z + 1/2 in slice units,
+ *     J_z = ceil(log2(2 T_z)), profile K_r(t dI / (Z - 1)); weight of a
+ *     neighbour = K~_r at n(x) - n(y); guard 1e-6 (sum |K~_s|) max |K~_r|.
  *
  * Parity pinned by tests/test_oracle_*.py; see the design doc for the pin list.
  */
@@ -1076,6 +1082,234 @@ int orc_approx3d_fast(const double *I, int H, int W,
     }
     if (ndegen) *ndegen = degen;
     free(num); free(den); free(g); free(S); free(F); free(cb); free(sb); free(boxes); free(nz); free(occupied);
+    plan_free(&p);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* The 3-D form with a Haar series in range: the range kernel's best   */
+/* N-term Haar expansion (Eqs. (17)-(20), selection Eq. (11)) on the   */
+/* slice axis; each term is a pair of boxes along z (Eqs. (28)-(29))    */
+/* ------------------------------------------------------------------ */
+
+/* int_a^b K_r(t step) dt for t in slice units (closed forms; the box kernel is 1 on |t step| <= sigma_r). */
+static double range_profile_int(int kind, double sigma_r, double step, double a, double b)
+{
+    if (!(b > a)) return 0.0;
+    double sz = sigma_r / step; /* the bandwidth in slices */
+    if (kind == ORC_GAUSSIAN) return spatial_profile_int(ORC_GAUSSIAN, sz, a, b);
+    if (kind == ORC_BOX) {
+        double lo = a > -sz ? a : -sz, hi = b < sz ? b : sz;
+        return hi > lo ? hi - lo : 0.0;
+    }
+    double s = 0.0; /* exponential exp(-|t| / sz), split at 0 */
+    if (a < 0) { double hi = b < 0 ? b : 0.0; s += sz * (exp(hi / sz) - exp(a / sz)); }
+    if (b > 0) { double lo = a > 0 ? a : 0.0; s += sz * (exp(-lo / sz) - exp(-b / sz)); }
+    return s;
+}
+
+/* The range series on the slice axis.  Domain [-T_z, T_z], T_z = R_z + 1/2 (R_z as in the 3-D form, so the
+ * truncated kernel covers the slice offsets |d| <= R_z); J_z = ceil(log2(2 T_z)) levels; the profile is
+ * K_r(t step), step = dI / (Z - 1).  Coefficients by Eq. (20); the N_r largest |c| kept (ties as for the
+ * spatial terms, ordered by (level, k) with phi first).  The weight table holds K~_r at the integer
+ * offsets d = n(x) - n(y) (the range argument I(x) - I(y) in slices), w[d + R_z]. */
+typedef struct {
+    int Rz, Jz, n;
+    double Tz, wmax;
+    int lev[ORC_MAX_NR], k[ORC_MAX_NR];
+    double c[ORC_MAX_NR];
+    double *w;
+} orc_zhaar;
+
+static void zhaar_free(orc_zhaar *h) { free(h->w); h->w = NULL; }
+
+static int zhaar_build(orc_zhaar *h, int rkind, double sigma_r, double Tr, int nr_terms, int Z, double data_range)
+{
+    memset(h, 0, sizeof(*h));
+    if (nr_terms < 1 || nr_terms > ORC_MAX_NR || Z < 2 || !(data_range > 0)) return ORC_EINVAL;
+    const double step = data_range / (Z - 1);
+    h->Rz = z_radius(Tr, Z, data_range);
+    if (h->Rz > 1023) return ORC_ECAP;
+    h->Tz = h->Rz + 0.5;
+    h->Jz = orc_haar_levels(h->Tz);
+    const int n = 1 << (h->Jz + 1);
+    cand2d *v = malloc(sizeof(cand2d) * n);
+    h->w = calloc((size_t)(2 * h->Rz + 1), sizeof(double));
+    if (!v || !h->w) { free(v); zhaar_free(h); return ORC_ECAP; }
+    for (int idx = 0; idx < n; idx++) {
+        int j, k;
+        double lo, mid, hi, c;
+        haar_index(idx, &j, &k);
+        haar_support(j, k, h->Tz, &lo, &mid, &hi);
+        if (j < 0) c = range_profile_int(rkind, sigma_r, step, lo, hi) / (2.0 * h->Tz);
+        else c = ldexp(1.0, j) * (range_profile_int(rkind, sigma_r, step, lo, mid) -
+                                  range_profile_int(rkind, sigma_r, step, mid, hi)) / (2.0 * h->Tz);
+        cand2d *e = &v[idx];
+        e->c = c; e->mag = fabs(c); e->t1 = j; e->t2 = k;
+        e->key[0] = j; e->key[1] = k; e->key[2] = e->key[3] = e->key[4] = 0;
+    }
+    int kept = rank_candidates(v, n);
+    h->n = nr_terms < kept ? nr_terms : kept;
+    for (int i = 0; i < h->n; i++) { h->lev[i] = v[i].t1; h->k[i] = v[i].t2; h->c[i] = v[i].c; }
+    free(v);
+    h->wmax = 0.0;
+    for (int d = -h->Rz; d <= h->Rz; d++) {
+        double s = 0.0;
+        for (int i = 0; i < h->n; i++) s += h->c[i] * orc_haar_eval(h->lev[i], h->k[i], h->Tz, d);
+        h->w[d + h->Rz] = s;
+        if (fabs(s) > h->wmax) h->wmax = fabs(s);
+    }
+    return ORC_OK;
+}
+
+/* The range series of a plan (for the tests): R_z, J_z and the kept terms (lev, k, c), and the table. */
+int orc_zhaar_info(int rkind, double sigma_r, double t_r, int nr_terms, int zbins, double data_range,
+                   int *ints_out, int *lev, int *kk, double *c, double *w, int w_cap)
+{
+    orc_zhaar h;
+    double Tr = t_r > 0 ? t_r : orc_default_tr(rkind, sigma_r);
+    int st = zhaar_build(&h, rkind, sigma_r, Tr, nr_terms, zbins, data_range);
+    if (st) { zhaar_free(&h); return st; }
+    ints_out[0] = h.Rz; ints_out[1] = h.Jz; ints_out[2] = h.n;
+    for (int i = 0; i < h.n; i++) { lev[i] = h.lev[i]; kk[i] = h.k[i]; c[i] = h.c[i]; }
+    if (w) {
+        if (w_cap < 2 * h.Rz + 1) { zhaar_free(&h); return ORC_ECAP; }
+        memcpy(w, h.w, sizeof(double) * (2 * h.Rz + 1));
+    }
+    zhaar_free(&h);
+    return ORC_OK;
+}
+
+/* O2-3D with the Haar range series: Eq. (1) with K~_s and the range weight w[n(x) - n(y) + R_z]
+ * (0 beyond R_z).  Guard: den <= 1e-6 (sum |K~_s|) max |w| -> I(x).  pts == NULL: every pixel into
+ * out[H W]; else the npts listed (row, col) pixels into out[npts].  den_out as out, or NULL. */
+int orc_approx3dh_direct(const double *I, int H, int W, int skind, double sigma_s, int radius, int ns_terms,
+                         int rkind, double sigma_r, double t_r, int nr_terms, int zbins, double data_range,
+                         const int *pts, int npts, double *out, double *den_out, int nthreads)
+{
+    if (!I || !out || H < 0 || W < 0 || zbins < 2 || !(data_range > 0) || (pts && npts < 0)) return ORC_EINVAL;
+    orc_plan p;
+    int st = plan_build(&p, skind, sigma_s, radius, ns_terms, rkind, sigma_r, t_r, 1, ORC_PAPER_3D, data_range);
+    if (st) { plan_free(&p); return st; }
+    orc_zhaar h;
+    st = zhaar_build(&h, rkind, sigma_r, p.Tr, nr_terms, zbins, data_range);
+    if (st) { zhaar_free(&h); plan_free(&p); return st; }
+    const int R = p.R, w = 2 * R + 1, Z = zbins, Rz = h.Rz;
+    const float zs = z_scale(Z, data_range);
+    double sk = 0.0;
+    for (int i = 0; i < w * w; i++) sk += fabs(p.Ks[i]);
+    const double eps = 1e-6 * sk * h.wmax;
+    const int n_out = pts ? npts : H * W;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+:bad) num_threads(nthreads > 0 ? nthreads : 1)
+    for (int o = 0; o < n_out; o++) {
+        int y = pts ? pts[2 * o] : o / W, x = pts ? pts[2 * o + 1] : o % W;
+        if (y < 0 || y >= H || x < 0 || x >= W) { out[o] = 0.0; bad++; continue; }
+        double ix = I[(size_t)y * W + x], num = 0.0, den = 0.0;
+        int nx = z_bin(ix, zs, Z);
+        for (int dy = -R; dy <= R; dy++) {
+            int yy = y + dy;
+            if (yy < 0 || yy >= H) continue;
+            for (int dx = -R; dx <= R; dx++) {
+                int xx = x + dx;
+                if (xx < 0 || xx >= W) continue;
+                double iy = I[(size_t)yy * W + xx];
+                int d = nx - z_bin(iy, zs, Z);
+                if (abs(d) > Rz) continue;
+                double ks = p.Ks[(-dy + R) * w + (-dx + R)];
+                num += ks * h.w[d + Rz] * iy;
+                den += ks * h.w[d + Rz];
+            }
+        }
+        out[o] = den <= eps ? ix : num / den;
+        if (den_out) den_out[o] = den;
+    }
+    zhaar_free(&h);
+    plan_free(&p);
+    return bad ? ORC_EINVAL : ORC_OK;
+}
+
+/* O3-3D with the Haar range series, the paper's steps: per slice z the 2-D box sums of the one-hot
+ * auxiliary images F(y, z) = (I(y), 1) [n(y) = z] (Eq. (28), summed-area tables); their running sum
+ * along z (the 1-D table of Eq. (29)); then for each kept range term, its pieces as slice windows
+ * relative to n(x) (App. A's boxes, in z), each a difference of two entries of the z table. */
+int orc_approx3dh_fast(const double *I, int H, int W, int skind, double sigma_s, int radius, int ns_terms,
+                       int rkind, double sigma_r, double t_r, int nr_terms, int zbins, double data_range,
+                       double *out, int *ndegen, int nthreads)
+{
+    if (!I || !out || H < 0 || W < 0 || zbins < 2 || !(data_range > 0)) return ORC_EINVAL;
+    orc_plan p;
+    int st = plan_build(&p, skind, sigma_s, radius, ns_terms, rkind, sigma_r, t_r, 1, ORC_PAPER_3D, data_range);
+    if (st) { plan_free(&p); return st; }
+    orc_zhaar h;
+    st = zhaar_build(&h, rkind, sigma_r, p.Tr, nr_terms, zbins, data_range);
+    if (st) { zhaar_free(&h); plan_free(&p); return st; }
+    size_t np = (size_t)H * W;
+    if (np == 0) { if (ndegen) *ndegen = 0; zhaar_free(&h); plan_free(&p); return ORC_OK; }
+    const int Z = zbins;
+    const float zs = z_scale(Z, data_range);
+    dbox *boxes = malloc(sizeof(dbox) * 16 * p.ns);
+    int nb = boxes ? plan_boxes(&p, boxes) : 0;
+    double *g = malloc(sizeof(double) * np * 2);
+    double *S = malloc(sizeof(double) * (size_t)(H + 1) * (W + 1) * 2);
+    double *Pz = malloc(sizeof(double) * np * 2 * (size_t)Z); /* [z][q][pixel]: sum over slices <= z */
+    int *nz = malloc(sizeof(int) * np);
+    if (!boxes || !g || !S || !Pz || !nz) {
+        free(boxes); free(g); free(S); free(Pz); free(nz); zhaar_free(&h); plan_free(&p);
+        return ORC_ECAP;
+    }
+    for (size_t i = 0; i < np; i++) nz[i] = z_bin(I[i], zs, Z);
+    int nt = nthreads > 0 ? nthreads : 1;
+    for (int z = 0; z < Z; z++) {
+        for (size_t i = 0; i < np; i++) {
+            int on = nz[i] == z;
+            g[i] = on ? I[i] : 0.0;
+            g[np + i] = on ? 1.0 : 0.0;
+        }
+        for (int q = 0; q < 2; q++) sat_build(g + q * np, H, W, S + (size_t)q * (H + 1) * (W + 1));
+        double *cur = Pz + (size_t)z * 2 * np, *prev = z > 0 ? Pz + (size_t)(z - 1) * 2 * np : NULL;
+#pragma omp parallel for schedule(static) num_threads(nt)
+        for (int y = 0; y < H; y++)
+            for (int x = 0; x < W; x++) {
+                size_t i = (size_t)y * W + x;
+                for (int q = 0; q < 2; q++) {
+                    double b = 0.0;
+                    for (int e = 0; e < nb; e++) {
+                        const dbox *bx = &boxes[e];
+                        b += bx->c * sat_rect(S + (size_t)q * (H + 1) * (W + 1), H, W, x + bx->x0, x + bx->x1,
+                                              y + bx->y0, y + bx->y1);
+                    }
+                    cur[q * np + i] = (prev ? prev[q * np + i] : 0.0) + b;
+                }
+            }
+    }
+    double sk = 0.0;
+    for (int i = 0; i < (2 * p.R + 1) * (2 * p.R + 1); i++) sk += fabs(p.Ks[i]);
+    const double eps = 1e-6 * sk * h.wmax;
+    int degen = 0;
+#pragma omp parallel for schedule(static) reduction(+:degen) num_threads(nt)
+    for (size_t i = 0; i < np; i++) {
+        double F[2] = {0.0, 0.0};
+        for (int t = 0; t < h.n; t++) {
+            drange rr[4];
+            int m = haar_ranges(h.lev[t], h.k[t], h.Tz, rr); /* neighbour slice offsets n(y) - n(x) */
+            for (int a = 0; a < m; a++) {
+                if (rr[a].lo > rr[a].hi) continue;
+                int zhi = nz[i] + rr[a].hi, zlo = nz[i] + rr[a].lo - 1;
+                if (zhi > Z - 1) zhi = Z - 1;
+                for (int q = 0; q < 2; q++) {
+                    double top = zhi >= 0 ? Pz[(size_t)zhi * 2 * np + q * np + i] : 0.0;
+                    double bot = zlo >= 0 ? Pz[(size_t)(zlo < Z - 1 ? zlo : Z - 1) * 2 * np + q * np + i] : 0.0;
+                    F[q] += h.c[t] * rr[a].w * (top - bot);
+                }
+            }
+        }
+        if (F[1] <= eps) { out[i] = I[i]; degen++; }
+        else out[i] = F[0] / F[1];
+    }
+    if (ndegen) *ndegen = degen;
+    free(boxes); free(g); free(S); free(Pz); free(nz);
+    zhaar_free(&h);
     plan_free(&p);
     return ORC_OK;
 }

@@ -10,6 +10,8 @@ exposes numpy-level functions:
 * ``approx_fast``    -- O3, the paper's algorithm (Eqs. (34)-(36), App. A boxes);
 * ``approx3d_direct`` / ``approx3d_fast`` -- O2 / O3 of the 3-D form (Sec. IV-D: P = T_r, the range box
   applied over Z intensity slices by dimension promotion, Eqs. (2), (28)-(29), (35)-(36));
+* ``approx3dh_direct`` / ``approx3dh_fast`` -- the same with a Haar series in range (best N-term Haar
+  expansion of the truncated range kernel on the slice axis; each term is boxes along z);
 * ``range_coeffs``, ``haar1d``, ``plan_info`` -- coefficient and selection steps.
 
 Every function follows the paper step by step; the C file header lists the
@@ -77,6 +79,9 @@ def _load():
         lib.orc_approx3d_direct_at.argtypes = [pd, i, i, i, d, i, i, i, d, d, i, i, d, i, pi, i, pd, pd, i]
         lib.orc_approx3d_fast.argtypes = [pd, i, i, i, d, i, i, i, d, d, i, i, d, i, pd, pi, i, pd]
         lib.orc_z_bins.argtypes = [d, i, d, pd, i, pi, pi]
+        lib.orc_zhaar_info.argtypes = [i, d, d, i, i, d, pi, pi, pi, pd, pd, i]
+        lib.orc_approx3dh_direct.argtypes = [pd, i, i, i, d, i, i, i, d, d, i, i, d, pi, i, pd, pd, i]
+        lib.orc_approx3dh_fast.argtypes = [pd, i, i, i, d, i, i, i, d, d, i, i, d, pd, pi, i]
         _lib = lib
     return _lib
 
@@ -351,3 +356,60 @@ def z_bins(I, t_r: float, zbins: int = 256, data_range: float = 1.0):
     if st:
         raise ValueError("orc_z_bins status %d" % st)
     return out.reshape(np.shape(I)), int(rz[0])
+
+
+def _hargs(desc: Desc, zbins: int, data_range: float):
+    return (desc.spatial, desc.sigma_s, desc.radius, desc.ns_terms, desc.range, desc.sigma_r, desc.t_r,
+            desc.nr_terms, zbins, data_range)
+
+
+@dataclass
+class ZHaarInfo:
+    Rz: int
+    Jz: int
+    lev: np.ndarray
+    k: np.ndarray
+    c: np.ndarray
+    w: np.ndarray          # K~_r at slice offsets d = n(x) - n(y), index d + Rz
+
+
+def zhaar_info(desc: Desc, zbins: int = 256, data_range: float = 1.0) -> ZHaarInfo:
+    lib = _load()
+    ints = np.zeros(3, dtype=np.int32)
+    n = desc.nr_terms
+    lev, kk, c = np.zeros(n, dtype=np.int32), np.zeros(n, dtype=np.int32), np.zeros(n)
+    w = np.zeros(2 * 4096 + 1)
+    st = lib.orc_zhaar_info(desc.range, desc.sigma_r, desc.t_r, n, zbins, data_range, _ip(ints), _ip(lev), _ip(kk),
+                            _dp(c), _dp(w), len(w))
+    if st:
+        raise ValueError("orc_zhaar_info status %d" % st)
+    Rz, Jz, m = int(ints[0]), int(ints[1]), int(ints[2])
+    return ZHaarInfo(Rz, Jz, lev[:m].copy(), kk[:m].copy(), c[:m].copy(), w[:2 * Rz + 1].copy())
+
+
+def approx3dh_direct(I, desc: Desc, zbins: int = 256, pts=None, threads: int = 1, data_range: float = 1.0):
+    """O2-3D with the Haar range series: (output, denominator), over the image or at (row, col) pts."""
+    I = _img(I)
+    H, W = I.shape
+    if pts is None:
+        out, den, pp, n = np.zeros((H, W)), np.zeros((H, W)), None, 0
+    else:
+        pts = np.ascontiguousarray(pts, dtype=np.int32).reshape(-1, 2)
+        out, den, pp, n = np.zeros(len(pts)), np.zeros(len(pts)), _ip(pts), len(pts)
+    st = _load().orc_approx3dh_direct(_dp(I), H, W, *_hargs(desc, zbins, data_range), pp, n, _dp(out), _dp(den),
+                                      threads)
+    if st:
+        raise ValueError("orc_approx3dh_direct status %d" % st)
+    return out, den
+
+
+def approx3dh_fast(I, desc: Desc, zbins: int = 256, threads: int = 1, data_range: float = 1.0):
+    """O3-3D with the Haar range series (per-slice tables, z table, boxes along z): (output, guard count)."""
+    I = _img(I)
+    H, W = I.shape
+    out = np.zeros((H, W))
+    nd = np.zeros(1, dtype=np.int32)
+    st = _load().orc_approx3dh_fast(_dp(I), H, W, *_hargs(desc, zbins, data_range), _dp(out), _ip(nd), threads)
+    if st:
+        raise ValueError("orc_approx3dh_fast status %d" % st)
+    return out, int(nd[0])
