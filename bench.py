@@ -404,7 +404,8 @@ def run_paper_3d(bf, dev, src, img, flush, alu_peak, reps=3):
     """The 3-D form of Sec. IV-D (P = T_r, the range box applied over 256 intensity slices, N_r = 8,
     N_s = 5) on the 1920x1080 image for every (sigma_s, sigma_r) of the sweep: device ms, Mpixel/s and
     PSNR against the exact filter, beside the collapsed form's PSNR at the same N_r, plus the same at
-    N_r = 4 (the 3-D form's series fits one period of the truncated kernel, so it needs fewer terms).
+    N_r = 4 (the 3-D form's series fits one period of the truncated kernel, so it needs fewer terms), and
+    the Haar range series with 64 terms (`haar64_*`: one constant cosine term per pass, weights by table).
     Each plan is autotuned first, as the sweep's plans are.  Work: one tile pass per (tile, slice present
     in the tile); `passes_per_px` = items x tile area / pixels, and the roofline fraction counts each pass
     as a filter pass over its tile's pixels."""
@@ -412,7 +413,7 @@ def run_paper_3d(bf, dev, src, img, flush, alu_peak, reps=3):
     out = torch.empty_like(src)
     ex = torch.empty_like(src)
     rows = []
-    total_ms = 0.0
+    total_ms = haar_ms = 0.0
     for ss in SIGMA_S:
         for sr in SIGMA_R:
             bf.bf_exact(src, ex, sigma_s=ss, sigma_r=sr)
@@ -440,9 +441,19 @@ def run_paper_3d(bf, dev, src, img, flush, alu_peak, reps=3):
                     row["passes_per_px"] = round(items * info["tw"] * info["th"] / (H * W), 1)
                     row["roofline_frac"] = round(ops / (t * 1e-3) / 1e12 / alu_peak, 4)
                     total_ms += t
+            # the Haar range series (64 terms: one constant cosine term per pass, the weights from a table)
+            ph = bf.Plan(sigma_s=ss, sigma_r=sr, nr_terms=64, ns_terms=NS, device=dev.index,
+                         policy=bf.RANGE_PAPER_3D, z_bins=256, range_series=bf.SERIES_HAAR)
+            bf.bf_autotune(ph, H, W)
+            t = timed_launches(bf, ph, src, out, flush, reps)
+            mseh = torch.mean((out.double() - ex.double()) ** 2).item()
+            row["haar64_ms"] = round(t, 3)
+            row["haar64_mpix_s"] = round(H * W / (t * 1e-3) / 1e6, 1)
+            row["haar64_psnr_db"] = round(10 * np.log10(1.0 / mseh), 2)
+            haar_ms += t
             rows.append(row)
     return {"z_bins": 256, "ns_terms": NS, "mpix_s_sweep": round(len(rows) * H * W / (total_ms * 1e-3) / 1e6, 1),
-            "by_combo": rows}
+            "haar64_mpix_s_sweep": round(len(rows) * H * W / (haar_ms * 1e-3) / 1e6, 1), "by_combo": rows}
 
 
 def run_bft_crossover(bf, dev, src, flush, reps=5):

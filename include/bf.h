@@ -87,6 +87,19 @@ typedef enum {
     BF_RANGE_PAPER_3D = 2
 } bf_range_policy;
 
+/* The series that approximates the range kernel. */
+typedef enum {
+    /* The truncated cosine series of Eqs. (13)-(15), best N_r terms (Eq. (33)).  Default. */
+    BF_SERIES_COSINE = 0,
+    /* BF_RANGE_PAPER_3D only: the best N_r-term Haar expansion (Eqs. (17)-(20), selection by Eq. (11))
+     * of the truncated range kernel on the slice axis, in slice units: domain [-T_z, T_z], T_z = R_z + 1/2,
+     * J_z = ceil(log2(2 T_z)) levels, profile K_r(t dI / (Z - 1)).  Each Haar term is a pair of boxes
+     * along z, so the filter is a sum of 3-D boxes with no cosine basis: a neighbour's weight is
+     * K~_s(x - y) K~_r(n(x) - n(y)), K~_r read from a table of the 2 R_z + 1 slice offsets.  R_z <= 1023.
+     * The paper uses Haar functions for the spatial kernel only; this applies them to the range kernel. */
+    BF_SERIES_HAAR = 1
+} bf_range_series;
+
 /* Storage precision.  The fused filter computes and exchanges everything in
  * fp32 and stores no basis image (in HBM or shared memory): basis values live
  * in registers at the rows where they enter or leave a window, and the kernel
@@ -126,6 +139,8 @@ typedef struct {
                            filtering returns BF_ERR_NO_DEVICE) */
     int z_bins;         /* BF_RANGE_PAPER_3D: intensity slices Z in [2, 4096]; 0 -> 256 (the
                            8-bit case of Sec. II-B).  Ignored by the other policies. */
+    int range_series;   /* bf_range_series; BF_SERIES_HAAR needs BF_RANGE_PAPER_3D.  nr_terms counts
+                           the kept terms of whichever series */
 } bf_plan_desc;
 
 typedef struct bf_plan bf_plan;
@@ -148,9 +163,10 @@ void bf_plan_desc_default(bf_plan_desc *desc);
  * Host memory only; the coefficient tables travel to the device as kernel
  * parameters.  *out receives a plan the caller releases with bf_plan_destroy.
  * Errors: BF_ERR_INVALID_ARG (NULL, sigma <= 0, N < 1, i_hi <= i_lo, bad enum,
- * z_bins outside [2, 4096] for BF_RANGE_PAPER_3D),
+ * z_bins outside [2, 4096] for BF_RANGE_PAPER_3D, BF_SERIES_HAAR without it),
  * BF_ERR_UNSUPPORTED (exponential spatial kernel with R > 255; a selection
- * needing more than 6 box windows per axis; 16-bit precision),
+ * needing more than 6 box windows per axis; 16-bit precision; BF_SERIES_HAAR
+ * with R_z > 1023),
  * BF_ERR_OOM, BF_ERR_NO_DEVICE (device >= 0 that does not exist). */
 bf_status bf_plan_create(const bf_plan_desc *desc, bf_plan **out);
 
@@ -185,6 +201,13 @@ typedef struct {
     int passes;                 /* term groups at the largest group size (ceil(nr / 16)) */
     int z_bins;                 /* BF_RANGE_PAPER_3D: slices Z; 0 for the other policies */
     int z_radius;               /* BF_RANGE_PAPER_3D: slice window half-width R_z; 0 otherwise */
+    int range_series;           /* bf_range_series.  For BF_SERIES_HAAR, k / a above hold the one
+                                   constant cosine term the kernel runs (k = 0, a = 1) and: */
+    int n_range_haar;           /* kept range Haar terms (0 for the cosine series) */
+    const int *range_haar;      /* [2 n_range_haar] level, k (level -1 = phi), in ranking order */
+    const double *range_haar_coef;  /* [n_range_haar] c */
+    const double *z_weights;    /* [2 z_radius + 1]: K~_r at slice offset d = n(x) - n(y), at [d + z_radius]
+                                   (BF_SERIES_HAAR); NULL otherwise */
 } bf_coeff_view;
 
 /* Fills *out with the plan's coefficients.  Errors: BF_ERR_INVALID_ARG. */

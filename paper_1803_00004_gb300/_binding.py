@@ -20,6 +20,7 @@ ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA, ERR_ADMISSION = 1, 2, 3, 4,
 ERR_TIMEOUT, ERR_DEVICE_TIMEOUT, ERR_RANGE, ERR_NO_DEVICE, ERR_NOT_FOUND, ERR_CANCELLED = 6, 7, 8, 9, 10, 11
 KERNEL_GAUSSIAN, KERNEL_EXPONENTIAL, KERNEL_BOX = 0, 1, 2
 RANGE_TRUNCATED_MIN_PERIOD, RANGE_UNTRUNCATED_FULL, RANGE_PAPER_3D = 0, 1, 2
+SERIES_COSINE, SERIES_HAAR = 0, 1
 PREC_FP32, PREC_BF16, PREC_FP16 = 0, 1, 2
 
 
@@ -27,7 +28,7 @@ class bf_plan_desc(C.Structure):
     _fields_ = [("spatial", C.c_int), ("sigma_s", C.c_double), ("radius", C.c_int), ("ns_terms", C.c_int),
                 ("range", C.c_int), ("sigma_r", C.c_double), ("t_r", C.c_double), ("nr_terms", C.c_int),
                 ("policy", C.c_int), ("i_lo", C.c_float), ("i_hi", C.c_float), ("precision", C.c_int),
-                ("kahan", C.c_int), ("device", C.c_int), ("z_bins", C.c_int)]
+                ("kahan", C.c_int), ("device", C.c_int), ("z_bins", C.c_int), ("range_series", C.c_int)]
 
 
 class bf_coeff_view(C.Structure):
@@ -37,7 +38,9 @@ class bf_coeff_view(C.Structure):
                 ("tie_split", C.c_int), ("kernel", C.POINTER(C.c_double)), ("n_vwin", C.c_int),
                 ("n_hwin", C.c_int), ("vwin", C.POINTER(C.c_int)), ("hwin", C.POINTER(C.c_int)),
                 ("wcoef", C.POINTER(C.c_double)), ("range_max_err", C.c_double), ("spatial_max_err", C.c_double),
-                ("den_eps", C.c_double), ("passes", C.c_int), ("z_bins", C.c_int), ("z_radius", C.c_int)]
+                ("den_eps", C.c_double), ("passes", C.c_int), ("z_bins", C.c_int), ("z_radius", C.c_int),
+                ("range_series", C.c_int), ("n_range_haar", C.c_int), ("range_haar", C.POINTER(C.c_int)),
+                ("range_haar_coef", C.POINTER(C.c_double)), ("z_weights", C.POINTER(C.c_double))]
 
 
 class bf_image(C.Structure):
@@ -195,7 +198,10 @@ def bf_coeffs(plan: Plan) -> dict:
         "hwin": [(v.hwin[2 * j], v.hwin[2 * j + 1]) for j in range(v.n_hwin)],
         "wcoef": [[v.wcoef[a * v.n_hwin + b] for b in range(v.n_hwin)] for a in range(v.n_vwin)],
         "range_max_err": v.range_max_err, "spatial_max_err": v.spatial_max_err, "den_eps": v.den_eps,
-        "passes": v.passes, "z_bins": v.z_bins, "z_radius": v.z_radius,
+        "passes": v.passes, "z_bins": v.z_bins, "z_radius": v.z_radius, "range_series": v.range_series,
+        "range_haar": [(v.range_haar[2 * t], v.range_haar[2 * t + 1]) for t in range(v.n_range_haar)],
+        "range_haar_coef": arr(v.range_haar_coef, v.n_range_haar),
+        "z_weights": arr(v.z_weights, 2 * v.z_radius + 1) if v.z_weights else [],
     }
 
 

@@ -24,10 +24,16 @@ extern const KernelClass kClassesM3[];
 extern const KernelClass kClassesM4to6[];
 extern const int kNumClassesM1, kNumClassesM2, kNumClassesM3, kNumClassesM4to6;
 
-// The 3-D form's slice kernels (packed family without the ring; bf_tile.cuh): kernels_z_*.cu.
-// fn[0] is the persistent slice kernel, fn[1] and batch_fn are unused.
-extern const KernelClass kZClassesM1M2[];
-extern const KernelClass kZClassesM3to6[];
+// The 3-D form's persistent slice kernels (packed family without the ring; bf_tile.cuh): kernels_z_*.cu.
+// box: the range box; haar: the Haar range series' weight table (NK = 2 only).  The *_small kernels are the
+// same bounded to CTAs of at most 256 threads and *_regs registers (nullptr where they would spill).
+struct ZKernelClass {
+    int m, nk;
+    const void *box, *box_small, *haar, *haar_small;
+    int box_small_regs, haar_small_regs;
+};
+extern const ZKernelClass kZClassesM1M2[];
+extern const ZKernelClass kZClassesM3to6[];
 extern const int kNumZClassesM1M2, kNumZClassesM3to6;
 
 // Scalar family (any term set; bf_tile_scalar.cuh): kernels_s_*.cu.

@@ -99,14 +99,33 @@ const void *find_kernel(int m, int nk, bool ring, bool packed) {
     return nullptr;
 }
 
-// The 3-D form's persistent slice kernel of class (m, nk).
-const void *find_zkernel(int m, int nk) {
+const ZKernelClass *find_zclass(int m, int nk) {
     for (const auto *t : {kZClassesM1M2, kZClassesM3to6}) {
         const int n = t == kZClassesM1M2 ? kNumZClassesM1M2 : kNumZClassesM3to6;
         for (int i = 0; i < n; ++i)
-            if (t[i].m == m && t[i].nk == nk) return t[i].fn[0];
+            if (t[i].m == m && t[i].nk == nk) return &t[i];
     }
     return nullptr;
+}
+
+// The 3-D form's persistent slice kernel of class (m, nk): zmode 1 the range box, 2 the Haar range
+// series' weights (nullptr where the class has none); `threads` <= 256 picks the register-bounded kernel
+// where the class has one.  *regs: the registers per thread the cost model assumes.
+const void *find_zkernel(int m, int nk, int zmode, int threads = 512, int *regs = nullptr) {
+    const ZKernelClass *c = find_zclass(m, nk);
+    if (regs) *regs = 128;
+    if (!c) return nullptr;
+    const void *small = zmode == 2 ? c->haar_small : c->box_small;
+    if (threads <= 256 && small) {
+        if (regs) *regs = zmode == 2 ? c->haar_small_regs : c->box_small_regs;
+        return small;
+    }
+    return zmode == 2 ? c->haar : c->box;
+}
+
+// Bytes of the Haar range series' weight table in the slice kernel's shared memory (16-byte multiple).
+size_t zweights_bytes(const FilterParams &p) {
+    return p.zmode == 2 ? ((sizeof(float) * (2 * (size_t)p.rz + 1) + 15) & ~(size_t)15) : 0;
 }
 
 // The 3-D form's work list: one CTA per tile marks the slices of the tile's output pixels in a shared
@@ -316,6 +335,7 @@ std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int w
     for (int packed = 1; packed >= (gapped_terms(p) && !z3d ? 0 : 1); --packed)
     for (const auto &cls : classes(packed)) {
         if (cls.m != p.m) continue;
+        if (z3d && !find_zkernel(cls.m, cls.nk, p.zmode)) continue;  // the Haar series runs NK = 2 only
         const int groups = family_groups(p, cls.nk, packed);
         if (packed && groups * cls.nk > kMaxSlots) continue;
         const double term_cost = packed ? 40.0 : 60.0;  // per term and window: the scalar family has no pairing
@@ -336,10 +356,12 @@ std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int w
                 const size_t smem = smem_bytes(p.m, cls.nk, ncols, tw, depth, !pring) +
                                     (ring ? ring_bytes(p, ncols, groups_need_anchor(p, cls.nk, packed)) : 0);
                 // the slice kernel keeps a few bytes of static shared memory besides the tile's
-                if (smem > 227 * 1024 - (z3d ? 256 : 0)) continue;
+                if (smem + zweights_bytes(p) > 227 * 1024 - (z3d ? 256 : 0)) continue;
                 const int by_smem = (int)((228 * 1024) / (smem + 1024));
                 const int by_threads = 2048 / (ncols + kScanThreads);
-                const int by_regs = 65536 / (128 * (ncols + kScanThreads));
+                int regs = 128;
+                if (z3d) find_zkernel(cls.m, cls.nk, p.zmode, ncols + kScanThreads, &regs);
+                const int by_regs = 65536 / (regs * (ncols + kScanThreads));
                 const int cps = std::max(1, std::min({by_smem, by_threads, by_regs}));
                 // three exchange buffers save a barrier per row; the slice kernel measured no gain from them
                 const double edge = (ring ? 60.0 + 12.0 * (2 * p.m + 1) : 60.0 * (2 * p.m + 1)) *
@@ -512,8 +534,11 @@ bf_status launch_filter_z3d(const FilterParams &p, const TileConfig &tc, const f
                             float *d_out, size_t out_pitch, float *d_scratch, int height, int width, void *stream) {
     if (p.zbins < 2 || p.zbins > kMaxZBins || p.rz < 0) return fail(BF_ERR_INVALID_ARG, "bad slice count");
     if (tc.ring || !tc.packed) return fail(BF_ERR_INVALID_ARG, "the 3-D form runs the packed family without the ring");
-    if (tc.smem > 227 * 1024 - 256) return fail(BF_ERR_UNSUPPORTED, "tile too large for the slice kernel");
-    const void *fn = find_zkernel(p.m, tc.nk);
+    if (p.zmode == 2 && (!p.zw || 2 * p.rz + 1 > kMaxZWeights))
+        return fail(BF_ERR_INVALID_ARG, "missing or oversized Haar range weight table");
+    const size_t zwb = zweights_bytes(p), smem = tc.smem + zwb;
+    if (smem > 227 * 1024 - 256) return fail(BF_ERR_UNSUPPORTED, "tile too large for the slice kernel");
+    const void *fn = find_zkernel(p.m, tc.nk, p.zmode, tc.threads);
     if (!fn) return fail(BF_ERR_UNSUPPORTED, "no slice kernel for this class");
     FilterParams pp;
     if (!term_layout(p, tc.nk, pp) || pp.nr != tc.groups * tc.nk)
@@ -535,10 +560,10 @@ bf_status launch_filter_z3d(const FilterParams &p, const TileConfig &tc, const f
                                                       cap, counters, pp);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "slice list launch");
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc.smem);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     int cps = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cps, fn, tc.threads, tc.smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cps, fn, tc.threads, smem);
     if (e != cudaSuccess || cps < 1) {
         cudaGetLastError();
         cps = 1;
@@ -546,14 +571,17 @@ bf_status launch_filter_z3d(const FilterParams &p, const TileConfig &tc, const f
     const long want = (long)cap * tc.groups;
     const int grid = (int)std::max(1L, std::min((long)device_sms() * cps, want));
     int tw = tc.tw, th = tc.th, ncols = tc.ncols, H = height, W = width, depth = tc.depth, groups = tc.groups;
-    int max_iter = cap * tc.groups;
+    int max_iter = cap * tc.groups, zw_off = (int)(tc.smem / sizeof(float));
     const float *in = d_in;
     float *out = d_out;
+    static thread_local ZWeights zwp;  // the table travels as a kernel parameter (copied at launch)
+    if (p.zmode == 2) std::copy(p.zw, p.zw + 2 * p.rz + 1, zwp.w);
     void *args[] = {(void *)&in, (void *)&in_pitch, (void *)&out, (void *)&out_pitch, (void *)&part, (void *)&H,
                     (void *)&W, (void *)&tw, (void *)&th, (void *)&ncols, (void *)&depth, (void *)&tiles_x,
-                    (void *)&groups, (void *)&items, (void *)&cap, (void *)&counters, (void *)&max_iter, (void *)&pp};
+                    (void *)&groups, (void *)&items, (void *)&cap, (void *)&counters, (void *)&max_iter,
+                    (void *)&zw_off, (void *)&pp, (void *)&zwp};
     if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");
-    e = cudaLaunchKernel(fn, dim3(grid), dim3(tc.threads), args, tc.smem, s);
+    e = cudaLaunchKernel(fn, dim3(grid), dim3(tc.threads), args, smem, s);
     if (e != cudaSuccess) return cuda_fail(e, "slice filter launch");
     if (tc.groups > 1) {
         if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");

@@ -48,10 +48,22 @@ struct FilterParams {
     int zbins;
     int rz;
     float zscale;
+    // zmode 1: the window is a box (weight 1 within rz slices).  zmode 2 (Haar range series): the weight of
+    // a neighbour is zw[n(x) - n(y) + rz], a host table of 2 rz + 1 floats that the launcher copies into the
+    // slice kernel's parameters (kernels never read this pointer).
+    int zmode;
+    const float *zw;
 };
 
-// Largest slice count of the 3-D form (the per-tile slice bitmap lives in shared memory).
+// Largest slice count of the 3-D form (the per-tile slice bitmap lives in shared memory), and the largest
+// weight table of the Haar range series (slice offsets |d| <= 1023).
 constexpr int kMaxZBins = 4096;
+constexpr int kMaxZWeights = 2047;
+
+// The Haar range series' weight table as a kernel parameter (copied into shared memory by the kernel).
+struct ZWeights {
+    float w[kMaxZWeights];
+};
 
 // Launch geometry chosen by the host.
 struct TileConfig {
@@ -161,4 +173,9 @@ struct bf_plan {
     double range_max_err = 0, spatial_max_err = 0, den_eps = 0;
     int m = 0;                      // kernel class (windows per axis)
     bfi::FilterParams kp;           // kernel parameters (all terms)
+    // Haar range series (BF_SERIES_HAAR): kept terms (level, k), coefficients, and the weight table in
+    // double (reported) and float (launched; kp.zw points at it)
+    std::vector<int> rh_terms;
+    std::vector<double> rh_coef, zw;
+    std::vector<float> zw_f;
 };

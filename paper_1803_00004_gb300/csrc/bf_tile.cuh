@@ -105,7 +105,9 @@ __device__ __forceinline__ void rot2(float2 &C, float2 &S, float2 cs, float2 ss,
 // cosine terms [g NK, g NK + NK) of p.  All threads of the CTA call it; it
 // ends on a barrier, so the shared memory can be reused right after.
 // ZB (the 3-D form, Eqs. (35)-(36) with the z axis): only neighbours whose slice lies within p.rz of
-// slice zc enter the window sums, and only output pixels of slice zc are stored.  `mode`:
+// slice zc enter the window sums, and only output pixels of slice zc are stored.  ZB = 1: with weight 1
+// (the range box); ZB = 2 (Haar range series): with weight zw[zc - n(y) + p.rz] (zw: shared memory).
+// `mode`:
 // kModeFinal divides and stores Î; kModePartial stores this group's numerator
 // and denominator planes (part); kModeCache / kModeCacheF16 / kModeCacheBF16
 // store the window sums of every frequency of the group (part = the cache
@@ -113,11 +115,11 @@ __device__ __forceinline__ void rot2(float2 &C, float2 &S, float2 cs, float2 ss,
 //
 // The NK terms are processed as NK / 2 pairs of consecutive terms with the packed pair instructions:
 // pair p holds terms (2p, 2p + 1) of the group in the two lanes of every float2.
-template <int NK, int M, bool RING, bool ZB = false>
+template <int NK, int M, bool RING, int ZB = 0>
 __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__restrict__ in, size_t in_pitch,
                                           float *__restrict__ out, size_t out_pitch, float *__restrict__ part, int H,
                                           int W, int x0, int y0, int tw, int th, int ncols, int g, int mode,
-                                          int depth, float *smem, int zc = 0) {
+                                          int depth, float *smem, int zc = 0, const float *zw = nullptr) {
     static_assert(NK % 2 == 0, "terms are processed in pairs");
     static_assert(!(ZB && RING), "the 3-D form runs without the ring");
     constexpr int NP = NK / 2;        // term pairs per group
@@ -201,8 +203,18 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
             if (off < p.vhi) vn = pixel(row + 1);
             if (row < 0 || row >= H) continue;
             float c1, s1, c0, s0;
-            const bool inz = !ZB || abs(z_slice(v, p) - zc) <= p.rz;  // 3-D form: the neighbour's slice window
+            bool inz = true;  // 3-D form: the neighbour's slice window (and its weight)
+            float wz = 1.f;
+            if (ZB) {
+                const int dz = zc - z_slice(v, p);
+                inz = abs(dz) <= p.rz;
+                if (ZB == 2) wz = inz ? zw[dz + p.rz] : 0.f;
+            }
             basis_start(v, p.inv_p, p.inv_p_lo, k0, colv && inz, c1, s1, c0, s0);
+            if (ZB == 2) {
+                c0 *= wz;
+                s0 *= wz;
+            }
             if (RING) {
                 const int sl = pos_mod(row, D) * ncols + tid;
                 ringA[sl] = make_float4(v, c1, s1, 0.f);
@@ -311,12 +323,21 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
                     // sums already hold at j == 0
                     v = valid ? Ie[e] : 0.f;
                     bool live = valid;
+                    float wz = 1.f;
                     if (ZB) {
                         const int n = z_slice(v, p);
-                        if (e < 2 * M) live = valid && abs(n - zc) <= p.rz;  // a window edge: the slice window
-                        else zrow |= (valid && n == zc) ? 1u : 0u;             // the output row: its own slice
+                        if (e < 2 * M) {  // a window edge: the slice window (and the weight of the offset)
+                            live = valid && abs(zc - n) <= p.rz;
+                            if (ZB == 2) wz = live ? zw[zc - n + p.rz] : 0.f;
+                        } else {          // the output row: its own slice
+                            zrow |= (valid && n == zc) ? 1u : 0u;
+                        }
                     }
                     basis_start(v, p.inv_p, p.inv_p_lo, k0, live, c1, s1, c0, s0);
+                    if (ZB == 2 && e < 2 * M) {  // the pair starts from the anchor: scaling it scales the edge
+                        c0 *= wz;
+                        s0 *= wz;
+                    }
                 }
                 float2 C, S, cs, ss, nss;
                 start_pair(c1, s1, c0, s0, C, S, cs, ss, nss);
@@ -559,15 +580,21 @@ bf_batch_kernel(const BatchImage *__restrict__ imgs, const FilterParams *__restr
 // The 3-D form (Sec. IV-D), persistent: each CTA repeatedly takes the next work item from the cursor
 // (counters[1]) and runs the tile body restricted to one slice.  items[0 .. counters[0]) hold (tile, slice)
 // for every slice present among a tile's output pixels; item i of term group g is i + g counters[0].  The
-// loop is bounded by max_iter.
-template <int NK, int M>
-__global__ void __launch_bounds__(512, 1)
-bf_zslice_kernel(const float *__restrict__ in, size_t in_pitch, float *__restrict__ out, size_t out_pitch,
-                 float *__restrict__ part, int H, int W, int tw, int th, int ncols, int depth, int tiles_x,
-                 int groups, const int2 *__restrict__ items, int cap, int *__restrict__ counters, int max_iter,
-                 const __grid_constant__ FilterParams p) {
+// loop is bounded by max_iter.  ZB = 2: the weight table (2 p.rz + 1 floats of zwp) is first copied into
+// dynamic shared memory at float offset zw_off, after the tile's exchange.
+template <int NK, int M, int ZB>
+__device__ __forceinline__ void zslice_body(const float *__restrict__ in, size_t in_pitch, float *__restrict__ out,
+                                            size_t out_pitch, float *__restrict__ part, int H, int W, int tw, int th,
+                                            int ncols, int depth, int tiles_x, int groups,
+                                            const int2 *__restrict__ items, int cap, int *__restrict__ counters,
+                                            int max_iter, int zw_off, const FilterParams &p, const ZWeights &zwp) {
     extern __shared__ __align__(16) float smem[];
     __shared__ int s_item;
+    float *zw = smem + zw_off;
+    if (ZB == 2) {
+        for (int i = threadIdx.x; i < 2 * p.rz + 1; i += blockDim.x) zw[i] = zwp.w[i];
+        __syncthreads();
+    }
     const int n = min(counters[0], cap);
     const int total = n * groups;
     for (int iter = 0; iter < max_iter; ++iter) {
@@ -578,14 +605,56 @@ bf_zslice_kernel(const float *__restrict__ in, size_t in_pitch, float *__restric
         const int g = it / n;
         const int2 w = items[it - g * n];
         const int ty = w.x / tiles_x, tx = w.x - ty * tiles_x;
-        tile_body<NK, M, false, true>(p, in, in_pitch, out, out_pitch, part, H, W, tx * tw, ty * th, tw, th, ncols,
-                                      g, groups > 1 ? kModePartial : kModeFinal, depth, smem, w.y);
+        tile_body<NK, M, false, ZB>(p, in, in_pitch, out, out_pitch, part, H, W, tx * tw, ty * th, tw, th, ncols,
+                                    g, groups > 1 ? kModePartial : kModeFinal, depth, smem, w.y, zw);
     }
 }
 
+#define BF_ZSLICE_PARAMS                                                                                        \
+    const float *__restrict__ in, size_t in_pitch, float *__restrict__ out, size_t out_pitch,                  \
+        float *__restrict__ part, int H, int W, int tw, int th, int ncols, int depth, int tiles_x, int groups, \
+        const int2 *__restrict__ items, int cap, int *__restrict__ counters, int max_iter, int zw_off,         \
+        const __grid_constant__ FilterParams p, const __grid_constant__ ZWeights zwp
+#define BF_ZSLICE_ARGS \
+    in, in_pitch, out, out_pitch, part, H, W, tw, th, ncols, depth, tiles_x, groups, items, cap, counters, max_iter, zw_off, p, zwp
+
+template <int NK, int M, int ZB>
+__global__ void __launch_bounds__(512, 1) bf_zslice_kernel(BF_ZSLICE_PARAMS) {
+    zslice_body<NK, M, ZB>(BF_ZSLICE_ARGS);
+}
+
+// Slice kernels for CTAs of at most 256 threads, bounded in registers so that more CTAs fit an SM (the
+// general kernel takes 100-128 registers and stops at two): the Haar series' NK = 2 kernel at 64 registers
+// (four CTAs), the range box's small classes at 80 (three).  Only classes that fit without spilling more
+// than a few bytes are instantiated.
+template <int NK, int M, int ZB>
+__global__ void __launch_bounds__(256, ZB == 2 ? 4 : 3) bf_zslice_small_kernel(BF_ZSLICE_PARAMS) {
+    zslice_body<NK, M, ZB>(BF_ZSLICE_ARGS);
+}
+constexpr int kZSmallRegs[3] = {0, 80, 64};  // by ZB
+
 }  // namespace
 
-#define BF_ZCLASS(M, NK) {M, NK, {(const void *)bf_zslice_kernel<NK, M>, nullptr}, nullptr}
+// The Haar range series runs one constant cosine term: its slice kernels exist for NK = 2 only.
+template <int NK, int M>
+constexpr const void *zhaar_kernel() {
+    if constexpr (NK == 2) return (const void *)bf_zslice_kernel<2, M, 2>;
+    else return nullptr;
+}
+template <int NK, int M>
+constexpr const void *zhaar_small_kernel() {  // more windows than two spill at 64 registers
+    if constexpr (NK == 2 && M <= 2) return (const void *)bf_zslice_small_kernel<2, M, 2>;
+    else return nullptr;
+}
+template <int NK, int M>
+constexpr const void *zbox_small_kernel() {  // within 8 bytes of spill at 80 registers
+    if constexpr ((M <= 2 && NK <= 4) || (M == 3 && NK == 2)) return (const void *)bf_zslice_small_kernel<NK, M, 1>;
+    else return nullptr;
+}
+
+#define BF_ZCLASS(M, NK)                                                                              \
+    {M, NK, (const void *)bf_zslice_kernel<NK, M, 1>, zbox_small_kernel<NK, M>(), zhaar_kernel<NK, M>(), \
+     zhaar_small_kernel<NK, M>(), kZSmallRegs[1], kZSmallRegs[2]}
 
 #define BF_CLASS(M, NK)                                                                                 \
     {M, NK, {(const void *)bf_fused_kernel<NK, M, false>, (const void *)bf_fused_kernel<NK, M, true>},  \

@@ -96,6 +96,7 @@ void bf_plan_desc_default(bf_plan_desc *d) {
     d->kahan = 1;
     d->device = 0;
     d->z_bins = 0;
+    d->range_series = BF_SERIES_COSINE;
 }
 
 bf_status bf_plan_create(const bf_plan_desc *desc, bf_plan **out) {
@@ -152,6 +153,11 @@ bf_status bf_coeffs(const bf_plan *p, bf_coeff_view *o) {
     o->passes = (int)((p->k.size() + 15) / 16);
     o->z_bins = p->kp.zbins;
     o->z_radius = p->kp.rz;
+    o->range_series = p->desc.range_series;
+    o->n_range_haar = (int)p->rh_coef.size();
+    o->range_haar = p->rh_terms.empty() ? nullptr : p->rh_terms.data();
+    o->range_haar_coef = p->rh_coef.empty() ? nullptr : p->rh_coef.data();
+    o->z_weights = p->zw.empty() ? nullptr : p->zw.data();
     return BF_OK;
 }
 

@@ -4,7 +4,7 @@
 
 namespace bfi {
 
-const KernelClass kZClassesM1M2[] = {BF_ZCLASS(1, 16), BF_ZCLASS(1, 8), BF_ZCLASS(1, 4), BF_ZCLASS(1, 2),
+const ZKernelClass kZClassesM1M2[] = {BF_ZCLASS(1, 16), BF_ZCLASS(1, 8), BF_ZCLASS(1, 4), BF_ZCLASS(1, 2),
                                      BF_ZCLASS(2, 8),  BF_ZCLASS(2, 4), BF_ZCLASS(2, 2)};
 const int kNumZClassesM1M2 = sizeof(kZClassesM1M2) / sizeof(kZClassesM1M2[0]);
 

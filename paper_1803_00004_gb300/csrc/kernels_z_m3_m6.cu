@@ -3,7 +3,7 @@
 
 namespace bfi {
 
-const KernelClass kZClassesM3to6[] = {BF_ZCLASS(3, 4), BF_ZCLASS(3, 2), BF_ZCLASS(4, 2), BF_ZCLASS(5, 2),
+const ZKernelClass kZClassesM3to6[] = {BF_ZCLASS(3, 4), BF_ZCLASS(3, 2), BF_ZCLASS(4, 2), BF_ZCLASS(5, 2),
                                       BF_ZCLASS(6, 2)};
 const int kNumZClassesM3to6 = sizeof(kZClassesM3to6) / sizeof(kZClassesM3to6[0]);
 

@@ -313,6 +313,64 @@ void split_profiles(const std::vector<std::vector<double>> &prof, int R, double 
     (void)w;
 }
 
+// The Haar range series of the 3-D form: the best N_r-term Haar expansion (Eqs. (17)-(20), selection
+// Eq. (11)) of the range kernel truncated to the slice window, in slice units.  Domain [-T_z, T_z],
+// T_z = R_z + 1/2, J_z = ceil(log2(2 T_z)); profile K_r(t step), step = dI / (Z - 1).  Ties are ordered by
+// (level, k) with phi first.  Fills the kept terms and the table K~_r(d), d = -R_z .. R_z.
+bf_status range_haar(const bf_plan_desc &d, double Tr, bf_plan &p) {
+    using bfi::fail;
+    const int Z = d.z_bins ? d.z_bins : 256;
+    const double dI = (double)d.i_hi - (double)d.i_lo, step = dI / (Z - 1);
+    const double rzd = std::floor(Tr * (Z - 1) / dI + 1e-9);
+    if (rzd > 1023) return fail(BF_ERR_UNSUPPORTED, "the Haar range series needs R_z <= 1023 slices");
+    const int rz = (int)rzd;
+    const double T = rz + 0.5;
+    const int J = (int)std::ceil(std::log2(2.0 * T));
+    const double sz = d.sigma_r / step;  // the bandwidth in slices
+    // int_a^b K_r(t step) dt: exact for the box; otherwise Gauss-Legendre on each side of the kink at 0,
+    // over the span where the profile is not below double precision's range
+    auto prof_int = [&](double a, double b) -> double {
+        if (!(b > a)) return 0.0;
+        if (d.range == BF_KERNEL_BOX) {
+            const double lo = std::max(a, -sz), hi = std::min(b, sz);
+            return hi > lo ? hi - lo : 0.0;
+        }
+        const bool gauss = d.range == BF_KERNEL_GAUSSIAN;
+        const double L = (gauss ? 40.0 : 800.0) * sz, width = (gauss ? 0.5 : 2.0) * sz;
+        auto part = [&](double lo, double hi) -> double {
+            lo = std::max(lo, -L);
+            hi = std::min(hi, L);
+            if (!(hi > lo)) return 0.0;
+            const int pieces = std::max(1, (int)std::ceil((hi - lo) / width));
+            return integrate([&](double t) { return range_value(d.range, d.sigma_r, t * step); }, lo, hi, pieces);
+        };
+        return (a < 0 && b > 0) ? part(a, 0.0) + part(0.0, b) : part(a, b);
+    };
+    std::vector<Haar1> dict = haar_dictionary(J, T);
+    std::vector<Cand> rc;
+    rc.reserve(dict.size());
+    for (size_t i = 0; i < dict.size(); ++i) {
+        const Haar1 &h = dict[i];
+        const double c = h.lev < 0 ? prof_int(h.lo, h.hi) / (2.0 * T)
+                                   : std::ldexp(1.0, h.lev) * (prof_int(h.lo, h.mid) - prof_int(h.mid, h.hi)) / (2.0 * T);
+        rc.push_back(Cand{std::fabs(c), c, {h.lev, h.k, 0, 0, 0}, (int)i, 0});
+    }
+    rank(rc);
+    const int n = std::min<int>(d.nr_terms, (int)rc.size());
+    if (n < 1) return fail(BF_ERR_INVALID_ARG, "range kernel has no non-zero Haar coefficient");
+    p.rh_terms.clear();
+    p.rh_coef.clear();
+    p.zw.assign(2 * rz + 1, 0.0);
+    for (int t = 0; t < n; ++t) {
+        const Haar1 &h = dict[rc[t].a];
+        p.rh_terms.insert(p.rh_terms.end(), {h.lev, h.k});
+        p.rh_coef.push_back(rc[t].c);
+        for (int dd = -rz; dd <= rz; ++dd) p.zw[dd + rz] += rc[t].c * haar_value(h, dd);
+    }
+    p.zw_f.assign(p.zw.begin(), p.zw.end());
+    return BF_OK;
+}
+
 bf_status build(const bf_plan_desc &d, bf_plan &p) {
     using bfi::fail;
     if (!(d.sigma_s > 0) || !(d.sigma_r > 0) || !std::isfinite(d.sigma_s) || !std::isfinite(d.sigma_r))
@@ -330,6 +388,10 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
         return fail(BF_ERR_INVALID_ARG, "unknown range policy");
     if (d.policy == BF_RANGE_PAPER_3D && d.z_bins != 0 && (d.z_bins < 2 || d.z_bins > bfi::kMaxZBins))
         return fail(BF_ERR_INVALID_ARG, "z_bins must be 0 (256) or in [2, 4096]");
+    if (d.range_series != BF_SERIES_COSINE && d.range_series != BF_SERIES_HAAR)
+        return fail(BF_ERR_INVALID_ARG, "unknown range series");
+    if (d.range_series == BF_SERIES_HAAR && d.policy != BF_RANGE_PAPER_3D)
+        return fail(BF_ERR_INVALID_ARG, "the Haar range series runs on the slice axis of BF_RANGE_PAPER_3D");
     if (d.precision < BF_PREC_FP32 || d.precision > BF_PREC_FP16)
         return fail(BF_ERR_INVALID_ARG, "unknown precision");
     if (d.precision != BF_PREC_FP32)
@@ -357,29 +419,39 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
         p.Tr = tr;
     }
 
-    // ---- range coefficients a_k on [-P, P] (Eqs. (14), (15)), first 20 N_r candidates (App. B)
-    const int ncand = 20 * d.nr_terms;
-    double L = std::min(p.Tr, p.P);
-    if (d.range == BF_KERNEL_BOX) L = std::min(L, d.sigma_r);
-    std::vector<Cand> rc(ncand);
-    for (int k = 0; k < ncand; ++k) {
-        double w = kPi * k / p.P;
-        int pieces = 4 + (int)std::ceil(2.0 * k * L / p.P);
-        double s = integrate(
-            [&](double t) { return (d.range == BF_KERNEL_BOX ? 1.0 : range_value(d.range, d.sigma_r, t)) * std::cos(w * t); },
-            0.0, L, pieces);
-        double ak = (k == 0 ? 1.0 : 2.0) * s / p.P;
-        rc[k] = Cand{std::fabs(ak), ak, {k, 0, 0, 0, 0}, k, 0};
-    }
-    rank(rc);
-    int nr = std::min<int>(d.nr_terms, (int)rc.size());
-    if (nr < 1) return fail(BF_ERR_INVALID_ARG, "range kernel has no non-zero coefficient");
-    std::vector<std::pair<int, double>> sel;
-    for (int i = 0; i < nr; ++i) sel.push_back({rc[i].a, rc[i].c});
-    std::sort(sel.begin(), sel.end());
-    for (auto &e : sel) {
-        p.k.push_back(e.first);
-        p.a.push_back(e.second);
+    const bool haar_range = d.range_series == BF_SERIES_HAAR;
+    if (haar_range) {
+        // the Haar range series: the kernel runs one constant cosine term (k = 0, a = 1) and weights the
+        // neighbours through the slice table
+        bf_status hs = range_haar(d, p.Tr, p);
+        if (hs != BF_OK) return hs;
+        p.k.push_back(0);
+        p.a.push_back(1.0);
+    } else {
+        // ---- range coefficients a_k on [-P, P] (Eqs. (14), (15)), first 20 N_r candidates (App. B)
+        const int ncand = 20 * d.nr_terms;
+        double L = std::min(p.Tr, p.P);
+        if (d.range == BF_KERNEL_BOX) L = std::min(L, d.sigma_r);
+        std::vector<Cand> rc(ncand);
+        for (int k = 0; k < ncand; ++k) {
+            double w = kPi * k / p.P;
+            int pieces = 4 + (int)std::ceil(2.0 * k * L / p.P);
+            double s = integrate(
+                [&](double t) { return (d.range == BF_KERNEL_BOX ? 1.0 : range_value(d.range, d.sigma_r, t)) * std::cos(w * t); },
+                0.0, L, pieces);
+            double ak = (k == 0 ? 1.0 : 2.0) * s / p.P;
+            rc[k] = Cand{std::fabs(ak), ak, {k, 0, 0, 0, 0}, k, 0};
+        }
+        rank(rc);
+        int nr = std::min<int>(d.nr_terms, (int)rc.size());
+        if (nr < 1) return fail(BF_ERR_INVALID_ARG, "range kernel has no non-zero coefficient");
+        std::vector<std::pair<int, double>> sel;
+        for (int i = 0; i < nr; ++i) sel.push_back({rc[i].a, rc[i].c});
+        std::sort(sel.begin(), sel.end());
+        for (auto &e : sel) {
+            p.k.push_back(e.first);
+            p.a.push_back(e.second);
+        }
     }
 
     // ---- 1-D Haar coefficients of the spatial profile (Eq. (20)); 2-D by separability (Eq. (22)), or
@@ -475,11 +547,21 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
     double sk = 0, sa = 0;
     for (double v : p.kernel) sk += std::fabs(v);
     for (double v : p.a) sa += std::fabs(v);
+    if (haar_range) {  // the range weights are the table's: scale the guard by its largest magnitude
+        sa = 0;
+        for (double v : p.zw) sa = std::max(sa, std::fabs(v));
+    }
     p.den_eps = 1e-6 * sk * sa;
     p.range_max_err = 0;
+    if (haar_range) {  // the table against the kernel at the slice offsets
+        const double step = dI / ((d.z_bins ? d.z_bins : 256) - 1);
+        const int rz = ((int)p.zw.size() - 1) / 2;
+        for (int dd = -rz; dd <= rz; ++dd)
+            p.range_max_err = std::max(p.range_max_err, std::fabs(p.zw[dd + rz] - range_value(d.range, d.sigma_r, dd * step)));
+    }
     // the 3-D form keeps the series only inside the range box [-T_r, T_r]
     const double tspan = d.policy == BF_RANGE_PAPER_3D ? std::min(dI, p.Tr) : dI;
-    for (int i = 0; i <= 4000; ++i) {
+    for (int i = 0; !haar_range && i <= 4000; ++i) {
         double t = -tspan + 2.0 * tspan * i / 4000.0, s = 0;
         for (size_t j = 0; j < p.k.size(); ++j) s += p.a[j] * std::cos(kPi * p.k[j] * t / p.P);
         p.range_max_err = std::max(p.range_max_err, std::fabs(s - range_value(d.range, d.sigma_r, t)));
@@ -508,6 +590,7 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
     kp.inv_p_lo = (float)(1.0 / p.P - (double)kp.inv_p);
     kp.i_lo = d.i_lo;
     kp.den_eps = (float)p.den_eps;
+    const int nr = (int)p.k.size();
     kp.nr = nr;
     for (int i = 0; i < nr; ++i) {
         kp.k[i] = p.k[i];
@@ -538,6 +621,8 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
         kp.zscale = (float)((Z - 1) / dI);
         const double rz = std::floor(p.Tr * (Z - 1) / dI + 1e-9);
         kp.rz = (int)std::min(rz, (double)Z);
+        kp.zmode = haar_range ? 2 : 1;
+        kp.zw = haar_range ? p.zw_f.data() : nullptr;
     }
     return BF_OK;
 }

@@ -21,7 +21,8 @@ namespace bfi {
 namespace {
 
 // (device, M, terms, reach, vlo, vhi, h, w, precision, selection kind): the kind is 1 for a gapped term
-// selection (the families on offer differ) plus 2 for the 3-D form (no ring)
+// selection (the families on offer differ) plus 2 for the 3-D form (no ring) plus 4 for its Haar range
+// series (NK = 2 only)
 using Key = std::tuple<int, int, int, int, int, int, int, int, int, int>;
 
 std::mutex g_mu;
@@ -34,7 +35,7 @@ Key make_key(const FilterParams &p, int h, int w, int precision) {
         cudaGetLastError();
         dev = -1;
     }
-    const int kind = (p.k[p.nr - 1] - p.k[0] + 1 != p.nr ? 1 : 0) + (p.zbins > 0 ? 2 : 0);
+    const int kind = (p.k[p.nr - 1] - p.k[0] + 1 != p.nr ? 1 : 0) + (p.zbins > 0 ? 2 : 0) + (p.zmode == 2 ? 4 : 0);
     return Key{dev, p.m, p.nr, p.rx, p.vlo, p.vhi, h, w, precision, kind};
 }
 

@@ -119,7 +119,22 @@ def test_paper_3d_plan_matches_oracle(sigma_r, z_bins, t_r):
     assert bf.Plan(device=-1).coeffs()["z_bins"] == 0
 
 
+@pytest.mark.parametrize("kw,Z", [(dict(sigma_r=0.1, nr_terms=8), 256), (dict(sigma_r=0.05, nr_terms=3, range=O.EXPONENTIAL), 256),
+                                  (dict(sigma_r=0.2, nr_terms=16, range=O.BOX), 128), (dict(sigma_r=0.1, nr_terms=40), 2048)])
+def test_haar_range_plan_matches_oracle(kw, Z):
+    """The Haar range series of the 3-D form: the kept terms, their coefficients and the weight table."""
+    c = bf.Plan(device=-1, policy=bf.RANGE_PAPER_3D, range_series=bf.SERIES_HAAR, z_bins=Z, **kw).coeffs()
+    info = O.zhaar_info(O.Desc(**kw), Z)
+    assert c["range_series"] == bf.SERIES_HAAR and c["z_radius"] == info.Rz
+    assert c["range_haar"] == [(int(a), int(b)) for a, b in zip(info.lev, info.k)]
+    assert np.max(np.abs(np.array(c["range_haar_coef"]) - info.c)) < 1e-13
+    assert np.max(np.abs(np.array(c["z_weights"]) - info.w)) < 1e-13
+    assert c["k"] == [0] and c["a"] == [1.0]
+
+
 @pytest.mark.parametrize("kw,status", [
+    (dict(range_series=bf.SERIES_HAAR), 1), (dict(range_series=7), 1),
+    (dict(policy=bf.RANGE_PAPER_3D, range_series=bf.SERIES_HAAR, z_bins=4096, sigma_r=0.1), 2),
     (dict(sigma_s=0.0), 1), (dict(sigma_r=-1.0), 1), (dict(ns_terms=0), 1), (dict(nr_terms=0), 1),
     (dict(i_lo=1.0, i_hi=1.0), 1), (dict(policy=bf.RANGE_PAPER_3D, z_bins=1), 1),
     (dict(policy=bf.RANGE_PAPER_3D, z_bins=4097), 1), (dict(policy=5), 1),

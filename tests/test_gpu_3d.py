@@ -155,9 +155,9 @@ def test_3d_every_candidate_family():
     cands = bf.bf_launch_candidates(plan, H, W)
     assert cands and all(c["ring"] == 0 and c["packed"] == 1 for c in cands)
     firsts = {}
-    for c in cands:
-        firsts.setdefault((c["nk"], c["depth"]), c)
-    assert len(firsts) >= 4
+    for c in cands:  # terms per CTA x depth x CTAs of at most 256 threads (register-bounded kernels) or more
+        firsts.setdefault((c["nk"], c["depth"], c["threads"] > 256), c)
+    assert len(firsts) >= 8
     try:
         for fam, c in firsts.items():
             bf.bf_set_launch(plan, H, W, c)
@@ -203,3 +203,112 @@ def test_3d_rejected_where_unsupported():
     with pytest.raises(bf.BFError) as ei:
         bf.Cache(plan, src, kmax=8)
     assert ei.value.status == 2  # BF_ERR_UNSUPPORTED
+
+
+# ---- the Haar range series (BF_SERIES_HAAR): a neighbour's weight is K~_s(x - y) K~_r(n(x) - n(y)), K~_r the
+# best N-term Haar expansion of the truncated range kernel on the slice axis
+
+def plan3dh(Z, **kw):
+    return bf.Plan(device=0, policy=bf.RANGE_PAPER_3D, range_series=bf.SERIES_HAAR, z_bins=Z, **kw)
+
+
+def check_haar(got, img, kw, Z):
+    """As check(), with the range weights of the Haar table: mass = sum |K~_s| |K~_r| over the neighbours."""
+    d = O.Desc(**kw)
+    ref, den = O.approx3dh_direct(img.astype(np.float64), d, Z, threads=THREADS)
+    p = O.plan_info(O.Desc(policy=O.PAPER_3D, **kw))
+    zi = O.zhaar_info(d, Z)
+    bins, _ = O.z_bins(img.astype(np.float64), zi.Rz / (Z - 1) + 1e-12, Z)
+    H, W = img.shape
+    R, Rz = p.R, zi.Rz
+    pb = np.full((H + 2 * R, W + 2 * R), -10 ** 6, dtype=np.int64)
+    pb[R:R + H, R:R + W] = bins
+    mass = np.zeros((H, W))
+    for dy in range(-R, R + 1):
+        for dx in range(-R, R + 1):
+            k = abs(p.Ks[-dy + R, -dx + R])
+            if k == 0.0:
+                continue
+            dd = bins - pb[R + dy:R + dy + H, R + dx:R + dx + W]
+            inw = np.abs(dd) <= Rz
+            mass += k * np.where(inw, np.abs(zi.w[np.clip(dd + Rz, 0, 2 * Rz)]), 0.0)
+    ratio = np.abs(den) / np.maximum(mass, 1e-300)
+    err = np.abs(got - ref)
+    assert np.all(np.isfinite(got))
+    good = ratio >= 0.01
+    assert good.mean() > 0.98, "too many ill-conditioned pixels: %g" % (1 - good.mean())
+    bound = TOL + 2e-7 * (1 + np.abs(ref)) / np.maximum(ratio, 1e-12)
+    worst = np.max(err[~good] / bound[~good]) if (~good).any() else 0.0
+    return err[good].max(), worst
+
+
+HCASES = [
+    ("haar_gauss_s2", synth.shapes(150, 203, 21, scale=0.2), dict(sigma_s=2.0, sigma_r=0.1, nr_terms=8), 256),
+    ("haar_exp_range", synth.shapes(140, 190, 22, scale=0.2),
+     dict(range=bf.KERNEL_EXPONENTIAL, sigma_r=0.05, nr_terms=6, sigma_s=2.0), 128),
+    ("haar_box_range", synth.blocks(120, 260, 23), dict(range=bf.KERNEL_BOX, sigma_r=0.2, nr_terms=16, sigma_s=3.0), 256),
+    ("haar_m3", synth.shapes(160, 170, 24, scale=0.2), dict(sigma_s=2.0, ns_terms=13, sigma_r=0.08, nr_terms=8), 256),
+    ("haar_sigma8", synth.shapes(200, 230, 25, scale=0.2), dict(sigma_s=8.0, sigma_r=0.1, nr_terms=16), 256),
+    ("haar_z2048", synth.shapes(90, 140, 26, scale=0.1), dict(sigma_s=2.0, sigma_r=0.1, nr_terms=24), 2048),
+    ("haar_nr7_uniform", synth.uniform(70, 110, 27), dict(sigma_s=1.5, sigma_r=0.1, nr_terms=7), 256),
+]
+
+
+@pytest.mark.parametrize("name,img,kw,Z", HCASES, ids=[c[0] for c in HCASES])
+def test_3d_haar_matches_oracle(name, img, kw, Z):
+    got = gpu(plan3dh(Z, **kw), img)
+    e_good, worst = check_haar(got, img, kw, Z)
+    assert e_good < TOL, "%s: max err %.3g" % (name, e_good)
+    assert worst < 1.0, "%s: error / bound %.3g on ill-conditioned pixels" % (name, worst)
+
+
+@pytest.mark.parametrize("H,W", [(1, 1), (3, 2), (1, 50), (7, 300)])
+def test_3d_haar_tiny_images(H, W):
+    img = synth.uniform(H, W, seed=H * 17 + W)
+    kw = dict(sigma_s=2.0, sigma_r=0.1, nr_terms=8)
+    got = gpu(plan3dh(256, **kw), img)
+    ref, _ = O.approx3dh_direct(img.astype(np.float64), O.Desc(**kw), 256)
+    assert np.max(np.abs(got - ref)) < TOL
+
+
+def test_3d_haar_box_kernels_on_8bit_data_are_exact_bf():
+    img = on_grid(97, 140, 31)
+    kw = dict(spatial=bf.KERNEL_BOX, sigma_s=1.0, radius=3, ns_terms=1, range=bf.KERNEL_BOX, sigma_r=4.5 / 255.0,
+              nr_terms=3)
+    got = gpu(plan3dh(256, **kw), img)
+    ref = O.exact_bf(img.astype(np.float64), O.Desc(**kw))
+    assert np.max(np.abs(got - ref)) < 2e-6
+
+
+def test_3d_haar_every_candidate_family():
+    img = synth.shapes(130, 240, 32, scale=0.2)
+    kw = dict(sigma_s=2.0, sigma_r=0.1, nr_terms=8)
+    plan = plan3dh(256, **kw)
+    H, W = img.shape
+    default = bf.bf_launch_info(plan, H, W)
+    cands = bf.bf_launch_candidates(plan, H, W)
+    assert cands and all(c["ring"] == 0 and c["packed"] == 1 and c["nk"] == 2 for c in cands)
+    firsts = {}
+    for c in cands:  # both depths, with CTAs of at most 256 threads (the register-bounded kernel) and more
+        firsts.setdefault((c["depth"], c["threads"] > 256), c)
+    assert len(firsts) == 4
+    try:
+        for fam, c in firsts.items():
+            bf.bf_set_launch(plan, H, W, c)
+            got = gpu(plan, img)
+            e_good, worst = check_haar(got, img, kw, 256)
+            assert e_good < TOL and worst < 1.0, (fam, e_good, worst)
+    finally:
+        bf.bf_set_launch(plan, H, W, default)
+
+
+def test_3d_haar_full_size_sampled():
+    img = synth.shapes(1080, 1920, seed=0)
+    kw = dict(sigma_s=8.0, sigma_r=0.1, nr_terms=8)
+    got = gpu(plan3dh(256, **kw), img)
+    assert np.all(np.isfinite(got))
+    rng = np.random.default_rng(6)
+    pts = np.stack([rng.integers(0, 1080, 3000), rng.integers(0, 1920, 3000)], axis=1)
+    pts[:4] = [[0, 0], [1079, 1919], [0, 1919], [1079, 0]]
+    ref, _ = O.approx3dh_direct(img.astype(np.float64), O.Desc(**kw), 256, pts=pts, threads=THREADS)
+    assert np.max(np.abs(got[pts[:, 0], pts[:, 1]] - ref)) < TOL
