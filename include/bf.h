@@ -423,6 +423,17 @@ int bf_version(void);
  * launches report BF_ERR_CUDA without launching.  Process-wide. */
 void bf_debug_fail_launches(int n);
 
+/* Debug aid for the input range (off by default; the environment variable
+ * BF_DEBUG_RANGE=1 switches it on at the first filtering call).  While on,
+ * bf_filter first counts the input pixels outside the plan's [i_lo, i_hi]
+ * (NaN included) on `stream`, waits for the count, and returns BF_ERR_RANGE
+ * without filtering if there are any: the collapsed range policies assume the
+ * data range (a difference beyond it can meet a periodic copy of the kernel).
+ * The check synchronises the stream and uses one per-device counter, so
+ * concurrent checked calls race; it is not for production.  Process-wide;
+ * on != 0 switches it on, 0 off. */
+void bf_debug_range_checks(int on);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,7 +68,7 @@ EXPORTS = ["bf_plan_desc_default", "bf_plan_create", "bf_plan_destroy", "bf_coef
            "bf_filter_batch",
            "bf_exact", "bf_exact_lut", "bf_precompute", "bf_filter_cached", "bf_cache_bytes", "bf_cache_destroy",
            "bf_serve_create", "bf_serve_submit", "bf_serve_poll", "bf_serve_cancel", "bf_serve_destroy",
-           "bf_status_string", "bf_last_error", "bf_version", "bf_debug_fail_launches"]
+           "bf_status_string", "bf_last_error", "bf_version", "bf_debug_fail_launches", "bf_debug_range_checks"]
 
 _lib = None
 _lock = threading.Lock()
@@ -121,6 +121,8 @@ def lib():
         L.bf_version.restype = i
         L.bf_debug_fail_launches.argtypes = [i]
         L.bf_debug_fail_launches.restype = None
+        L.bf_debug_range_checks.argtypes = [i]
+        L.bf_debug_range_checks.restype = None
         _lib = L
     return _lib
 
@@ -337,6 +339,10 @@ def bf_version() -> int:
 
 def bf_debug_fail_launches(n: int) -> None:
     lib().bf_debug_fail_launches(int(n))
+
+
+def bf_debug_range_checks(on: bool) -> None:
+    lib().bf_debug_range_checks(1 if on else 0)
 
 
 class Server:

@@ -32,6 +32,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -307,6 +308,52 @@ bf_status cuda_fail(cudaError_t e, const char *what) {
 }
 
 }  // namespace
+
+// The input range check of bf_debug_range_checks: pixels outside [lo, hi] (NaN included), counted into one
+// per-device counter.
+__device__ unsigned long long g_out_of_range;
+
+__global__ void bf_range_count_kernel(const float *__restrict__ in, size_t in_pitch, int H, int W, float lo, float hi) {
+    unsigned long long n = 0;
+    const size_t total = (size_t)H * W;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const float v = __ldg(in + (i / W) * in_pitch + i % W);
+        n += (v >= lo && v <= hi) ? 0 : 1;
+    }
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_down_sync(0xffffffffu, n, o);
+    if ((threadIdx.x & 31) == 0 && n) atomicAdd(&g_out_of_range, n);
+}
+
+std::atomic<int> g_range_checks{-1};  // -1: not yet read from the environment
+
+bool debug_range_checks() {
+    int v = g_range_checks.load();
+    if (v < 0) {
+        const char *e = std::getenv("BF_DEBUG_RANGE");
+        int want = (e && e[0] == '1') ? 1 : 0;
+        g_range_checks.compare_exchange_strong(v, want);
+        v = g_range_checks.load();
+    }
+    return v > 0;
+}
+
+void debug_set_range_checks(bool on) { g_range_checks.store(on ? 1 : 0); }
+
+bf_status count_out_of_range(const float *d_in, size_t in_pitch, int h, int w, float lo, float hi, void *stream,
+                             unsigned long long *count) {
+    cudaStream_t s = (cudaStream_t)stream;
+    void *addr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&addr, g_out_of_range);
+    if (e == cudaSuccess) e = cudaMemsetAsync(addr, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "range check");
+    const int blocks = (int)std::min<size_t>(((size_t)h * w + 255) / 256, (size_t)device_sms() * 8);
+    bf_range_count_kernel<<<std::max(blocks, 1), 256, 0, s>>>(d_in, in_pitch, h, w, lo, hi);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(count, addr, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "range check");
+    return BF_OK;
+}
 
 bool debug_consume_launch_failure() {
     int n = g_fail_launches.load();

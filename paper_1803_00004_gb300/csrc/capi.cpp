@@ -25,6 +25,10 @@ bf_status fail(bf_status st, const std::string &msg) {
 }
 
 void debug_set_fail_launches(int n);
+void debug_set_range_checks(bool on);
+bool debug_range_checks();
+bf_status count_out_of_range(const float *d_in, size_t in_pitch_elems, int h, int w, float lo, float hi, void *stream,
+                             unsigned long long *count);
 
 // Runs `fn` with `device` current, restoring the caller's device afterwards.
 template <class F>
@@ -168,6 +172,14 @@ bf_status bf_filter(const bf_plan *plan, const float *d_in, size_t in_pitch, flo
     if (st != BF_OK || height == 0 || width == 0) return st;
     if (plan->desc.device < 0) return fail(BF_ERR_NO_DEVICE, "host-only plan (device = -1)");
     return with_device(plan->desc.device, [&]() -> bf_status {
+        if (debug_range_checks()) {
+            unsigned long long n = 0;
+            bf_status rs = count_out_of_range(d_in, in_pitch / sizeof(float), height, width, plan->desc.i_lo,
+                                              plan->desc.i_hi, stream, &n);
+            if (rs != BF_OK) return rs;
+            if (n > 0)
+                return fail(BF_ERR_RANGE, std::to_string(n) + " input pixels outside [i_lo, i_hi] (range check on)");
+        }
         TileConfig tc = choose_tile(plan->kp, height, width, plan->desc.precision);
         float *scratch = nullptr;
         cudaStream_t s = (cudaStream_t)stream;
@@ -242,5 +254,7 @@ const char *bf_last_error(void) { return g_last_error.c_str(); }
 int bf_version(void) { return (0 << 16) | 1; }
 
 void bf_debug_fail_launches(int n) { bfi::debug_set_fail_launches(n); }
+
+void bf_debug_range_checks(int on) { bfi::debug_set_range_checks(on != 0); }
 
 }  // extern "C"

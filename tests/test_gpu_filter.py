@@ -173,6 +173,36 @@ def test_in_place_rejected_and_injected_failure():
     assert np.max(np.abs(dst.cpu().numpy() - ref)) < TOL
 
 
+def test_debug_range_check():
+    """bf_debug_range_checks: pixels outside [i_lo, i_hi] (NaN included) make bf_filter return BF_ERR_RANGE
+    with their count and filter nothing; in-range images filter as usual; off, nothing is checked."""
+    img = synth.blocks(70, 90, 3)
+    plan = bf.Plan(device=0)
+    src = torch.from_numpy(img).cuda()
+    bad = src.clone()
+    bad[5, 7] = 1.5
+    bad[60, 80] = -0.25
+    bad[33, 0] = float("nan")
+    dst = torch.full_like(src, 7.0)
+    bf.bf_debug_range_checks(True)
+    try:
+        with pytest.raises(bf.BFError) as ei:
+            bf.bf_filter(plan, bad, dst)
+        assert ei.value.status == 8 and "3 input pixels" in bf.lib().bf_last_error().decode()
+        torch.cuda.synchronize()
+        assert torch.all(dst == 7.0)  # nothing filtered
+        bf.bf_filter(plan, src, dst)
+        torch.cuda.synchronize()
+        ref, _ = O.approx_fast(img.astype(np.float64), odesc())
+        assert np.max(np.abs(dst.cpu().numpy() - ref)) < TOL
+        wide = bf.Plan(device=0, i_lo=-1.0, i_hi=2.0)
+        bf.bf_filter(wide, torch.nan_to_num(bad, nan=0.5), dst)  # inside the wider data range
+    finally:
+        bf.bf_debug_range_checks(False)
+    bf.bf_filter(plan, bad, dst)  # unchecked
+    torch.cuda.synchronize()
+
+
 @pytest.mark.parametrize("kw", [dict(sigma_s=2.0, sigma_r=0.1), dict(sigma_s=3.0, sigma_r=0.2, range=bf.KERNEL_EXPONENTIAL),
                                 dict(sigma_s=1.0, sigma_r=0.15, spatial=bf.KERNEL_BOX, radius=4),
                                 dict(sigma_s=2.5, sigma_r=0.1, spatial=bf.KERNEL_EXPONENTIAL)])
