@@ -169,7 +169,9 @@ def run_ours(args):
     combos = [(a, b) for a in SIGMA_S for b in SIGMA_R]
     if args.only:
         combos = [tuple(float(v) for v in args.only.split(","))]
+    t_plan = time.perf_counter()
     plans = [bf.Plan(sigma_s=ss, sigma_r=sr, nr_terms=NR, ns_terms=NS, device=local) for ss, sr in combos]
+    plan_build_ms = (time.perf_counter() - t_plan) * 1e3 / len(plans)
     coeffs = [p.coeffs() for p in plans]
     outs = [torch.empty_like(src) for _ in plans]
     stream = torch.cuda.current_stream(dev)
@@ -255,11 +257,12 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = run_e2e(args, bf, plans, img, dev, stream)
 
-    batched = serving = nr_sweep = large = bft = pre = p3d = None
+    batched = serving = nr_sweep = ns_sweep = large = bft = pre = p3d = None
     if not args.no_extras and world == 1:
         batched = run_batched(bf, dev)
         serving = run_serving(bf, dev)
         nr_sweep = run_nr_sweep(bf, dev, src, flush)
+        ns_sweep = run_ns_sweep(bf, dev, flush)
         large = run_large(bf, dev, flush)
         bft = run_bft_crossover(bf, dev, src, flush)
         pre = run_precompute(bf, dev, src, flush)
@@ -273,6 +276,7 @@ def run_ours(args):
                    "height": H, "width": W, "images_per_step": len(plans),
                    "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "single"},
         "psnr_db_vs_exact": [round(x, 2) for x in psnr], "min_psnr_db": round(min(psnr), 2) if psnr else None,
+        "plan_build_ms": round(plan_build_ms, 2),
         "per_combo_ms": [round(x, 4) for x in lm.mean(0)],
         "tiles": [[t["tw"], t["th"], t["threads"], t["nk"], t["groups"], t["ring"], t["depth"], t["ncols"], t["packed"]] for t in tiles],
         "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
@@ -281,7 +285,7 @@ def run_ours(args):
         "hbm": {"achieved_gbs": round(hbm_gbs, 1), "peak_gbs": hbm_peak, "frac": round(hbm_gbs / hbm_peak, 5),
                 "bytes_per_px": 8},
         "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
-        "batched": batched, "serving": serving, "nr_sweep": nr_sweep, "large_images": large,
+        "batched": batched, "serving": serving, "nr_sweep": nr_sweep, "ns_sweep": ns_sweep, "large_images": large,
         "bft_crossover": bft, "precompute": pre, "paper_3d": p3d,
         "e2e": e2e,
     }
@@ -475,6 +479,30 @@ def run_bft_crossover(bf, dev, src, flush, reps=5):
     return {"sigma_r": 0.1, "levels": 256, "by_radius": rows}
 
 
+def run_ns_sweep(bf, dev, flush, reps=5):
+    """Config 1 (256 x 256 blocks, sigma_s = 4, sigma_r = 0.1, N_r = 8): PSNR against the exact filter and
+    device ms as the Haar terms N_s grow, and the smallest N_s reaching 40 dB.  Selections that need more
+    box windows per axis than the kernel classes hold are listed as unsupported."""
+    import torch
+    from paper_1803_00004_gb300 import synth
+    src = torch.from_numpy(synth.blocks(256, 256, 0)).to(dev)
+    out, ex = torch.empty_like(src), torch.empty_like(src)
+    bf.bf_exact(src, ex, sigma_s=4.0, sigma_r=0.1)
+    rows, first = [], None
+    for ns in (1, 2, 3, 4, 5, 7, 9, 13, 17, 25, 41, 61):
+        try:
+            p = bf.Plan(sigma_s=4.0, sigma_r=0.1, nr_terms=NR, ns_terms=ns, device=dev.index)
+        except bf.BFError:
+            rows.append({"ns": ns, "unsupported": True})
+            continue
+        t = timed_launches(bf, p, src, out, flush, reps)
+        psnr = 10 * np.log10(1.0 / torch.mean((out.double() - ex.double()) ** 2).item())
+        if first is None and psnr >= 40.0:
+            first = ns
+        rows.append({"ns": ns, "windows": len(p.coeffs()["vwin"]), "psnr_db": round(psnr, 2), "ms": round(t, 4)})
+    return {"image": "256x256 blocks", "sigma_s": 4.0, "sigma_r": 0.1, "nr": NR, "min_ns_40db": first, "by_ns": rows}
+
+
 def run_nr_sweep(bf, dev, src, flush, reps=5):
     """Mpixel/s on the 1920x1080 image for N_r in 4..32 at each sigma_s (sigma_r = 0.1), autotuned:
     the per-pixel cost against sigma_s at fixed N_r."""
@@ -562,10 +590,11 @@ def run_batched(bf, dev, n=512, lo=64, hi=2048, reps=3):
             "sequential_mpix_s": round(px / (t_seq * 1e-3) / 1e6, 1), "sequential_ms": round(t_seq, 3)}
 
 
-def run_serving(bf, dev, n=160, lo=128, hi=2048, load=0.8):
-    """Poisson stream at `load` x the measured saturation rate through the continuous-batching
-    server (pinned host buffers): p50/p99 latency and Mpixel/s; plus the plain per-image path
-    (H2D, bf_filter, D2H, one request at a time) on the same requests."""
+def run_serving(bf, dev, n=96, lo=128, hi=4096, loads=(0.25, 0.5, 0.8, 1.0, 1.2)):
+    """Config 5: Poisson streams at each `load` x the measured saturation rate through the
+    continuous-batching server (pinned host buffers; sides log-uniform 128..4096, mixed kernels as
+    in config 4): p50/p99 latency and Mpixel/s per load; plus the plain per-image path (H2D,
+    bf_filter, D2H, one request at a time) on the same requests."""
     import torch
     work = mixed_requests(n, lo, hi, seed=4321)
     hin = [torch.from_numpy(img).pin_memory() for img, _ in work]
@@ -591,10 +620,15 @@ def run_serving(bf, dev, n=160, lo=128, hi=2048, load=0.8):
 
     burst(None)                                   # warm-up (plans, memory pool)
     t_sat, _ = burst(None)                        # saturation: all requests at once
-    rate = load * n / t_sat                       # requests/s
     rng = np.random.default_rng(7)
-    delays = list(rng.exponential(1.0 / rate, n))[::-1]
-    t_run, lat = burst(delays)
+    by_load = []
+    for load in loads:
+        rate = load * n / t_sat                   # requests/s
+        delays = list(rng.exponential(1.0 / rate, n))[::-1]
+        t_run, lat = burst(delays)
+        by_load.append({"load": load, "rate_req_s": round(rate, 1),
+                        "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                        "p99_ms": round(float(np.percentile(lat, 99)), 3), "mpix_s": round(px / t_run / 1e6, 1)})
     srv.close()
     # plain per-image path
     plans = [bf.Plan(d) for d in descs]
@@ -608,10 +642,11 @@ def run_serving(bf, dev, n=160, lo=128, hi=2048, load=0.8):
         ho.copy_(do, non_blocking=True)
         torch.cuda.synchronize()
     t_plain = time.perf_counter() - t0
-    return {"requests": n, "sides": [lo, hi], "load": load, "rate_req_s": round(rate, 1),
-            "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
-            "mpix_s": round(px / t_run / 1e6, 1), "saturation_mpix_s": round(px / t_sat / 1e6, 1),
-            "plain_per_image_mpix_s": round(px / t_plain / 1e6, 1)}
+    at = next(r for r in by_load if r["load"] == 0.8)
+    return {"requests": n, "sides": [lo, hi], "megapixels": round(px / 1e6, 1), "load": 0.8,
+            "p50_ms": at["p50_ms"], "p99_ms": at["p99_ms"], "mpix_s": at["mpix_s"],
+            "saturation_mpix_s": round(px / t_sat / 1e6, 1), "plain_per_image_mpix_s": round(px / t_plain / 1e6, 1),
+            "by_load": by_load}
 
 
 def cpu_baseline(img, rows: int = 1080, combos=None):
@@ -625,10 +660,25 @@ def cpu_baseline(img, rows: int = 1080, combos=None):
     for ss, sr in combos:
         O.approx_fast(band, O.Desc(sigma_s=ss, sigma_r=sr, nr_terms=NR, ns_terms=NS), threads=threads)
     dt = time.perf_counter() - t0
-    return {"value": round(len(combos) * band.shape[0] * band.shape[1] / dt / 1e6, 4), "unit": "Mpixel/s",
-            "cores": threads, "kind": "oracle",
-            "sample": "%d combos on a %dx%d band of the image, FP64 approx_fast, %.1f s" % (len(combos), band.shape[0],
-                                                                                          band.shape[1], dt)}
+    out = {"value": round(len(combos) * band.shape[0] * band.shape[1] / dt / 1e6, 4), "unit": "Mpixel/s",
+           "cores": threads, "kind": "oracle",
+           "sample": "%d combos on a %dx%d band of the image, FP64 approx_fast, %.1f s" % (len(combos), band.shape[0],
+                                                                                         band.shape[1], dt)}
+    if combos is None or len(combos) > 1:
+        # one thread (beside the paper's single-core timings): O3 at sigma_s = 8, sigma_r = 0.1 on 64 rows
+        small = band[:64]
+        t0 = time.perf_counter()
+        O.approx_fast(small, O.Desc(sigma_s=8.0, sigma_r=0.1, nr_terms=NR, ns_terms=NS), threads=1)
+        out["single_thread_mpix_s"] = round(small.size / (time.perf_counter() - t0) / 1e6, 4)
+        # the exact filter O1 (brute force, (2R + 1)^2 taps per pixel), all cores, 16 rows
+        exact = {}
+        for ss in SIGMA_S:
+            t0 = time.perf_counter()
+            mid = band.shape[0] // 2
+            O.exact_bf(band, O.Desc(sigma_s=ss, sigma_r=0.1), rows=np.arange(mid - 8, mid + 8), threads=threads)
+            exact[str(int(ss))] = round(16 * band.shape[1] / (time.perf_counter() - t0) / 1e6, 4)
+        out["exact_bf_mpix_s_by_sigma_s"] = exact
+    return out
 
 
 def run_reference(args):
