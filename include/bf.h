@@ -13,7 +13,9 @@
  * the range term into per-term basis images cos(w_k I), sin(w_k I) and their
  * products with I; every basis image is box-filtered and the results are
  * weighted by cos/sin(w_k I(x)) and summed into numerator and denominator
- * (Eq. (36)) before the final divide.
+ * (Eq. (36)) before the final divide.  The paper's own 3-D form (period
+ * P = T_r, the range box applied over intensity slices by dimension
+ * promotion, Eqs. (2), (28)-(29), (35)-(36)) is the BF_RANGE_PAPER_3D policy.
  *
  * Conventions for every entry point:
  *   - Status codes only; nothing throws or aborts across this boundary.  A
@@ -22,7 +24,8 @@
  *   - Images are single-channel float32, row-major, with a row pitch in
  *     bytes (a multiple of 4, >= width * 4).  Input values are expected in
  *     [i_lo, i_hi] of the plan (default [0, 1]); values outside are filtered
- *     but the accuracy statements of the plan no longer hold.
+ *     but the accuracy statements of the plan no longer hold
+ *     (bf_debug_range_checks makes bf_filter reject them instead).
  *   - Device pointers are CUDA device memory on the plan's device; the
  *     caller owns them.  "stream" is a cudaStream_t (NULL = legacy default
  *     stream).  Filtering calls are asynchronous with respect to the host.
