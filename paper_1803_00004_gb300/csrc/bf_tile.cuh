@@ -111,7 +111,7 @@ __device__ __forceinline__ void rot2(float2 &C, float2 &S, float2 cs, float2 ss,
 // kModeFinal divides and stores Î; kModePartial stores this group's numerator
 // and denominator planes (part); kModeCache / kModeCacheF16 / kModeCacheBF16
 // store the window sums of every frequency of the group (part = the cache
-// planes [k][4][H][W], of fp32 / fp16 / bf16).
+// [k][H][W][4], of fp32 / fp16 / bf16).
 //
 // The NK terms are processed as NK / 2 pairs of consecutive terms with the packed pair instructions:
 // pair p holds terms (2p, 2p + 1) of the group in the two lanes of every float2.
@@ -486,24 +486,28 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
                     for (int q = 1; q < M; ++q) F[t] = add2(F[t], zq[q][zo + (q * 4 + t) * NP + i]);
                 }
                 if (mode >= kModeCache) {
-                    // the window sums of frequencies k0 + 2i, k0 + 2i + 1: planes [k][t] of the cache, stored as
-                    // fp32, or rounded once to fp16 / bf16
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        const size_t ia = ((size_t)(k0 + 2 * i) * 4 + t) * plane + px;
-                        const size_t ib = ((size_t)(k0 + 2 * i + 1) * 4 + t) * plane + px;
-                        if (mode == kModeCache) {
-                            part[ia] = F[t].x;
-                            part[ib] = F[t].y;
-                        } else if (mode == kModeCacheF16) {
-                            __half *h = reinterpret_cast<__half *>(part);
-                            h[ia] = __float2half_rn(F[t].x);
-                            h[ib] = __float2half_rn(F[t].y);
-                        } else {
-                            __nv_bfloat16 *h = reinterpret_cast<__nv_bfloat16 *>(part);
-                            h[ia] = __float2bfloat16_rn(F[t].x);
-                            h[ib] = __float2bfloat16_rn(F[t].y);
-                        }
+                    // the window sums of frequencies k0 + 2i, k0 + 2i + 1: the cache is [k][pixel][t], the four sums
+                    // of a pixel and frequency side by side (one 16-byte fp32 or 8-byte 16-bit load when weighting),
+                    // stored as fp32, or rounded once to fp16 / bf16
+                    const size_t ia = ((size_t)(k0 + 2 * i) * plane + px) * 4;
+                    const size_t ib = ((size_t)(k0 + 2 * i + 1) * plane + px) * 4;
+                    if (mode == kModeCache) {
+                        *reinterpret_cast<float4 *>(part + ia) = make_float4(F[0].x, F[1].x, F[2].x, F[3].x);
+                        *reinterpret_cast<float4 *>(part + ib) = make_float4(F[0].y, F[1].y, F[2].y, F[3].y);
+                    } else if (mode == kModeCacheF16) {
+                        __half2 *h = reinterpret_cast<__half2 *>(reinterpret_cast<__half *>(part) + ia);
+                        h[0] = __floats2half2_rn(F[0].x, F[1].x);
+                        h[1] = __floats2half2_rn(F[2].x, F[3].x);
+                        h = reinterpret_cast<__half2 *>(reinterpret_cast<__half *>(part) + ib);
+                        h[0] = __floats2half2_rn(F[0].y, F[1].y);
+                        h[1] = __floats2half2_rn(F[2].y, F[3].y);
+                    } else {
+                        __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<__nv_bfloat16 *>(part) + ia);
+                        h[0] = __floats2bfloat162_rn(F[0].x, F[1].x);
+                        h[1] = __floats2bfloat162_rn(F[2].x, F[3].x);
+                        h = reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<__nv_bfloat16 *>(part) + ib);
+                        h[0] = __floats2bfloat162_rn(F[0].y, F[1].y);
+                        h[1] = __floats2bfloat162_rn(F[2].y, F[3].y);
                     }
                     continue;
                 }

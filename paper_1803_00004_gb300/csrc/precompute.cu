@@ -23,7 +23,7 @@ struct bf_cache {
     int kslots = 0;           // frequencies 0 .. kslots - 1 are stored
     int height = 0, width = 0, device = 0;
     int precision = 0;        // bf_precision of the stored sums
-    float *planes = nullptr;  // [kslots][4][height][width]: sums of cos I, sin I, cos, sin (fp32, fp16 or bf16)
+    float *planes = nullptr;  // [kslots][height][width][4]: sums of cos I, sin I, cos, sin (fp32, fp16 or bf16)
     size_t bytes = 0;
 };
 
@@ -33,9 +33,24 @@ namespace {
 // Weighting of the cached sums (Eq. (36)): for each selected term k, (cos, sin)(pi k t) at the centre pixel
 // (t = (I(x) - i_lo) / P carried as two floats, sincospi corrected to first order in the low part), then
 // num / den.  Guard as the fused kernel: den <= den_eps -> I(x).
-__device__ __forceinline__ float load_sum(const float *p) { return __ldg(p); }
-__device__ __forceinline__ float load_sum(const __half *p) { return __half2float(*p); }
-__device__ __forceinline__ float load_sum(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+// The four sums of one pixel and frequency, side by side: one 16-byte (fp32) or 8-byte (16-bit) load of the
+// raw bits, widened to fp32 when used.
+template <typename T> struct Raw { using type = uint2; };
+template <> struct Raw<float> { using type = float4; };
+__device__ __forceinline__ float4 load_raw(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+__device__ __forceinline__ uint2 load_raw(const __half *p) { return __ldg(reinterpret_cast<const uint2 *>(p)); }
+__device__ __forceinline__ uint2 load_raw(const __nv_bfloat16 *p) { return __ldg(reinterpret_cast<const uint2 *>(p)); }
+__device__ __forceinline__ float4 widen(float4 v, const float *) { return v; }
+__device__ __forceinline__ float4 widen(uint2 u, const __half *) {
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float4 widen(uint2 u, const __nv_bfloat16 *) {
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
 
 template <typename T>
 __global__ void bf_cached_kernel(const float *__restrict__ in, size_t in_pitch, float *__restrict__ out,
@@ -50,7 +65,11 @@ __global__ void bf_cached_kernel(const float *__restrict__ in, size_t in_pitch, 
     const float tl = fmaf(v, p.inv_p, -th) + v * p.inv_p_lo;
     const size_t plane = (size_t)H * W, px = (size_t)y * W + x;
     float num = 0.f, den = 0.f;
+    // each term's sums are loaded one term ahead of its arithmetic
+    typename Raw<T>::type fn = load_raw(planes + ((size_t)p.k[0] * plane + px) * 4);
     for (int j = 0; j < p.nr; ++j) {
+        const typename Raw<T>::type f = fn;
+        if (j + 1 < p.nr) fn = load_raw(planes + ((size_t)p.k[j + 1] * plane + px) * 4);
         const float kf = (float)p.k[j];
         const float kh = kf * th;
         const float kl = fmaf(kf, th, -kh) + kf * tl;
@@ -58,10 +77,10 @@ __global__ void bf_cached_kernel(const float *__restrict__ in, size_t in_pitch, 
         sincospif(kh, &s, &c);
         const float d = kPiF * kl;
         const float ck = fmaf(-d, s, c), sk = fmaf(d, c, s);
-        const T *f = planes + (size_t)p.k[j] * 4 * plane + px;
         const float a = p.a[j];
-        num = fmaf(a, fmaf(ck, load_sum(f), sk * load_sum(f + plane)), num);
-        den = fmaf(a, fmaf(ck, load_sum(f + 2 * plane), sk * load_sum(f + 3 * plane)), den);
+        const float4 w = widen(f, planes);
+        num = fmaf(a, fmaf(ck, w.x, sk * w.y), num);
+        den = fmaf(a, fmaf(ck, w.z, sk * w.w), den);
     }
     out[(size_t)y * out_pitch + x] = den > p.den_eps ? num / den + p.i_lo : ix;
 }
