@@ -312,3 +312,24 @@ def test_3d_haar_full_size_sampled():
     pts[:4] = [[0, 0], [1079, 1919], [0, 1919], [1079, 0]]
     ref, _ = O.approx3dh_direct(img.astype(np.float64), O.Desc(**kw), 256, pts=pts, threads=THREADS)
     assert np.max(np.abs(got[pts[:, 0], pts[:, 1]] - ref)) < TOL
+
+
+@pytest.mark.parametrize("series", [0, 1])
+def test_3d_pitched_buffers_leave_padding(series):
+    """Pitched input and output: the slice list and slice kernels read and write inside the width only
+    (the output padding keeps its NaN canary), and the result matches the oracle."""
+    img = synth.shapes(70, 150, 51, scale=0.15)
+    kw = dict(sigma_s=2.0, sigma_r=0.1, nr_terms=6 if series == 0 else 16)
+    plan = bf.Plan(device=0, policy=bf.RANGE_PAPER_3D, z_bins=256, range_series=series, **kw)
+    big = torch.full((70, 192), 0.5, dtype=torch.float32, device="cuda")
+    big[:, :150] = torch.from_numpy(img).cuda()
+    out = torch.full((70, 200), float("nan"), dtype=torch.float32, device="cuda")
+    bf.bf_filter(plan, big[:, :150], out[:, :150])
+    torch.cuda.synchronize()
+    assert torch.isnan(out[:, 150:]).all()
+    got = out[:, :150].cpu().numpy().astype(np.float64)
+    if series == 0:
+        ref, _ = O.approx3d_direct(img.astype(np.float64), odesc(kw), 256)
+    else:
+        ref, _ = O.approx3dh_direct(img.astype(np.float64), O.Desc(**kw), 256)
+    assert np.max(np.abs(got - ref)) < TOL
