@@ -47,7 +47,7 @@ extern "C" {
 typedef enum {
     BF_OK = 0,
     BF_ERR_INVALID_ARG = 1,     /* bad pointer, size, pitch or parameter */
-    BF_ERR_UNSUPPORTED = 2,     /* valid request this build does not implement */
+    BF_ERR_UNSUPPORTED = 2,     /* valid request the library does not implement */
     BF_ERR_OOM = 3,             /* host or device allocation failed */
     BF_ERR_CUDA = 4,            /* a CUDA runtime call failed (detail in bf_last_error) */
     BF_ERR_ADMISSION = 5,       /* server: request can never fit the memory budget */

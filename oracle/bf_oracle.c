@@ -36,7 +36,7 @@
  *     N-term Haar expansion (Eqs. (17)-(20), (11)) on the slice axis, each term
  *     a pair of boxes along z evaluated through a running sum over slices.
  *
- * Readings of points the paper leaves open (all listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - square spatial window |y-x|_inf <= R, R = round(3 sigma_s) by default,
  *     Haar interval T_s = R + 1/2;
  *   - Haar functions take the mean of their one-sided limits at a jump
@@ -59,7 +59,8 @@
  *     J_z = ceil(log2(2 T_z)), profile K_r(t dI / (Z - 1)); weight of a
  *     neighbour = K~_r at n(x) - n(y); guard 1e-6 (sum |K~_s|) max |K~_r|.
  *
- * Parity pinned by tests/test_oracle_*.py; see the design doc for the pin list.
+ * Parity pinned by tests/test_oracle_*.py (worked values, closed forms,
+ * brute force on tiny inputs and invariants).
  */
 #include <math.h>
 #include <stdlib.h>

@@ -580,7 +580,7 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
     p.m = std::max(p.nv, p.nh);
     if (!bfi::kernel_class_supported(p.m))
         return fail(BF_ERR_UNSUPPORTED, "spatial approximation needs " + std::to_string(p.m) +
-                                            " box windows per axis; this build supports up to " +
+                                            " box windows per axis; the library supports up to " +
                                             std::to_string(bfi::kMaxWin) + " (reduce ns_terms)");
     if ((int)p.k.size() > bfi::kMaxTerms)
         return fail(BF_ERR_UNSUPPORTED, "more than " + std::to_string(bfi::kMaxTerms) + " cosine terms per plan");

@@ -95,7 +95,7 @@ TileConfig choose_tile(const FilterParams &p, int height, int width, int precisi
         std::lock_guard<std::mutex> lk(g_mu);
         load_locked();
         auto it = g_table.find(make_key(p, height, width, precision));
-        // an entry stays usable only while its term grouping matches this build's layout
+        // an entry stays usable only while its term grouping matches the library's current layout
         if (it != g_table.end() &&
             it->second.groups == (it->second.packed ? term_groups(p, it->second.nk) : (p.nr + it->second.nk - 1) / it->second.nk) &&
             (p.zbins == 0 || (it->second.packed && !it->second.ring)))

@@ -2,7 +2,7 @@
 
 The paper evaluates on natural 8-bit photographs that are not available here;
 these generators stand in for them (piecewise-constant regions with sharp edges
-plus noise, which is what an edge-preserving filter is judged on).  All images
+plus noise, the structure an edge-preserving filter is meant for).  All images
 are float32 in [0, 1].  This module holds input generation only: no step of the
 filter's arithmetic lives here, so both the CUDA path and the CPU oracle can be
 fed from it.

@@ -155,6 +155,34 @@ def test_deterministic_and_stream():
     assert torch.equal(a, b)
 
 
+def test_concurrent_streams_share_one_input():
+    """Several plans (one with two term groups and a grouped scratch plane) filtering one input at once on
+    three streams, as the benchmark's step runs them: each result equals the same plan's result alone."""
+    img = synth.shapes(270, 490, 14, scale=0.2)
+    kws = [dict(sigma_s=ss, sigma_r=sr, nr_terms=8, ns_terms=5) for ss in (2.0, 8.0, 32.0) for sr in (0.05, 0.3)]
+    kws.append(dict(sigma_s=8.0, sigma_r=0.1, nr_terms=16, ns_terms=5))
+    plans = [bf.Plan(device=0, **kw) for kw in kws]
+    src = torch.from_numpy(img).cuda()
+    alone = [torch.full_like(src, float("nan")) for _ in plans]
+    for p, o in zip(plans, alone):
+        bf.bf_filter(p, src, o)
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    for rep in range(3):
+        outs = [torch.full_like(src, float("nan")) for _ in plans]
+        fork = torch.cuda.Event()
+        fork.record()
+        for s in streams:
+            s.wait_event(fork)
+        for j, (p, o) in enumerate(zip(plans, outs)):
+            bf.bf_filter(p, src, o, stream=streams[j % 3])
+        for s in streams:
+            torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        for kw, a, o in zip(kws, alone, outs):
+            assert torch.equal(a, o), (rep, kw)
+
+
 def test_in_place_rejected_and_injected_failure():
     img = synth.blocks(64, 64, 0)
     plan = bf.Plan(device=0)
