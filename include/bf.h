@@ -256,9 +256,10 @@ bf_status bf_filter_noalloc(const bf_plan *plan, const float *d_in, size_t in_pi
  * Errors: BF_ERR_INVALID_ARG. */
 bf_status bf_launch_info(const bf_plan *plan, int height, int width, int *info);
 
-/* Autotuner: times candidate launch geometries (the cost model's best five of
- * each family: tile width, tile height, cosine terms per CTA, with or without
- * the shared-memory ring of basis inputs, exchange depth) for this plan on a synthetic height x width
+/* Autotuner: times candidate launch geometries (the cost model's best four of
+ * each family -- ring of basis inputs or not, exchange depth, kernel family,
+ * cosine terms per CTA -- within each residency class of 1, 2, or 3 and more
+ * CTAs per SM by shared memory) for this plan on a synthetic height x width
  * image and remembers the fastest for later bf_filter / bf_filter_batch calls
  * with the same kernel class, reach and image size on this device.  Allocates
  * and frees its own device buffers and synchronizes `stream`; do not call it
@@ -266,6 +267,25 @@ bf_status bf_launch_info(const bf_plan *plan, int height, int width, int *info);
  * geometry as in bf_launch_info.  BF_TUNE_CACHE=<file> persists results.
  * Errors: BF_ERR_INVALID_ARG, BF_ERR_NO_DEVICE, BF_ERR_OOM, BF_ERR_CUDA. */
 bf_status bf_autotune(const bf_plan *plan, int height, int width, void *stream, int *info);
+
+/* Autotuner for plans that filter at the same time: n plans (1..256, all on
+ * one device) run as a caller runs them concurrently, plan i on stream
+ * i mod n_streams (1..8) in the given order, forked from and joined to one
+ * stream.  The fastest launch geometries for that whole group are found by
+ * coordinate descent (one kernel class at a time over the candidates
+ * bf_autotune times, two sweeps), timed with CUDA events from the fork to the
+ * join on synthetic height x width images in the first plan's data range, and
+ * pinned as bf_set_launch does.  Plans with the same kernel class, reach and
+ * image size share one geometry.  A geometry that is slower alone can win in
+ * the group: a grid of fewer CTAs than SMs leaves SMs to the other streams.
+ * Allocates its own buffers (one input, n outputs, scratch) and streams, and
+ * synchronizes them before returning; do not call it during stream capture.
+ * infos (12 x n ints, may be NULL) receives each plan's geometry as in
+ * bf_launch_info.  The geometry changes rounding order only.
+ * Errors: BF_ERR_INVALID_ARG (no plans, a null plan, plans on several
+ * devices, n_streams out of range), BF_ERR_NO_DEVICE (a host-only plan),
+ * BF_ERR_UNSUPPORTED, BF_ERR_OOM, BF_ERR_CUDA. */
+bf_status bf_autotune_group(const bf_plan *const *plans, int n, int height, int width, int n_streams, int *infos);
 
 /* Launch geometries of this plan for a height x width image, best first by the
  * cost model: up to max_n records of 12 ints each (as in bf_launch_info) into

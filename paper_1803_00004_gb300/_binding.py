@@ -63,6 +63,7 @@ class bf_result(C.Structure):
 
 
 EXPORTS = ["bf_plan_desc_default", "bf_plan_create", "bf_plan_destroy", "bf_coeffs", "bf_launch_info", "bf_autotune",
+           "bf_autotune_group",
            "bf_launch_candidates", "bf_set_launch",
            "bf_filter", "bf_filter_noalloc",
            "bf_filter_batch",
@@ -99,6 +100,7 @@ def lib():
         L.bf_set_launch.argtypes = [vp, i, i, P(i)]
         L.bf_filter_noalloc.argtypes = [vp, vp, sz, vp, sz, i, i, vp]
         L.bf_autotune.argtypes = [vp, i, i, vp, P(i)]
+        L.bf_autotune_group.argtypes = [P(vp), i, i, i, i, P(i)]
         L.bf_filter_batch.argtypes = [P(vp), P(bf_image), i, vp]
         L.bf_exact.argtypes = [vp, sz, vp, sz, i, i, i, d, i, i, d, vp]
         L.bf_exact_lut.argtypes = [vp, sz, vp, sz, i, i, i, d, i, i, d, d, i, vp]
@@ -239,6 +241,17 @@ def bf_autotune(plan: Plan, height: int, width: int, stream=None) -> dict:
     _check(lib().bf_autotune(plan.handle, height, width, _stream_handle(stream), info), "bf_autotune")
     keys = INFO_KEYS
     return dict(zip(keys, list(info)))
+
+
+def bf_autotune_group(plans, height: int, width: int, n_streams: int = 3) -> list:
+    """Tunes the geometries of plans filtering concurrently (plan i on stream i mod n_streams) and pins
+    them; returns each plan's geometry."""
+    n = len(plans)
+    hs = (C.c_void_p * max(n, 1))(*[p.handle for p in plans])
+    infos = (C.c_int * (len(INFO_KEYS) * max(n, 1)))()
+    _check(lib().bf_autotune_group(hs, n, height, width, n_streams, infos), "bf_autotune_group")
+    k = len(INFO_KEYS)
+    return [dict(zip(INFO_KEYS, list(infos[j * k:(j + 1) * k]))) for j in range(n)]
 
 
 def _ptr_pitch(t):

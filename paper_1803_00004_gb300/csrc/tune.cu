@@ -88,6 +88,27 @@ __global__ void fill_kernel(float *img, size_t n, int width, float lo, float hi,
     }
 }
 
+// The geometries the tuners time: the cost model's best four of every family (ring, exchange depth, kernel
+// family, terms per CTA) within every residency class (1, 2, or 3 and more CTAs per SM by shared memory).
+// The model ranks well within a residency class; across classes it misjudges how much latency the extra
+// resident CTAs hide.
+std::vector<TileConfig> timed_candidates(const FilterParams &p, int height, int width, int precision) {
+    int smem_sm = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        smem_sm <= 0) {
+        cudaGetLastError();
+        smem_sm = 228 * 1024;
+    }
+    std::vector<TileConfig> ranked = tile_candidates(p, height, width, precision, 100000), out;
+    std::map<std::tuple<int, int, int>, int> per_class;
+    for (const auto &c : ranked) {
+        const int res = (int)std::min<size_t>(3, (size_t)smem_sm / (c.smem + 1024));  // 1 KiB reserved per CTA
+        if (per_class[std::make_tuple(c.ring * 4 + c.depth + 8 * c.packed, c.nk, res)]++ < 4) out.push_back(c);
+    }
+    return out;
+}
+
 }  // namespace
 
 TileConfig choose_tile(const FilterParams &p, int height, int width, int precision) {
@@ -125,11 +146,7 @@ extern "C" bf_status bf_autotune(const bf_plan *plan, int height, int width, voi
         return fail(BF_ERR_NO_DEVICE, "cannot select the plan's device");
     }
     cudaStream_t s = (cudaStream_t)stream;
-    // the cost model is coarse: keep the best few of every family (ring or not, terms per CTA)
-    std::vector<TileConfig> ranked = tile_candidates(plan->kp, height, width, plan->desc.precision, 100000), cands;
-    std::map<std::pair<int, int>, int> per_family;
-    for (const auto &c : ranked)
-        if (per_family[{c.ring * 4 + c.depth + 8 * c.packed, c.nk}]++ < 4) cands.push_back(c);
+    const std::vector<TileConfig> cands = timed_candidates(plan->kp, height, width, plan->desc.precision);
     bf_status st = BF_OK;
     float *in = nullptr, *out = nullptr, *scratch = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -180,6 +197,146 @@ extern "C" bf_status bf_autotune(const bf_plan *plan, int height, int width, voi
         }
     }
     cudaStreamSynchronize(s);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(in);
+    cudaFree(out);
+    cudaFree(scratch);
+    cudaSetDevice(prev);
+    return st;
+}
+
+extern "C" bf_status bf_autotune_group(const bf_plan *const *plans, int n, int height, int width, int n_streams,
+                                       int *infos) {
+    if (!plans || n < 1 || n > 256 || height < 1 || width < 1 || n_streams < 1 || n_streams > 8)
+        return fail(BF_ERR_INVALID_ARG, "bad group-autotune arguments");
+    for (int i = 0; i < n; ++i)
+        if (!plans[i]) return fail(BF_ERR_INVALID_ARG, "null plan in the group");
+    for (int i = 0; i < n; ++i) {
+        if (plans[i]->desc.device < 0) return fail(BF_ERR_NO_DEVICE, "host-only plan (device = -1)");
+        if (plans[i]->desc.device != plans[0]->desc.device)
+            return fail(BF_ERR_INVALID_ARG, "the group's plans are on different devices");
+    }
+    int prev = 0;
+    if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(plans[0]->desc.device) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BF_ERR_NO_DEVICE, "cannot select the plans' device");
+    }
+    // plans with one table key (kernel class, reach, image size, precision) share one geometry
+    std::vector<Key> keys;
+    std::vector<int> cls(n), rep;
+    for (int i = 0; i < n; ++i) {
+        const Key k = make_key(plans[i]->kp, height, width, plans[i]->desc.precision);
+        const auto it = std::find(keys.begin(), keys.end(), k);
+        cls[i] = (int)(it - keys.begin());
+        if (it == keys.end()) {
+            keys.push_back(k);
+            rep.push_back(i);
+        }
+    }
+    const int nc = (int)keys.size();
+    std::vector<std::vector<TileConfig>> cands(nc);
+    std::vector<TileConfig> cur(nc);
+    bf_status st = BF_OK;
+    bool smooth = false;
+    for (int c = 0; c < nc && st == BF_OK; ++c) {
+        const bf_plan *pl = plans[rep[c]];
+        cands[c] = timed_candidates(pl->kp, height, width, pl->desc.precision);
+        cur[c] = choose_tile(pl->kp, height, width, pl->desc.precision);  // the pinned or modelled start
+        if (cands[c].empty()) st = fail(BF_ERR_UNSUPPORTED, "no launch geometry for a plan of the group");
+        smooth = smooth || pl->kp.zbins > 0;
+    }
+    // one input, one output per plan, and per plan the largest scratch any of its class's geometries needs
+    const size_t npx = (size_t)height * width;
+    std::vector<size_t> soff(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        size_t need = scratch_bytes(cur[cls[i]], height, width, plans[i]->kp.zbins);
+        for (const auto &c : cands[cls[i]]) need = std::max(need, scratch_bytes(c, height, width, plans[i]->kp.zbins));
+        soff[i + 1] = soff[i] + (need + 255) / 256 * 256;
+    }
+    float *in = nullptr, *out = nullptr;
+    char *scratch = nullptr;
+    std::vector<cudaStream_t> ss(n_streams, nullptr);
+    std::vector<cudaEvent_t> join(n_streams, nullptr);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (st == BF_OK && (cudaMalloc((void **)&in, npx * sizeof(float)) != cudaSuccess ||
+                        cudaMalloc((void **)&out, (size_t)n * npx * sizeof(float)) != cudaSuccess ||
+                        (soff[n] && cudaMalloc((void **)&scratch, soff[n]) != cudaSuccess))) {
+        cudaGetLastError();
+        st = fail(BF_ERR_OOM, "group-autotune buffers");
+    }
+    for (int j = 0; j < n_streams && st == BF_OK; ++j)
+        if (cudaStreamCreateWithFlags(&ss[j], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&join[j], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            st = fail(BF_ERR_CUDA, "group-autotune streams");
+        }
+    if (st == BF_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) {
+        cudaGetLastError();
+        st = fail(BF_ERR_CUDA, "group-autotune events");
+    }
+    // the group as a caller runs it: plan i on stream i mod n_streams, in the given order, forked from and
+    // joined to the first stream; the time is the first stream's, from the fork to the join
+    auto run_group = [&](float *ms) -> bool {
+        bool ok = cudaEventRecord(e0, ss[0]) == cudaSuccess;
+        for (int j = 1; j < n_streams; ++j) ok = ok && cudaStreamWaitEvent(ss[j], e0, 0) == cudaSuccess;
+        for (int i = 0; i < n && ok; ++i)
+            ok = launch_filter(plans[i]->kp, plans[i]->desc.precision, plans[i]->desc.kahan, cur[cls[i]], in, width,
+                               out + (size_t)i * npx, width, reinterpret_cast<float *>(scratch ? scratch + soff[i] : nullptr),
+                               height, width, ss[i % n_streams]) == BF_OK;
+        for (int j = 1; j < n_streams; ++j) {
+            cudaEventRecord(join[j], ss[j]);
+            cudaStreamWaitEvent(ss[0], join[j], 0);
+        }
+        cudaEventRecord(e1, ss[0]);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if (ms) cudaEventElapsedTime(ms, e0, e1);
+        return ok;
+    };
+    auto time_group = [&]() -> float {
+        float t[5];
+        if (!run_group(nullptr)) return 1e30f;  // warm-up
+        for (int r = 0; r < 5; ++r)
+            if (!run_group(&t[r])) return 1e30f;
+        std::sort(t, t + 5);
+        return t[2];
+    };
+    if (st == BF_OK) {
+        fill_kernel<<<256, 256, 0, ss[0]>>>(in, npx, width, plans[0]->desc.i_lo, plans[0]->desc.i_hi, smooth ? 1 : 0);
+        // coordinate descent: one class at a time over its candidates, the others held; two sweeps.  A change
+        // must win by 0.5 %, so timing noise does not move a class off a geometry that is as good.
+        float best = time_group();
+        for (int sweep = 0; sweep < 2; ++sweep)
+            for (int c = 0; c < nc; ++c) {
+                TileConfig keep = cur[c];
+                for (const auto &cand : cands[c]) {
+                    cur[c] = cand;
+                    const float t = time_group();
+                    if (t < best * 0.995f) {
+                        best = t;
+                        keep = cand;
+                    }
+                }
+                cur[c] = keep;
+            }
+        if (best >= 1e30f) st = fail(BF_ERR_CUDA, "no geometry of the group ran");
+    }
+    if (st == BF_OK) {
+        for (int c = 0; c < nc; ++c)
+            remember_tile(plans[rep[c]]->kp, height, width, plans[rep[c]]->desc.precision, cur[c]);
+        if (infos)
+            for (int i = 0; i < n; ++i) fill_info(cur[cls[i]], height, width, infos + kInfoInts * i, plans[i]->kp.zbins);
+    }
+    for (int j = 0; j < n_streams; ++j) {
+        if (ss[j]) {
+            cudaStreamSynchronize(ss[j]);
+            cudaStreamDestroy(ss[j]);
+        }
+        if (join[j]) cudaEventDestroy(join[j]);
+    }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFree(in);

@@ -204,6 +204,22 @@ def test_launch_info_and_autotune_without_gpu():
     assert ei.value.status == 9
 
 
+def test_group_autotune_argument_checks_without_gpu():
+    import ctypes as C
+    p, q = bf.Plan(device=-1), bf.Plan(device=-1, sigma_s=8.0)
+    for plans, h, w, ns, status in [([p, q], 64, 64, 3, 9),      # host-only plans: no device to time on
+                                    ([], 64, 64, 3, 1),          # no plans
+                                    ([p], 64, 64, 0, 1),         # stream count out of range
+                                    ([p], 64, 64, 9, 1),
+                                    ([p], 0, 64, 1, 1)]:
+        with pytest.raises(bf.BFError) as ei:
+            bf.bf_autotune_group(plans, h, w, n_streams=ns)
+        assert ei.value.status == status, (len(plans), h, ns)
+    hs = (C.c_void_p * 2)(p.handle, None)
+    assert bf.lib().bf_autotune_group(hs, 2, 64, 64, 2, None) == 1   # a null plan
+    assert bf.lib().bf_autotune_group(None, 1, 64, 64, 2, None) == 1
+
+
 def test_launch_candidates_and_pinning_host_only():
     # host-only plan: the geometry table is keyed without a device
     plan = bf.Plan(device=-1, sigma_s=32.0, sigma_r=0.3)

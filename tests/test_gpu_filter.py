@@ -112,19 +112,23 @@ def sample_points(H, W, n, seed):
 
 
 def test_full_size_sampled_parity():
-    """1920x1080 (the benchmark workload) at each (sigma_s, sigma_r) of the sweep, in the autotuned
-    launch geometry the benchmark times: sampled pixels, including the image border rows/columns,
-    against the oracle's direct evaluation."""
+    """1920x1080 (the benchmark workload) at each (sigma_s, sigma_r) of the sweep, in the launch geometry
+    the benchmark times (each plan autotuned, then the nine tuned as a group on three streams, longest
+    first): sampled pixels, including the image border rows/columns, against the oracle's direct
+    evaluation."""
     img = synth.shapes(1080, 1920, seed=0)
     pts = sample_points(1080, 1920, 160, 0)
-    for ss in (2.0, 8.0, 32.0):
-        for sr in (0.05, 0.1, 0.3):
-            kw = dict(sigma_s=ss, sigma_r=sr, nr_terms=8, ns_terms=5)
-            bf.bf_autotune(bf.Plan(device=0, **kw), 1080, 1920)
-            got = run(img, **kw)[pts[:, 0], pts[:, 1]]
-            ref = O.approx_direct_at(img.astype(np.float64), odesc(**kw), pts, threads=THREADS)
-            err = np.max(np.abs(got - ref))
-            assert err < TOL, "sigma_s=%g sigma_r=%g: %.3g" % (ss, sr, err)
+    kws = [dict(sigma_s=ss, sigma_r=sr, nr_terms=8, ns_terms=5) for ss in (32.0, 8.0, 2.0) for sr in (0.05, 0.1, 0.3)]
+    plans = [bf.Plan(device=0, **kw) for kw in kws]
+    for p in plans:
+        bf.bf_autotune(p, 1080, 1920)
+    chosen = bf.bf_autotune_group(plans, 1080, 1920, n_streams=3)
+    for p, kw, c in zip(plans, kws, chosen):
+        assert bf.bf_launch_info(p, 1080, 1920) == c
+        got = run(img, **kw)[pts[:, 0], pts[:, 1]]
+        ref = O.approx_direct_at(img.astype(np.float64), odesc(**kw), pts, threads=THREADS)
+        err = np.max(np.abs(got - ref))
+        assert err < TOL, "sigma_s=%g sigma_r=%g (%s): %.3g" % (kw["sigma_s"], kw["sigma_r"], c, err)
 
 
 @pytest.mark.parametrize("H,W,scale", [(2160, 3840, 2.0), (8192, 8192, 4.0)])
@@ -181,6 +185,32 @@ def test_concurrent_streams_share_one_input():
         torch.cuda.synchronize()
         for kw, a, o in zip(kws, alone, outs):
             assert torch.equal(a, o), (rep, kw)
+
+
+def test_group_autotune_pins_valid_geometries():
+    """bf_autotune_group over a mixed group (two term groups with partial planes, two plans of one kernel
+    class, a 3-D plan): it pins one geometry per class, bf_filter then launches it, and every result
+    matches the oracle."""
+    H, W = 70, 150
+    img = synth.shapes(H, W, 51, scale=0.15)
+    kws = [dict(sigma_s=8.0, sigma_r=0.1, nr_terms=16, ns_terms=5), dict(sigma_s=2.0, sigma_r=0.1),
+           dict(sigma_s=2.0, sigma_r=0.3)]
+    k3 = dict(sigma_s=2.0, sigma_r=0.1, nr_terms=6)
+    plans = [bf.Plan(device=0, **kw) for kw in kws] + [bf.Plan(device=0, policy=bf.RANGE_PAPER_3D, z_bins=256, **k3)]
+    chosen = bf.bf_autotune_group(plans, H, W, n_streams=2)
+    assert chosen[1] == chosen[2]                      # one kernel class, reach and size: one geometry
+    assert chosen[3]["packed"] == 1 and chosen[3]["ring"] == 0
+    for p, c in zip(plans, chosen):
+        assert bf.bf_launch_info(p, H, W) == c
+    for kw in kws:
+        ref, _ = O.approx_fast(img.astype(np.float64), odesc(**kw))
+        assert np.max(np.abs(run(img, **kw) - ref)) < TOL, kw
+    src = torch.from_numpy(img).cuda()
+    dst = torch.full_like(src, float("nan"))
+    bf.bf_filter(plans[3], src, dst)
+    torch.cuda.synchronize()
+    ref, _ = O.approx3d_direct(img.astype(np.float64), O.Desc(policy=O.PAPER_3D, **k3), 256)
+    assert np.max(np.abs(dst.cpu().numpy() - ref)) < TOL
 
 
 def test_in_place_rejected_and_injected_failure():
