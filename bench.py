@@ -40,9 +40,9 @@ WORKLOAD = "1920x1080 shapes+noise(0.03), Gaussian/Gaussian, sigma_s in {2,8,32}
 
 
 # DRAM bytes (read + write) per launch of the fused kernel, from the ncu capture of this kernel version at 1920x1080
-# (sigma_s = 2: 8.335 MB, sigma_s = 32: 8.337 MB, writes 0: the output stays in L2 during the kernel; an earlier
-# capture of the same code read 8.339 / 8.388 MB).  Reset to None whenever the kernel changes until it is captured
-# again.
+# in the geometries the step is tuned to (sigma_s = 2: 8.335 MB, sigma_s = 32: 8.337 MB, writes 0: the output stays
+# in L2 during the kernel; earlier captures of the same code in other geometries read 8.335-8.388 MB).  Reset to
+# None whenever the kernel changes until it is captured again.
 TRAFFIC_BYTES_PER_LAUNCH = 8.34e6
 
 
