@@ -488,9 +488,9 @@ def run_paper_3d(bf, dev, src, img, flush, alu_peak, reps=3):
     PSNR against the exact filter, beside the collapsed form's PSNR at the same N_r, plus the same at
     N_r = 4 (the 3-D form's series fits one period of the truncated kernel, so it needs fewer terms), and
     the Haar range series with 64 terms (`haar64_*`: one constant cosine term per pass, weights by table).
-    Each plan is autotuned first, as the sweep's plans are.  Work: one tile pass per (tile, slice present
-    in the tile); `passes_per_px` = items x tile area / pixels, and the roofline fraction counts each pass
-    as a filter pass over its tile's pixels."""
+    Each plan is autotuned first on the benchmark image (bf_autotune_image: its slice content sets the
+    work).  Work: one tile pass per (tile, slice present in the tile); `passes_per_px` = items x tile area /
+    pixels, and the roofline fraction counts each pass as a filter pass over its tile's pixels."""
     import torch
     out = torch.empty_like(src)
     ex = torch.empty_like(src)
@@ -503,7 +503,7 @@ def run_paper_3d(bf, dev, src, img, flush, alu_peak, reps=3):
             for nr in (8, 4):
                 p3 = bf.Plan(sigma_s=ss, sigma_r=sr, nr_terms=nr, ns_terms=NS, device=dev.index,
                              policy=bf.RANGE_PAPER_3D, z_bins=256)
-                bf.bf_autotune(p3, H, W)
+                bf.bf_autotune_image(p3, src)
                 t = timed_launches(bf, p3, src, out, flush, reps)
                 mse3 = torch.mean((out.double() - ex.double()) ** 2).item()
                 pc = bf.Plan(sigma_s=ss, sigma_r=sr, nr_terms=nr, ns_terms=NS, device=dev.index)
@@ -526,7 +526,7 @@ def run_paper_3d(bf, dev, src, img, flush, alu_peak, reps=3):
             # the Haar range series (64 terms: one constant cosine term per pass, the weights from a table)
             ph = bf.Plan(sigma_s=ss, sigma_r=sr, nr_terms=64, ns_terms=NS, device=dev.index,
                          policy=bf.RANGE_PAPER_3D, z_bins=256, range_series=bf.SERIES_HAAR)
-            bf.bf_autotune(ph, H, W)
+            bf.bf_autotune_image(ph, src)
             t = timed_launches(bf, ph, src, out, flush, reps)
             mseh = torch.mean((out.double() - ex.double()) ** 2).item()
             row["haar64_ms"] = round(t, 3)

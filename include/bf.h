@@ -268,6 +268,16 @@ bf_status bf_launch_info(const bf_plan *plan, int height, int width, int *info);
  * Errors: BF_ERR_INVALID_ARG, BF_ERR_NO_DEVICE, BF_ERR_OOM, BF_ERR_CUDA. */
 bf_status bf_autotune(const bf_plan *plan, int height, int width, void *stream, int *info);
 
+/* As bf_autotune, but the candidates are timed on the caller's image: d_in
+ * (device, height x width fp32, row pitch in_pitch bytes, a multiple of 4 and
+ * at least width x 4; read only, caller-owned).  For the 3-D form the work is
+ * one tile pass per intensity slice present in a tile, so the fastest
+ * geometry depends on the content; a representative image finds it where the
+ * synthetic one may not.  Errors: as bf_autotune, and BF_ERR_INVALID_ARG for
+ * a NULL image or a bad pitch. */
+bf_status bf_autotune_image(const bf_plan *plan, const float *d_in, size_t in_pitch, int height, int width,
+                            void *stream, int *info);
+
 /* Autotuner for plans that filter at the same time: n plans (1..256, all on
  * one device) run as a caller runs them concurrently, plan i on stream
  * i mod n_streams (1..8) in the given order, forked from and joined to one

@@ -63,7 +63,7 @@ class bf_result(C.Structure):
 
 
 EXPORTS = ["bf_plan_desc_default", "bf_plan_create", "bf_plan_destroy", "bf_coeffs", "bf_launch_info", "bf_autotune",
-           "bf_autotune_group",
+           "bf_autotune_group", "bf_autotune_image",
            "bf_launch_candidates", "bf_set_launch",
            "bf_filter", "bf_filter_noalloc",
            "bf_filter_batch",
@@ -101,6 +101,7 @@ def lib():
         L.bf_filter_noalloc.argtypes = [vp, vp, sz, vp, sz, i, i, vp]
         L.bf_autotune.argtypes = [vp, i, i, vp, P(i)]
         L.bf_autotune_group.argtypes = [P(vp), i, i, i, i, P(i)]
+        L.bf_autotune_image.argtypes = [vp, vp, sz, i, i, vp, P(i)]
         L.bf_filter_batch.argtypes = [P(vp), P(bf_image), i, vp]
         L.bf_exact.argtypes = [vp, sz, vp, sz, i, i, i, d, i, i, d, vp]
         L.bf_exact_lut.argtypes = [vp, sz, vp, sz, i, i, i, d, i, i, d, d, i, vp]
@@ -241,6 +242,14 @@ def bf_autotune(plan: Plan, height: int, width: int, stream=None) -> dict:
     _check(lib().bf_autotune(plan.handle, height, width, _stream_handle(stream), info), "bf_autotune")
     keys = INFO_KEYS
     return dict(zip(keys, list(info)))
+
+
+def bf_autotune_image(plan: Plan, src, stream=None) -> dict:
+    """bf_autotune timed on the caller's image (a 2-D float32 device tensor)."""
+    ip, ipitch, h, w = _ptr_pitch(src)
+    info = (C.c_int * len(INFO_KEYS))()
+    _check(lib().bf_autotune_image(plan.handle, ip, ipitch, h, w, _stream_handle(stream), info), "bf_autotune_image")
+    return dict(zip(INFO_KEYS, list(info)))
 
 
 def bf_autotune_group(plans, height: int, width: int, n_streams: int = 3) -> list:

@@ -137,7 +137,12 @@ void remember_tile(const FilterParams &p, int height, int width, int precision, 
 
 using namespace bfi;
 
-extern "C" bf_status bf_autotune(const bf_plan *plan, int height, int width, void *stream, int *info) {
+namespace {
+
+// Times the candidates on `sample` (pitch in floats; nullptr: a synthetic image in the plan's data range)
+// and pins the fastest.
+bf_status autotune_plan(const bf_plan *plan, const float *sample, size_t sample_pitch, int height, int width,
+                        void *stream, int *info) {
     if (!plan || height < 1 || width < 1) return fail(BF_ERR_INVALID_ARG, "bad autotune arguments");
     if (plan->desc.device < 0) return fail(BF_ERR_NO_DEVICE, "host-only plan (device = -1)");
     int prev = 0;
@@ -153,7 +158,7 @@ extern "C" bf_status bf_autotune(const bf_plan *plan, int height, int width, voi
     size_t n = (size_t)height * width, need = 0;
     for (const auto &c : cands) need = std::max(need, scratch_bytes(c, height, width, plan->kp.zbins));
     if (cands.empty()) st = fail(BF_ERR_UNSUPPORTED, "no launch geometry for this plan");
-    if (st == BF_OK && (cudaMalloc((void **)&in, n * sizeof(float)) != cudaSuccess ||
+    if (st == BF_OK && ((!sample && cudaMalloc((void **)&in, n * sizeof(float)) != cudaSuccess) ||
                         cudaMalloc((void **)&out, n * sizeof(float)) != cudaSuccess ||
                         (need && cudaMalloc((void **)&scratch, need) != cudaSuccess))) {
         cudaGetLastError();
@@ -166,17 +171,20 @@ extern "C" bf_status bf_autotune(const bf_plan *plan, int height, int width, voi
     TileConfig best{};
     float best_ms = 1e30f;
     if (st == BF_OK) {
-        fill_kernel<<<256, 256, 0, s>>>(in, n, width, plan->desc.i_lo, plan->desc.i_hi, plan->kp.zbins > 0 ? 1 : 0);
+        const float *src = sample ? sample : in;
+        const size_t src_pitch = sample ? sample_pitch : (size_t)width;
+        if (!sample)
+            fill_kernel<<<256, 256, 0, s>>>(in, n, width, plan->desc.i_lo, plan->desc.i_hi, plan->kp.zbins > 0 ? 1 : 0);
         for (const auto &c : cands) {
-            bf_status r = launch_filter(plan->kp, plan->desc.precision, plan->desc.kahan, c, in, width, out, width,
+            bf_status r = launch_filter(plan->kp, plan->desc.precision, plan->desc.kahan, c, src, src_pitch, out, width,
                                         scratch, height, width, stream);  // warm-up
             if (r != BF_OK) continue;
             float t[3];
             bool ok = true;
             for (int rep = 0; rep < 3 && ok; ++rep) {
                 cudaEventRecord(e0, s);
-                ok = launch_filter(plan->kp, plan->desc.precision, plan->desc.kahan, c, in, width, out, width, scratch,
-                                   height, width, stream) == BF_OK;
+                ok = launch_filter(plan->kp, plan->desc.precision, plan->desc.kahan, c, src, src_pitch, out, width,
+                                   scratch, height, width, stream) == BF_OK;
                 cudaEventRecord(e1, s);
                 if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
                 else cudaEventElapsedTime(&t[rep], e0, e1);
@@ -204,6 +212,19 @@ extern "C" bf_status bf_autotune(const bf_plan *plan, int height, int width, voi
     cudaFree(scratch);
     cudaSetDevice(prev);
     return st;
+}
+
+}  // namespace
+
+extern "C" bf_status bf_autotune(const bf_plan *plan, int height, int width, void *stream, int *info) {
+    return autotune_plan(plan, nullptr, 0, height, width, stream, info);
+}
+
+extern "C" bf_status bf_autotune_image(const bf_plan *plan, const float *d_in, size_t in_pitch, int height, int width,
+                                       void *stream, int *info) {
+    if (!d_in || height < 1 || width < 1 || in_pitch % sizeof(float) || in_pitch < (size_t)width * sizeof(float))
+        return fail(BF_ERR_INVALID_ARG, "bad sample image (NULL, empty, or pitch not a multiple of 4 bytes >= width * 4)");
+    return autotune_plan(plan, d_in, in_pitch / sizeof(float), height, width, stream, info);
 }
 
 extern "C" bf_status bf_autotune_group(const bf_plan *const *plans, int n, int height, int width, int n_streams,

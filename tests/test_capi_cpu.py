@@ -220,6 +220,18 @@ def test_group_autotune_argument_checks_without_gpu():
     assert bf.lib().bf_autotune_group(None, 1, 64, 64, 2, None) == 1
 
 
+def test_image_autotune_argument_checks_without_gpu():
+    # no pointer is dereferenced: every call returns at its argument or device check
+    L, p = bf.lib(), bf.Plan(device=-1)
+    fake = 1 << 40
+    assert L.bf_autotune_image(p.handle, None, 256, 64, 64, None, None) == 1       # no image
+    assert L.bf_autotune_image(p.handle, fake, 255, 64, 64, None, None) == 1       # pitch not a multiple of 4
+    assert L.bf_autotune_image(p.handle, fake, 252, 64, 64, None, None) == 1       # pitch below width * 4
+    assert L.bf_autotune_image(p.handle, fake, 256, 0, 64, None, None) == 1        # empty
+    assert L.bf_autotune_image(p.handle, fake, 256, 64, 64, None, None) == 9       # host-only plan
+    assert L.bf_autotune_image(None, fake, 256, 64, 64, None, None) == 1           # no plan
+
+
 def test_launch_candidates_and_pinning_host_only():
     # host-only plan: the geometry table is keyed without a device
     plan = bf.Plan(device=-1, sigma_s=32.0, sigma_r=0.3)

@@ -333,3 +333,19 @@ def test_3d_pitched_buffers_leave_padding(series):
     else:
         ref, _ = O.approx3dh_direct(img.astype(np.float64), O.Desc(**kw), 256)
     assert np.max(np.abs(got - ref)) < TOL
+
+
+def test_autotune_on_the_callers_image():
+    """bf_autotune_image times the geometries on the caller's image (here a pitched view), pins one that
+    bf_filter then launches, and the result matches the oracle."""
+    H, W = 150, 260
+    img = synth.shapes(H, W, 52, scale=0.2)
+    kw = dict(sigma_s=2.0, sigma_r=0.1, nr_terms=6)
+    plan = plan3d(256, **kw)
+    big = torch.zeros((H, 288), dtype=torch.float32, device="cuda")
+    big[:, :W] = torch.from_numpy(img).cuda()
+    info = bf.bf_autotune_image(plan, big[:, :W])
+    assert info["packed"] == 1 and info["ring"] == 0
+    assert bf.bf_launch_info(plan, H, W) == info
+    e_good, worst = check(gpu(plan, img), img, kw, 256)
+    assert e_good < TOL and worst < 1.0, (e_good, worst)
