@@ -403,8 +403,9 @@ def run_e2e(args, bf, plans, img, dev, stream, cstreams, order):
     return {"value": round(value, 3), "unit": "Mpixel/s", "h2d_bytes_per_step": 4 * H * W,
             "d2h_bytes_per_step": 4 * H * W * len(plans),
             "note": "uploads and downloads overlap the filters (copy streams, double buffers); filters on %d "
-                    "compute streams; no L2 flush between steps (each step's copies pass through L2), so it can "
-                    "read above the device-timed value" % len(cstreams)}
+                    "compute streams; every step's input arrives by its own H2D copy (nothing is reused from an "
+                    "earlier step), and the copy leaves it in L2 for that step's filters, so it can read above the "
+                    "device-timed value, whose steps start from a flushed L2" % len(cstreams)}
 
 
 def timed_calls(fn, flush, reps):
