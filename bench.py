@@ -640,8 +640,9 @@ def mixed_requests(n, lo, hi, seed):
 
 
 def run_batched(bf, dev, n=512, lo=64, hi=2048, reps=3):
-    """One bf_filter_batch call over n images (persistent launch, graph replay) vs a
-    sequential bf_filter loop over the same images."""
+    """One bf_filter_batch call over n images (persistent launch, graph replay), with the default batch
+    geometry and after bf_autotune_batch on this batch (untimed), vs a sequential bf_filter loop over the
+    same images."""
     import torch
     work = mixed_requests(n, lo, hi, seed=1234)
     plans = [bf.Plan(device=dev.index or 0, **kw) for _, kw in work]
@@ -663,10 +664,15 @@ def run_batched(bf, dev, n=512, lo=64, hi=2048, reps=3):
             ts.append(e0.elapsed_time(e1))
         return float(np.median(ts))
 
+    t_default = timed(lambda: bf.bf_filter_batch(plans, srcs, dsts, stream=stream))
+    t0 = time.perf_counter()
+    bf.bf_autotune_batch(plans, srcs, dsts, stream=stream)
+    tune_s = time.perf_counter() - t0
     t_batch = timed(lambda: bf.bf_filter_batch(plans, srcs, dsts, stream=stream))
     t_seq = timed(lambda: [bf.bf_filter(p, x, y, stream=stream) for p, x, y in zip(plans, srcs, dsts)])
     return {"images": n, "sides": [lo, hi], "mpix": round(px / 1e6, 2),
             "batched_mpix_s": round(px / (t_batch * 1e-3) / 1e6, 1), "batched_ms": round(t_batch, 3),
+            "batched_default_mpix_s": round(px / (t_default * 1e-3) / 1e6, 1), "autotune_s": round(tune_s, 1),
             "sequential_mpix_s": round(px / (t_seq * 1e-3) / 1e6, 1), "sequential_ms": round(t_seq, 3)}
 
 

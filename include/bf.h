@@ -371,6 +371,20 @@ typedef struct {
  * be on the same device.  Errors: as bf_filter. */
 bf_status bf_filter_batch(const bf_plan *const *plans, const bf_image *images, int n, void *stream);
 
+/* Autotuner of the batched launch: runs this batch (the same arguments as
+ * bf_filter_batch) under candidate geometries of each kernel class -- column
+ * threads beyond the widest halo (64..384), minimum tile height (24..192) and
+ * terms per CTA (as many as fit, at most 4, at most 2) -- by coordinate descent
+ * (one class and one parameter at a time, two sweeps), timing the whole batch
+ * with CUDA events on `stream`.  The fastest geometry of each class is kept
+ * per (device, windows per axis, kernel family, widest reach) for later
+ * bf_filter_batch calls and the server, and the captured graphs of the device
+ * are dropped so the next call captures it.  The outputs receive valid results
+ * (every geometry gives them within the same error bound).  Synchronizes
+ * `stream`; do not call it during stream capture.  Errors: as
+ * bf_filter_batch. */
+bf_status bf_autotune_batch(const bf_plan *const *plans, const bf_image *images, int n, void *stream);
+
 /* Exact bilateral filter of Eq. (1) by brute force on the device (fp32,
  * |y - x|_inf <= radius, untruncated range kernel): the accuracy reference
  * for images too large for the CPU.  O(radius^2) per pixel. */

@@ -66,7 +66,7 @@ EXPORTS = ["bf_plan_desc_default", "bf_plan_create", "bf_plan_destroy", "bf_coef
            "bf_autotune_group", "bf_autotune_image",
            "bf_launch_candidates", "bf_set_launch",
            "bf_filter", "bf_filter_noalloc",
-           "bf_filter_batch",
+           "bf_filter_batch", "bf_autotune_batch",
            "bf_exact", "bf_exact_lut", "bf_precompute", "bf_filter_cached", "bf_cache_bytes", "bf_cache_destroy",
            "bf_serve_create", "bf_serve_submit", "bf_serve_poll", "bf_serve_cancel", "bf_serve_destroy",
            "bf_status_string", "bf_last_error", "bf_version", "bf_debug_fail_launches", "bf_debug_range_checks"]
@@ -103,6 +103,7 @@ def lib():
         L.bf_autotune_group.argtypes = [P(vp), i, i, i, i, P(i)]
         L.bf_autotune_image.argtypes = [vp, vp, sz, i, i, vp, P(i)]
         L.bf_filter_batch.argtypes = [P(vp), P(bf_image), i, vp]
+        L.bf_autotune_batch.argtypes = [P(vp), P(bf_image), i, vp]
         L.bf_exact.argtypes = [vp, sz, vp, sz, i, i, i, d, i, i, d, vp]
         L.bf_exact_lut.argtypes = [vp, sz, vp, sz, i, i, i, d, i, i, d, d, i, vp]
         L.bf_precompute.argtypes = [vp, vp, sz, i, i, i, i, vp, P(vp)]
@@ -293,7 +294,7 @@ def bf_filter(plan: Plan, src, dst, stream=None) -> None:
     _check(lib().bf_filter(plan.handle, ip, ipitch, op, opitch, h, w, _stream_handle(stream)), "bf_filter")
 
 
-def bf_filter_batch(plans, srcs, dsts, stream=None) -> None:
+def _batch_args(plans, srcs, dsts):
     n = len(srcs)
     if len(plans) != n or len(dsts) != n:
         raise ValueError("plans, inputs and outputs must have the same length")
@@ -306,7 +307,18 @@ def bf_filter_batch(plans, srcs, dsts, stream=None) -> None:
             raise ValueError("image %d: input and output shapes differ" % j)
         imgs[j] = bf_image(ip, ipitch, op, opitch, h, w)
         hs[j] = plans[j].handle
+    return hs, imgs, n
+
+
+def bf_filter_batch(plans, srcs, dsts, stream=None) -> None:
+    hs, imgs, n = _batch_args(plans, srcs, dsts)
     _check(lib().bf_filter_batch(hs, imgs, n, _stream_handle(stream)), "bf_filter_batch")
+
+
+def bf_autotune_batch(plans, srcs, dsts, stream=None) -> None:
+    """Tunes the batched launch's geometry on this batch (bf_filter_batch's arguments); dsts receive results."""
+    hs, imgs, n = _batch_args(plans, srcs, dsts)
+    _check(lib().bf_autotune_batch(hs, imgs, n, _stream_handle(stream)), "bf_autotune_batch")
 
 
 def bf_exact(src, dst, spatial=KERNEL_GAUSSIAN, sigma_s=4.0, radius=0, range=KERNEL_GAUSSIAN, sigma_r=0.1,

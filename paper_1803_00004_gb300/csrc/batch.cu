@@ -20,6 +20,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "bf_internal.h"
@@ -35,6 +36,27 @@ struct ClassLaunch {
     size_t item_off;   // byte offset of the class's first item in the buffer
     size_t cursor_off;
 };
+
+// Geometry of one batch class: column threads = the widest halo plus `extra` (whole warps, at most 448),
+// tile height at least th_min (and the window span), at most nk_cap terms per CTA (0: as many as fit).
+// bf_autotune_batch fills the table; classes without an entry take the defaults.
+struct BatchTune {
+    int extra = 128, th_min = 48, nk_cap = 0;
+};
+using ClassId = std::pair<int, int>;                    // (windows per axis, packed family)
+using TuneKey = std::tuple<int, int, int, int>;         // device, windows per axis, packed family, widest reach
+using TuneOverride = std::map<ClassId, BatchTune>;
+std::mutex g_tmu;
+std::map<TuneKey, BatchTune> g_tune;
+
+int current_device() {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess) {
+        cudaGetLastError();
+        d = -1;
+    }
+    return d;
+}
 
 }  // namespace
 
@@ -64,7 +86,8 @@ struct BatchLayout {
     size_t upload_bytes() const { return off_scratch; }
 };
 
-bf_status build_batch(const bf_plan *const *plans, const bf_image *images, int n, BatchLayout &L) {
+bf_status build_batch(const bf_plan *const *plans, const bf_image *images, int n, BatchLayout &L,
+                      const TuneOverride *ov = nullptr) {
     L = BatchLayout();
     L.n = n;
     const int sms = device_sm_count();
@@ -86,12 +109,20 @@ bf_status build_batch(const bf_plan *const *plans, const bf_image *images, int n
         const bool packed = kv.first.second != 0;
         int rx_max = 0;
         for (int i : kv.second) rx_max = std::max(rx_max, plans[i]->kp.rx);
-        // column threads: room for a 128-column tile next to the widest halo
-        int ncols = std::min(448, ((2 * rx_max + 128 + 31) / 32) * 32);
-        int nk = batch_class_nk(m, ncols, packed);
+        BatchTune tn;
+        if (ov && ov->count(kv.first)) {
+            tn = ov->at(kv.first);
+        } else {
+            std::lock_guard<std::mutex> lk(g_tmu);
+            const auto it = g_tune.find(TuneKey{current_device(), m, packed ? 1 : 0, rx_max});
+            if (it != g_tune.end()) tn = it->second;
+        }
+        // column threads: room for a tile of `extra` columns next to the widest halo
+        int ncols = std::min(448, ((2 * rx_max + tn.extra + 31) / 32) * 32);
+        int nk = batch_class_nk(m, ncols, packed, tn.nk_cap);
         while (nk == 0 && ncols > 2 * rx_max + 32) {
             ncols -= 32;
-            nk = batch_class_nk(m, ncols, packed);
+            nk = batch_class_nk(m, ncols, packed, tn.nk_cap);
         }
         if (nk == 0 || ncols < 2 * rx_max + 8) return fail(BF_ERR_UNSUPPORTED, "batched tile cannot hold this reach");
         std::vector<std::pair<double, WorkItem>> its;
@@ -103,7 +134,7 @@ bf_status build_batch(const bf_plan *const *plans, const bf_image *images, int n
             int tw = ((ncols - 2 * kp.rx) / 8) * 8;
             tw = std::min(tw, ((im.width + 7) / 8) * 8);
             const int vspan = kp.vhi - kp.vlo + 1;
-            const int th = std::min(im.height, std::max(48, vspan));
+            const int th = std::min(im.height, std::max(tn.th_min, vspan));
             if (!packed) L.params[i] = kp;
             else if (!term_layout(kp, nk, L.params[i]))
                 return fail(BF_ERR_UNSUPPORTED, "the plan's terms need more than 128 slots at this class");
@@ -176,9 +207,10 @@ bf_status enqueue_batch(const BatchLayout &L, uint8_t *d_buf, const uint8_t *h_s
                                  L.max_h, L.max_w, d_params, s);
 }
 
-bf_status enqueue_batch_direct(const bf_plan *const *plans, const bf_image *images, int n, void *stream) {
+bf_status enqueue_batch_with(const bf_plan *const *plans, const bf_image *images, int n, void *stream,
+                             const TuneOverride *ov) {
     BatchLayout L;
-    bf_status st = build_batch(plans, images, n, L);
+    bf_status st = build_batch(plans, images, n, L, ov);
     if (st != BF_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     uint8_t *d_buf = nullptr;
@@ -192,6 +224,10 @@ bf_status enqueue_batch_direct(const bf_plan *const *plans, const bf_image *imag
     st = enqueue_batch(L, d_buf, staging.data(), s);
     cudaFreeAsync(d_buf, s);
     return st;
+}
+
+bf_status enqueue_batch_direct(const bf_plan *const *plans, const bf_image *images, int n, void *stream) {
+    return enqueue_batch_with(plans, images, n, stream, nullptr);
 }
 
 size_t batch_device_bytes(const bf_plan *const *plans, const bf_image *images, int n) {
@@ -292,20 +328,23 @@ bf_status check_image(const float *d_in, size_t in_pitch, const float *d_out, si
 
 using namespace bfi;
 
-extern "C" bf_status bf_filter_batch(const bf_plan *const *plans, const bf_image *images, int n, void *stream) {
+namespace {
+
+// Argument checks shared by bf_filter_batch and bf_autotune_batch; the non-empty images and their plans go to
+// ps / ims, and their device to *device.
+bf_status collect_batch(const bf_plan *const *plans, const bf_image *images, int n, std::vector<const bf_plan *> &ps,
+                        std::vector<bf_image> &ims, int *device) {
     if (n < 0) return fail(BF_ERR_INVALID_ARG, "negative batch size");
     if (n == 0) return BF_OK;
     if (!plans || !images) return fail(BF_ERR_INVALID_ARG, "NULL batch arrays");
-    int device = -2;
-    std::vector<const bf_plan *> ps;
-    std::vector<bf_image> ims;
+    *device = -2;
     for (int i = 0; i < n; ++i) {
         if (!plans[i]) return fail(BF_ERR_INVALID_ARG, "NULL plan in batch");
         if (plans[i]->desc.device < 0) return fail(BF_ERR_NO_DEVICE, "host-only plan in batch");
         if (plans[i]->kp.zbins > 0)
             return fail(BF_ERR_UNSUPPORTED, "the 3-D form (BF_RANGE_PAPER_3D) runs through bf_filter, not in batches");
-        if (device == -2) device = plans[i]->desc.device;
-        if (plans[i]->desc.device != device) return fail(BF_ERR_INVALID_ARG, "plans of one batch must share a device");
+        if (*device == -2) *device = plans[i]->desc.device;
+        if (plans[i]->desc.device != *device) return fail(BF_ERR_INVALID_ARG, "plans of one batch must share a device");
         const bf_image &im = images[i];
         bf_status st = check_image(im.d_in, im.in_pitch_bytes, im.d_out, im.out_pitch_bytes, im.height, im.width);
         if (st != BF_OK) return st;
@@ -313,6 +352,110 @@ extern "C" bf_status bf_filter_batch(const bf_plan *const *plans, const bf_image
         ps.push_back(plans[i]);
         ims.push_back(im);
     }
+    return BF_OK;
+}
+
+}  // namespace
+
+extern "C" bf_status bf_autotune_batch(const bf_plan *const *plans, const bf_image *images, int n, void *stream) {
+    std::vector<const bf_plan *> ps;
+    std::vector<bf_image> ims;
+    int device = -2;
+    bf_status st = collect_batch(plans, images, n, ps, ims, &device);
+    if (st != BF_OK || ps.empty()) return st;
+    int prev = 0;
+    if (cudaGetDevice(&prev) != cudaSuccess || (prev != device && cudaSetDevice(device) != cudaSuccess)) {
+        cudaGetLastError();
+        return fail(BF_ERR_NO_DEVICE, "cannot select the plans' device");
+    }
+    const int nb = (int)ps.size();
+    // the classes of this batch, their widest reach, and their current geometry (table entry or defaults)
+    std::map<ClassId, int> reach;
+    for (const bf_plan *p : ps) {
+        const ClassId c{p->m, p->kp.k[p->kp.nr - 1] - p->kp.k[0] + 1 == p->kp.nr ? 1 : 0};
+        reach[c] = std::max(reach.count(c) ? reach[c] : 0, p->kp.rx);
+    }
+    TuneOverride cur;
+    {
+        std::lock_guard<std::mutex> lk(g_tmu);
+        for (const auto &kv : reach) {
+            const auto it = g_tune.find(TuneKey{device, kv.first.first, kv.first.second, kv.second});
+            cur[kv.first] = it != g_tune.end() ? it->second : BatchTune();
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        st = fail(BF_ERR_CUDA, "batch-autotune events");
+    }
+    // device time of the whole batch (upload, persistent launches, finalize): the faster of two runs after a warm-up
+    auto time_batch = [&]() -> float {
+        float best = 1e30f;
+        for (int r = 0; r < 3; ++r) {
+            cudaEventRecord(e0, s);
+            if (enqueue_batch_with(ps.data(), ims.data(), nb, s, &cur) != BF_OK) return 1e30f;
+            cudaEventRecord(e1, s);
+            float ms = 0.f;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                cudaGetLastError();
+                return 1e30f;
+            }
+            if (r > 0) best = std::min(best, ms);
+        }
+        return best;
+    };
+    if (st == BF_OK) {
+        // coordinate descent, one class and one parameter at a time, two sweeps; a change must win by 1 %
+        const int extras[] = {64, 128, 192, 256, 384};
+        const int heights[] = {24, 48, 96, 192};
+        const int caps[] = {0, 4, 2};
+        float best = time_batch();
+        for (int sweep = 0; sweep < 2; ++sweep)
+            for (auto &kv : cur)
+                for (int dim = 0; dim < 3; ++dim) {
+                    const BatchTune keep = kv.second;
+                    BatchTune win = keep;
+                    const int nv = dim == 0 ? 5 : dim == 1 ? 4 : 3;
+                    for (int v = 0; v < nv; ++v) {
+                        BatchTune t = keep;
+                        if (dim == 0) t.extra = extras[v];
+                        else if (dim == 1) t.th_min = heights[v];
+                        else t.nk_cap = caps[v];
+                        if (t.extra == keep.extra && t.th_min == keep.th_min && t.nk_cap == keep.nk_cap) continue;
+                        kv.second = t;
+                        const float ms = time_batch();
+                        if (ms < best * 0.99f) {
+                            best = ms;
+                            win = t;
+                        }
+                    }
+                    kv.second = win;
+                }
+        if (best >= 1e30f) st = fail(BF_ERR_CUDA, "no batch geometry ran");
+    }
+    if (st == BF_OK) {
+        {
+            std::lock_guard<std::mutex> lk(g_tmu);
+            for (const auto &kv : cur) g_tune[TuneKey{device, kv.first.first, kv.first.second, reach[kv.first]}] = kv.second;
+        }
+        // captured batches of this device were built with the old geometry
+        std::lock_guard<std::mutex> lk(g_gmu);
+        g_graphs.remove_if([&](const std::unique_ptr<GraphEntry> &g) { return g->device == device; });
+    }
+    cudaStreamSynchronize(s);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (prev != device) cudaSetDevice(prev);
+    return st;
+}
+
+extern "C" bf_status bf_filter_batch(const bf_plan *const *plans, const bf_image *images, int n, void *stream) {
+    std::vector<const bf_plan *> ps;
+    std::vector<bf_image> ims;
+    int device = -2;
+    bf_status st0 = collect_batch(plans, images, n, ps, ims, &device);
+    if (st0 != BF_OK) return st0;
     if (ps.empty()) return BF_OK;
     int prev = 0;
     if (cudaGetDevice(&prev) != cudaSuccess || (prev != device && cudaSetDevice(device) != cudaSuccess)) {

@@ -463,9 +463,9 @@ int device_sm_count() { return device_sms(); }
 
 size_t batch_smem_bytes(int m, int nk, int ncols) { return smem_bytes(m, nk, ncols, ncols); }
 
-int batch_class_nk(int m, int ncols, bool packed) {
+int batch_class_nk(int m, int ncols, bool packed, int cap) {
     for (const auto &c : classes(packed))  // classes are listed with the largest term count first
-        if (c.m == m && batch_smem_bytes(m, c.nk, ncols) <= 220 * 1024) return c.nk;
+        if (c.m == m && (cap <= 0 || c.nk <= cap) && batch_smem_bytes(m, c.nk, ncols) <= 220 * 1024) return c.nk;
     return 0;
 }
 

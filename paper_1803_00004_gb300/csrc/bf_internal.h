@@ -134,9 +134,10 @@ bf_status launch_exact_lut(const float *d_in, size_t in_pitch, float *d_out, siz
 bool debug_consume_launch_failure();
 
 // ---- persistent batched launch (bf_filter.cu) ----
-// Terms per CTA used for kernel class m in batched launches, the shared-memory
-// bytes a launch with `ncols` column threads needs, and the resident CTAs per SM.
-int batch_class_nk(int m, int ncols, bool packed);
+// Terms per CTA used for kernel class m in batched launches (the largest that fits, at most cap when
+// cap > 0; 0 if none), the shared-memory bytes a launch with `ncols` column threads needs, and the
+// resident CTAs per SM.
+int batch_class_nk(int m, int ncols, bool packed, int cap = 0);
 size_t batch_smem_bytes(int m, int nk, int ncols);
 int batch_ctas_per_sm(int m, int nk, int ncols);
 int device_sm_count();

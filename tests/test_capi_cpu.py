@@ -185,6 +185,14 @@ def test_batch_and_server_argument_checks_without_gpu():
     plans = (C.c_void_p * 1)(p.handle.value)
     imgs = (bf._binding.bf_image * 1)(bf._binding.bf_image(4096, 256, 1 << 20, 256, 4, 64))
     assert L.bf_filter_batch(plans, imgs, 1, None) == 9          # host-only plan
+    # the batch autotuner takes the same arguments and checks them the same way
+    assert L.bf_autotune_batch(None, None, 0, None) == 0
+    assert L.bf_autotune_batch(None, None, -1, None) == 1
+    assert L.bf_autotune_batch(None, None, 2, None) == 1
+    assert L.bf_autotune_batch(plans, imgs, 1, None) == 9
+    p3 = bf.Plan(device=-1, policy=bf.RANGE_PAPER_3D)
+    plans3 = (C.c_void_p * 1)(p3.handle.value)
+    assert L.bf_autotune_batch(plans3, imgs, 1, None) == 9        # device checked before the form
     cfg = bf._binding.bf_serve_config(0, 0, 0, 0, 0)
     h = C.c_void_p()
     assert L.bf_serve_create(C.byref(cfg), C.byref(h)) == 9      # no device here

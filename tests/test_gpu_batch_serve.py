@@ -180,3 +180,23 @@ def test_server_destroy_with_pending_requests():
     for i, o in bufs:
         srv.submit(bf.desc(), i.data_ptr(), o.data_ptr(), 256, 256)
     srv.close()  # drains admitted work, cancels the rest; must return
+
+
+def test_batch_autotune_keeps_results_within_the_bar():
+    """bf_autotune_batch times this batch under the candidate geometries of each class: its own outputs, and
+    those of bf_filter_batch afterwards (re-captured with the tuned geometry), match the oracle."""
+    work = mixed_workload(8, 40, 220, seed=11)
+    plans = [bf.Plan(device=0, **kw) for _, kw in work]
+    srcs = [torch.from_numpy(img).cuda() for img, _ in work]
+    refs = [O.approx_fast(img.astype(np.float64), O.Desc(**kw), threads=16)[0] for img, kw in work]
+    dsts = [torch.full_like(s, float("nan")) for s in srcs]
+    bf.bf_filter_batch(plans, srcs, dsts)        # a graph captured before tuning must not be replayed after it
+    bf.bf_autotune_batch(plans, srcs, dsts)
+    torch.cuda.synchronize()
+    for d, ref in zip(dsts, refs):
+        assert np.max(np.abs(d.cpu().numpy() - ref)) < TOL
+    dsts = [torch.full_like(s, float("nan")) for s in srcs]
+    bf.bf_filter_batch(plans, srcs, dsts)
+    torch.cuda.synchronize()
+    for d, ref in zip(dsts, refs):
+        assert np.max(np.abs(d.cpu().numpy() - ref)) < TOL
