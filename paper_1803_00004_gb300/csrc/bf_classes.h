@@ -26,10 +26,11 @@ extern const int kNumClassesM1, kNumClassesM2, kNumClassesM3, kNumClassesM4to6;
 
 // The 3-D form's persistent slice kernels (packed family without the ring; bf_tile.cuh): kernels_z_*.cu.
 // box: the range box; haar: the Haar range series' weight table (NK = 2 only).  The *_small kernels are the
-// same bounded to CTAs of at most 256 threads and *_regs registers (nullptr where they would spill).
+// same bounded to CTAs of at most 256 threads and *_regs registers (nullptr where they would spill);
+// haar_mid is the Haar kernel for CTAs of up to 512 threads at haar_small_regs registers.
 struct ZKernelClass {
     int m, nk;
-    const void *box, *box_small, *haar, *haar_small;
+    const void *box, *box_small, *haar, *haar_small, *haar_mid;
     int box_small_regs, haar_small_regs;
 };
 extern const ZKernelClass kZClassesM1M2[];

@@ -111,7 +111,8 @@ const ZKernelClass *find_zclass(int m, int nk) {
 
 // The 3-D form's persistent slice kernel of class (m, nk): zmode 1 the range box, 2 the Haar range
 // series' weights (nullptr where the class has none); `threads` <= 256 picks the register-bounded kernel
-// where the class has one.  *regs: the registers per thread the cost model assumes.
+// where the class has one, and for the Haar series `threads` <= 512 its 512-thread form.  *regs: the
+// registers per thread the cost model assumes.
 const void *find_zkernel(int m, int nk, int zmode, int threads = 512, int *regs = nullptr) {
     const ZKernelClass *c = find_zclass(m, nk);
     if (regs) *regs = 128;
@@ -120,6 +121,10 @@ const void *find_zkernel(int m, int nk, int zmode, int threads = 512, int *regs 
     if (threads <= 256 && small) {
         if (regs) *regs = zmode == 2 ? c->haar_small_regs : c->box_small_regs;
         return small;
+    }
+    if (zmode == 2 && threads <= 512 && c->haar_mid) {
+        if (regs) *regs = c->haar_small_regs;
+        return c->haar_mid;
     }
     return zmode == 2 ? c->haar : c->box;
 }

@@ -637,6 +637,13 @@ __global__ void __launch_bounds__(256, ZB == 2 ? 4 : 3) bf_zslice_small_kernel(B
 }
 constexpr int kZSmallRegs[3] = {0, 80, 64};  // by ZB
 
+// The Haar series' NK = 2 kernel for CTAs of up to 512 threads with the 64-register budget of its 256-thread
+// form: two CTAs per SM where shared memory allows, instead of one at 100-128 registers.
+template <int NK, int M, int ZB>
+__global__ void __launch_bounds__(512, 2) bf_zslice_mid_kernel(BF_ZSLICE_PARAMS) {
+    zslice_body<NK, M, ZB>(BF_ZSLICE_ARGS);
+}
+
 }  // namespace
 
 // The Haar range series runs one constant cosine term: its slice kernels exist for NK = 2 only.
@@ -651,6 +658,11 @@ constexpr const void *zhaar_small_kernel() {  // more windows than two spill at 
     else return nullptr;
 }
 template <int NK, int M>
+constexpr const void *zhaar_mid_kernel() {  // the same classes as the 256-thread form
+    if constexpr (NK == 2 && M <= 2) return (const void *)bf_zslice_mid_kernel<2, M, 2>;
+    else return nullptr;
+}
+template <int NK, int M>
 constexpr const void *zbox_small_kernel() {  // within 8 bytes of spill at 80 registers
     if constexpr ((M <= 2 && NK <= 4) || (M == 3 && NK == 2)) return (const void *)bf_zslice_small_kernel<NK, M, 1>;
     else return nullptr;
@@ -658,7 +670,7 @@ constexpr const void *zbox_small_kernel() {  // within 8 bytes of spill at 80 re
 
 #define BF_ZCLASS(M, NK)                                                                              \
     {M, NK, (const void *)bf_zslice_kernel<NK, M, 1>, zbox_small_kernel<NK, M>(), zhaar_kernel<NK, M>(), \
-     zhaar_small_kernel<NK, M>(), kZSmallRegs[1], kZSmallRegs[2]}
+     zhaar_small_kernel<NK, M>(), zhaar_mid_kernel<NK, M>(), kZSmallRegs[1], kZSmallRegs[2]}
 
 #define BF_CLASS(M, NK)                                                                                 \
     {M, NK, {(const void *)bf_fused_kernel<NK, M, false>, (const void *)bf_fused_kernel<NK, M, true>},  \
