@@ -302,10 +302,15 @@ def test_3d_haar_every_candidate_family():
         bf.bf_set_launch(plan, H, W, default)
 
 
-def test_3d_haar_full_size_sampled():
+@pytest.mark.parametrize("sigma_s,nr", [(8.0, 8), (32.0, 64)])
+def test_3d_haar_full_size_sampled(sigma_s, nr):
+    """The 1920 x 1080 sweep image, 256 slices, in the geometry the benchmark's 3-D lines use (tuned on the
+    image itself; sigma_s = 32 runs the 512-thread, 64-register slice kernel): 3000 sampled pixels."""
     img = synth.shapes(1080, 1920, seed=0)
-    kw = dict(sigma_s=8.0, sigma_r=0.1, nr_terms=8)
-    got = gpu(plan3dh(256, **kw), img)
+    kw = dict(sigma_s=sigma_s, sigma_r=0.1, nr_terms=nr)
+    plan = plan3dh(256, **kw)
+    bf.bf_autotune_image(plan, torch.from_numpy(img).cuda())
+    got = gpu(plan, img)
     assert np.all(np.isfinite(got))
     rng = np.random.default_rng(6)
     pts = np.stack([rng.integers(0, 1080, 3000), rng.integers(0, 1920, 3000)], axis=1)
