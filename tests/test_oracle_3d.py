@@ -123,3 +123,23 @@ def test_slice_rule():
     assert list(bins) == [0, 255, 0, 255]             # clamped to the axis
     bins, rz = O.z_bins(np.array([0.2, 0.49, 0.51]), 0.25, 3)
     assert list(bins) == [0, 1, 1] and rz == 0        # three levels 0, 1/2, 1
+
+
+@pytest.mark.parametrize("series", [0, 1])
+def test_pointwise_evaluators_equal_the_whole_image(series):
+    """The pointwise forms the full-size GPU tests sample with (O2-3D at chosen pixels, and the Haar series'
+    definition with `pts`) give exactly the whole-image definition's values there, image corners included."""
+    I = synth.blocks(23, 31, seed=5, noise=0.08)
+    rng = np.random.default_rng(3)
+    pts = np.concatenate([np.stack([rng.integers(0, 23, 40), rng.integers(0, 31, 40)], 1),
+                          [[0, 0], [22, 30], [0, 30], [22, 0]]])
+    if series == 0:
+        desc = D(sigma_s=2.0, sigma_r=0.1, nr_terms=6, policy=O.PAPER_3D)
+        whole, _, den = O.approx3d_direct(I, desc, 64, return_den=True)
+        at, den_at = O.approx3d_direct_at(I, desc, pts, 64)
+        assert np.max(np.abs(den_at - den[pts[:, 0], pts[:, 1]])) < 1e-12
+    else:
+        desc = D(sigma_s=2.0, sigma_r=0.1, nr_terms=12)
+        whole, _ = O.approx3dh_direct(I, desc, 64)
+        at, _ = O.approx3dh_direct(I, desc, 64, pts=pts)
+    assert np.max(np.abs(np.asarray(at).ravel() - whole[pts[:, 0], pts[:, 1]])) < 1e-13
