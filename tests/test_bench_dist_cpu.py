@@ -52,3 +52,36 @@ def test_single_process_helpers():
     import bench
     assert bench.reduce_max_ms(3.5) == 3.5
     assert abs(bench.whole_job_value(2e6, 10, 100.0, 1) - 200.0) < 1e-9
+
+
+def _run_bench(args, env_extra=None):
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, **(env_extra or {}))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py")] + args, capture_output=True, text=True,
+                       timeout=600, env=env, cwd=root)
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    return r.returncode, [json.loads(ln) for ln in lines]
+
+
+def test_reference_arm_line():
+    """`bench.py --impl reference` (the oracle on the host cores, each step the nine filters on a band) prints
+    one JSON line with the contract's keys, the metric and workload of the GPU arm."""
+    import bench
+    rc, out = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0"])
+    assert rc == 0 and len(out) == 1
+    d = out[0]
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "Mpixel/s"
+    assert d["higher_is_better"] is True and d["value"] > 0 and d["steps"] == 1 and d["n_gpus"] == 1
+    assert d["config"]["workload"] == bench.WORKLOAD
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_print_nothing():
+    rc, out = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0"],
+                         {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert rc == 0 and out == []
