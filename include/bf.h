@@ -56,7 +56,8 @@ typedef enum {
     BF_ERR_RANGE = 8,           /* value outside the supported range */
     BF_ERR_NO_DEVICE = 9,       /* no usable CUDA device */
     BF_ERR_NOT_FOUND = 10,      /* server: unknown or already collected ticket */
-    BF_ERR_CANCELLED = 11       /* server: request cancelled before it ran */
+    BF_ERR_CANCELLED = 11,      /* server: request cancelled before it ran */
+    BF_ERR_SCRATCH = 12         /* bf_filter_noalloc: no launch geometry's scratch fits its fixed array */
 } bf_status;
 
 typedef enum {
@@ -231,14 +232,19 @@ bf_status bf_filter(const bf_plan *plan, const float *d_in, size_t in_pitch_byte
  * an allocation may synchronise or fail mid-frame).  The paper has no
  * counterpart; this is a deployment variant of the same computation.
  * Plans whose cosine terms are split into groups need partial numerator and
- * denominator planes (2 x groups x height x width floats); here they live in a
- * fixed 64 MiB array inside the library (16,777,216 floats), which every GPU
- * that loads the library holds until the process exits.  The first call on a
- * device looks the array's address up; make that call before any stream
- * capture.  All calls share the array: calls whose work overlaps on the GPU
- * (other streams, other threads) race, so order them.  Arguments, layout,
- * ownership and results as bf_filter.  Errors: as bf_filter, plus
- * BF_ERR_RANGE when no launch geometry's planes fit the array. */
+ * denominator planes (2 x groups x height x width floats), and the 3-D form a
+ * slice work list; here they live in a fixed 64 MiB array inside the library
+ * (16,777,216 floats), which every GPU that loads the library holds until the
+ * process exits.  The launch geometry is bf_filter's, else the best-ranked one
+ * whose scratch fits the array.  The array's address is looked up once per
+ * CUDA context by the first call that needs it; make that first call before
+ * any stream capture.  All calls share the array and it keeps the last call's
+ * contents: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it, so order them on one stream or with events, and
+ * consume each result before a later call runs.  Arguments, layout, ownership
+ * and results as bf_filter; with the debug range check on, it checks the input
+ * as bf_filter does.  Errors: as bf_filter (never BF_ERR_OOM), plus
+ * BF_ERR_SCRATCH when no launch geometry's scratch fits the array. */
 bf_status bf_filter_noalloc(const bf_plan *plan, const float *d_in, size_t in_pitch_bytes,
                             float *d_out, size_t out_pitch_bytes, int height, int width, void *stream);
 
@@ -455,6 +461,25 @@ bf_status bf_serve_cancel(bf_server *server, uint64_t ticket);
 
 /* Drains all admitted requests and stops the server (NULL is a no-op). */
 void bf_serve_destroy(bf_server *server);
+
+/* ---------------------------------------------------------------------- */
+/* Measurement                                                             */
+/* ---------------------------------------------------------------------- */
+
+/* Measured fp32 throughput of `device`, the denominator of the fused
+ * filter's roofline (the paper has no counterpart; it times its method on a
+ * CPU).  Runs two kernels that fill every SM (2048 threads each) with eight
+ * independent fused multiply-add chains per thread: one issuing the scalar
+ * FFMA, one the two-wide FFMA2 that the filter's hot loops use.  Each is
+ * timed with CUDA events over `iters` x 128 FMAs per thread, best of three
+ * after a warm-up launch.  *ffma_ops and *ffma2_ops receive fp32 lane
+ * operations per second (an FMA on one lane is one operation; an FFMA2
+ * instruction is two).  Allocates and frees a 1 KB device buffer and a
+ * stream, and synchronizes; about 2 x 4 x iters x 40 ns of GPU time on a
+ * 152-SM device (iters = 20000: ~6 ms per launch).  Not for use during
+ * stream capture.  Errors: BF_ERR_INVALID_ARG (NULL, iters outside
+ * [1, 2^24]), BF_ERR_NO_DEVICE, BF_ERR_CUDA. */
+bf_status bf_fp32_peak(int device, int iters, double *ffma_ops, double *ffma2_ops);
 
 /* ---------------------------------------------------------------------- */
 

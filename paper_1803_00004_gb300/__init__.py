@@ -9,7 +9,7 @@ from ._binding import (BFError, Cache, Plan, Server, bf_coeffs, bf_exact, bf_exa
                        bf_autotune_batch,
                        bf_version,
                        bf_launch_info, bf_autotune, bf_autotune_group, bf_autotune_image, bf_launch_candidates, bf_set_launch,
-                       bf_debug_fail_launches, bf_debug_range_checks, desc, lib, LIB_PATH, EXPORTS)
+                       bf_debug_fail_launches, bf_debug_range_checks, bf_fp32_peak, desc, lib, LIB_PATH, EXPORTS)
 from ._binding import (KERNEL_GAUSSIAN, KERNEL_EXPONENTIAL, KERNEL_BOX, RANGE_TRUNCATED_MIN_PERIOD,  # noqa: F401
                        RANGE_UNTRUNCATED_FULL, RANGE_PAPER_3D, SERIES_COSINE, SERIES_HAAR, PREC_FP32, PREC_BF16,
                        PREC_FP16)

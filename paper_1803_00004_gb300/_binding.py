@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libbf.so")
 OK = 0
 ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA, ERR_ADMISSION = 1, 2, 3, 4, 5
 ERR_TIMEOUT, ERR_DEVICE_TIMEOUT, ERR_RANGE, ERR_NO_DEVICE, ERR_NOT_FOUND, ERR_CANCELLED = 6, 7, 8, 9, 10, 11
+ERR_SCRATCH = 12
 KERNEL_GAUSSIAN, KERNEL_EXPONENTIAL, KERNEL_BOX = 0, 1, 2
 RANGE_TRUNCATED_MIN_PERIOD, RANGE_UNTRUNCATED_FULL, RANGE_PAPER_3D = 0, 1, 2
 SERIES_COSINE, SERIES_HAAR = 0, 1
@@ -69,7 +70,8 @@ EXPORTS = ["bf_plan_desc_default", "bf_plan_create", "bf_plan_destroy", "bf_coef
            "bf_filter_batch", "bf_autotune_batch",
            "bf_exact", "bf_exact_lut", "bf_precompute", "bf_filter_cached", "bf_cache_bytes", "bf_cache_destroy",
            "bf_serve_create", "bf_serve_submit", "bf_serve_poll", "bf_serve_cancel", "bf_serve_destroy",
-           "bf_status_string", "bf_last_error", "bf_version", "bf_debug_fail_launches", "bf_debug_range_checks"]
+           "bf_status_string", "bf_last_error", "bf_version", "bf_debug_fail_launches", "bf_debug_range_checks",
+           "bf_fp32_peak"]
 
 _lib = None
 _lock = threading.Lock()
@@ -127,6 +129,7 @@ def lib():
         L.bf_debug_fail_launches.restype = None
         L.bf_debug_range_checks.argtypes = [i]
         L.bf_debug_range_checks.restype = None
+        L.bf_fp32_peak.argtypes = [i, i, P(d), P(d)]
         _lib = L
     return _lib
 
@@ -369,6 +372,13 @@ class Cache:
 
 def bf_version() -> int:
     return int(lib().bf_version())
+
+
+def bf_fp32_peak(device: int = 0, iters: int = 20000) -> dict:
+    """Measured fp32 lane operations per second of the scalar FFMA and the two-wide FFMA2."""
+    a, b = C.c_double(), C.c_double()
+    _check(lib().bf_fp32_peak(device, iters, C.byref(a), C.byref(b)), "bf_fp32_peak")
+    return {"ffma_ops": a.value, "ffma2_ops": b.value}
 
 
 def bf_debug_fail_launches(n: int) -> None:

@@ -245,6 +245,7 @@ const char *bf_status_string(bf_status s) {
         case BF_ERR_NO_DEVICE: return "no CUDA device";
         case BF_ERR_NOT_FOUND: return "not found";
         case BF_ERR_CANCELLED: return "cancelled";
+        case BF_ERR_SCRATCH: return "scratch does not fit the fixed array";
     }
     return "unknown status";
 }

@@ -33,8 +33,11 @@ def test_exports_every_declared_symbol():
 
 def test_status_strings_and_version():
     L = bf.lib()
-    for s in range(12):
-        assert L.bf_status_string(s)
+    for s in range(13):
+        assert L.bf_status_string(s) and L.bf_status_string(s) != b"unknown status"
+    # the fixed-scratch status of bf_filter_noalloc is its own code, not the input-range one
+    assert bf.ERR_SCRATCH == 12 and bf.ERR_SCRATCH != bf.ERR_RANGE
+    assert b"scratch" in L.bf_status_string(bf.ERR_SCRATCH)
     assert bf.bf_version() >= 1
 
 
