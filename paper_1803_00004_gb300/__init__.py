@@ -13,3 +13,5 @@ from ._binding import (BFError, Cache, Plan, Server, bf_coeffs, bf_exact, bf_exa
 from ._binding import (KERNEL_GAUSSIAN, KERNEL_EXPONENTIAL, KERNEL_BOX, RANGE_TRUNCATED_MIN_PERIOD,  # noqa: F401
                        RANGE_UNTRUNCATED_FULL, RANGE_PAPER_3D, SERIES_COSINE, SERIES_HAAR, PREC_FP32, PREC_BF16,
                        PREC_FP16)
+from ._binding import (OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA, ERR_ADMISSION, ERR_TIMEOUT,  # noqa: F401
+                       ERR_DEVICE_TIMEOUT, ERR_RANGE, ERR_NO_DEVICE, ERR_NOT_FOUND, ERR_CANCELLED, ERR_SCRATCH)
