@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--no-ramp", action="store_true", help="skip the untimed clock-ramp load (profiling)")
     ap.add_argument("--no-tune", action="store_true", help="use the pinned (BF_TUNE_CACHE) or cost-model geometry instead of autotuning")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving sub-measurements")
+    ap.add_argument("--tiles", default=None,
+                    help="pin each combination's launch geometry instead of autotuning: the JSON list of the line's "
+                         "'tiles' field, one [tw, th, threads, nk, groups, ring, depth, ncols, packed] per combination "
+                         "in the line's order")
     return ap.parse_args()
 
 
@@ -143,17 +147,43 @@ def whole_job_value(px_per_rank_step: float, steps: int, max_ms: float, world: i
     return world * px_per_rank_step * steps / (max_ms * 1e-3) / 1e6
 
 
+def haar_intervals(lev: int, k: int, T: float):
+    """Support pieces of one 1-D Haar function on [-T, T] (App. A): phi is one piece, psi_{j,k} two
+    (positive and negative half); level 0 is psi_00 on the whole interval."""
+    if lev < 0:
+        return [(-T, T)]
+    z = 0.0 if lev == 0 else (1.0 if k > 0 else -1.0) * (2.0 * abs(k) - 1.0) * T
+    s = 2.0 ** -lev
+    return [(s * (z - T), s * z), (s * z, s * (z + T))]
+
+
+def box_counts(coeffs: dict):
+    """(n_x, n_xy, n_pm) of the selected Haar terms' signed boxes: distinct box widths, distinct box shapes
+    (width, height), and the number of signed boxes, with the widths the lengths of App. A's intervals."""
+    T = coeffs["t_s"]
+    width = lambda a, b: round((b - a) / T, 9)
+    wx, shapes, n = set(), set(), 0
+    for lx, kx, ly, ky in coeffs["haar_terms"]:
+        for ax, bx in haar_intervals(lx, kx, T):
+            for ay, by in haar_intervals(ly, ky, T):
+                w, h = width(ax, bx), width(ay, by)
+                wx.add(w)
+                shapes.add((w, h))
+                n += 1
+    return len(wx), len(shapes), n
+
+
 def algorithmic_ops_per_pixel(coeffs: dict) -> float:
-    """FP32 operations per pixel of a separable running-sum evaluation of Eq. (36):
-    per basis image, 2 adds per vertical window, the window mixing (nonzero weights),
-    2 adds per horizontal window, one FMA into numerator/denominator; per cosine term
-    6 for the basis (angle-addition step and two products); the divide."""
-    nv, nh = len(coeffs["vwin"]), len(coeffs["hwin"])
-    nnz = sum(1 for r in coeffs["wcoef"] for v in r if abs(v) > 0)
+    """FP32 operations per pixel of the box-filter evaluation of Eq. (36), the count F of the hot-path scope:
+    per basis image, 2 running-sum operations per distinct box width along rows and 2 per distinct box shape
+    along columns, and one multiply-add per signed box (App. A); 4 per cosine term beyond the first to
+    accumulate numerator and denominator; 6 per frequency up to the largest for the basis (angle-addition
+    step and the two products with I); 2 for the divide and the guard.
+    F = N_img (2 n_x + 2 n_xy + n_pm) + 4 (N_r - 1) + 6 k_max + 2,  N_img = 4 N_r (- 2 when k = 0 is kept)."""
+    n_x, n_xy, n_pm = box_counts(coeffs)
     nk = len(coeffs["k"])
     nimg = 4 * nk - (2 if 0 in coeffs["k"] else 0)
-    per_img = 2 * nv + nnz + 2 * nh + 1
-    return nimg * per_img + 6 * nk + 2
+    return nimg * (2 * n_x + 2 * n_xy + n_pm) + 4 * (nk - 1) + 6 * max(coeffs["k"]) + 2
 
 
 def run_ours(args):
@@ -193,7 +223,16 @@ def run_ours(args):
     # that one filter's last partial wave of tiles overlaps the next filter's first.
     cstreams = [torch.cuda.Stream(dev) for _ in range(N_STREAMS)]
     order = sorted(range(len(plans)), key=lambda j: -combos[j][0])
-    if not args.no_tune:  # launch geometry (untimed): each plan alone, then the nine as the step runs them
+    if args.tiles:  # geometries pinned from an earlier line (reproducible profiles)
+        rows = json.loads(args.tiles)
+        if len(rows) != len(plans):
+            raise SystemExit("--tiles: %d geometries for %d combinations" % (len(rows), len(plans)))
+        keys = ("tw", "th", "threads", "nk", "groups", "ring", "depth", "ncols", "packed")
+        for p, r in zip(plans, rows):
+            info = {k: 0 for k in bf._binding.INFO_KEYS}
+            info.update(dict(zip(keys, r)))
+            bf.bf_set_launch(p, H, W, info)
+    elif not args.no_tune:  # launch geometry (untimed): each plan alone, then the nine as the step runs them
         for p in plans:
             bf.bf_autotune(p, H, W)
         bf.bf_autotune_group([plans[j] for j in order], H, W, n_streams=N_STREAMS)
@@ -272,7 +311,11 @@ def run_ours(args):
     clocks = sampler.summary()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     max_mhz = clocks.get("sm_max_mhz") or 2070.0
-    alu_peak = sms * 128 * max_mhz * 1e6 / 1e12  # FP32 lanes x clock, T op/s
+    nominal_peak = sms * 128 * max_mhz * 1e6 / 1e12  # FP32 lanes x clock, T op/s (context only)
+    # measured fp32 issue rate on this GPU (scalar FFMA and two-wide FFMA2, lane operations per second); the
+    # roofline divides by the faster of the two, since the fused kernel issues both
+    fp32 = bf.bf_fp32_peak(local)
+    alu_peak = max(fp32["ffma_ops"], fp32["ffma2_ops"]) / 1e12
     achieved = ops_per_launch / mean_launch_s / 1e12
     achieved_alone = ops_per_launch / mean_alone_s / 1e12
     hbm_gbs = 8.0 * H * W / mean_launch_s / 1e9
@@ -316,7 +359,13 @@ def run_ours(args):
                      "launch_ms": round(mean_launch_s * 1e3, 4),
                      "alone": {"launch_ms": round(mean_alone_s * 1e3, 4), "achieved": round(achieved_alone, 3),
                                "frac": round(achieved_alone / alu_peak, 4)},
-                     "note": "FP32 lane-ops/s of the fused kernel (algorithmic count) vs SMs x 128 x max SM clock; "
+                     "ops_per_px": [algorithmic_ops_per_pixel(c) for c in coeffs],
+                     "measured_fp32": {"ffma_tops": round(fp32["ffma_ops"] / 1e12, 2),
+                                       "ffma2_tops": round(fp32["ffma2_ops"] / 1e12, 2),
+                                       "nominal_tops": round(nominal_peak, 2)},
+                     "note": "FP32 lane-ops/s of the fused kernel, algorithmic count F = N_img (2 n_x + 2 n_xy + n_pm) "
+                             "+ 4 (N_r - 1) + 6 k_max + 2 per pixel, against the measured fp32 rate of this GPU "
+                             "(bf_fp32_peak: the faster of scalar FFMA and FFMA2, an FFMA2 counted as two lane-ops); "
                              "launch_ms = step device time / launches (launches overlap on %d streams), alone = "
                              "events around each launch run one at a time" % N_STREAMS},
         "hbm": {"achieved_gbs": round(hbm_gbs, 1), "peak_gbs": hbm_peak, "frac": round(hbm_gbs / hbm_peak, 5),
