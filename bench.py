@@ -61,8 +61,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving sub-measurements")
     ap.add_argument("--tiles", default=None,
                     help="pin each combination's launch geometry instead of autotuning: the JSON list of the line's "
-                         "'tiles' field, one [tw, th, threads, nk, groups, ring, depth, ncols, packed] per combination "
-                         "in the line's order")
+                         "'tiles' field, one [tw, th, threads, nk, groups, ring, depth, ncols, packed, pre] per "
+                         "combination in the line's order")
     return ap.parse_args()
 
 
@@ -227,7 +227,7 @@ def run_ours(args):
         rows = json.loads(args.tiles)
         if len(rows) != len(plans):
             raise SystemExit("--tiles: %d geometries for %d combinations" % (len(rows), len(plans)))
-        keys = ("tw", "th", "threads", "nk", "groups", "ring", "depth", "ncols", "packed")
+        keys = ("tw", "th", "threads", "nk", "groups", "ring", "depth", "ncols", "packed", "pre")
         for p, r in zip(plans, rows):
             info = {k: 0 for k in bf._binding.INFO_KEYS}
             info.update(dict(zip(keys, r)))
@@ -353,7 +353,8 @@ def run_ours(args):
         "plan_build_ms": round(plan_build_ms, 2),
         "per_combo_ms": [round(x, 4) for x in la.mean(0)],
         "per_combo_ms_overlapped": [round(x, 4) for x in lm.mean(0)],
-        "tiles": [[t["tw"], t["th"], t["threads"], t["nk"], t["groups"], t["ring"], t["depth"], t["ncols"], t["packed"]] for t in tiles],
+        "tiles": [[t["tw"], t["th"], t["threads"], t["nk"], t["groups"], t["ring"], t["depth"], t["ncols"], t["packed"],
+                   t["pre"]] for t in tiles],
         "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
                      "frac": round(achieved / alu_peak, 4), "traffic": TRAFFIC_BYTES_PER_LAUNCH,
                      "launch_ms": round(mean_launch_s * 1e3, 4),

@@ -215,7 +215,7 @@ def bf_coeffs(plan: Plan) -> dict:
 
 
 INFO_KEYS = ("tw", "th", "threads", "nk", "groups", "launches", "smem", "scratch_kib", "ring", "depth", "ncols",
-             "packed")
+             "packed", "pre")
 
 
 def bf_launch_info(plan: Plan, height: int, width: int) -> dict:

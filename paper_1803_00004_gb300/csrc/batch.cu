@@ -97,6 +97,8 @@ bf_status build_batch(const bf_plan *const *plans, const bf_image *images, int n
     for (int i = 0; i < n; ++i) {
         const FilterParams &kp = plans[i]->kp;
         if (kp.zbins > 0) return fail(BF_ERR_UNSUPPORTED, "the 3-D form (BF_RANGE_PAPER_3D) runs through bf_filter");
+        if (plans[i]->desc.precision != BF_PREC_FP32)
+            return fail(BF_ERR_UNSUPPORTED, "16-bit basis storage runs through bf_filter; batched launches are fp32");
         by_class[{plans[i]->m, kp.k[kp.nr - 1] - kp.k[0] + 1 == kp.nr ? 1 : 0}].push_back(i);
     }
     L.params.resize(n);

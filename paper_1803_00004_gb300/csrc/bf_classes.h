@@ -24,6 +24,16 @@ extern const KernelClass kClassesM3[];
 extern const KernelClass kClassesM4to6[];
 extern const int kNumClassesM1, kNumClassesM2, kNumClassesM3, kNumClassesM4to6;
 
+// Pre-pass variants of the packed family (no ring; bf_tile.cuh): fn[PRE - 1] reads the basis inputs stored by
+// the pre-pass in fp32 (PRE = 1), fp16 (2) or bf16 (3): kernels_p*.cu.
+struct PreKernelClass {
+    int m, nk;
+    const void *fn[3];
+};
+extern const PreKernelClass kPreClassesM1[];
+extern const PreKernelClass kPreClassesM2M3[];
+extern const int kNumPreClassesM1, kNumPreClassesM2M3;
+
 // The 3-D form's persistent slice kernels (packed family without the ring; bf_tile.cuh): kernels_z_*.cu.
 // box: the range box; haar: the Haar range series' weight table (NK = 2 only).  The *_small kernels are the
 // same bounded to CTAs of at most 256 threads and *_regs registers (nullptr where they would spill);

@@ -100,6 +100,17 @@ const void *find_kernel(int m, int nk, bool ring, bool packed) {
     return nullptr;
 }
 
+// The pre-pass variant `pre` (1 fp32, 2 fp16, 3 bf16) of packed class (m, nk), nullptr where none is built.
+const void *find_pre_kernel(int m, int nk, int pre) {
+    if (pre < 1 || pre > 3) return nullptr;
+    for (const auto *t : {kPreClassesM1, kPreClassesM2M3}) {
+        const int n = t == kPreClassesM1 ? kNumPreClassesM1 : kNumPreClassesM2M3;
+        for (int i = 0; i < n; ++i)
+            if (t[i].m == m && t[i].nk == nk) return t[i].fn[pre - 1];
+    }
+    return nullptr;
+}
+
 const ZKernelClass *find_zclass(int m, int nk) {
     for (const auto *t : {kZClassesM1M2, kZClassesM3to6}) {
         const int n = t == kZClassesM1M2 ? kNumZClassesM1M2 : kNumZClassesM3to6;
@@ -397,8 +408,12 @@ std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int w
             if (tw < 8) continue;
             tw = std::min(tw, wpad);
             if (ncols > ((tw + 2 * p.rx + 31) / 32) * 32) break;  // wider tiles than the image gain nothing
-            for (int variant = 0; variant < 4; ++variant) {
-                const int ring = variant & 1, depth = 2 + (variant >> 1);
+            for (int variant = 0; variant < 8; ++variant) {
+                // variants 4..7: the basis inputs read from the pre-pass buffer in the plan's storage precision
+                const int ring = variant & 1, depth = 2 + ((variant >> 1) & 1);
+                const int pre = variant < 4 ? 0 : precision == BF_PREC_FP16 ? 2 : precision == BF_PREC_BF16 ? 3 : 1;
+                if (!pre_allowed(precision, pre)) continue;
+                if (pre && (ring || z3d || !packed || !find_pre_kernel(cls.m, cls.nk, pre))) continue;
                 if (ring && z3d) continue;
                 // the ring serves the output row too, so it must lie inside the window span
                 if (ring && !(p.vlo <= 0 && p.vhi >= 0)) continue;
@@ -416,8 +431,9 @@ std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int w
                 const int by_regs = 65536 / (regs * (ncols + kScanThreads));
                 const int cps = std::max(1, std::min({by_smem, by_threads, by_regs}));
                 // three exchange buffers save a barrier per row; the slice kernel measured no gain from them
+                // (pre-pass variants: ranked just behind the in-kernel basis of the same geometry)
                 const double edge = (ring ? 60.0 + 12.0 * (2 * p.m + 1) : 60.0 * (2 * p.m + 1)) *
-                                    (depth == 3 && !z3d ? 0.9 : 1.0);
+                                    (depth == 3 && !z3d ? 0.9 : 1.0) * (pre == 1 ? 1.02 : 1.0);
                 for (int th : {16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 1024}) {
                     const int the = std::min(th, std::max(height, 1));
                     const long ctas = (long)((width + tw - 1) / tw) * ((height + the - 1) / the) * groups;
@@ -446,6 +462,7 @@ std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int w
                     tc.depth = depth;
                     tc.packed = packed;
                     tc.smem = smem;
+                    tc.pre = pre;
                     all.push_back({cost, tc});
                     if (the >= height) break;
                 }
@@ -556,6 +573,7 @@ void fill_info(const TileConfig &tc, int height, int width, int *info, int zbins
     info[9] = tc.depth;
     info[10] = tc.ncols;
     info[11] = tc.packed;
+    info[12] = tc.pre;
 }
 
 namespace {
@@ -573,8 +591,15 @@ size_t zlist_cap(const TileConfig &tc, int height, int width, int zbins) {
 }
 }  // namespace
 
+// The pre-pass buffer of a PRE geometry: one element per pixel (16 bytes fp32, 8 bytes 16-bit), after the
+// partial planes.
+size_t pre_bytes(const TileConfig &tc, int height, int width) {
+    return tc.pre ? (size_t)(tc.pre == 1 ? 16 : 8) * height * width : 0;
+}
+
 size_t scratch_bytes(const TileConfig &tc, int height, int width, int zbins) {
     const size_t part = partial_bytes(tc, height, width);
+    if (tc.pre) return align256(part) + pre_bytes(tc, height, width);
     if (zbins <= 0) return part;
     // [partial planes][counters: 2 ints, 256 bytes reserved][items: int2 each]
     return align256(part) + 256 + sizeof(int2) * zlist_cap(tc, height, width, zbins);
@@ -652,7 +677,9 @@ bf_status launch_filter(const FilterParams &p, int precision, int kahan, const T
     (void)precision;
     (void)kahan;
     if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");
-    const void *fn = find_kernel(p.m, tc.nk, tc.ring != 0, tc.packed != 0);
+    if (tc.pre < 0 || tc.pre > 3 || (tc.pre && (!tc.packed || tc.ring || p.zbins > 0 || cache_mode)))
+        return fail(BF_ERR_INVALID_ARG, "malformed launch geometry (pre-pass variant)");
+    const void *fn = tc.pre ? find_pre_kernel(p.m, tc.nk, tc.pre) : find_kernel(p.m, tc.nk, tc.ring != 0, tc.packed != 0);
     if (!fn || tc.ncols <= 0) return fail(BF_ERR_UNSUPPORTED, "no kernel class for this plan and image");
     if (tc.threads > 512) return fail(BF_ERR_UNSUPPORTED, "horizontal reach too large for one CTA");
     // the tile body needs whole warps of column threads (its two scan warps meet on a 64-thread named
@@ -662,7 +689,7 @@ bf_status launch_filter(const FilterParams &p, int precision, int kahan, const T
         (tc.packed && tc.nk % 2 != 0))
         return fail(BF_ERR_INVALID_ARG, "malformed launch geometry");
     if (tc.smem > 227 * 1024) return fail(BF_ERR_UNSUPPORTED, "tile needs more than 227 KB of shared memory");
-    if ((tc.groups > 1 || cache_mode || p.zbins > 0) && !d_scratch)
+    if ((tc.groups > 1 || cache_mode || p.zbins > 0 || tc.pre) && !d_scratch)
         return fail(BF_ERR_INVALID_ARG, "missing scratch for grouped launch");
     if (cache_mode && !tc.packed) return fail(BF_ERR_INVALID_ARG, "the pre-computation runs the packed family");
     if (p.zbins > 0) {
@@ -680,8 +707,27 @@ bf_status launch_filter(const FilterParams &p, int precision, int kahan, const T
                   : tc.groups != (p.nr + tc.nk - 1) / tc.nk)
         return fail(BF_ERR_INVALID_ARG, "launch geometry does not match the plan's term groups");
     int mode = cache_mode ? cache_mode : tc.groups > 1 ? kModePartial : kModeFinal;
-    void *args[] = {(void *)&in, (void *)&in_pitch, (void *)&out, (void *)&out_pitch, (void *)&part, (void *)&H,
-                    (void *)&W, (void *)&tw, (void *)&th, (void *)&ncols, (void *)&depth, (void *)&mode, (void *)&pp};
+    // the pre-pass: basis inputs of every pixel, after the partial planes in the scratch
+    const void *pre = nullptr;
+    if (tc.pre) {
+        void *buf = reinterpret_cast<char *>(d_scratch) + align256(partial_bytes(tc, height, width));
+        pre = buf;
+        if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");
+        const int blocks = (int)std::max<size_t>(1, std::min<size_t>(((size_t)height * width + 255) / 256,
+                                                                    (size_t)device_sms() * 8));
+        cudaStream_t s = (cudaStream_t)stream;
+        if (tc.pre == 1)
+            bf_basis_kernel<1><<<blocks, 256, 0, s>>>(d_in, in_pitch, buf, height, width, p.inv_p, p.inv_p_lo, p.i_lo);
+        else if (tc.pre == 2)
+            bf_basis_kernel<2><<<blocks, 256, 0, s>>>(d_in, in_pitch, buf, height, width, p.inv_p, p.inv_p_lo, p.i_lo);
+        else
+            bf_basis_kernel<3><<<blocks, 256, 0, s>>>(d_in, in_pitch, buf, height, width, p.inv_p, p.inv_p_lo, p.i_lo);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "basis pre-pass launch");
+    }
+    void *args[] = {(void *)&in,  (void *)&in_pitch, (void *)&out,   (void *)&out_pitch, (void *)&part,
+                    (void *)&H,   (void *)&W,        (void *)&tw,    (void *)&th,        (void *)&ncols,
+                    (void *)&depth, (void *)&mode,   (void *)&pp,    (void *)&pre};
     e = cudaLaunchKernel(fn, grid, dim3(tc.threads), args, tc.smem, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "filter launch");
     if (tc.groups > 1 && !cache_mode) {

@@ -77,6 +77,7 @@ struct TileConfig {
     int depth;     // exchange buffers: 2 (two barriers per row) or 3 (one barrier per row)
     int packed;    // 1: packed-pair family (consecutive term groups); 0: scalar family (any term set)
     size_t smem;   // dynamic shared memory bytes
+    int pre = 0;   // basis inputs: 0 computed in the kernel; 1, 2, 3 read from a pre-pass buffer in fp32, fp16, bf16
 };
 
 // One image of a persistent batched launch (device copy).
@@ -111,8 +112,16 @@ bool kernel_class_supported(int m);
 int term_groups(const FilterParams &p, int nk);
 bool term_layout(const FilterParams &p, int nk, FilterParams &out);
 
+// Basis storage (TileConfig::pre) a plan's precision allows: fp32 plans compute the basis in the kernel or read
+// an fp32 pre-pass (the same values); 16-bit plans read the pre-pass in their format.
+inline bool pre_allowed(int precision, int pre) {
+    if (precision == BF_PREC_FP16) return pre == 2;
+    if (precision == BF_PREC_BF16) return pre == 3;
+    return pre == 0 || pre == 1;
+}
+
 // Writes the geometry record (kInfoInts ints) of bf_launch_info / bf_autotune.
-constexpr int kInfoInts = 12;
+constexpr int kInfoInts = 13;
 void fill_info(const TileConfig &tc, int height, int width, int *info, int zbins = 0);
 
 std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int width, int precision, int max_n);

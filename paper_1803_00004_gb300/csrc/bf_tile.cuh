@@ -51,6 +51,74 @@ __device__ __forceinline__ void basis_start(float v, float inv_p, float inv_p_lo
     }
 }
 
+// Basis inputs stored by the pre-pass (bf_basis_kernel) for the PRE variants of the tile body, one element per
+// pixel, [H][W]: PRE = 1: float4 (v, cos pi t, sin pi t, 0) in fp32, the values basis_start computes; PRE = 2 / 3:
+// v in fp32 and the base rotation (cos, sin)(pi t) as one fp16 / bf16 pair, 8 bytes (x = v, y = the pair's bits).
+// v is the pixel minus i_lo, t = v / P.
+template <int PRE>
+struct PreElem {
+    using T = float2;
+};
+template <>
+struct PreElem<0> {
+    using T = float;  // PRE = 0: the pixel itself; the basis is computed in the tile body
+};
+template <>
+struct PreElem<1> {
+    using T = float4;
+};
+
+// (v, cos pi t, sin pi t) from a stored element.  The 16-bit pair is rescaled to unit length, so that its
+// rounding moves only the angle (by at most ~2^-12 rad in fp16, ~2^-9 in bf16), not the magnitude that the
+// recurrence would raise to the power of the term offset.
+template <int PRE>
+__device__ __forceinline__ void pre_basis(const typename PreElem<PRE>::T &e, float &v, float &c1, float &s1) {
+    if constexpr (PRE == 1) {
+        v = e.x;
+        c1 = e.y;
+        s1 = e.z;
+    } else if constexpr (PRE >= 2) {
+        v = e.x;
+        const unsigned u = __float_as_uint(e.y);
+        float2 f;
+        if constexpr (PRE == 2) f = __half22float2(*reinterpret_cast<const __half2 *>(&u));
+        else f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u));
+        const float n2 = fmaf(f.x, f.x, f.y * f.y);
+        const float r = n2 > 0.f ? rsqrtf(n2) : 0.f;
+        c1 = f.x * r;
+        s1 = f.y * r;
+    }
+}
+
+// The starting value (cos, sin)(pi k0 t) of a term group from stored basis inputs: k0 = 0, 1 from the stored
+// base rotation; k0 >= 2 by a direct sincospi of the two-float angle (as basis_start), so every group's
+// recurrence runs at most NK - 1 steps from an fp32 anchor.  Invalid pixels start from (0, 0).
+__device__ __forceinline__ void pre_anchor(float v, float inv_p, float inv_p_lo, int k0, bool valid, float c1, float s1,
+                                           float &c0, float &s0) {
+    if (!valid) {
+        c0 = 0.f;
+        s0 = 0.f;
+    } else if (k0 == 0) {
+        c0 = 1.f;
+        s0 = 0.f;
+    } else if (k0 == 1) {
+        c0 = c1;
+        s0 = s1;
+    } else {
+        constexpr float kPiF = 3.14159265358979f;
+        const float th = v * inv_p;
+        const float tl = fmaf(v, inv_p, -th) + v * inv_p_lo;
+        const float kf = (float)k0;
+        const float kh = kf * th;
+        const float kl = fmaf(kf, th, -kh) + kf * tl;
+        float sk, ck;
+        sincospif(kh, &sk, &ck);
+        const float dk = kPiF * kl;
+        c0 = fmaf(-dk, sk, ck);
+        s0 = fmaf(dk, ck, sk);
+    }
+}
+
 // Slice of the 3-D form's z axis holding intensity v (minus i_lo): the nearest of the zbins levels,
 // rint(v zscale) in fp32 (ties to even), clamped to [0, zbins - 1].
 __device__ __forceinline__ int z_slice(float v, const FilterParams &p) {
@@ -115,13 +183,18 @@ __device__ __forceinline__ void rot2(float2 &C, float2 &S, float2 cs, float2 ss,
 //
 // The NK terms are processed as NK / 2 pairs of consecutive terms with the packed pair instructions:
 // pair p holds terms (2p, 2p + 1) of the group in the two lanes of every float2.
-template <int NK, int M, bool RING, int ZB = 0>
+// PRE > 0: the pixel and its base rotation are read from the pre-pass buffer `pre` ([H][W] elements of
+// PreElem<PRE>) instead of the input and a sincospi per window edge.
+template <int NK, int M, bool RING, int ZB = 0, int PRE = 0>
 __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__restrict__ in, size_t in_pitch,
                                           float *__restrict__ out, size_t out_pitch, float *__restrict__ part, int H,
                                           int W, int x0, int y0, int tw, int th, int ncols, int g, int mode,
-                                          int depth, float *smem, int zc = 0, const float *zw = nullptr) {
+                                          int depth, float *smem, int zc = 0, const float *zw = nullptr,
+                                          const void *__restrict__ pre = nullptr) {
     static_assert(NK % 2 == 0, "terms are processed in pairs");
     static_assert(!(ZB && RING), "the 3-D form runs without the ring");
+    static_assert(!(PRE && (ZB || RING)), "the pre-pass variants run without the ring and the slice window");
+    using PF = typename PreElem<PRE>::T;
     constexpr int NP = NK / 2;        // term pairs per group
     constexpr int NROW = M * NK * 4;  // exchange rows per image row: windows x basis images x terms
     constexpr int NE = 2 * M + 1;     // edges per step: M entering rows, M leaving rows, the output row
@@ -193,16 +266,40 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
     auto pixel = [&](int row) -> float {
         return (colv && row >= 0 && row < H) ? __ldg(in + (size_t)row * in_pitch + xcol) - p.i_lo : 0.f;
     };
+    // what an edge loads one step ahead: the pixel, or (PRE) its pre-pass element (zero outside the image)
+    auto edge_load = [&](int row) -> PF {
+        if constexpr (PRE == 0) {
+            return pixel(row);
+        } else {
+            PF z;
+            if constexpr (PRE == 1) z = make_float4(0.f, 0.f, 0.f, 0.f);
+            else z = make_float2(0.f, 0.f);
+            return (colv && row >= 0 && row < H) ? __ldg(reinterpret_cast<const PF *>(pre) + (size_t)row * W + xcol) : z;
+        }
+    };
+    // the pixel and the basis of a loaded element: v (0 when !valid), base rotation (c1, s1) and the group's
+    // starting value (c0, s0) ((0, 0) when !live)
+    auto edge_basis = [&](const PF &e, bool valid, bool live, float &v, float &c1, float &s1, float &c0, float &s0) {
+        if constexpr (PRE == 0) {
+            v = valid ? e : 0.f;
+            basis_start(v, p.inv_p, p.inv_p_lo, k0, live, c1, s1, c0, s0);
+        } else {
+            pre_basis<PRE>(e, v, c1, s1);
+            if (!valid) v = 0.f;
+            pre_anchor(v, p.inv_p, p.inv_p_lo, k0, live, c1, s1, c0, s0);
+        }
+    };
 
     // window sums at the first output row: every row of the span once
     if (is_col) {
-        float vn = pixel(y0 + p.vlo);  // the next row's pixel is loaded one iteration ahead
+        PF vn = edge_load(y0 + p.vlo);  // the next row's pixel is loaded one iteration ahead
         for (int off = p.vlo; off <= p.vhi; ++off) {
             const int row = y0 + off;
-            const float v = vn;
-            if (off < p.vhi) vn = pixel(row + 1);
+            const PF ve = vn;
+            if (off < p.vhi) vn = edge_load(row + 1);
             if (row < 0 || row >= H) continue;
-            float c1, s1, c0, s0;
+            float v, c1, s1, c0, s0;
+            if constexpr (PRE == 0) v = ve;
             bool inz = true;  // 3-D form: the neighbour's slice window (and its weight)
             float wz = 1.f;
             if (ZB) {
@@ -210,7 +307,7 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
                 inz = abs(dz) <= p.rz;
                 if (ZB == 2) wz = inz ? zw[dz + p.rz] : 0.f;
             }
-            basis_start(v, p.inv_p, p.inv_p_lo, k0, colv && inz, c1, s1, c0, s0);
+            edge_basis(ve, true, colv && inz, v, c1, s1, c0, s0);
             if (ZB == 2) {
                 c0 *= wz;
                 s0 *= wz;
@@ -250,22 +347,24 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
     auto edge_off = [&](int e) -> int { return e < M ? p.v1[e] : (e < 2 * M ? p.v0[e - M] - 1 : 0); };
     // The pixels a step needs from global memory are loaded one step ahead, so their latency overlaps the
     // previous step: RING: the row entering the ring; otherwise the 2M + 1 edge rows.
-    float pf[RING ? 1 : NE];
+    PF pf[RING ? 1 : NE];
     // ZB: bit d = the output row y - d of this column lies in slice zc (set in the column phase of row y)
     unsigned zrow = 0;
-    if (RING) {
+    if constexpr (RING) {
         pf[0] = pixel(y0 + 1 + p.vhi);
     } else {
 #pragma unroll
-        for (int e = 0; e < NE; ++e) pf[e] = e == 2 * M ? pixel(y0) : 0.f;  // at j == 0 only the output edge is live
+        for (int e = 0; e < NE; ++e)  // at j == 0 only the output edge is live
+            if (e == 2 * M) pf[e] = edge_load(y0);
+            else pf[e] = PF{};
     }
     for (int j = 0; j < nout + lag; ++j) {
         const int y = y0 + j;
         if (ZB) zrow <<= 1;
         if (is_col && j < nout) {
-            float Ie[NE];
+            PF Ie[NE];
             float vr = 0.f;
-            if (RING) {
+            if constexpr (RING) {
                 // pf[0] holds row y + vhi from step 1 on; step 0 inserts nothing
                 if (j > 0) {
                     vr = pf[0];
@@ -276,7 +375,7 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
                 for (int e = 0; e < NE; ++e) Ie[e] = pf[e];
                 if (j + 1 < nout) {
 #pragma unroll
-                    for (int e = 0; e < NE; ++e) pf[e] = pixel(y + 1 + edge_off(e));
+                    for (int e = 0; e < NE; ++e) pf[e] = edge_load(y + 1 + edge_off(e));
                 }
             }
             if (RING && j > 0) {  // the newest row of the span enters the ring
@@ -321,7 +420,7 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
                 } else {
                     // the prefetched value is 0 outside the image; `valid` also masks the rows that the
                     // sums already hold at j == 0
-                    v = valid ? Ie[e] : 0.f;
+                    if constexpr (PRE == 0) v = valid ? Ie[e] : 0.f;
                     bool live = valid;
                     float wz = 1.f;
                     if (ZB) {
@@ -333,7 +432,7 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
                             zrow |= (valid && n == zc) ? 1u : 0u;
                         }
                     }
-                    basis_start(v, p.inv_p, p.inv_p_lo, k0, live, c1, s1, c0, s0);
+                    edge_basis(Ie[e], valid, live, v, c1, s1, c0, s0);
                     if (ZB == 2 && e < 2 * M) {  // the pair starts from the anchor: scaling it scales the edge
                         c0 *= wz;
                         s0 *= wz;
@@ -543,14 +642,45 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
     }
 }
 
-template <int NK, int M, bool RING>
+template <int NK, int M, bool RING, int PRE = 0>
 __global__ void __launch_bounds__(512, 1)
 bf_fused_kernel(const float *__restrict__ in, size_t in_pitch, float *__restrict__ out, size_t out_pitch,
                 float *__restrict__ part, int H, int W, int tw, int th, int ncols, int depth, int mode,
-                const __grid_constant__ FilterParams p) {
+                const __grid_constant__ FilterParams p, const void *__restrict__ pre) {
     extern __shared__ __align__(16) float smem[];
-    tile_body<NK, M, RING>(p, in, in_pitch, out, out_pitch, part, H, W, blockIdx.x * tw, blockIdx.y * th, tw, th, ncols,
-                           blockIdx.z, mode, depth, smem);
+    tile_body<NK, M, RING, 0, PRE>(p, in, in_pitch, out, out_pitch, part, H, W, blockIdx.x * tw, blockIdx.y * th, tw, th,
+                                   ncols, blockIdx.z, mode, depth, smem, 0, nullptr, pre);
+}
+
+// The basis pre-pass of the PRE variants: per pixel, v = I - i_lo and the base rotation (cos, sin)(pi v / P) exactly
+// as the tile body computes them (basis_start), stored as PreElem<PRE> ([H][W], packed rows).  HBM-bound: 4 bytes
+// read and 16 (fp32) or 8 (16-bit) written per pixel.
+template <int PRE>
+__global__ void __launch_bounds__(256) bf_basis_kernel(const float *__restrict__ in, size_t in_pitch,
+                                                       void *__restrict__ pre, int H, int W, float inv_p,
+                                                       float inv_p_lo, float i_lo) {
+    using PF = typename PreElem<PRE>::T;
+    PF *dst = reinterpret_cast<PF *>(pre);
+    const size_t n = (size_t)H * W;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t y = i / W, x = i - y * W;
+        const float v = __ldg(in + y * in_pitch + x) - i_lo;
+        float c1, s1, c0, s0;
+        basis_start(v, inv_p, inv_p_lo, 0, true, c1, s1, c0, s0);
+        if constexpr (PRE == 1) {
+            dst[i] = make_float4(v, c1, s1, 0.f);
+        } else {
+            unsigned u;
+            if constexpr (PRE == 2) {
+                const __half2 h = __floats2half2_rn(c1, s1);
+                u = *reinterpret_cast<const unsigned *>(&h);
+            } else {
+                const __nv_bfloat162 h = __floats2bfloat162_rn(c1, s1);
+                u = *reinterpret_cast<const unsigned *>(&h);
+            }
+            dst[i] = make_float2(v, __uint_as_float(u));
+        }
+    }
 }
 
 // Persistent batched form: each CTA repeatedly takes the next work item from
@@ -671,6 +801,10 @@ constexpr const void *zbox_small_kernel() {  // within 8 bytes of spill at 80 re
 #define BF_ZCLASS(M, NK)                                                                              \
     {M, NK, (const void *)bf_zslice_kernel<NK, M, 1>, zbox_small_kernel<NK, M>(), zhaar_kernel<NK, M>(), \
      zhaar_small_kernel<NK, M>(), zhaar_mid_kernel<NK, M>(), kZSmallRegs[1], kZSmallRegs[2]}
+
+#define BF_PRE_CLASS(M, NK)                                                                          \
+    {M, NK, {(const void *)bf_fused_kernel<NK, M, false, 1>, (const void *)bf_fused_kernel<NK, M, false, 2>, \
+             (const void *)bf_fused_kernel<NK, M, false, 3>}}
 
 #define BF_CLASS(M, NK)                                                                                 \
     {M, NK, {(const void *)bf_fused_kernel<NK, M, false>, (const void *)bf_fused_kernel<NK, M, true>},  \

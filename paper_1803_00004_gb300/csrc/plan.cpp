@@ -394,9 +394,9 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
         return fail(BF_ERR_INVALID_ARG, "the Haar range series runs on the slice axis of BF_RANGE_PAPER_3D");
     if (d.precision < BF_PREC_FP32 || d.precision > BF_PREC_FP16)
         return fail(BF_ERR_INVALID_ARG, "unknown precision");
-    if (d.precision != BF_PREC_FP32)
-        return fail(BF_ERR_UNSUPPORTED, "plans are fp32 (the fused kernel stores no basis image); 16-bit storage "
-                                        "applies to the pre-computation cache (bf_precompute)");
+    if (d.precision != BF_PREC_FP32 && d.policy == BF_RANGE_PAPER_3D)
+        return fail(BF_ERR_UNSUPPORTED, "16-bit basis storage applies to the collapsed range policies; the 3-D form "
+                                        "is fp32");
 
     p.desc = d;
     const double dI = (double)d.i_hi - (double)d.i_lo;

@@ -130,8 +130,14 @@ bf_status bf_precompute(const bf_plan *plan, const float *d_in, size_t in_pitch,
         pv.k[i] = i;
         pv.a[i] = 1.f;
     }
-    // the cost model's packed-family geometry (consecutive frequencies: every candidate is packed)
-    TileConfig tc = model_tile(pv, height, width, plan->desc.precision);
+    // the cost model's best packed-family geometry (consecutive frequencies: every candidate is packed) that
+    // computes its basis in the kernel (the cache modes have no pre-pass variant)
+    TileConfig tc{};
+    for (const auto &c : tile_candidates(pv, height, width, BF_PREC_FP32, 1 << 20))
+        if (c.pre == 0) {
+            tc = c;
+            break;
+        }
     bf_cache *c = nullptr;
     if (tc.ncols == 0 || !tc.packed) st = fail(BF_ERR_UNSUPPORTED, "no launch geometry for the pre-computation");
     if (st == BF_OK) {

@@ -49,9 +49,9 @@ void load_locked() {
     int k[10];
     TileConfig tc;
     unsigned long smem;
-    while (std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %lu", &k[0], &k[1], &k[2], &k[3], &k[4],
-                       &k[5], &k[6], &k[7], &k[8], &k[9], &tc.tw, &tc.th, &tc.ncols, &tc.threads, &tc.nk, &tc.groups,
-                       &tc.ring, &tc.depth, &tc.packed, &smem) == 20) {
+    while (std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %lu %d", &k[0], &k[1], &k[2], &k[3],
+                       &k[4], &k[5], &k[6], &k[7], &k[8], &k[9], &tc.tw, &tc.th, &tc.ncols, &tc.threads, &tc.nk,
+                       &tc.groups, &tc.ring, &tc.depth, &tc.packed, &smem, &tc.pre) == 21) {
         tc.smem = smem;
         g_table[Key{k[0], k[1], k[2], k[3], k[4], k[5], k[6], k[7], k[8], k[9]}] = tc;
     }
@@ -63,10 +63,10 @@ void save_locked(const Key &key, const TileConfig &tc) {
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %lu\n", std::get<0>(key), std::get<1>(key),
-                 std::get<2>(key), std::get<3>(key), std::get<4>(key), std::get<5>(key), std::get<6>(key),
-                 std::get<7>(key), std::get<8>(key), std::get<9>(key), tc.tw, tc.th, tc.ncols, tc.threads, tc.nk, tc.groups, tc.ring,
-                 tc.depth, tc.packed, (unsigned long)tc.smem);
+    std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %lu %d\n", std::get<0>(key),
+                 std::get<1>(key), std::get<2>(key), std::get<3>(key), std::get<4>(key), std::get<5>(key),
+                 std::get<6>(key), std::get<7>(key), std::get<8>(key), std::get<9>(key), tc.tw, tc.th, tc.ncols,
+                 tc.threads, tc.nk, tc.groups, tc.ring, tc.depth, tc.packed, (unsigned long)tc.smem, tc.pre);
     std::fclose(f);
 }
 
@@ -104,7 +104,7 @@ std::vector<TileConfig> timed_candidates(const FilterParams &p, int height, int 
     std::map<std::tuple<int, int, int>, int> per_class;
     for (const auto &c : ranked) {
         const int res = (int)std::min<size_t>(3, (size_t)smem_sm / (c.smem + 1024));  // 1 KiB reserved per CTA
-        if (per_class[std::make_tuple(c.ring * 4 + c.depth + 8 * c.packed, c.nk, res)]++ < 4) out.push_back(c);
+        if (per_class[std::make_tuple(c.ring * 4 + c.depth + 8 * c.packed + 16 * c.pre, c.nk, res)]++ < 4) out.push_back(c);
     }
     return out;
 }
@@ -119,7 +119,8 @@ TileConfig choose_tile(const FilterParams &p, int height, int width, int precisi
         // an entry stays usable only while its term grouping matches the library's current layout
         if (it != g_table.end() &&
             it->second.groups == (it->second.packed ? term_groups(p, it->second.nk) : (p.nr + it->second.nk - 1) / it->second.nk) &&
-            (p.zbins == 0 || (it->second.packed && !it->second.ring)))
+            (p.zbins == 0 || (it->second.packed && !it->second.ring)) && pre_allowed(precision, it->second.pre) &&
+            (it->second.pre == 0 || (it->second.packed && !it->second.ring && p.zbins == 0)))
             return it->second;
     }
     return model_tile(p, height, width, precision);
@@ -408,7 +409,7 @@ extern "C" bf_status bf_set_launch(const bf_plan *plan, int height, int width, c
         fill_info(c, height, width, got, plan->kp.zbins);
         // the fields a caller chooses; the rest (threads, launches, bytes) follow from them
         if (got[0] == info[0] && got[1] == info[1] && got[3] == info[3] && got[8] == info[8] && got[9] == info[9] &&
-            got[10] == info[10] && got[11] == info[11]) {
+            got[10] == info[10] && got[11] == info[11] && got[12] == info[12]) {
             remember_tile(plan->kp, height, width, plan->desc.precision, c);
             return BF_OK;
         }

@@ -142,7 +142,7 @@ def test_haar_range_plan_matches_oracle(kw, Z):
     (dict(i_lo=1.0, i_hi=1.0), 1), (dict(policy=bf.RANGE_PAPER_3D, z_bins=1), 1),
     (dict(policy=bf.RANGE_PAPER_3D, z_bins=4097), 1), (dict(policy=5), 1),
     (dict(spatial=bf.KERNEL_EXPONENTIAL, sigma_s=100.0), 2),
-    (dict(spatial=7), 1), (dict(precision=9), 1), (dict(radius=-2), 1), (dict(precision=bf.PREC_BF16), 2), (dict(precision=bf.PREC_FP16), 2),
+    (dict(spatial=7), 1), (dict(precision=9), 1), (dict(radius=-2), 1), (dict(precision=bf.PREC_BF16, policy=bf.RANGE_PAPER_3D), 2), (dict(precision=bf.PREC_FP16, policy=bf.RANGE_PAPER_3D), 2),
 ])
 def test_plan_create_rejects(kw, status):
     with pytest.raises(bf.BFError) as ei:
@@ -300,7 +300,7 @@ print(json.dumps(out))
     written, read = json.loads(w.stdout), json.loads(r.stdout)
     assert written == read
     lines = cache.read_text().splitlines()
-    assert len(lines) == 3 and all(len(x.split()) == 20 for x in lines)
+    assert len(lines) == 3 and all(len(x.split()) == 21 for x in lines)
     fresh = json.loads(subprocess.run([sys.executable, "-c", code, "read"], env=dict(os.environ, PYTHONPATH=ROOT),
                                       capture_output=True, text=True, check=True).stdout)
     assert fresh != read                               # without the file: the cost model's choice
@@ -399,3 +399,19 @@ def test_random_plans_match_oracle(kw):
         for h, (u0, u1) in enumerate(c["hwin"]):
             rec[v0 + R:v1 + R + 1, u0 + R:u1 + R + 1] += c["wcoef"][v][h]
     assert np.max(np.abs(rec - K[::-1, ::-1])) < 1e-12 * max(1.0, np.max(np.abs(K)))
+
+
+def test_basis_storage_of_the_geometries_follows_the_precision():
+    """fp32 plans compute the basis in the kernel or read an fp32 pre-pass; fp16 / bf16 plans (16-bit basis
+    storage) read the pre-pass in their format, in the packed family without the ring."""
+    for prec, allowed in ((bf.PREC_FP32, {0, 1}), (bf.PREC_FP16, {2}), (bf.PREC_BF16, {3})):
+        plan = bf.Plan(device=-1, sigma_s=8.0, precision=prec)
+        cands = bf.bf_launch_candidates(plan, 1080, 1920)
+        seen = {c["pre"] for c in cands}
+        assert seen == allowed, (prec, seen)
+        assert all(c["packed"] == 1 and c["ring"] == 0 for c in cands if c["pre"])
+        info = bf.bf_launch_info(plan, 1080, 1920)
+        assert info["pre"] in allowed
+        # the pre-pass buffer is scratch: 16 bytes per pixel in fp32, 8 in 16 bits
+        if info["pre"]:
+            assert info["scratch_kib"] * 1024 >= (16 if info["pre"] == 1 else 8) * 1080 * 1920 - 1024

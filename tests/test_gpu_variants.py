@@ -24,7 +24,7 @@ def cuda():
 
 
 def family(c):
-    return (c["packed"], c["ring"], c["depth"], c["nk"])
+    return (c["packed"], c["ring"], c["depth"], c["nk"], c["pre"])
 
 
 CASES = [
