@@ -251,6 +251,46 @@ void rank(std::vector<Cand> &v) {
     }
 }
 
+// rank() restricted to what a best-`need` selection reads: afterwards v[0 .. need] (as far as v reaches) hold
+// the entries rank() would put there, in its order; the rest of v is unspecified.  The top entries are
+// selected by partial sorting, widened until the tie group that holds position `need` lies inside.
+void rank_top(std::vector<Cand> &v, size_t need) {
+    double mx = 0;
+    for (auto &e : v) mx = std::max(mx, e.mag);
+    v.erase(std::remove_if(v.begin(), v.end(), [&](const Cand &e) { return !(e.mag > 0) || e.mag < 1e-14 * mx; }),
+            v.end());
+    auto better = [](const Cand &x, const Cand &y) {
+        if (x.mag != y.mag) return x.mag > y.mag;
+        return key_less(x, y);
+    };
+    size_t k = std::min(v.size(), need + 64);
+    for (;;) {
+        std::partial_sort(v.begin(), v.begin() + k, v.end(), better);
+        if (k == v.size()) break;
+        // greedy tie groups over the sorted prefix (rank()'s rule); the group holding `need` must end before k
+        size_t i = 0, end = 0;
+        while (i < k) {
+            size_t j = i + 1;
+            while (j < k && v[j].mag >= v[i].mag * (1.0 - 1e-12)) ++j;
+            if (i <= need && need < j) {
+                end = j;
+                break;
+            }
+            i = j;
+        }
+        if (end != 0 && end < k) break;
+        k = std::min(v.size(), 2 * k);
+    }
+    size_t i = 0;
+    while (i < k) {
+        size_t j = i + 1;
+        while (j < k && v[j].mag >= v[i].mag * (1.0 - 1e-12)) ++j;
+        std::sort(v.begin() + i, v.begin() + j, key_less);
+        if (i > need) break;
+        i = j;
+    }
+}
+
 // ---------------------------------------------------------------- windows
 
 // Splits a set of 1-D profiles p_i(d), d in [-R, R], into shared windows:
@@ -432,14 +472,48 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
         const int ncand = 20 * d.nr_terms;
         double L = std::min(p.Tr, p.P);
         if (d.range == BF_KERNEL_BOX) L = std::min(L, d.sigma_r);
+        // One composite 20-point Gauss-Legendre node set on [0, L] with at most one period of the highest
+        // candidate frequency per piece (the rule's error there is ~1e-28 relative), 4 + k_max L / (2 P) pieces,
+        // serves every candidate: a_k = (2 - [k = 0]) / P sum_i w_i K_r(t_i)
+        // cos(pi k t_i / P).  cos(k theta_i) comes from the angle-addition recurrence over k, all nodes at once,
+        // re-anchored by a direct cos / sin every 16 frequencies so its rounding stays within ~16 ulp.
+        const GaussLegendre &gq = gl20();
+        const int pieces = L > 0 ? 4 + (int)std::ceil(0.5 * (ncand - 1) * L / p.P) : 0;
+        const int ng = (int)gq.x.size(), nn = pieces * ng;
+        std::vector<double> f(nn), th(nn), c1(nn), s1(nn), ck(nn), sk(nn);
+        const double hq = pieces > 0 ? L / pieces : 0.0;
+        for (int q = 0; q < pieces; ++q) {
+            const double lo = q * hq, hi = (q == pieces - 1) ? L : lo + hq;
+            const double c = 0.5 * (lo + hi), r = 0.5 * (hi - lo);
+            for (int i = 0; i < ng; ++i) {
+                const double t = c + r * gq.x[i];
+                f[q * ng + i] = r * gq.w[i] * (d.range == BF_KERNEL_BOX ? 1.0 : range_value(d.range, d.sigma_r, t));
+                th[q * ng + i] = kPi * t / p.P;
+            }
+        }
+        for (int n = 0; n < nn; ++n) {
+            c1[n] = std::cos(th[n]);
+            s1[n] = std::sin(th[n]);
+        }
+        std::vector<double> acc(ncand, 0.0);
+        for (int k = 0; k < ncand; ++k) {
+            if (k % 16 == 0)
+                for (int n = 0; n < nn; ++n) {
+                    ck[n] = k == 0 ? 1.0 : std::cos(k * th[n]);
+                    sk[n] = k == 0 ? 0.0 : std::sin(k * th[n]);
+                }
+            double a = 0.0;
+            for (int n = 0; n < nn; ++n) a += f[n] * ck[n];
+            acc[k] = a;
+            for (int n = 0; n < nn; ++n) {
+                const double cn = ck[n] * c1[n] - sk[n] * s1[n];
+                sk[n] = sk[n] * c1[n] + ck[n] * s1[n];
+                ck[n] = cn;
+            }
+        }
         std::vector<Cand> rc(ncand);
         for (int k = 0; k < ncand; ++k) {
-            double w = kPi * k / p.P;
-            int pieces = 4 + (int)std::ceil(2.0 * k * L / p.P);
-            double s = integrate(
-                [&](double t) { return (d.range == BF_KERNEL_BOX ? 1.0 : range_value(d.range, d.sigma_r, t)) * std::cos(w * t); },
-                0.0, L, pieces);
-            double ak = (k == 0 ? 1.0 : 2.0) * s / p.P;
+            double ak = (k == 0 ? 1.0 : 2.0) * acc[k] / p.P;
             rc[k] = Cand{std::fabs(ak), ak, {k, 0, 0, 0, 0}, k, 0};
         }
         rank(rc);
@@ -475,15 +549,32 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
         if (p.J > 9) return fail(BF_ERR_UNSUPPORTED, "radius too large for the non-separable spatial kernel (R <= 255)");
         c2 = haar2d_radial_exp(dict, d.sigma_s, p.Ts, p.J);
     }
+    // 2-D candidates.  Separable kernels: the coefficient of (i1, i2) is c1[i1] c1[i2], so with the 1-D
+    // magnitudes sorted descending, a_1 >= a_2 >= ..., every product outside the top-K1 block is at most
+    // a_1 a_{K1+1}, while the block holds K1 products >= a_1 a_{K1}.  With K1 > N_s and a_{K1+1} below the
+    // tie threshold of a_{K1}, the best N_s terms and the whole tie group at the cut lie in the block, so
+    // only its K1^2 pairs are ranked.  Non-separable kernels rank every pair.
+    std::vector<int> top(n1);
+    for (int i = 0; i < n1; ++i) top[i] = i;
+    int k1 = n1;
+    if (c2.empty()) {
+        std::sort(top.begin(), top.end(), [&](int x, int y) {
+            const double ax = std::fabs(c1[x]), ay = std::fabs(c1[y]);
+            return ax != ay ? ax > ay : x < y;
+        });
+        k1 = std::min(n1, d.ns_terms + 2);
+        while (k1 < n1 && std::fabs(c1[top[k1]]) >= std::fabs(c1[top[k1 - 1]]) * (1.0 - 1e-12)) ++k1;
+    }
     std::vector<Cand> sc;
-    sc.reserve((size_t)n1 * n1);
-    for (int i1 = 0; i1 < n1; ++i1)
-        for (int i2 = 0; i2 < n1; ++i2) {
+    sc.reserve((size_t)k1 * k1);
+    for (int a = 0; a < k1; ++a)
+        for (int b = 0; b < k1; ++b) {
+            const int i1 = top[a], i2 = top[b];
             double c = c2.empty() ? c1[i1] * c1[i2] : c2[(size_t)i2 * n1 + i1];
             int j1 = dict[i1].lev, j2 = dict[i2].lev;
             sc.push_back(Cand{std::fabs(c), c, {std::max(j1, j2), j1, j2, dict[i1].k, dict[i2].k}, i1, i2});
         }
-    rank(sc);
+    rank_top(sc, (size_t)d.ns_terms);
     int ns = std::min<int>(d.ns_terms, (int)sc.size());
     p.tie_split = (ns < (int)sc.size() && sc[ns].mag >= sc[ns - 1].mag * (1.0 - 1e-12)) ? 1 : 0;
     const int R = p.R, w = 2 * R + 1;
@@ -562,8 +653,16 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
     // the 3-D form keeps the series only inside the range box [-T_r, T_r]
     const double tspan = d.policy == BF_RANGE_PAPER_3D ? std::min(dI, p.Tr) : dI;
     for (int i = 0; !haar_range && i <= 4000; ++i) {
+        // cos(pi k t / P) for k = 0 .. k_max by the angle-addition recurrence (a report: ~k_max ulp is ample)
         double t = -tspan + 2.0 * tspan * i / 4000.0, s = 0;
-        for (size_t j = 0; j < p.k.size(); ++j) s += p.a[j] * std::cos(kPi * p.k[j] * t / p.P);
+        const double th = kPi * t / p.P, cth = std::cos(th), sth = std::sin(th);
+        double ck = 1.0, sk = 0.0;
+        for (int k = 0, j = 0; j < (int)p.k.size(); ++k) {
+            if (p.k[j] == k) s += p.a[j++] * ck;
+            const double cn = ck * cth - sk * sth;
+            sk = sk * cth + ck * sth;
+            ck = cn;
+        }
         p.range_max_err = std::max(p.range_max_err, std::fabs(s - range_value(d.range, d.sigma_r, t)));
     }
     p.spatial_max_err = 0;
