@@ -726,63 +726,102 @@ def run_batched(bf, dev, n=512, lo=64, hi=2048, reps=3):
             "sequential_mpix_s": round(px / (t_seq * 1e-3) / 1e6, 1), "sequential_ms": round(t_seq, 3)}
 
 
-def run_serving(bf, dev, n=96, lo=128, hi=4096, loads=(0.25, 0.5, 0.8, 1.0, 1.2)):
-    """Config 5: Poisson streams at each `load` x the measured saturation rate through the
-    continuous-batching server (pinned host buffers; sides log-uniform 128..4096, mixed kernels as
-    in config 4): p50/p99 latency and Mpixel/s per load; plus the plain per-image path (H2D,
-    bf_filter, D2H, one request at a time) on the same requests."""
+def run_serving(bf, dev, n=1000, lo=128, hi=4096, loads=(0.25, 0.5, 0.8, 1.0, 1.2), n_img=64, copies=3):
+    """Config 5: Poisson streams at each `load` x the measured saturation rate through the continuous-batching
+    server (pinned host buffers; sides log-uniform 128..4096; every request draws fresh parameters as in
+    config 4, sigma_s ~ U[2,32], sigma_r ~ U[0.05,0.3], Gaussian or exponential range kernel, N_r in {8,16},
+    so its plan is built inside its latency).  n requests per load point over n_img distinct images, each
+    with `copies` output buffers reused in turn (a request waits for the one that last used its buffer).
+    p50 / p99 latency, plan and queue time and Mpixel/s per load; plus the plain per-image path on the same
+    requests (plan build, H2D, bf_filter, D2H on one stream, one request after another)."""
     import torch
-    work = mixed_requests(n, lo, hi, seed=4321)
-    hin = [torch.from_numpy(img).pin_memory() for img, _ in work]
-    hout = [torch.empty_like(x).pin_memory() for x in hin]
-    descs = [bf.desc(**kw) for _, kw in work]
-    px = sum(img.size for img, _ in work)
-    srv = bf.Server(device=dev.index or 0, max_slots=32, n_streams=4, max_batch=8)
+    from paper_1803_00004_gb300 import synth
+    sizes = synth.batch_sizes(n_img, lo, hi, seed=4321)
+    imgs = [synth.shapes(sz, sz, seed=4321 * 7919 + i, scale=sz / 1080.0) for i, sz in enumerate(sizes)]
+    hin = [torch.from_numpy(im).pin_memory() for im in imgs]
+    hout = [[torch.empty_like(x).pin_memory() for _ in range(copies)] for x in hin]
+    srv = bf.Server(device=dev.index or 0, max_slots=64, n_streams=4, max_batch=8, plan_threads=6)
+    rng = np.random.default_rng(7)
 
-    def burst(delays):
+    def fresh(m):
+        return [bf.desc(sigma_s=float(rng.uniform(2, 32)), sigma_r=float(rng.uniform(0.05, 0.3)),
+                        range=int(rng.integers(0, 2)), nr_terms=int(rng.choice([8, 16])), ns_terms=NS)
+                for _ in range(m)]
+
+    def stream_of(descs, delays):
+        """Submits descs[i] on image i mod n_img at the given inter-arrival delays; returns the wall time
+        from the first submission to the last result, and the results."""
+        res = [None] * len(descs)
+        owner = {}
         t0 = time.perf_counter()
+        t_next = t0
         tickets = []
-        for d, (img, _), hi_, ho in zip(descs, work, hin, hout):
-            if delays is not None:
-                time.sleep(delays.pop())
-            tickets.append(srv.submit(d, hi_.data_ptr(), ho.data_ptr(), img.shape[0], img.shape[1]))
-        lat = []
-        for t in tickets:
-            st, r = srv.poll(t, -1)
+
+        def collect(i):
+            st, r = srv.poll(tickets[i], -1)
             if st != 0 or r.status != 0:
                 raise RuntimeError("serving request failed: %d/%d" % (st, r.status))
-            lat.append(r.latency_ms)
-        return time.perf_counter() - t0, lat
+            res[i] = (r.latency_ms, r.plan_ms, r.queue_ms)
 
-    burst(None)                                   # warm-up (plans, memory pool)
-    t_sat, _ = burst(None)                        # saturation: all requests at once
-    rng = np.random.default_rng(7)
+        for i, d in enumerate(descs):
+            j, c = i % n_img, (i // n_img) % copies
+            prev = owner.get((j, c))
+            if prev is not None and res[prev] is None:
+                collect(prev)                         # its output buffer is needed again
+            if delays is not None:
+                t_next += delays[i]
+                wait = t_next - time.perf_counter()
+                if wait > 0:
+                    time.sleep(wait)
+            im = imgs[j]
+            tickets.append(srv.submit(d, hin[j].data_ptr(), hout[j][c].data_ptr(), im.shape[0], im.shape[1]))
+            owner[(j, c)] = i
+        for i in range(len(descs)):
+            if res[i] is None:
+                collect(i)
+        return time.perf_counter() - t0, res
+
+    px_of = lambda m: sum(imgs[i % n_img].size for i in range(m))
+    stream_of(fresh(min(n, 200)), None)          # warm-up
+    n_sat = min(n, 400)
+    t_sat, _ = stream_of(fresh(n_sat), None)     # saturation: every request at once
+    rate_sat = n_sat / t_sat
     by_load = []
     for load in loads:
-        rate = load * n / t_sat                   # requests/s
-        delays = list(rng.exponential(1.0 / rate, n))[::-1]
-        t_run, lat = burst(delays)
-        by_load.append({"load": load, "rate_req_s": round(rate, 1),
+        rate = load * rate_sat
+        t_run, res = stream_of(fresh(n), list(rng.exponential(1.0 / rate, n)))
+        lat = np.array([r[0] for r in res])
+        by_load.append({"load": load, "rate_req_s": round(rate, 1), "requests": n,
                         "p50_ms": round(float(np.percentile(lat, 50)), 3),
-                        "p99_ms": round(float(np.percentile(lat, 99)), 3), "mpix_s": round(px / t_run / 1e6, 1)})
+                        "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                        "plan_ms_mean": round(float(np.mean([r[1] for r in res])), 3),
+                        "queue_ms_p50": round(float(np.percentile([r[2] for r in res], 50)), 3),
+                        "mpix_s": round(px_of(n) / t_run / 1e6, 1)})
     srv.close()
-    # plain per-image path
-    plans = [bf.Plan(d) for d in descs]
+    # the plain per-image path on fresh requests: plan build, upload, filter, download, one after another
+    descs = fresh(n)
     stream = torch.cuda.current_stream(dev)
-    d_in = [torch.empty(img.shape, dtype=torch.float32, device=dev) for img, _ in work]
+    d_in = [torch.empty(im.shape, dtype=torch.float32, device=dev) for im in imgs]
     d_out = [torch.empty_like(x) for x in d_in]
+    keep = []
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for p, hi_, ho, di, do in zip(plans, hin, hout, d_in, d_out):
-        di.copy_(hi_, non_blocking=True)
-        bf.bf_filter(p, di, do, stream=stream)
-        ho.copy_(do, non_blocking=True)
-        torch.cuda.synchronize()
+    for i, d in enumerate(descs):
+        j = i % n_img
+        p = bf.Plan(d)
+        keep.append(p)
+        d_in[j].copy_(hin[j], non_blocking=True)
+        bf.bf_filter(p, d_in[j], d_out[j], stream=stream)
+        hout[j][0].copy_(d_out[j], non_blocking=True)
+    torch.cuda.synchronize()
     t_plain = time.perf_counter() - t0
     at = next(r for r in by_load if r["load"] == 0.8)
-    return {"requests": n, "sides": [lo, hi], "megapixels": round(px / 1e6, 1), "load": 0.8,
-            "p50_ms": at["p50_ms"], "p99_ms": at["p99_ms"], "mpix_s": at["mpix_s"],
-            "saturation_mpix_s": round(px / t_sat / 1e6, 1), "plain_per_image_mpix_s": round(px / t_plain / 1e6, 1),
-            "by_load": by_load}
+    return {"requests_per_load": n, "distinct_images": n_img, "sides": [lo, hi], "megapixels_per_load": round(px_of(n) / 1e6, 1),
+            "fresh_parameters": True, "latency_includes": "plan build (host FP64 fit on the server's plan threads), "
+            "queueing, H2D, the batched launch and D2H",
+            "load": 0.8, "p50_ms": at["p50_ms"], "p99_ms": at["p99_ms"], "mpix_s": at["mpix_s"],
+            "saturation_mpix_s": round(px_of(n_sat) / t_sat / 1e6, 1),
+            "plain_per_image_mpix_s": round(px_of(n) / t_plain / 1e6, 1), "by_load": by_load}
 
 
 def cpu_baseline(img, rows: int = 1080, combos=None, reps: int = 3, extras: bool = True):

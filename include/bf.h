@@ -419,35 +419,61 @@ bf_status bf_exact_lut(const float *d_in, size_t in_pitch_bytes, float *d_out, s
 typedef struct bf_server bf_server;
 
 typedef struct {
-    size_t hbm_budget_bytes;    /* device bytes the server may hold for request buffers; 0 -> 1/2 of free */
+    size_t hbm_budget_bytes;    /* device bytes of the server's arena, reserved once at creation (one
+                                   cudaMalloc) and shared out to admitted requests; 0 -> 1/4 of the free
+                                   device memory, at most 16 GiB */
     int max_slots;              /* requests resident on the device at once; 0 -> 64 */
     int n_streams;              /* CUDA streams the server launches on; 0 -> 4 */
     int device;                 /* CUDA device ordinal */
     int max_batch;              /* requests merged into one batched launch; 0 -> 16 */
+    int plan_threads;           /* host threads building plans for new parameters; 0 -> 4 */
 } bf_serve_config;
 
+/* Where a request's images live. */
+typedef enum {
+    BF_MEM_DEVICE = 0,  /* device memory of the server's device, caller-owned: the server filters in to out */
+    BF_MEM_HOST = 1     /* host memory (pinned recommended): the server copies through its arena */
+} bf_memory;
+
 typedef struct {
-    bf_plan_desc desc;          /* filter parameters; plans are cached by value */
-    const float *h_in;          /* host input (pinned memory recommended), row-major, packed */
-    float *h_out;               /* host output, row-major, packed */
+    bf_plan_desc desc;          /* filter parameters (the device field is ignored); plans are built by the
+                                   server's plan thread and cached by value */
+    const float *in;            /* input, height rows of width floats, row pitch in_pitch_bytes */
+    size_t in_pitch_bytes;      /* a multiple of 4, >= width * 4 */
+    float *out;                 /* output, same shape, row pitch out_pitch_bytes; must not overlap in */
+    size_t out_pitch_bytes;
     int height, width;
+    int memory;                 /* bf_memory of in and out */
 } bf_request;
 
 typedef struct {
-    int status;                 /* bf_status of the request */
-    double latency_ms;          /* submit -> result on host */
-    double queue_ms;            /* submit -> admitted */
-    double device_ms;           /* device time of the request's launch group */
+    int status;                 /* bf_status of the request (plan errors included) */
+    uint64_t latency_ns;        /* submit -> the result in out (device) or copied to the host buffer */
+    uint64_t queue_ns;          /* submit -> admitted: the plan build or cache look-up plus the wait for
+                                   arena memory and a slot */
+    uint64_t plan_ns;           /* the plan build or cache look-up (part of queue_ns) */
+    uint64_t device_ns;         /* device time of the launch group that ran the request (copies included) */
 } bf_result;
 
 /* Starts a server thread for one device.  Errors: BF_ERR_INVALID_ARG,
  * BF_ERR_NO_DEVICE, BF_ERR_CUDA, BF_ERR_OOM. */
 bf_status bf_serve_create(const bf_serve_config *cfg, bf_server **out);
 
-/* Queues a request; never waits for GPU work.  The host buffers must stay
- * valid until the request's result has been polled.  Errors:
- * BF_ERR_INVALID_ARG, BF_ERR_ADMISSION (larger than the whole budget),
- * plan errors of bf_plan_create. */
+/* Queues a request and returns its ticket; never waits for GPU work or for
+ * the plan: the request's plan is built (or found in the server's cache) by
+ * one of the server's plan threads after submission, inside the request's
+ * latency.
+ * The request is admitted, in order of readiness, once its plan exists and
+ * the arena has room for its buffers (host requests: staging for in and out;
+ * every request: its share of the batched launch's parameters, work list
+ * and partial planes) and a slot is free; admitted requests are merged into
+ * batched launches on the server's streams.  The buffers must stay valid
+ * until the result has been polled.  Errors at submission:
+ * BF_ERR_INVALID_ARG (NULL, bad image or pitch, overlap, unknown memory),
+ * BF_ERR_UNSUPPORTED (BF_RANGE_PAPER_3D), BF_ERR_ADMISSION (the staging alone
+ * exceeds the arena).  Plan errors, and a request whose buffers exceed the
+ * arena once its plan is known (BF_ERR_ADMISSION), are reported by poll in
+ * the result's status. */
 bf_status bf_serve_submit(bf_server *server, const bf_request *req, uint64_t *ticket);
 
 /* Waits up to timeout_ms (0: just check; < 0: wait without limit) for a

@@ -14,4 +14,5 @@ from ._binding import (KERNEL_GAUSSIAN, KERNEL_EXPONENTIAL, KERNEL_BOX, RANGE_TR
                        RANGE_UNTRUNCATED_FULL, RANGE_PAPER_3D, SERIES_COSINE, SERIES_HAAR, PREC_FP32, PREC_BF16,
                        PREC_FP16)
 from ._binding import (OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA, ERR_ADMISSION, ERR_TIMEOUT,  # noqa: F401
-                       ERR_DEVICE_TIMEOUT, ERR_RANGE, ERR_NO_DEVICE, ERR_NOT_FOUND, ERR_CANCELLED, ERR_SCRATCH)
+                       ERR_DEVICE_TIMEOUT, ERR_RANGE, ERR_NO_DEVICE, ERR_NOT_FOUND, ERR_CANCELLED, ERR_SCRATCH,
+                       MEM_DEVICE, MEM_HOST)

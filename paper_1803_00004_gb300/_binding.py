@@ -51,16 +51,26 @@ class bf_image(C.Structure):
 
 class bf_serve_config(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_slots", C.c_int), ("n_streams", C.c_int),
-                ("device", C.c_int), ("max_batch", C.c_int)]
+                ("device", C.c_int), ("max_batch", C.c_int), ("plan_threads", C.c_int)]
+
+
+MEM_DEVICE, MEM_HOST = 0, 1
 
 
 class bf_request(C.Structure):
-    _fields_ = [("desc", bf_plan_desc), ("h_in", C.c_void_p), ("h_out", C.c_void_p), ("height", C.c_int),
-                ("width", C.c_int)]
+    _fields_ = [("desc", bf_plan_desc), ("in_", C.c_void_p), ("in_pitch_bytes", C.c_size_t), ("out", C.c_void_p),
+                ("out_pitch_bytes", C.c_size_t), ("height", C.c_int), ("width", C.c_int), ("memory", C.c_int)]
 
 
 class bf_result(C.Structure):
-    _fields_ = [("status", C.c_int), ("latency_ms", C.c_double), ("queue_ms", C.c_double), ("device_ms", C.c_double)]
+    _fields_ = [("status", C.c_int), ("latency_ns", C.c_uint64), ("queue_ns", C.c_uint64), ("plan_ns", C.c_uint64),
+                ("device_ns", C.c_uint64)]
+
+    # milliseconds, for convenience
+    latency_ms = property(lambda self: self.latency_ns * 1e-6)
+    queue_ms = property(lambda self: self.queue_ns * 1e-6)
+    plan_ms = property(lambda self: self.plan_ns * 1e-6)
+    device_ms = property(lambda self: self.device_ns * 1e-6)
 
 
 EXPORTS = ["bf_plan_desc_default", "bf_plan_create", "bf_plan_destroy", "bf_coeffs", "bf_launch_info", "bf_autotune",
@@ -392,14 +402,17 @@ def bf_debug_range_checks(on: bool) -> None:
 class Server:
     """Owns a bf_server* (continuous-batching request loop on one device)."""
 
-    def __init__(self, hbm_budget_bytes=0, max_slots=0, n_streams=0, device=0, max_batch=0):
-        cfg = bf_serve_config(hbm_budget_bytes, max_slots, n_streams, device, max_batch)
+    def __init__(self, hbm_budget_bytes=0, max_slots=0, n_streams=0, device=0, max_batch=0, plan_threads=0):
+        cfg = bf_serve_config(hbm_budget_bytes, max_slots, n_streams, device, max_batch, plan_threads)
         h = C.c_void_p()
         _check(lib().bf_serve_create(C.byref(cfg), C.byref(h)), "bf_serve_create")
         self._h = h
 
-    def submit(self, d: bf_plan_desc, h_in_ptr: int, h_out_ptr: int, height: int, width: int) -> int:
-        req = bf_request(d, h_in_ptr, h_out_ptr, height, width)
+    def submit(self, d: bf_plan_desc, in_ptr: int, out_ptr: int, height: int, width: int, in_pitch: int = 0,
+               out_pitch: int = 0, memory: int = MEM_HOST) -> int:
+        """Queues a request; pointers are host memory (memory=MEM_HOST) or device memory of the server's device
+        (MEM_DEVICE); pitches in bytes (0: packed rows)."""
+        req = bf_request(d, in_ptr, in_pitch or width * 4, out_ptr, out_pitch or width * 4, height, width, memory)
         t = C.c_uint64()
         _check(lib().bf_serve_submit(self._h, C.byref(req), C.byref(t)), "bf_serve_submit")
         return t.value

@@ -228,6 +228,17 @@ bf_status enqueue_batch_with(const bf_plan *const *plans, const bf_image *images
     return st;
 }
 
+bf_status enqueue_batch_into(const bf_plan *const *plans, const bf_image *images, int n, void *stream, void *d_buf,
+                             size_t cap) {
+    BatchLayout L;
+    bf_status st = build_batch(plans, images, n, L);
+    if (st != BF_OK) return st;
+    if (L.total > cap) return fail(BF_ERR_OOM, "batch needs more than its reserved buffer");
+    std::vector<uint8_t> staging(std::max<size_t>(L.upload_bytes(), 1));
+    L.fill(staging.data(), reinterpret_cast<uintptr_t>(d_buf));
+    return enqueue_batch(L, static_cast<uint8_t *>(d_buf), staging.data(), (cudaStream_t)stream);
+}
+
 bf_status enqueue_batch_direct(const bf_plan *const *plans, const bf_image *images, int n, void *stream) {
     return enqueue_batch_with(plans, images, n, stream, nullptr);
 }

@@ -32,7 +32,8 @@ struct PreKernelClass {
 };
 extern const PreKernelClass kPreClassesM1[];
 extern const PreKernelClass kPreClassesM2M3[];
-extern const int kNumPreClassesM1, kNumPreClassesM2M3;
+extern const PreKernelClass kPreClassesM4to6[];
+extern const int kNumPreClassesM1, kNumPreClassesM2M3, kNumPreClassesM4to6;
 
 // The 3-D form's persistent slice kernels (packed family without the ring; bf_tile.cuh): kernels_z_*.cu.
 // box: the range box; haar: the Haar range series' weight table (NK = 2 only).  The *_small kernels are the

@@ -103,8 +103,8 @@ const void *find_kernel(int m, int nk, bool ring, bool packed) {
 // The pre-pass variant `pre` (1 fp32, 2 fp16, 3 bf16) of packed class (m, nk), nullptr where none is built.
 const void *find_pre_kernel(int m, int nk, int pre) {
     if (pre < 1 || pre > 3) return nullptr;
-    for (const auto *t : {kPreClassesM1, kPreClassesM2M3}) {
-        const int n = t == kPreClassesM1 ? kNumPreClassesM1 : kNumPreClassesM2M3;
+    for (const auto *t : {kPreClassesM1, kPreClassesM2M3, kPreClassesM4to6}) {
+        const int n = t == kPreClassesM1 ? kNumPreClassesM1 : t == kPreClassesM2M3 ? kNumPreClassesM2M3 : kNumPreClassesM4to6;
         for (int i = 0; i < n; ++i)
             if (t[i].m == m && t[i].nk == nk) return t[i].fn[pre - 1];
     }

@@ -158,6 +158,10 @@ bf_status launch_batch_class(int m, int nk, bool packed, int ncols, const BatchI
 // buffers allocated and freed stream-ordered on `stream`), and the device bytes
 // such a batch needs.
 bf_status enqueue_batch_direct(const bf_plan *const *plans, const bf_image *images, int n, void *stream);
+// The same into a device buffer the caller reserved (cap bytes, 256-byte aligned, at least
+// batch_device_bytes of the batch); allocates no device memory.
+bf_status enqueue_batch_into(const bf_plan *const *plans, const bf_image *images, int n, void *stream, void *d_buf,
+                             size_t cap);
 size_t batch_device_bytes(const bf_plan *const *plans, const bf_image *images, int n);
 bf_status check_image(const float *d_in, size_t in_pitch, const float *d_out, size_t out_pitch, int h, int w);
 // Sums and divides the partial planes of the listed images (d_list: n_list indices).

@@ -200,3 +200,47 @@ def test_batch_autotune_keeps_results_within_the_bar():
     torch.cuda.synchronize()
     for d, ref in zip(dsts, refs):
         assert np.max(np.abs(d.cpu().numpy() - ref)) < TOL
+
+
+def test_server_device_pointer_requests_with_pitches():
+    """Requests on caller-owned device buffers with row pitches wider than the image: the server filters in to
+    out without staging; each result equals bf_filter's within the bar, and the padding stays untouched."""
+    srv = bf.Server(max_slots=8, n_streams=2, max_batch=4)
+    work = mixed_workload(6, 64, 400, seed=21)
+    bufs, tickets = [], []
+    for img, kw in work:
+        H, W = img.shape
+        big_in = torch.zeros((H, W + 24), device="cuda")
+        big_in[:, :W] = torch.from_numpy(img).cuda()
+        big_out = torch.full((H, W + 40), float("nan"), device="cuda")
+        torch.cuda.synchronize()
+        tickets.append(srv.submit(bf.desc(**kw), big_in.data_ptr(), big_out.data_ptr(), H, W,
+                                  in_pitch=big_in.stride(0) * 4, out_pitch=big_out.stride(0) * 4,
+                                  memory=bf.MEM_DEVICE))
+        bufs.append((big_in, big_out))
+    for t, (img, kw), (_, big_out) in zip(tickets, work, bufs):
+        st, r = srv.poll(t, -1)
+        assert st == 0 and r.status == 0
+        W = img.shape[1]
+        got = big_out[:, :W].cpu().numpy()
+        assert np.max(np.abs(got - alone(img, kw))) < MIX_TOL
+        assert torch.isnan(big_out[:, W:]).all()
+    srv.close()
+
+
+def test_server_plan_build_is_inside_the_latency():
+    """A request with parameters the server has not seen: its plan is built after submission, and the
+    reported latency covers the plan build and the queueing."""
+    srv = bf.Server(max_slots=4, n_streams=1)
+    img = synth.shapes(256, 256, 3, scale=0.3)
+    hin, hout = pinned(img)
+    t = srv.submit(bf.desc(sigma_s=27.3, sigma_r=0.137), hin.data_ptr(), hout.data_ptr(), 256, 256)
+    st, r = srv.poll(t, -1)
+    assert st == 0 and r.status == 0
+    assert r.plan_ns > 0 and r.queue_ns >= r.plan_ns and r.latency_ns >= r.queue_ns + r.device_ns * 0
+    assert np.max(np.abs(hout.numpy() - alone(img, dict(sigma_s=27.3, sigma_r=0.137)))) < MIX_TOL
+    # a plan error is reported by poll
+    t = srv.submit(bf.desc(sigma_s=-1.0), hin.data_ptr(), hout.data_ptr(), 256, 256)
+    st, r = srv.poll(t, -1)
+    assert st == 0 and r.status == bf.ERR_INVALID_ARG
+    srv.close()
