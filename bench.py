@@ -385,77 +385,32 @@ def run_ours(args):
 
 
 def run_e2e(args, bf, plans, img, dev, stream, cstreams, order):
-    """Same metric through the public API with host buffers: each step copies the image host->device
-    (pinned), filters it with the nine plans and copies the nine results back.  The copies overlap the
-    filters as a pipelining caller would arrange them: the next step's image goes up on its own stream
-    while this step filters (double-buffered input), and each result comes back on a copy stream as soon
-    as its filter ends (double-buffered outputs, reused only after their copy has finished).  The filters
-    run on the compute streams of the device-timed step, in the same order.  The timed region holds every
-    step's uploads and downloads."""
+    """Same metric through the C ABI's host-buffer call: each step is one bf_filter_host call that uploads the
+    image from pinned host memory, filters it with the nine plans on the library's compute streams (the same
+    stream count and order as the device-timed step) and downloads the nine results, each as soon as its
+    filter ends.  The timed region holds every step's upload and downloads; calls are chained on the device
+    (a step's upload waits for the previous step's last download)."""
     import torch
     h_in = torch.from_numpy(img).pin_memory()
     h_out = [torch.empty(img.shape, dtype=torch.float32).pin_memory() for _ in plans]
-    d_in = [torch.empty(img.shape, dtype=torch.float32, device=dev) for _ in range(2)]
-    d_out = [[torch.empty_like(d_in[0]) for _ in plans] for _ in range(2)]
-    up, down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-    ev = lambda: torch.cuda.Event()
-    ev_up = [ev(), ev()]                                  # input b uploaded
-    ev_used = [ev(), ev()]                                # input b no longer read (last filter issued after)
-    ev_f = [[ev() for _ in plans] for _ in range(2)]      # filter j of buffer b done
-    ev_down = [[ev() for _ in plans] for _ in range(2)]   # result j of buffer b copied back
-    state = {"fresh": [True, True]}
-
-    def upload(b):
-        if not state["fresh"][b]:
-            up.wait_event(ev_used[b])
-        with torch.cuda.stream(up):
-            d_in[b].copy_(h_in, non_blocking=True)
-        ev_up[b].record(up)
-
-    def run(nsteps):
-        upload(0)
-        for s_ in range(nsteps):
-            b = s_ % 2
-            if s_ + 1 < nsteps:
-                upload(1 - b)                             # the next image goes up while this one filters
-            for cs in cstreams:
-                cs.wait_event(ev_up[b])
-            for n, j in enumerate(order):
-                cs = cstreams[n % len(cstreams)]
-                if not state["fresh"][b]:
-                    cs.wait_event(ev_down[b][j])          # the previous result in this buffer is home
-                bf.bf_filter(plans[j], d_in[b], d_out[b][j], stream=cs)
-                ev_f[b][j].record(cs)
-                down.wait_event(ev_f[b][j])
-                with torch.cuda.stream(down):
-                    h_out[j].copy_(d_out[b][j], non_blocking=True)
-                ev_down[b][j].record(down)
-            for cs in cstreams:
-                stream.wait_stream(cs)
-            ev_used[b].record(stream)                     # after every filter of this step
-            state["fresh"][b] = False
-        stream.wait_stream(down)
-        stream.wait_stream(up)
-
-    run(max(1, args.warmup))
+    ordered = [plans[j] for j in order]
+    outs = [h_out[j] for j in order]
+    for _ in range(max(1, args.warmup)):
+        bf.bf_filter_host(ordered, h_in, outs, n_streams=len(cstreams), stream=stream)
     torch.cuda.synchronize()
-    state["fresh"] = [True, True]
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for s_ in [up, down] + list(cstreams):
-        s_.wait_event(e0)
-    run(args.steps)
+    for _ in range(args.steps):
+        bf.bf_filter_host(ordered, h_in, outs, n_streams=len(cstreams), stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     value = len(plans) * H * W * args.steps / (ms * 1e-3) / 1e6
     return {"value": round(value, 3), "unit": "Mpixel/s", "h2d_bytes_per_step": 4 * H * W,
-            "d2h_bytes_per_step": 4 * H * W * len(plans),
-            "note": "uploads and downloads overlap the filters (copy streams, double buffers); filters on %d "
-                    "compute streams; every step's input arrives by its own H2D copy (nothing is reused from an "
-                    "earlier step), and the copy leaves it in L2 for that step's filters, so it can read above the "
-                    "device-timed value, whose steps start from a flushed L2" % len(cstreams)}
+            "d2h_bytes_per_step": 4 * H * W * len(plans), "api": "bf_filter_host",
+            "note": "one bf_filter_host call per step: H2D of the image from pinned memory, the nine filters on %d "
+                    "library streams, nine D2H; steps chained on the device" % len(cstreams)}
 
 
 def timed_calls(fn, flush, reps):

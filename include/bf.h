@@ -248,6 +248,26 @@ bf_status bf_filter(const bf_plan *plan, const float *d_in, size_t in_pitch_byte
 bf_status bf_filter_noalloc(const bf_plan *plan, const float *d_in, size_t in_pitch_bytes,
                             float *d_out, size_t out_pitch_bytes, int height, int width, void *stream);
 
+/* Filters one image in host memory with each of n plans (1..256, all on one
+ * device): the paper's use of one image under several parameter settings
+ * (Sec. V-C).  Uploads h_in (height rows of width floats, row pitch in_pitch
+ * bytes; pinned memory makes the copies asynchronous), filters it with plan i
+ * on internal stream i mod n_streams (1..8), forked from and joined back to
+ * `stream`, and downloads result i into h_outs[i] (row pitch out_pitch bytes)
+ * on the same internal stream as soon as its filter ends.  Asynchronous on
+ * `stream`: synchronize it before reading h_outs.  The device buffers (input,
+ * n outputs, each plan's scratch) are one block per device owned by the
+ * library, allocated by the first call and grown when a call needs more;
+ * calls on a device are chained on the device (each call's upload waits for
+ * the previous call's last download), so calls from several streams or
+ * threads are safe and run one after another.  Plans' geometries as
+ * bf_filter's; the debug input-range check does not apply.  Errors:
+ * BF_ERR_INVALID_ARG (NULL, n or n_streams out of range, bad pitch, overlap,
+ * plans on several devices), BF_ERR_NO_DEVICE, BF_ERR_OOM, BF_ERR_CUDA. */
+bf_status bf_filter_host(const bf_plan *const *plans, int n, const float *h_in, size_t in_pitch,
+                         float *const *h_outs, size_t out_pitch, int height, int width, int n_streams,
+                         void *stream);
+
 /* Launch geometry bf_filter would use for this plan on a height x width image:
  * info[0] tile width, [1] tile height, [2] threads per CTA, [3] cosine terms per
  * CTA, [4] term groups (grid depth), [5] kernel launches, [6] shared memory

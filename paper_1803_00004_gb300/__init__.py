@@ -6,6 +6,7 @@ generators in ``synth``.  Importing the package does not load the library; the
 first call does, and raises if it has not been built.
 """
 from ._binding import (BFError, Cache, Plan, Server, bf_coeffs, bf_exact, bf_exact_lut, bf_filter, bf_filter_batch,  # noqa: F401
+                       bf_filter_host,
                        bf_autotune_batch,
                        bf_version,
                        bf_launch_info, bf_autotune, bf_autotune_group, bf_autotune_image, bf_launch_candidates, bf_set_launch,

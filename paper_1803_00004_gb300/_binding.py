@@ -81,7 +81,7 @@ EXPORTS = ["bf_plan_desc_default", "bf_plan_create", "bf_plan_destroy", "bf_coef
            "bf_exact", "bf_exact_lut", "bf_precompute", "bf_filter_cached", "bf_cache_bytes", "bf_cache_destroy",
            "bf_serve_create", "bf_serve_submit", "bf_serve_poll", "bf_serve_cancel", "bf_serve_destroy",
            "bf_status_string", "bf_last_error", "bf_version", "bf_debug_fail_launches", "bf_debug_range_checks",
-           "bf_fp32_peak"]
+           "bf_fp32_peak", "bf_filter_host"]
 
 _lib = None
 _lock = threading.Lock()
@@ -140,6 +140,7 @@ def lib():
         L.bf_debug_range_checks.argtypes = [i]
         L.bf_debug_range_checks.restype = None
         L.bf_fp32_peak.argtypes = [i, i, P(d), P(d)]
+        L.bf_filter_host.argtypes = [P(vp), i, vp, sz, P(vp), sz, i, i, i, vp]
         _lib = L
     return _lib
 
@@ -305,6 +306,23 @@ def bf_filter(plan: Plan, src, dst, stream=None) -> None:
     if (h, w) != (h2, w2):
         raise ValueError("input and output shapes differ")
     _check(lib().bf_filter(plan.handle, ip, ipitch, op, opitch, h, w, _stream_handle(stream)), "bf_filter")
+
+
+def bf_filter_host(plans, src, dsts, n_streams: int = 3, stream=None) -> None:
+    """Filters one host image (a 2-D float32 CPU tensor, pinned for asynchronous copies) with each plan into
+    the host tensors dsts (same shape); asynchronous on `stream` (synchronize before reading dsts)."""
+    n = len(plans)
+    if len(dsts) != n:
+        raise ValueError("one output per plan")
+    for t in [src] + list(dsts):
+        if t.dim() != 2 or t.dtype.itemsize != 4 or t.stride(1) != 1 or t.is_cuda:
+            raise ValueError("expected 2-D float32 host tensors with unit column stride")
+        if t.shape != src.shape or t.stride(0) != dsts[0].stride(0) and t is not src:
+            raise ValueError("outputs must share the input's shape and one row pitch")
+    hs = (C.c_void_p * n)(*[p.handle for p in plans])
+    outs = (C.c_void_p * n)(*[t.data_ptr() for t in dsts])
+    _check(lib().bf_filter_host(hs, n, src.data_ptr(), src.stride(0) * 4, outs, dsts[0].stride(0) * 4,
+                                src.shape[0], src.shape[1], n_streams, _stream_handle(stream)), "bf_filter_host")
 
 
 def _batch_args(plans, srcs, dsts):
