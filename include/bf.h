@@ -391,7 +391,9 @@ typedef struct {
 
 /* Filters n images, image i with plans[i] (plans may differ per image), in
  * one persistent launch per kernel class that walks a work list of
- * (image, tile) items across uneven images; the launch sequence is captured
+ * (image, tile) items across uneven images; images whose plans that kernel
+ * does not run (the 3-D form, 16-bit basis storage) follow as one launch
+ * sequence each, in their bf_filter geometry.  The whole sequence is captured
  * once into a CUDA graph per batch shape and replayed.  Each image's result
  * equals bf_filter's for the same plan within fp32 rounding.  All plans must
  * be on the same device.  Errors: as bf_filter. */

@@ -71,6 +71,17 @@ struct BatchLayout {
     size_t off_params = 0, off_imgs = 0, off_items = 0, off_list = 0, off_cursors = 0, off_scratch = 0, total = 0;
     std::vector<size_t> scratch_off;  // per image, relative to off_scratch (or SIZE_MAX)
     int max_h = 0, max_w = 0;
+    // Images of plans the persistent kernel does not run (the 3-D form; 16-bit basis storage): launched one by
+    // one after the persistent launches, in their own geometry, with their scratch in the buffer's scratch area.
+    struct Direct {
+        FilterParams kp;
+        int precision, kahan;
+        TileConfig tc;
+        bf_image im;
+        size_t scratch_off;  // relative to off_scratch
+        size_t scratch_bytes;
+    };
+    std::vector<Direct> direct;
 
     void fill(uint8_t *staging, uintptr_t d_base) {
         std::vector<BatchImage> im = imgs;
@@ -86,6 +97,8 @@ struct BatchLayout {
     size_t upload_bytes() const { return off_scratch; }
 };
 
+using LayoutDirect = BatchLayout::Direct;
+
 bf_status build_batch(const bf_plan *const *plans, const bf_image *images, int n, BatchLayout &L,
                       const TuneOverride *ov = nullptr) {
     L = BatchLayout();
@@ -94,17 +107,28 @@ bf_status build_batch(const bf_plan *const *plans, const bf_image *images, int n
     // one persistent launch per (windows per axis, kernel family): plans whose selected terms are
     // consecutive use the packed-pair family, the others the scalar family (no padded term groups)
     std::map<std::pair<int, int>, std::vector<int>> by_class;
+    size_t scratch = 0;
     for (int i = 0; i < n; ++i) {
         const FilterParams &kp = plans[i]->kp;
-        if (kp.zbins > 0) return fail(BF_ERR_UNSUPPORTED, "the 3-D form (BF_RANGE_PAPER_3D) runs through bf_filter");
-        if (plans[i]->desc.precision != BF_PREC_FP32)
-            return fail(BF_ERR_UNSUPPORTED, "16-bit basis storage runs through bf_filter; batched launches are fp32");
+        if (kp.zbins > 0 || plans[i]->desc.precision != BF_PREC_FP32) {
+            LayoutDirect d;
+            d.kp = kp;
+            d.precision = plans[i]->desc.precision;
+            d.kahan = plans[i]->desc.kahan;
+            d.tc = choose_tile(kp, images[i].height, images[i].width, d.precision);
+            if (d.tc.ncols == 0) return fail(BF_ERR_UNSUPPORTED, "no launch geometry for a batched 3-D or 16-bit plan");
+            d.im = images[i];
+            d.scratch_bytes = scratch_bytes(d.tc, images[i].height, images[i].width, kp.zbins);
+            d.scratch_off = scratch;
+            scratch = align_up(scratch + d.scratch_bytes, 256);
+            L.direct.push_back(d);
+            continue;
+        }
         by_class[{plans[i]->m, kp.k[kp.nr - 1] - kp.k[0] + 1 == kp.nr ? 1 : 0}].push_back(i);
     }
     L.params.resize(n);
     L.imgs.resize(n);
     L.scratch_off.assign(n, SIZE_MAX);
-    size_t scratch = 0;
     std::vector<std::vector<WorkItem>> class_items;
     for (auto &kv : by_class) {
         const int m = kv.first.first;
@@ -205,8 +229,15 @@ bf_status enqueue_batch(const BatchLayout &L, uint8_t *d_buf, const uint8_t *h_s
                                           reinterpret_cast<int *>(d_buf + cl.cursor_off), cl.grid, s);
         if (st != BF_OK) return st;
     }
-    return launch_batch_finalize(d_imgs, reinterpret_cast<const int *>(d_buf + L.off_list), (int)L.list.size(),
-                                 L.max_h, L.max_w, d_params, s);
+    bf_status st = launch_batch_finalize(d_imgs, reinterpret_cast<const int *>(d_buf + L.off_list), (int)L.list.size(),
+                                         L.max_h, L.max_w, d_params, s);
+    for (size_t i = 0; i < L.direct.size() && st == BF_OK; ++i) {
+        const auto &d = L.direct[i];
+        float *scr = d.scratch_bytes ? reinterpret_cast<float *>(d_buf + L.off_scratch + d.scratch_off) : nullptr;
+        st = launch_filter(d.kp, d.precision, d.kahan, d.tc, d.im.d_in, d.im.in_pitch_bytes / sizeof(float), d.im.d_out,
+                           d.im.out_pitch_bytes / sizeof(float), scr, d.im.height, d.im.width, s);
+    }
+    return st;
 }
 
 bf_status enqueue_batch_with(const bf_plan *const *plans, const bf_image *images, int n, void *stream,
@@ -354,8 +385,6 @@ bf_status collect_batch(const bf_plan *const *plans, const bf_image *images, int
     for (int i = 0; i < n; ++i) {
         if (!plans[i]) return fail(BF_ERR_INVALID_ARG, "NULL plan in batch");
         if (plans[i]->desc.device < 0) return fail(BF_ERR_NO_DEVICE, "host-only plan in batch");
-        if (plans[i]->kp.zbins > 0)
-            return fail(BF_ERR_UNSUPPORTED, "the 3-D form (BF_RANGE_PAPER_3D) runs through bf_filter, not in batches");
         if (*device == -2) *device = plans[i]->desc.device;
         if (plans[i]->desc.device != *device) return fail(BF_ERR_INVALID_ARG, "plans of one batch must share a device");
         const bf_image &im = images[i];

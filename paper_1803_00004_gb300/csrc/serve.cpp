@@ -461,8 +461,6 @@ bf_status bf_serve_submit(bf_server *S, const bf_request *req, uint64_t *ticket)
     bf_status st = bfi::check_image(req->in, req->in_pitch_bytes, req->out, req->out_pitch_bytes, req->height,
                                     req->width);
     if (st != BF_OK) return st;
-    if (req->desc.policy == BF_RANGE_PAPER_3D)
-        return bfi::fail(BF_ERR_UNSUPPORTED, "the 3-D form (BF_RANGE_PAPER_3D) runs through bf_filter, not the server");
     Request r;
     r.desc = req->desc;
     r.desc.device = S->cfg.device;

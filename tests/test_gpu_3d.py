@@ -193,13 +193,40 @@ def test_3d_full_size_sampled():
     assert np.max(err) < TOL
 
 
+def test_3d_in_batches_and_the_server():
+    """3-D plans in a batch with collapsed ones (launched one by one after the persistent launches, captured in
+    the same graph) and through the server: each result equals bf_filter's within the bar and the oracle's."""
+    imgs = [synth.shapes(120, 200, 61, scale=0.2), synth.blocks(96, 130, 62), synth.shapes(150, 90, 63, scale=0.2)]
+    plans = [plan3d(256, sigma_s=2.0, sigma_r=0.1, nr_terms=4), bf.Plan(device=0, sigma_s=3.0),
+             bf.Plan(device=0, policy=bf.RANGE_PAPER_3D, range_series=bf.SERIES_HAAR, z_bins=256, sigma_s=2.0,
+                     sigma_r=0.1, nr_terms=8)]
+    srcs = [torch.from_numpy(im).cuda() for im in imgs]
+    for _ in range(2):  # the second call replays the captured graph
+        dsts = [torch.full_like(x, float("nan")) for x in srcs]
+        bf.bf_filter_batch(plans, srcs, dsts)
+        torch.cuda.synchronize()
+        for p, x, d in zip(plans, srcs, dsts):
+            ref = torch.empty_like(x)
+            bf.bf_filter(p, x, ref)
+            torch.cuda.synchronize()
+            assert torch.max(torch.abs(d - ref)).item() < TOL
+    want = O.approx3d_direct(imgs[0].astype(np.float64), odesc(dict(sigma_s=2.0, sigma_r=0.1, nr_terms=4)), 256,
+                             threads=THREADS)[0]
+    assert np.max(np.abs(dsts[0].cpu().numpy() - want)) < TOL
+    srv = bf.Server(max_slots=4, n_streams=2)
+    hin = torch.from_numpy(imgs[0]).pin_memory()
+    hout = torch.full_like(hin, float("nan")).pin_memory()
+    t = srv.submit(bf.desc(policy=bf.RANGE_PAPER_3D, z_bins=256, sigma_s=2.0, sigma_r=0.1, nr_terms=4),
+                   hin.data_ptr(), hout.data_ptr(), 120, 200)
+    st, r = srv.poll(t, -1)
+    assert st == 0 and r.status == 0
+    assert np.max(np.abs(hout.numpy() - want)) < TOL
+    srv.close()
+
+
 def test_3d_rejected_where_unsupported():
     plan = plan3d(256, sigma_s=2.0)
     src = torch.rand(64, 64, device="cuda")
-    dst = torch.empty_like(src)
-    with pytest.raises(bf.BFError) as ei:
-        bf.bf_filter_batch([plan], [src], [dst])
-    assert ei.value.status == 2  # BF_ERR_UNSUPPORTED
     with pytest.raises(bf.BFError) as ei:
         bf.Cache(plan, src, kmax=8)
     assert ei.value.status == 2  # BF_ERR_UNSUPPORTED

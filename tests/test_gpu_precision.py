@@ -122,13 +122,19 @@ def test_16bit_basis_full_size_and_accuracy_against_exact(prec):
         assert 10 * np.log10(1.0 / mse) >= 40.0
 
 
-def test_16bit_plans_rejected_where_unsupported():
+def test_16bit_plans_in_batches_and_rejected_for_the_3d_form():
     with pytest.raises(bf.BFError) as ei:
         bf.Plan(device=0, precision=bf.PREC_FP16, policy=bf.RANGE_PAPER_3D)
     assert ei.value.status == bf.ERR_UNSUPPORTED
-    p = bf.Plan(device=0, precision=bf.PREC_BF16)
-    src = torch.zeros((64, 64), device="cuda")
-    dst = torch.empty_like(src)
-    with pytest.raises(bf.BFError) as ei:
-        bf.bf_filter_batch([p], [src], [dst])
-    assert ei.value.status == bf.ERR_UNSUPPORTED
+    # 16-bit plans in a batch run one by one after the persistent launches: bf_filter's result
+    imgs = [synth.shapes(140, 230, 46, scale=0.2), synth.blocks(100, 90, 47)]
+    plans = [bf.Plan(device=0, precision=bf.PREC_BF16), bf.Plan(device=0, sigma_s=2.0)]
+    srcs = [torch.from_numpy(im).cuda() for im in imgs]
+    dsts = [torch.full_like(x, float("nan")) for x in srcs]
+    bf.bf_filter_batch(plans, srcs, dsts)
+    torch.cuda.synchronize()
+    for p, x, d in zip(plans, srcs, dsts):
+        ref = torch.empty_like(x)
+        bf.bf_filter(p, x, ref)
+        torch.cuda.synchronize()
+        assert torch.max(torch.abs(d - ref)).item() < 1e-5
