@@ -462,32 +462,18 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
                     }
                 }
             }
-            // mix per horizontal window and publish; a zero weight of the first vertical window (the paper's
-            // five-term kernel has C = [[0, B], [B, A]]) is skipped, the test uniform across the CTA
+            // mix per horizontal window and publish
 #pragma unroll
-            for (int q = 0; q < M; ++q) {
-                if (M > 1 && p.C[0][q] == 0.f) {
+            for (int i = 0; i < NP; ++i)
 #pragma unroll
-                    for (int i = 0; i < NP; ++i)
+                for (int q = 0; q < M; ++q)
 #pragma unroll
-                        for (int t = 0; t < 4; ++t) {
-                            float2 z = mul2(pair(p.C[1][q]), V[i][t][M > 1 ? 1 : 0]);
+                    for (int t = 0; t < 4; ++t) {
+                        float2 z = mul2(pair(p.C[0][q]), V[i][t][0]);
 #pragma unroll
-                            for (int r = 2; r < M; ++r) z = fma2(pair(p.C[r][q]), V[i][t][r], z);
-                            zb[(q * 4 + t) * NP + i] = z;
-                        }
-                } else {
-#pragma unroll
-                    for (int i = 0; i < NP; ++i)
-#pragma unroll
-                        for (int t = 0; t < 4; ++t) {
-                            float2 z = mul2(pair(p.C[0][q]), V[i][t][0]);
-#pragma unroll
-                            for (int r = 1; r < M; ++r) z = fma2(pair(p.C[r][q]), V[i][t][r], z);
-                            zb[(q * 4 + t) * NP + i] = z;
-                        }
-                }
-            }
+                        for (int r = 1; r < M; ++r) z = fma2(pair(p.C[r][q]), V[i][t][r], z);
+                        zb[(q * 4 + t) * NP + i] = z;
+                    }
         } else if (!is_col && j >= 1 && j - 1 < nout) {
             const int st = tid - ncols;
             const int seg = st >> 5, l = st & 31;  // scan warp, lane = row pair
