@@ -495,20 +495,24 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
             c1[n] = std::cos(th[n]);
             s1[n] = std::sin(th[n]);
         }
+        // (nodes in blocks of 256, so that a block's arrays stay in the L1 cache over the frequency loop)
         std::vector<double> acc(ncand, 0.0);
-        for (int k = 0; k < ncand; ++k) {
-            if (k % 16 == 0)
-                for (int n = 0; n < nn; ++n) {
-                    ck[n] = k == 0 ? 1.0 : std::cos(k * th[n]);
-                    sk[n] = k == 0 ? 0.0 : std::sin(k * th[n]);
+        for (int n0 = 0; n0 < nn; n0 += 256) {
+            const int n1 = std::min(nn, n0 + 256);
+            for (int k = 0; k < ncand; ++k) {
+                if (k % 16 == 0)
+                    for (int n = n0; n < n1; ++n) {
+                        ck[n] = k == 0 ? 1.0 : std::cos(k * th[n]);
+                        sk[n] = k == 0 ? 0.0 : std::sin(k * th[n]);
+                    }
+                double a = 0.0;
+                for (int n = n0; n < n1; ++n) a += f[n] * ck[n];
+                acc[k] += a;
+                for (int n = n0; n < n1; ++n) {
+                    const double cn = ck[n] * c1[n] - sk[n] * s1[n];
+                    sk[n] = sk[n] * c1[n] + ck[n] * s1[n];
+                    ck[n] = cn;
                 }
-            double a = 0.0;
-            for (int n = 0; n < nn; ++n) a += f[n] * ck[n];
-            acc[k] = a;
-            for (int n = 0; n < nn; ++n) {
-                const double cn = ck[n] * c1[n] - sk[n] * s1[n];
-                sk[n] = sk[n] * c1[n] + ck[n] * s1[n];
-                ck[n] = cn;
             }
         }
         std::vector<Cand> rc(ncand);
