@@ -260,8 +260,10 @@ bf_status bf_filter_noalloc(const bf_plan *plan, const float *d_in, size_t in_pi
  * library, allocated by the first call and grown when a call needs more;
  * calls on a device are chained on the device (each call's upload waits for
  * the previous call's last download), so calls from several streams or
- * threads are safe and run one after another.  Plans' geometries as
- * bf_filter's; the debug input-range check does not apply.  Errors:
+ * threads are safe and run one after another.  A call that allocates or
+ * grows the block synchronizes with the previous call's work: make the first
+ * call (at the largest size and plan count) outside stream capture.  Plans'
+ * geometries as bf_filter's; the debug input-range check does not apply.  Errors:
  * BF_ERR_INVALID_ARG (NULL, n or n_streams out of range, bad pitch, overlap,
  * plans on several devices), BF_ERR_NO_DEVICE, BF_ERR_OOM, BF_ERR_CUDA. */
 bf_status bf_filter_host(const bf_plan *const *plans, int n, const float *h_in, size_t in_pitch,

@@ -193,6 +193,7 @@ void complete_locked(bf_server *S, Request &r, int status) {
 
 // Plan thread: arrival order; cache hit or host build (outside the lock); then the request is ready.
 void planner_main(bf_server *S) {
+    cudaSetDevice(S->cfg.device);  // launch geometries are looked up for the current device
     std::unique_lock<std::mutex> lk(S->mu);
     for (;;) {
         S->cv_plan.wait(lk, [&] { return S->stop || !S->pending.empty(); });

@@ -237,7 +237,7 @@ def test_server_plan_build_is_inside_the_latency():
     t = srv.submit(bf.desc(sigma_s=27.3, sigma_r=0.137), hin.data_ptr(), hout.data_ptr(), 256, 256)
     st, r = srv.poll(t, -1)
     assert st == 0 and r.status == 0
-    assert r.plan_ns > 0 and r.queue_ns >= r.plan_ns and r.latency_ns >= r.queue_ns + r.device_ns * 0
+    assert r.plan_ns > 0 and r.queue_ns >= r.plan_ns and r.latency_ns >= r.queue_ns
     assert np.max(np.abs(hout.numpy() - alone(img, dict(sigma_s=27.3, sigma_r=0.137)))) < MIX_TOL
     # a plan error is reported by poll
     t = srv.submit(bf.desc(sigma_s=-1.0), hin.data_ptr(), hout.data_ptr(), 256, 256)
