@@ -104,21 +104,26 @@ typedef enum {
     BF_SERIES_HAAR = 1
 } bf_range_series;
 
-/* Storage precision.  The fused filter computes and exchanges everything in
- * fp32 and stores no basis image (in HBM or shared memory): basis values live
- * in registers at the rows where they enter or leave a window, and the kernel
- * is bound by fp32 issue, so it has nothing to store in 16 bits.  Plans are
- * therefore fp32 (bf_plan_create rejects the 16-bit values with
- * BF_ERR_UNSUPPORTED).  The one stored intermediate is the pre-computation
- * cache of bf_precompute (Sec. V-C, Case 1): its window sums may be stored as
- * fp16 or bf16 (rounded once from the fp32 sums), halving the cache and the
- * traffic of bf_filter_cached, with a relative error of at most u = 2^-11
- * (fp16) or 2^-8 (bf16) per sum, so |delta I^| <= 2 u sum|a_k| mass (1 + |I^|)
- * / |den| (mass = sum |K~_s| over the window). */
+/* Storage precision of the basis inputs.  The fused filter computes every
+ * running sum, the weighting and the divide in fp32 (Kahan-compensated
+ * horizontal sums), whatever the precision.  BF_PREC_FP32: the basis is
+ * computed in the kernel from each pixel at every window edge (or read from an
+ * fp32 pre-pass of the same values, a geometry the autotuners may time).
+ * BF_PREC_FP16 / BF_PREC_BF16: a pre-pass stores each pixel's base rotation
+ * (cos, sin)(pi t) as one fp16 / bf16 pair beside the fp32 pixel, and the
+ * kernel reads it at every edge, rescaled to unit length; term k of a group is
+ * reached from an fp32 anchor by m_k <= min(k, NK) rotations, so with unit
+ * roundoff u (2^-11 fp16, 2^-8 bf16) |delta I^| <= 2 u sum_k m_k |a_k| mass
+ * (1 + |I^|) / |den| beyond the fp32 path's error (mass = sum |K~_s| over the
+ * window).  16-bit plans take the collapsed range policies (not
+ * BF_RANGE_PAPER_3D); bf_filter_batch and the server run them one by one.
+ * The pre-computation cache of bf_precompute has its own storage precision
+ * (same enum): its window sums may be stored as fp16 or bf16, rounded once
+ * from the fp32 sums, with |delta I^| <= 2 u sum|a_k| mass (1 + |I^|) / |den|. */
 typedef enum {
     BF_PREC_FP32 = 0,  /* fp32 */
-    BF_PREC_BF16 = 1,  /* bf16 storage of the pre-computation cache */
-    BF_PREC_FP16 = 2   /* fp16 storage of the pre-computation cache */
+    BF_PREC_BF16 = 1,  /* bf16 storage of the base rotation (plans) or of the cached sums (bf_precompute) */
+    BF_PREC_FP16 = 2   /* fp16 storage of the base rotation (plans) or of the cached sums (bf_precompute) */
 } bf_precision;
 
 /* Plan parameters (Sec. IV-A..C).  Fill with bf_plan_desc_default() first. */
@@ -169,8 +174,8 @@ void bf_plan_desc_default(bf_plan_desc *desc);
  * Errors: BF_ERR_INVALID_ARG (NULL, sigma <= 0, N < 1, i_hi <= i_lo, bad enum,
  * z_bins outside [2, 4096] for BF_RANGE_PAPER_3D, BF_SERIES_HAAR without it),
  * BF_ERR_UNSUPPORTED (exponential spatial kernel with R > 255; a selection
- * needing more than 6 box windows per axis; 16-bit precision; BF_SERIES_HAAR
- * with R_z > 1023),
+ * needing more than 6 box windows per axis; 16-bit precision with
+ * BF_RANGE_PAPER_3D; BF_SERIES_HAAR with R_z > 1023),
  * BF_ERR_OOM, BF_ERR_NO_DEVICE (device >= 0 that does not exist). */
 bf_status bf_plan_create(const bf_plan_desc *desc, bf_plan **out);
 
@@ -279,19 +284,21 @@ bf_status bf_filter_host(const bf_plan *const *plans, int n, const float *h_in, 
  * kernel family: 1 packed (cosine terms in consecutive pairs on the two-wide
  * fp32 instructions; a gapped selection is covered by groups of consecutive
  * frequencies with zero weights), 0 scalar (any set of terms; offered only for
- * gapped selections).  info must hold 12 ints.  Host only; needs no
+ * gapped selections), [12] basis inputs: 0 computed in the kernel, 1 / 2 / 3
+ * read from a pre-pass buffer in fp32 / fp16 / bf16 (its 16 or 8 bytes per
+ * pixel are part of the scratch).  info must hold 13 ints.  Host only; needs no
  * device for host-only plans (uses 152 SMs as the device size then).
  * Errors: BF_ERR_INVALID_ARG. */
 bf_status bf_launch_info(const bf_plan *plan, int height, int width, int *info);
 
 /* Autotuner: times candidate launch geometries (the cost model's best four of
  * each family -- ring of basis inputs or not, exchange depth, kernel family,
- * cosine terms per CTA -- within each residency class of 1, 2, or 3 and more
+ * cosine terms per CTA, basis pre-pass -- within each residency class of 1, 2, or 3 and more
  * CTAs per SM by shared memory) for this plan on a synthetic height x width
  * image and remembers the fastest for later bf_filter / bf_filter_batch calls
  * with the same kernel class, reach and image size on this device.  Allocates
  * and frees its own device buffers and synchronizes `stream`; do not call it
- * during stream capture.  info (12 ints, may be NULL) receives the chosen
+ * during stream capture.  info (13 ints, may be NULL) receives the chosen
  * geometry as in bf_launch_info.  BF_TUNE_CACHE=<file> persists results.
  * Errors: BF_ERR_INVALID_ARG, BF_ERR_NO_DEVICE, BF_ERR_OOM, BF_ERR_CUDA. */
 bf_status bf_autotune(const bf_plan *plan, int height, int width, void *stream, int *info);
@@ -318,7 +325,7 @@ bf_status bf_autotune_image(const bf_plan *plan, const float *d_in, size_t in_pi
  * the group: a grid of fewer CTAs than SMs leaves SMs to the other streams.
  * Allocates its own buffers (one input, n outputs, scratch) and streams, and
  * synchronizes them before returning; do not call it during stream capture.
- * infos (12 x n ints, may be NULL) receives each plan's geometry as in
+ * infos (13 x n ints, may be NULL) receives each plan's geometry as in
  * bf_launch_info.  The geometry changes rounding order only.
  * Errors: BF_ERR_INVALID_ARG (no plans, a null plan, plans on several
  * devices, n_streams out of range), BF_ERR_NO_DEVICE (a host-only plan),
@@ -326,16 +333,16 @@ bf_status bf_autotune_image(const bf_plan *plan, const float *d_in, size_t in_pi
 bf_status bf_autotune_group(const bf_plan *const *plans, int n, int height, int width, int n_streams, int *infos);
 
 /* Launch geometries of this plan for a height x width image, best first by the
- * cost model: up to max_n records of 12 ints each (as in bf_launch_info) into
- * infos (caller-owned, 12 x max_n ints); *n_out receives how many were written.
+ * cost model: up to max_n records of 13 ints each (as in bf_launch_info) into
+ * infos (caller-owned, 13 x max_n ints); *n_out receives how many were written.
  * Host only.
  * Errors: BF_ERR_INVALID_ARG. */
 bf_status bf_launch_candidates(const bf_plan *plan, int height, int width, int max_n, int *infos, int *n_out);
 
 /* Pins the launch geometry bf_filter / bf_filter_noalloc use for this plan's
  * kernel class on height x width images of the plan's device (as bf_autotune
- * does with the fastest one).  info (12 ints, caller-owned) must match one
- * record of bf_launch_candidates in fields 0, 1, 3, 8, 9, 10 and 11; the other
+ * does with the fastest one).  info (13 ints, caller-owned) must match one
+ * record of bf_launch_candidates in fields 0, 1, 3, 8, 9, 10, 11 and 12; the other
  * fields are ignored.  The geometry changes rounding order only: every one gives
  * the result within the same error bound.  BF_TUNE_CACHE=<file> persists it.
  * Errors: BF_ERR_INVALID_ARG (no such geometry), BF_ERR_NO_DEVICE. */
