@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-ramp", action="store_true", help="skip the untimed clock-ramp load (profiling)")
     ap.add_argument("--no-tune", action="store_true", help="use the pinned (BF_TUNE_CACHE) or cost-model geometry instead of autotuning")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving sub-measurements")
+    ap.add_argument("--streams", type=int, default=N_STREAMS, help="compute streams the step's filters are spread over")
     ap.add_argument("--tiles", default=None,
                     help="pin each combination's launch geometry instead of autotuning: the JSON list of the line's "
                          "'tiles' field, one [tw, th, threads, nk, groups, ring, depth, ncols, packed, pre] per "
@@ -219,9 +220,10 @@ def run_ours(args):
         mse = torch.mean((o.double() - ex.double()) ** 2).item()
         psnr.append(10 * np.log10(1.0 / mse) if mse > 0 else float("inf"))
 
-    # The nine filters are independent: they go out on N_STREAMS streams, longest first (largest sigma_s), so
+    # The nine filters are independent: they go out on n_streams streams, longest first (largest sigma_s), so
     # that one filter's last partial wave of tiles overlaps the next filter's first.
-    cstreams = [torch.cuda.Stream(dev) for _ in range(N_STREAMS)]
+    n_streams = max(1, args.streams)
+    cstreams = [torch.cuda.Stream(dev) for _ in range(n_streams)]
     order = sorted(range(len(plans)), key=lambda j: -combos[j][0])
     if args.tiles:  # geometries pinned from an earlier line (reproducible profiles)
         rows = json.loads(args.tiles)
@@ -235,7 +237,7 @@ def run_ours(args):
     elif not args.no_tune:  # launch geometry (untimed): each plan alone, then the nine as the step runs them
         for p in plans:
             bf.bf_autotune(p, H, W)
-        bf.bf_autotune_group([plans[j] for j in order], H, W, n_streams=N_STREAMS)
+        bf.bf_autotune_group([plans[j] for j in order], H, W, n_streams=n_streams)
     tiles = [bf.bf_launch_info(p, H, W) for p in plans]
     launches_per_step = sum(t["launches"] for t in tiles)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
@@ -246,7 +248,7 @@ def run_ours(args):
         for s in cstreams:
             s.wait_event(fork)
         for n, j in enumerate(order):
-            s = cstreams[n % N_STREAMS]
+            s = cstreams[n % n_streams]
             if ev is not None:
                 ev[j][0].record(s)
             bf.bf_filter(plans[j], src, outs[j], stream=s)
@@ -347,7 +349,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD if not args.only else "1920x1080, sigma_s,sigma_r = " + args.only,
                    "height": H, "width": W, "images_per_step": len(plans),
-                   "l2": "flushed between steps (256 MB write)", "streams": N_STREAMS,
+                   "l2": "flushed between steps (256 MB write)", "streams": n_streams,
                    "parallelism": "replicas" if world > 1 else "single"},
         "psnr_db_vs_exact": [round(x, 2) for x in psnr], "min_psnr_db": round(min(psnr), 2) if psnr else None,
         "plan_build_ms": round(plan_build_ms, 2),
@@ -368,7 +370,7 @@ def run_ours(args):
                              "+ 4 (N_r - 1) + 6 k_max + 2 per pixel, against the measured fp32 rate of this GPU "
                              "(bf_fp32_peak: the faster of scalar FFMA and FFMA2, an FFMA2 counted as two lane-ops); "
                              "launch_ms = step device time / launches (launches overlap on %d streams), alone = "
-                             "events around each launch run one at a time" % N_STREAMS},
+                             "events around each launch run one at a time" % n_streams},
         "hbm": {"achieved_gbs": round(hbm_gbs, 1), "peak_gbs": hbm_peak, "frac": round(hbm_gbs / hbm_peak, 5),
                 "bytes_per_px": 8},
         "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
