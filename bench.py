@@ -4,7 +4,7 @@ Workload (the 1920x1080 sweep): a seeded 1920x1080 float32 image of uniform
 rectangles and ellipses plus N(0, 0.03^2) noise; one step filters it once with
 each of the nine (sigma_s, sigma_r) in {2, 8, 32} x {0.05, 0.1, 0.3} (Gaussian
 kernels, N_r = 8 cosine terms, N_s = 5 Haar terms), i.e. 9 x 2,073,600 pixels,
-the nine independent filters spread over three CUDA streams.
+the nine independent filters spread over four CUDA streams.
 The metric is Mpixel/s over the step; every combination's PSNR against the exact
 bilateral filter (GPU brute force, untimed) is checked to be >= 40 dB.
 
@@ -34,7 +34,7 @@ H, W = 1080, 1920
 SIGMA_S = (2.0, 8.0, 32.0)
 SIGMA_R = (0.05, 0.1, 0.3)
 NR, NS = 8, 5
-N_STREAMS = 3   # compute streams the step's filters are spread over
+N_STREAMS = 4   # compute streams the step's filters are spread over
 METRIC = "Mpixel/s at >=40 dB vs exact BF (1920x1080, 9 sigma combos)"
 WORKLOAD = "1920x1080 shapes+noise(0.03), Gaussian/Gaussian, sigma_s in {2,8,32} x sigma_r in {0.05,0.1,0.3}, N_r=8, N_s=5"
 

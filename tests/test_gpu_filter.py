@@ -124,17 +124,17 @@ def test_full_size_parity_every_pixel():
     plans = [bf.Plan(device=0, **kw) for kw in kws]
     for p in plans:
         bf.bf_autotune(p, 1080, 1920)
-    chosen = bf.bf_autotune_group(plans, 1080, 1920, n_streams=3)
+    chosen = bf.bf_autotune_group(plans, 1080, 1920, n_streams=4)
     src = torch.from_numpy(img).cuda()
     outs = [torch.full_like(src, float("nan")) for _ in plans]
     main = torch.cuda.current_stream()
-    streams = [torch.cuda.Stream() for _ in range(3)]
+    streams = [torch.cuda.Stream() for _ in range(4)]
     fork = torch.cuda.Event()
     fork.record(main)
     for s in streams:
         s.wait_event(fork)
     for n, (p, o) in enumerate(zip(plans, outs)):
-        bf.bf_filter(p, src, o, stream=streams[n % 3])
+        bf.bf_filter(p, src, o, stream=streams[n % 4])
     for s in streams:
         main.wait_stream(s)
     torch.cuda.synchronize()
