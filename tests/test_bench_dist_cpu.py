@@ -85,3 +85,19 @@ def test_reference_arm_other_ranks_print_nothing():
     rc, out = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0"],
                          {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert rc == 0 and out == []
+
+
+def test_roofline_op_count_of_the_benchmark_plans():
+    """F = N_img (2 n_x + 2 n_xy + n_pm) + 4 (N_r - 1) + 6 k_max + 2 per pixel.  The five-term Gaussian of the
+    benchmark (phi phi, phi psi_{1,+-1}, psi_{1,+-1} phi) has two box widths (2 T_s and T_s), three shapes and nine
+    signed boxes; with N_r = 8 (k = 0..7) N_img = 30, so F = 30 * 19 + 28 + 42 + 2 = 642 at every sigma."""
+    import bench
+    import paper_1803_00004_gb300 as bf
+    for ss in (2.0, 8.0, 32.0):
+        c = bf.Plan(device=-1, sigma_s=ss, sigma_r=0.1, nr_terms=8, ns_terms=5).coeffs()
+        assert bench.box_counts(c) == (2, 3, 9)
+        assert bench.algorithmic_ops_per_pixel(c) == 642
+    # a single box (N_s = 1): one width, one shape, one box
+    c = bf.Plan(device=-1, sigma_s=4.0, sigma_r=0.1, nr_terms=8, ns_terms=1).coeffs()
+    assert bench.box_counts(c) == (1, 1, 1)
+    assert bench.algorithmic_ops_per_pixel(c) == 30 * 5 + 28 + 42 + 2
