@@ -318,8 +318,8 @@ bf_status bf_autotune_image(const bf_plan *plan, const float *d_in, size_t in_pi
  * i mod n_streams (1..8) in the given order, forked from and joined to one
  * stream.  The fastest launch geometries for that whole group are found by
  * coordinate descent (one kernel class at a time over the candidates
- * bf_autotune times, two sweeps, then every tile width and height of each
- * class's chosen family and terms per CTA), timed with CUDA events from the fork to the
+ * bf_autotune times, two sweeps, then every tile height of each class's chosen
+ * width and family), timed with CUDA events from the fork to the
  * join on synthetic height x width images in the first plan's data range, and
  * pinned as bf_set_launch does.  Plans with the same kernel class, reach and
  * image size share one geometry.  A geometry that is slower alone can win in

@@ -344,19 +344,17 @@ extern "C" bf_status bf_autotune_group(const bf_plan *const *plans, int n, int h
                 }
                 cur[c] = keep;
             }
-        // tile-shape refinement: the cost model ranks geometries by a launch's own cost, so its best
-        // candidates rarely include a taller or narrower tile; in a concurrent group one can win (fewer CTAs leave
-        // SMs to the other streams, and the window start-up is spread over more rows).  Each class keeps its
-        // chosen family, exchange depth and terms per CTA and tries every tile width and height.
+        // tile-height refinement: the cost model ranks geometries by a launch's own cost, so its best
+        // candidates rarely include a taller tile; in a concurrent group one can win (fewer CTAs leave SMs to the
+        // other streams, and the window start-up is spread over more rows).  Each class keeps its chosen width,
+        // family and terms per CTA and tries every tile height.
         for (int c = 0; c < nc && best < 1e30f; ++c) {
             const bf_plan *pl = plans[rep[c]];
             TileConfig keep = cur[c];
-            const TileConfig base = cur[c];
             for (const auto &cand : tile_candidates(pl->kp, height, width, pl->desc.precision, 1 << 20)) {
-                if (cand.nk != base.nk || cand.ring != base.ring || cand.depth != base.depth ||
-                    cand.packed != base.packed || cand.pre != base.pre ||
-                    (cand.tw == keep.tw && cand.th == keep.th && cand.ncols == keep.ncols) ||
-                    scratch_bytes(cand, height, width, pl->kp.zbins) > scratch_bytes(base, height, width, pl->kp.zbins))
+                if (cand.tw != keep.tw || cand.ncols != keep.ncols || cand.nk != keep.nk || cand.ring != keep.ring ||
+                    cand.depth != keep.depth || cand.packed != keep.packed || cand.pre != keep.pre || cand.th == keep.th ||
+                    scratch_bytes(cand, height, width, pl->kp.zbins) > scratch_bytes(keep, height, width, pl->kp.zbins))
                     continue;
                 cur[c] = cand;
                 const float t = time_group();
