@@ -244,3 +244,43 @@ def test_server_plan_build_is_inside_the_latency():
     st, r = srv.poll(t, -1)
     assert st == 0 and r.status == bf.ERR_INVALID_ARG
     srv.close()
+
+
+def test_server_mixed_memory_precision_and_3d_requests():
+    """Host and device-pointer requests, fp32, 16-bit basis and 3-D plans arriving together: each result equals
+    the same plan filtered alone by bf_filter (within the bar; bit-equal is not required, the batched launch may
+    pick another geometry)."""
+    rng = np.random.default_rng(31)
+    srv = bf.Server(max_slots=16, n_streams=3, max_batch=5)
+    jobs = []
+    for i in range(18):
+        s = int(rng.integers(48, 400))
+        img = synth.shapes(s, s + int(rng.integers(0, 60)), 900 + i, scale=s / 1080.0)
+        kind = i % 3
+        kw = dict(sigma_s=float(rng.uniform(1.5, 12.0)), sigma_r=float(rng.uniform(0.05, 0.3)))
+        if kind == 1:
+            kw["precision"] = bf.PREC_FP16 if i % 2 else bf.PREC_BF16
+        if kind == 2:
+            kw.update(policy=bf.RANGE_PAPER_3D, z_bins=256, nr_terms=4)
+        dev = bool(rng.integers(0, 2))
+        H, W = img.shape
+        if dev:
+            src = torch.from_numpy(img).cuda()
+            dst = torch.full_like(src, float("nan"))
+            torch.cuda.synchronize()
+            t = srv.submit(bf.desc(**kw), src.data_ptr(), dst.data_ptr(), H, W, memory=bf.MEM_DEVICE)
+        else:
+            src, dst = pinned(img)
+            t = srv.submit(bf.desc(**kw), src.data_ptr(), dst.data_ptr(), H, W)
+        jobs.append((t, img, kw, src, dst))
+    for t, img, kw, src, dst in jobs:
+        st, r = srv.poll(t, -1)
+        assert st == 0 and r.status == 0, (kw, st, r.status)
+        plan = bf.Plan(device=0, **kw)
+        x = torch.from_numpy(img).cuda()
+        y = torch.empty_like(x)
+        bf.bf_filter(plan, x, y)
+        torch.cuda.synchronize()
+        got = dst.cpu().numpy() if dst.is_cuda else dst.numpy()
+        assert np.max(np.abs(got - y.cpu().numpy())) < MIX_TOL, kw
+    srv.close()

@@ -156,3 +156,42 @@ def test_random_3d_plan_and_geometry_match_oracle(H, W, gen, seed_img, seed_geo,
         got = dst.cpu().numpy().astype(np.float64)
         err = np.abs(got - ref)
         assert np.all(err[check] <= bound[check]), (kw, series, Z, geo, float(np.max(err[check] / bound[check])))
+
+
+@pytest.mark.parametrize("H,W,gen,seed_img,seed_geo,kw", _cases(12, 2028))
+def test_random_plan_with_16bit_basis_within_its_bound(H, W, gen, seed_img, seed_geo, kw):
+    """Random plans with the base rotation stored in fp16 or bf16 (alternating by seed), in the default and a
+    random geometry: every pixel within the fp32 bound plus the 16-bit storage term 2 u sum m_k |a_k|
+    (1 + |I^|) mass / |den|, m_k <= min(k, NK) rotations from an fp32 anchor, u the unit roundoff."""
+    from scipy import ndimage
+    prec = bf.PREC_FP16 if seed_geo % 2 == 0 else bf.PREC_BF16
+    u = 2.0 ** -11 if prec == bf.PREC_FP16 else 2.0 ** -8
+    img = _image(H, W, gen, seed_img)
+    plan = bf.Plan(device=0, precision=prec, **kw)
+    ref, _, den = O.approx_fast(img.astype(np.float64), O.Desc(**kw), threads=16, return_den=True)
+    p = O.plan_info(O.Desc(**kw))
+    mass = ndimage.correlate(np.ones(img.shape), np.abs(p.Ks[::-1, ::-1]), mode="constant", cval=0.0)
+    ratio = np.abs(den) / mass
+    ak = np.abs(np.asarray(p.ak))
+    ks = np.asarray(p.ks)
+    src = torch.from_numpy(img).cuda()
+    default = bf.bf_launch_info(plan, H, W)
+    cands = bf.bf_launch_candidates(plan, H, W)
+    assert cands and all(c["pre"] == (2 if prec == bf.PREC_FP16 else 3) for c in cands)
+    pick = cands[np.random.default_rng(seed_geo).integers(0, len(cands))]
+    check = np.abs(den) > 10 * plan.coeffs()["den_eps"]
+    for geo in (None, pick):
+        nk = (geo or default)["nk"]
+        coef = 2e-7 * ak.sum() + 2.0 * u * float(np.sum(np.minimum(ks, nk) * ak))
+        bound = TOL + coef * (1 + np.abs(ref)) / np.maximum(ratio, 1e-12)
+        if geo is not None:
+            bf.bf_set_launch(plan, H, W, geo)
+        dst = torch.full_like(src, float("nan"))
+        try:
+            bf.bf_filter(plan, src, dst)
+            torch.cuda.synchronize()
+        finally:
+            if geo is not None:
+                bf.bf_set_launch(plan, H, W, default)
+        err = np.abs(dst.cpu().numpy().astype(np.float64) - ref)
+        assert np.all(err[check] <= bound[check]), (kw, prec, geo, float(np.max(err[check] / bound[check])))
