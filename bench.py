@@ -691,7 +691,15 @@ def run_batched(bf, dev, n=512, lo=64, hi=2048, reps=3):
     tune_s = time.perf_counter() - t0
     t_batch = timed(lambda: bf.bf_filter_batch(plans, srcs, dsts, stream=stream))
     t_seq = timed(lambda: [bf.bf_filter(p, x, y, stream=stream) for p, x, y in zip(plans, srcs, dsts)])
+    # the same batch with the basis stored in fp16 (each image one launch sequence inside the batch's graph): its
+    # throughput, and its largest difference from the fp32 batch
+    import torch as _t
+    ref = [d.clone() for d in dsts]
+    plans16 = [bf.Plan(device=dev.index or 0, precision=bf.PREC_FP16, **kw) for _, kw in work]
+    t_b16 = timed(lambda: bf.bf_filter_batch(plans16, srcs, dsts, stream=stream))
+    d16 = max(_t.max(_t.abs(a - b)).item() for a, b in zip(dsts, ref))
     return {"images": n, "sides": [lo, hi], "mpix": round(px / 1e6, 2),
+            "batched_fp16_basis_mpix_s": round(px / (t_b16 * 1e-3) / 1e6, 1), "fp16_max_abs_vs_fp32": round(d16, 6),
             "batched_mpix_s": round(px / (t_batch * 1e-3) / 1e6, 1), "batched_ms": round(t_batch, 3),
             "batched_default_mpix_s": round(px / (t_default * 1e-3) / 1e6, 1), "autotune_s": round(tune_s, 1),
             "sequential_mpix_s": round(px / (t_seq * 1e-3) / 1e6, 1), "sequential_ms": round(t_seq, 3)}
