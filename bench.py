@@ -698,8 +698,12 @@ def run_batched(bf, dev, n=512, lo=64, hi=2048, reps=3):
     plans16 = [bf.Plan(device=dev.index or 0, precision=bf.PREC_FP16, **kw) for _, kw in work]
     t_b16 = timed(lambda: bf.bf_filter_batch(plans16, srcs, dsts, stream=stream))
     d16 = max(_t.max(_t.abs(a - b)).item() for a, b in zip(dsts, ref))
+    sq = sum(_t.sum((a.double() - b.double()) ** 2).item() for a, b in zip(dsts, ref))
+    big = sum(int(_t.sum(_t.abs(a - b) > 1e-3).item()) for a, b in zip(dsts, ref))
     return {"images": n, "sides": [lo, hi], "mpix": round(px / 1e6, 2),
             "batched_fp16_basis_mpix_s": round(px / (t_b16 * 1e-3) / 1e6, 1), "fp16_max_abs_vs_fp32": round(d16, 6),
+            "fp16_psnr_db_vs_fp32": round(10 * np.log10(px / sq), 2) if sq > 0 else None,
+            "fp16_pixels_off_by_1e-3": big,
             "batched_mpix_s": round(px / (t_batch * 1e-3) / 1e6, 1), "batched_ms": round(t_batch, 3),
             "batched_default_mpix_s": round(px / (t_default * 1e-3) / 1e6, 1), "autotune_s": round(tune_s, 1),
             "sequential_mpix_s": round(px / (t_seq * 1e-3) / 1e6, 1), "sequential_ms": round(t_seq, 3)}
