@@ -131,6 +131,12 @@ __device__ __forceinline__ int pos_mod(int a, int d) {
     return r < 0 ? r + d : r;
 }
 
+// j mod depth for j >= 0 and the exchange depths the launch accepts (2 or 3): a mask or a division by the
+// constant 3, not a division by a runtime value.
+__device__ __forceinline__ int mod_depth(int j, int depth) {
+    return depth == 2 ? (j & 1) : (int)((unsigned)j % 3u);
+}
+
 // Ring slot of row y + off given ys = y mod D and off in [-D, D].
 __device__ __forceinline__ int ring_slot(int ys, int off, int D) {
     int s = ys + off;
@@ -388,8 +394,8 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
                     if (k0 >= 2) ringB[sl] = make_float2(c, s);
                 }
             }
-            float2 *zb = reinterpret_cast<float2 *>(zb0 + ((j % depth) * ZC + tid + 1) * NRP);
-            float4 *wb = wb0 + (j % depth) * NP * tw;
+            float2 *zb = reinterpret_cast<float2 *>(zb0 + (mod_depth(j, depth) * ZC + tid + 1) * NRP);
+            float4 *wb = wb0 + mod_depth(j, depth) * NP * tw;
             // one edge at a time: its term pairs update the sums of its window (only one edge's state is live)
 #pragma unroll
             for (int e = 0; e < NE; ++e) {
@@ -482,7 +488,7 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
             if (l < NROW / 2) {
                 const int q = (2 * l) / (4 * NK);
                 const int u0 = p.u0[q], u1 = p.u1[q];
-                float2 *row = reinterpret_cast<float2 *>(zb0 + ((j - 1) % depth) * ZC * NRP) + l;
+                float2 *row = reinterpret_cast<float2 *>(zb0 + mod_depth(j - 1, depth) * ZC * NRP) + l;
                 // tile column c is buffer column c + rx + 1; Z(c) at row[(c + rx + 1) * NP2]
                 float2 S = make_float2(0.f, 0.f), comp = make_float2(0.f, 0.f);
                 if (seg == 0 && cB > 0) {
@@ -553,8 +559,8 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
         if (depth == 2) __syncthreads();
         if (is_out && j >= lag && (!ZB || ((zrow >> lag) & 1u))) {
             const int yo = y - lag;
-            const int zo = ((j - lag) % depth) * ZC * NP2;
-            const float4 *wp = wb0 + ((j - lag) % depth) * NP * tw + xl;
+            const int zo = mod_depth(j - lag, depth) * ZC * NP2;
+            const float4 *wp = wb0 + mod_depth(j - lag, depth) * NP * tw + xl;
             const int x = x0 + xl;
             const size_t plane = (size_t)H * W, px = (size_t)yo * W + x;
             float2 num2 = make_float2(0.f, 0.f), den2 = make_float2(0.f, 0.f);

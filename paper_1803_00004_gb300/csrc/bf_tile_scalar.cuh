@@ -56,6 +56,12 @@ __device__ __forceinline__ int pos_mod(int a, int d) {
     return r < 0 ? r + d : r;
 }
 
+// j mod depth for j >= 0 and the exchange depths the launch accepts (2 or 3): a mask or a division by the
+// constant 3, not a division by a runtime value.
+__device__ __forceinline__ int mod_depth(int j, int depth) {
+    return depth == 2 ? (j & 1) : (int)((unsigned)j % 3u);
+}
+
 // Ring slot of row y + off given ys = y mod D and off in [-D, D].
 __device__ __forceinline__ int ring_slot(int ys, int off, int D) {
     int s = ys + off;
@@ -265,8 +271,8 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
                     basis_start(Ie[e], p.inv_p, p.inv_p_lo, k0, valid, c1[e], s1[e], ce[e], se[e]);
                 }
             }
-            float2 *zb = reinterpret_cast<float2 *>(zb0 + ((j % depth) * ZC + tid + 1) * NRP);
-            float2 *wb = wb0 + (j % depth) * NK * tw;
+            float2 *zb = reinterpret_cast<float2 *>(zb0 + (mod_depth(j, depth) * ZC + tid + 1) * NRP);
+            float2 *wb = wb0 + mod_depth(j, depth) * NK * tw;
 #pragma unroll
             for (int i = 0; i < NK; ++i) {
                 if (i > 0) {  // one uniform branch per term
@@ -308,7 +314,7 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
                 // slide has consumed (index c + u0 + 1 in buffer coordinates)
                 const int q = r / (NK * 4);
                 const int u0 = p.u0[q], u1 = p.u1[q];
-                float *row = zb0 + ((j - 1) % depth) * ZC * NRP + r;
+                float *row = zb0 + mod_depth(j - 1, depth) * ZC * NRP + r;
                 float S = 0.f, comp = 0.f;
                 int b = p.rx + u0 + 1;
                 const int bend = p.rx + u1 + 1;
@@ -338,8 +344,8 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
         if (depth == 2) __syncthreads();
         if (is_out && j >= lag) {
             const int yo = y - lag;
-            const int zo = ((j - lag) % depth) * ZC * (NRP / 2);
-            const float2 *wp = wb0 + ((j - lag) % depth) * NK * tw + xl;
+            const int zo = mod_depth(j - lag, depth) * ZC * (NRP / 2);
+            const float2 *wp = wb0 + mod_depth(j - lag, depth) * NK * tw + xl;
             float num = 0.f, den = 0.f;
 #pragma unroll
             for (int i = 0; i < NK; ++i) {
