@@ -223,8 +223,8 @@ typedef struct {
 bf_status bf_coeffs(const bf_plan *plan, bf_coeff_view *out);
 
 /* Filters one image on the device (hot path, Eq. (36) then divide).
- * d_in / d_out: device buffers of height rows with the given pitches.
- * height, width >= 0 (0 is a no-op).  Asynchronous on `stream`.
+ * d_in / d_out: device buffers of height rows with the given pitches (bytes, multiples of 4, at least
+ * width * 4 and below 4 GiB).  height, width >= 0 (0 is a no-op).  Asynchronous on `stream`.
  * Errors: BF_ERR_INVALID_ARG (NULL, pitch, overlap), BF_ERR_NO_DEVICE
  * (host-only plan), BF_ERR_CUDA (launch failure), BF_ERR_OOM (scratch for
  * multi-pass plans could not be allocated). */

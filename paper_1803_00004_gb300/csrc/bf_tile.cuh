@@ -268,9 +268,17 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
         ss = pair(s2);
         nss = pair(-s2);
     };
+    // Row addresses as one 32 x 32 -> 64-bit multiply-add on this column's base address (the launch keeps row
+    // pitches below 2^32 bytes; rows are loaded only inside [0, H)).
+    const char *col_in = reinterpret_cast<const char *>(in + (colv ? xcol : 0));
+    const unsigned in_pb = (unsigned)(in_pitch * sizeof(float));
+    const char *col_pre = reinterpret_cast<const char *>(pre) + (PRE && colv ? (size_t)xcol * sizeof(PF) : 0);
+    const unsigned pre_pb = (unsigned)((size_t)W * sizeof(PF));
     // pixel (minus i_lo) of this thread's column at image row `row`, 0 outside the image
     auto pixel = [&](int row) -> float {
-        return (colv && row >= 0 && row < H) ? __ldg(in + (size_t)row * in_pitch + xcol) - p.i_lo : 0.f;
+        return (colv && (unsigned)row < (unsigned)H)
+                   ? __ldg(reinterpret_cast<const float *>(col_in + (size_t)(unsigned)row * in_pb)) - p.i_lo
+                   : 0.f;
     };
     // what an edge loads one step ahead: the pixel, or (PRE) its pre-pass element (zero outside the image)
     auto edge_load = [&](int row) -> PF {
@@ -280,7 +288,9 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
             PF z;
             if constexpr (PRE == 1) z = make_float4(0.f, 0.f, 0.f, 0.f);
             else z = make_float2(0.f, 0.f);
-            return (colv && row >= 0 && row < H) ? __ldg(reinterpret_cast<const PF *>(pre) + (size_t)row * W + xcol) : z;
+            return (colv && (unsigned)row < (unsigned)H)
+                       ? __ldg(reinterpret_cast<const PF *>(col_pre + (size_t)(unsigned)row * pre_pb))
+                       : z;
         }
     };
     // the pixel and the basis of a loaded element: v (0 when !valid), base rotation (c1, s1) and the group's

@@ -60,6 +60,8 @@ bf_status check_image(const float *d_in, size_t in_pitch, const float *d_out, si
         return fail(BF_ERR_INVALID_ARG, "pitch must be a multiple of 4 bytes");
     if (in_pitch < (size_t)w * sizeof(float) || out_pitch < (size_t)w * sizeof(float))
         return fail(BF_ERR_INVALID_ARG, "pitch smaller than width * 4");
+    // the kernels form row addresses with a 32-bit byte pitch
+    if (in_pitch > 0xffffffffu || out_pitch > 0xffffffffu) return fail(BF_ERR_INVALID_ARG, "pitch of 4 GiB or more");
     size_t in_len = (size_t)(h - 1) * in_pitch + (size_t)w * sizeof(float);
     size_t out_len = (size_t)(h - 1) * out_pitch + (size_t)w * sizeof(float);
     if (ranges_overlap(d_in, in_len, d_out, out_len))

@@ -112,7 +112,7 @@ bf_status bf_precompute(const bf_plan *plan, const float *d_in, size_t in_pitch,
     if (!plan || !out || kmax < 2 || kmax > kMaxSlots || precision < BF_PREC_FP32 || precision > BF_PREC_FP16)
         return fail(BF_ERR_INVALID_ARG, "bad pre-computation arguments");
     if (height < 1 || width < 1) return fail(BF_ERR_INVALID_ARG, "empty image");
-    if (!d_in || in_pitch % sizeof(float) || in_pitch < (size_t)width * sizeof(float))
+    if (!d_in || in_pitch % sizeof(float) || in_pitch < (size_t)width * sizeof(float) || in_pitch > 0xffffffffu)
         return fail(BF_ERR_INVALID_ARG, "NULL input or bad pitch");
     bf_status st = BF_OK;
     if (plan->kp.zbins > 0)
