@@ -410,6 +410,7 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
 #pragma unroll
             for (int e = 0; e < NE; ++e) {
                 if (RING && e == 2 * M) continue;  // RING: the output phase rebuilds the output row's basis
+                if (e == 2 * M && !is_out) continue;  // the output row's weights are only needed by output columns
                 const int off = edge_off(e);
                 const int row = y + off;
                 // at j == 0 the sums already hold row y0: only the output-row edge is live
