@@ -259,16 +259,19 @@ bf_status bf_filter_noalloc(const bf_plan *plan, const float *d_in, size_t in_pi
  * bytes; pinned memory makes the copies asynchronous), filters it with plan i
  * on internal stream i mod n_streams (1..8), forked from and joined back to
  * `stream`, and downloads result i into h_outs[i] (row pitch out_pitch bytes)
- * on the same internal stream as soon as its filter ends.  Asynchronous on
+ * on an internal copy stream as soon as its filter ends.  Asynchronous on
  * `stream`: synchronize it before reading h_outs.  The device buffers (input,
- * n outputs, each plan's scratch) are one block per device owned by the
- * library, allocated by the first call and grown when a call needs more;
- * calls on a device are chained on the device (each call's upload waits for
- * the previous call's last download), so calls from several streams or
- * threads are safe and run one after another.  A call that allocates or
- * grows the block synchronizes with the previous call's work: make the first
- * call (at the largest size and plan count) outside stream capture.  Plans'
- * geometries as bf_filter's; the debug input-range check does not apply.  Errors:
+ * n outputs, each plan's scratch) are two blocks per device owned by the
+ * library, used by alternate calls, allocated by the first calls and grown
+ * when a call needs more.  A call's upload waits for the last download of the
+ * call two before it on the device (the previous user of its block), so calls
+ * from several streams or threads are safe, and a call issued on another
+ * stream than the one before it uploads its image while that call still
+ * filters (double buffering); calls on one stream run one after another.  A
+ * call that allocates or grows a block synchronizes with that block's previous
+ * call: make the first two calls (at the largest size and plan count) outside
+ * stream capture.  Plans' geometries as bf_filter's; the debug input-range
+ * check does not apply.  Errors:
  * BF_ERR_INVALID_ARG (NULL, n or n_streams out of range, bad pitch, overlap,
  * plans on several devices), BF_ERR_NO_DEVICE, BF_ERR_OOM, BF_ERR_CUDA. */
 bf_status bf_filter_host(const bf_plan *const *plans, int n, const float *h_in, size_t in_pitch,

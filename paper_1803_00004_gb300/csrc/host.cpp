@@ -1,12 +1,14 @@
 // bf_filter_host: the filter for images in host memory.  One call uploads the
 // image, filters it with each of n plans (the paper's use of one image under
 // several parameter settings, Sec. V-C) on internal compute streams, and
-// downloads each result as soon as its filter ends.  Device buffers (the
-// input, n outputs and each plan's scratch) come from one block per device,
-// allocated on first use and grown when a call needs more, so steady-state
-// calls allocate nothing.  Calls on a device are chained on the device by an
-// event (each call's upload waits for the previous call's last download), so
-// the shared block is never used by two calls at once.
+// downloads each result on an internal copy stream as soon as its filter ends.
+// Device buffers (the input, n outputs and each plan's scratch) come from two
+// blocks per device, used by alternate calls, allocated on first use and grown
+// when a call needs more, so steady-state calls allocate nothing.  A call's
+// upload waits for the last download of the call two before it (the previous
+// user of its block), so a call issued on another stream than the one before it
+// uploads while that one still computes; calls on one stream run one after
+// another, as that stream orders them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -24,14 +26,22 @@ bf_status filter_image(const bf_plan *plan, const TileConfig &tc, const float *d
 namespace {
 
 constexpr int kMaxStreams = 8;
+constexpr int kCopyStreams = 2;
+constexpr int kBlocks = 2;
 constexpr int kMaxDevices = 64;
+
+struct Block {
+    char *mem = nullptr;
+    size_t bytes = 0;
+    cudaEvent_t done = nullptr;  // the last download of the call that used this block last
+};
 
 struct DeviceState {
     std::mutex mu;
-    char *block = nullptr;
-    size_t bytes = 0;
-    cudaStream_t streams[kMaxStreams] = {};
-    cudaEvent_t fork = nullptr, joins[kMaxStreams] = {}, done = nullptr;
+    Block blocks[kBlocks];
+    unsigned next = 0;  // block of the next call
+    cudaStream_t streams[kMaxStreams] = {}, copies[kCopyStreams] = {};
+    cudaEvent_t fork = nullptr, filtered[kMaxStreams] = {}, copied[kCopyStreams] = {};
     bool ready = false;
 };
 
@@ -46,15 +56,21 @@ bf_status cuda_fail(cudaError_t e, const char *what) {
 
 bf_status setup(DeviceState &d) {
     if (d.ready) return BF_OK;
-    cudaError_t e = cudaEventCreateWithFlags(&d.fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d.done, cudaEventDisableTiming);
+    const unsigned flags = cudaEventDisableTiming;
+    cudaError_t e = cudaEventCreateWithFlags(&d.fork, flags);
     for (int i = 0; i < kMaxStreams && e == cudaSuccess; ++i) {
         e = cudaStreamCreateWithFlags(&d.streams[i], cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d.joins[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d.filtered[i], flags);
     }
-    if (e != cudaSuccess) return cuda_fail(e, "host-filter streams");
-    e = cudaEventRecord(d.done, d.streams[0]);  // nothing to wait for yet
-    if (e != cudaSuccess) return cuda_fail(e, "host-filter events");
+    for (int i = 0; i < kCopyStreams && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&d.copies[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d.copied[i], flags);
+    }
+    for (int b = 0; b < kBlocks && e == cudaSuccess; ++b) {
+        e = cudaEventCreateWithFlags(&d.blocks[b].done, flags);
+        if (e == cudaSuccess) e = cudaEventRecord(d.blocks[b].done, d.streams[0]);  // nothing to wait for yet
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "host-filter streams and events");
     d.ready = true;
     return BF_OK;
 }
@@ -93,55 +109,71 @@ extern "C" bf_status bf_filter_host(const bf_plan *const *plans, int n, const fl
         scr[i] = align_up(bfi::scratch_bytes(tcs[i], height, width, plans[i]->kp.zbins));
         need += scr[i];
     }
+    Block &blk = d.blocks[d.next % kBlocks];
     cudaStream_t s = (cudaStream_t)stream;
-    if (st == BF_OK && need > d.bytes) {
-        // the previous call's work must finish before its block goes
-        cudaError_t e = cudaEventSynchronize(d.done);
-        if (e == cudaSuccess && d.block) e = cudaFree(d.block);
-        d.block = nullptr;
-        d.bytes = 0;
-        if (e == cudaSuccess) e = cudaMalloc((void **)&d.block, need);
+    if (st == BF_OK && need > blk.bytes) {
+        // the block's previous call must finish before the block goes
+        cudaError_t e = cudaEventSynchronize(blk.done);
+        if (e == cudaSuccess && blk.mem) e = cudaFree(blk.mem);
+        blk.mem = nullptr;
+        blk.bytes = 0;
+        if (e == cudaSuccess) e = cudaMalloc((void **)&blk.mem, need);
         if (e != cudaSuccess) {
             cudaGetLastError();
             st = bfi::fail(BF_ERR_OOM, "host-filter device block of " + std::to_string(need) + " bytes");
         } else {
-            d.bytes = need;
+            blk.bytes = need;
         }
     }
-    cudaError_t e = cudaSuccess;
-    float *d_in = reinterpret_cast<float *>(d.block);
-    if (st == BF_OK) {
-        // upload after the previous call's last download, then fork to the compute streams
-        e = cudaStreamWaitEvent(s, d.done, 0);
-        if (e == cudaSuccess) e = cudaMemcpy2DAsync(d_in, row, h_in, in_pitch, row, height, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaEventRecord(d.fork, s);
-        for (int k = 0; k < n_streams && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(d.streams[k], d.fork, 0);
-        if (e != cudaSuccess) st = cuda_fail(e, "host-filter upload");
+    if (st != BF_OK) {
+        if (prev != device) cudaSetDevice(prev);
+        return st;
     }
-    char *scratch = d.block + img * (1 + (size_t)n);
+    ++d.next;
+    cudaError_t e = cudaSuccess;
+    float *d_in = reinterpret_cast<float *>(blk.mem);
+    // upload once the block's previous call has downloaded its last result, then fork to the compute streams
+    e = cudaStreamWaitEvent(s, blk.done, 0);
+    if (e == cudaSuccess) e = cudaMemcpy2DAsync(d_in, row, h_in, in_pitch, row, height, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(d.fork, s);
+    for (int k = 0; k < n_streams && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(d.streams[k], d.fork, 0);
+    // the copy streams start after the fork too, so that a join below never waits on older work only
+    for (int k = 0; k < kCopyStreams && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(d.copies[k], d.fork, 0);
+    if (e != cudaSuccess) st = cuda_fail(e, "host-filter upload");
+    char *scratch = blk.mem + img * (1 + (size_t)n);
     for (int i = 0; i < n && st == BF_OK; ++i) {
-        cudaStream_t cs = d.streams[i % n_streams];
-        float *d_out = reinterpret_cast<float *>(d.block + img * (1 + (size_t)i));
+        const int k = i % n_streams;
+        cudaStream_t cs = d.streams[k], ds = d.copies[i % kCopyStreams];
+        float *d_out = reinterpret_cast<float *>(blk.mem + img * (1 + (size_t)i));
         st = bfi::filter_image(plans[i], tcs[i], d_in, row, d_out, row, height, width,
                                scr[i] ? reinterpret_cast<float *>(scratch) : nullptr, cs);
         scratch += scr[i];
         if (st == BF_OK) {
-            e = cudaMemcpy2DAsync(h_outs[i], out_pitch, d_out, row, row, height, cudaMemcpyDeviceToHost, cs);
+            // the download waits for this filter only (the event's record at this point of the compute stream)
+            e = cudaEventRecord(d.filtered[k], cs);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(ds, d.filtered[k], 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DAsync(h_outs[i], out_pitch, d_out, row, row, height, cudaMemcpyDeviceToHost, ds);
             if (e != cudaSuccess) st = cuda_fail(e, "host-filter download");
         }
     }
-    // join (also after a failure, so that the chain stays ordered)
-    if (d.ready && d.block) {
-        for (int k = 0; k < n_streams; ++k)
-            if (cudaEventRecord(d.joins[k], d.streams[k]) != cudaSuccess ||
-                cudaStreamWaitEvent(s, d.joins[k], 0) != cudaSuccess) {
-                cudaGetLastError();
-                if (st == BF_OK) st = bfi::fail(BF_ERR_CUDA, "host-filter join");
-            }
-        if (cudaEventRecord(d.done, s) != cudaSuccess) {
+    // join the compute and copy streams back to `stream` (also after a failure, so that the block's next call
+    // waits for everything this one enqueued)
+    for (int k = 0; k < n_streams; ++k)
+        if (cudaEventRecord(d.filtered[k], d.streams[k]) != cudaSuccess ||
+            cudaStreamWaitEvent(s, d.filtered[k], 0) != cudaSuccess) {
             cudaGetLastError();
             if (st == BF_OK) st = bfi::fail(BF_ERR_CUDA, "host-filter join");
         }
+    for (int k = 0; k < kCopyStreams; ++k)
+        if (cudaEventRecord(d.copied[k], d.copies[k]) != cudaSuccess ||
+            cudaStreamWaitEvent(s, d.copied[k], 0) != cudaSuccess) {
+            cudaGetLastError();
+            if (st == BF_OK) st = bfi::fail(BF_ERR_CUDA, "host-filter join");
+        }
+    if (cudaEventRecord(blk.done, s) != cudaSuccess) {
+        cudaGetLastError();
+        if (st == BF_OK) st = bfi::fail(BF_ERR_CUDA, "host-filter join");
     }
     if (prev != device) cudaSetDevice(prev);
     return st;

@@ -75,3 +75,25 @@ def test_host_call_pitched_buffers_and_errors():
     with pytest.raises(bf.BFError) as ei:
         bf.bf_filter_host([plan], big_in[:, :200], [big_out[:, :200]], n_streams=9)
     assert ei.value.status == bf.ERR_INVALID_ARG
+
+
+def test_host_calls_alternating_streams_overlap_without_mixing_images():
+    # consecutive calls on two streams use the library's two device blocks in turn and overlap on the GPU; every
+    # call's outputs must still be its own image's, also when a block grows in the middle of the run
+    plans = [bf.Plan(device=0, sigma_s=ss, sigma_r=0.1) for ss in (2.0, 6.0, 16.0)]
+    imgs = [synth.shapes(360, 480, 60 + i, scale=0.4) for i in range(3)] + [synth.blocks(420, 560, 63)]
+    order = [0, 1, 2, 0, 3, 1, 3, 2]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    res = []
+    for k, ii in enumerate(order):
+        h_in = torch.from_numpy(imgs[ii]).pin_memory()
+        outs = [torch.full(imgs[ii].shape, float("nan")).pin_memory() for _ in plans]
+        bf.bf_filter_host(plans, h_in, outs, n_streams=3, stream=streams[k % 2])
+        res.append((ii, h_in, outs))
+    torch.cuda.synchronize()
+    refs = {}
+    for ii, _, outs in res:
+        if ii not in refs:
+            refs[ii] = [device_ref(p, imgs[ii]) for p in plans]
+        for o, r in zip(outs, refs[ii]):
+            assert torch.equal(o, r)
