@@ -34,7 +34,7 @@ H, W = 1080, 1920
 SIGMA_S = (2.0, 8.0, 32.0)
 SIGMA_R = (0.05, 0.1, 0.3)
 NR, NS = 8, 5
-N_STREAMS = 4   # compute streams the step's filters are spread over
+N_STREAMS = 9   # compute streams the step's filters are spread over (one per filter)
 METRIC = "Mpixel/s at >=40 dB vs exact BF (1920x1080, 9 sigma combos)"
 WORKLOAD = "1920x1080 shapes+noise(0.03), Gaussian/Gaussian, sigma_s in {2,8,32} x sigma_r in {0.05,0.1,0.3}, N_r=8, N_s=5"
 

@@ -257,7 +257,7 @@ bf_status bf_filter_noalloc(const bf_plan *plan, const float *d_in, size_t in_pi
  * device): the paper's use of one image under several parameter settings
  * (Sec. V-C).  Uploads h_in (height rows of width floats, row pitch in_pitch
  * bytes; pinned memory makes the copies asynchronous), filters it with plan i
- * on internal stream i mod n_streams (1..8), forked from and joined back to
+ * on internal stream i mod n_streams (1..16), forked from and joined back to
  * `stream`, and downloads result i into h_outs[i] (row pitch out_pitch bytes)
  * on an internal copy stream as soon as its filter ends.  Asynchronous on
  * `stream`: synchronize it before reading h_outs.  The device buffers (input,
@@ -318,7 +318,7 @@ bf_status bf_autotune_image(const bf_plan *plan, const float *d_in, size_t in_pi
 
 /* Autotuner for plans that filter at the same time: n plans (1..256, all on
  * one device) run as a caller runs them concurrently, plan i on stream
- * i mod n_streams (1..8) in the given order, forked from and joined to one
+ * i mod n_streams (1..16) in the given order, forked from and joined to one
  * stream.  The fastest launch geometries for that whole group are found by
  * coordinate descent (one kernel class at a time over the candidates
  * bf_autotune times, two sweeps, then every tile height of each class's chosen

@@ -25,7 +25,7 @@ bf_status filter_image(const bf_plan *plan, const TileConfig &tc, const float *d
 
 namespace {
 
-constexpr int kMaxStreams = 8;
+constexpr int kMaxStreams = 16;
 constexpr int kCopyStreams = 2;
 constexpr int kBlocks = 2;
 constexpr int kMaxDevices = 64;

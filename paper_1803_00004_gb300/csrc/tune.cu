@@ -230,7 +230,7 @@ extern "C" bf_status bf_autotune_image(const bf_plan *plan, const float *d_in, s
 
 extern "C" bf_status bf_autotune_group(const bf_plan *const *plans, int n, int height, int width, int n_streams,
                                        int *infos) {
-    if (!plans || n < 1 || n > 256 || height < 1 || width < 1 || n_streams < 1 || n_streams > 8)
+    if (!plans || n < 1 || n > 256 || height < 1 || width < 1 || n_streams < 1 || n_streams > 16)
         return fail(BF_ERR_INVALID_ARG, "bad group-autotune arguments");
     for (int i = 0; i < n; ++i)
         if (!plans[i]) return fail(BF_ERR_INVALID_ARG, "null plan in the group");

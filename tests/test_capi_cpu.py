@@ -221,7 +221,7 @@ def test_group_autotune_argument_checks_without_gpu():
     for plans, h, w, ns, status in [([p, q], 64, 64, 3, 9),      # host-only plans: no device to time on
                                     ([], 64, 64, 3, 1),          # no plans
                                     ([p], 64, 64, 0, 1),         # stream count out of range
-                                    ([p], 64, 64, 9, 1),
+                                    ([p], 64, 64, 17, 1),
                                     ([p], 0, 64, 1, 1)]:
         with pytest.raises(bf.BFError) as ei:
             bf.bf_autotune_group(plans, h, w, n_streams=ns)

@@ -116,25 +116,25 @@ def sample_points(H, W, n, seed):
 
 def test_full_size_parity_every_pixel():
     """1920x1080 (the benchmark workload) at each (sigma_s, sigma_r) of the sweep, run as the benchmark runs
-    its step: each plan autotuned, then the nine tuned as a group, filtering concurrently on three streams
-    forked from one, longest first.  Every pixel of every output against the oracle (Eq. (36) and the
+    its step: each plan autotuned, then the nine tuned as a group, filtering concurrently on nine streams
+    forked from one (one per filter), longest first.  Every pixel of every output against the oracle (Eq. (36) and the
     divide of Eq. (1)), under the conditioned 1e-5 bar."""
     img = synth.shapes(1080, 1920, seed=0)
     kws = [dict(sigma_s=ss, sigma_r=sr, nr_terms=8, ns_terms=5) for ss in (32.0, 8.0, 2.0) for sr in (0.05, 0.1, 0.3)]
     plans = [bf.Plan(device=0, **kw) for kw in kws]
     for p in plans:
         bf.bf_autotune(p, 1080, 1920)
-    chosen = bf.bf_autotune_group(plans, 1080, 1920, n_streams=4)
+    chosen = bf.bf_autotune_group(plans, 1080, 1920, n_streams=9)
     src = torch.from_numpy(img).cuda()
     outs = [torch.full_like(src, float("nan")) for _ in plans]
     main = torch.cuda.current_stream()
-    streams = [torch.cuda.Stream() for _ in range(4)]
+    streams = [torch.cuda.Stream() for _ in range(9)]
     fork = torch.cuda.Event()
     fork.record(main)
     for s in streams:
         s.wait_event(fork)
     for n, (p, o) in enumerate(zip(plans, outs)):
-        bf.bf_filter(p, src, o, stream=streams[n % 4])
+        bf.bf_filter(p, src, o, stream=streams[n % 9])
     for s in streams:
         main.wait_stream(s)
     torch.cuda.synchronize()

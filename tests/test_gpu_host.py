@@ -73,7 +73,7 @@ def test_host_call_pitched_buffers_and_errors():
     assert torch.equal(big_out[:, :200], device_ref(plan, img))
     assert torch.isnan(big_out[:, 200:]).all()
     with pytest.raises(bf.BFError) as ei:
-        bf.bf_filter_host([plan], big_in[:, :200], [big_out[:, :200]], n_streams=9)
+        bf.bf_filter_host([plan], big_in[:, :200], [big_out[:, :200]], n_streams=17)
     assert ei.value.status == bf.ERR_INVALID_ARG
 
 
