@@ -163,6 +163,9 @@ def test_filter_argument_checks_without_gpu():
     # bad pitch
     assert L.bf_filter(p.handle, 4096, 6, 1 << 20, 256, 4, 64, None) == 1
     assert L.bf_filter(p.handle, 4096, 64, 1 << 20, 256, 4, 64, None) == 1
+    # pitches of 4 GiB or more (the kernels form row addresses with a 32-bit byte pitch)
+    assert L.bf_filter(p.handle, 1 << 20, 1 << 32, 1 << 44, 256, 2, 64, None) == 1
+    assert L.bf_filter(p.handle, 1 << 20, 256, 1 << 44, (1 << 32) + 256, 2, 64, None) == 1
     # empty image is a no-op
     assert L.bf_filter(p.handle, 0, 0, 0, 0, 0, 5, None) == 0
     # host-only plan cannot filter
