@@ -96,6 +96,19 @@ __device__ __forceinline__ void rotn(float &c, float &s, float c1, float s1, int
     for (int n = 0; n < steps; ++n) rot1(c, s, c1, s1);
 }
 
+// The same with the double rotation (c2, s2) = (cos, sin)(2 pi t) at hand: steps / 2 double steps, then one
+// single step if `steps` is odd (a step of 2, the commonest gap of a best-N selection, is one rotation).
+__device__ __forceinline__ void rotn2(float &c, float &s, float c1, float s1, float c2, float s2, int steps) {
+    for (int n = 0; n + 1 < steps; n += 2) rot1(c, s, c2, s2);
+    if (steps & 1) rot1(c, s, c1, s1);
+}
+
+// (cos, sin) of twice an angle from its (cos, sin).
+__device__ __forceinline__ void double_angle(float c1, float s1, float &c2, float &s2) {
+    c2 = fmaf(c1, c1, -s1 * s1);
+    s2 = 2.f * c1 * s1;
+}
+
 // One tile: output columns [x0, x0 + tw) x rows [y0, y0 + th) of one image,
 // cosine terms [g NK, g NK + NK) of p.  All threads of the CTA call it; it
 // ends on a barrier, so the shared memory can be reused right after.  `grouped`:
@@ -149,6 +162,11 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
         aa[i] = ok ? p.a[j] : 0.f;
     }
     const int k0 = kk[0];
+    // the group steps by 2 or more between some of its frequencies: the double rotation is then computed once per
+    // pixel and edge and used for those steps (uniform over the CTA)
+    bool wide = false;
+#pragma unroll
+    for (int i = 1; i < NK; ++i) wide = wide || kk[i] - kk[i - 1] >= 2;
 
     float V[NK][4][M];
 #pragma unroll
@@ -180,9 +198,14 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
             bool in_w[M];
 #pragma unroll
             for (int r = 0; r < M; ++r) in_w[r] = off >= p.v0[r] && off <= p.v1[r];
+            float c2 = 0.f, s2 = 0.f;
+            if (wide) double_angle(c1, s1, c2, s2);
 #pragma unroll
             for (int i = 0; i < NK; ++i) {
-                if (i > 0) rotn(c, s, c1, s1, kk[i] - kk[i - 1]);
+                if (i > 0) {
+                    if (wide) rotn2(c, s, c1, s1, c2, s2, kk[i] - kk[i - 1]);
+                    else rotn(c, s, c1, s1, kk[i] - kk[i - 1]);
+                }
                 const float gi[4] = {c * v, s * v, c, s};
 #pragma unroll
                 for (int r = 0; r < M; ++r)
@@ -271,6 +294,15 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
                     basis_start(Ie[e], p.inv_p, p.inv_p_lo, k0, valid, c1[e], s1[e], ce[e], se[e]);
                 }
             }
+            // per edge double rotations for the classes with few windows (more edges would spill registers)
+            constexpr bool DBL = M <= 2;
+            float c2[NE], s2[NE];
+#pragma unroll
+            for (int e = 0; e < NE; ++e) {
+                c2[e] = 0.f;
+                s2[e] = 0.f;
+                if (DBL && wide) double_angle(c1[e], s1[e], c2[e], s2[e]);
+            }
             float2 *zb = reinterpret_cast<float2 *>(zb0 + (mod_depth(j, depth) * ZC + tid + 1) * NRP);
             float2 *wb = wb0 + mod_depth(j, depth) * NK * tw;
 #pragma unroll
@@ -280,6 +312,12 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
                     if (steps == 1) {
 #pragma unroll
                         for (int e = 0; e < NE; ++e) rot1(ce[e], se[e], c1[e], s1[e]);
+                    } else if (DBL && steps == 2) {
+#pragma unroll
+                        for (int e = 0; e < NE; ++e) rot1(ce[e], se[e], c2[e], s2[e]);
+                    } else if (DBL) {
+#pragma unroll
+                        for (int e = 0; e < NE; ++e) rotn2(ce[e], se[e], c1[e], s1[e], c2[e], s2[e], steps);
                     } else {
 #pragma unroll
                         for (int e = 0; e < NE; ++e) rotn(ce[e], se[e], c1[e], s1[e], steps);
