@@ -84,6 +84,21 @@ __device__ __forceinline__ void sum_add(float &s, float &c, int compensated, flo
     else s += x;
 }
 
+// The same on a pair of sums (Blackwell's two-wide fp32 instructions; each lane rounded as the scalar
+// instruction would round it): the horizontal pass slides two exchange rows per lane.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ void kahan_add2(float2 &s, float2 &c, float2 x) {
+    const float2 y = sub2(x, c);
+    const float2 t = add2(s, y);
+    c = sub2(sub2(t, s), y);
+    s = t;
+}
+__device__ __forceinline__ void sum_add2(float2 &s, float2 &c, int compensated, float2 x) {
+    if (compensated) kahan_add2(s, c, x);
+    else s = add2(s, x);
+}
+
 // (c, s) = (cos, sin)(pi k t) advanced by one multiple of the base rotation (c1, s1) = (cos, sin)(pi t).
 __device__ __forceinline__ void rot1(float &c, float &s, float c1, float s1) {
     const float cn = fmaf(c, c1, -s * s1);
@@ -125,6 +140,7 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
     // that row pairs move as float2, and NRP / 2 is odd so that a warp's float2 accesses to consecutive
     // columns, and its lanes' float accesses along a column, hit distinct banks.
     constexpr int NRP = NROW + 2;
+    constexpr int NP2 = NRP / 2;  // column pitch in float2 (odd: a warp's float2 accesses along a column hit distinct banks)
     const int ZC = ncols + 2;  // tile column c at index c + 1; columns 0 and ncols + 1 stay 0
     // `depth` exchange buffers: 2 -> the output phase reads the row the scan finished in the same step (two
     // barriers per row); 3 -> it reads the row scanned one step earlier (one barrier per row)
@@ -144,6 +160,9 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
     const int nout = min(y0 + th, H) - y0;
     const int xl = tid - halo;
     const bool is_out = is_col && xl >= 0 && xl < tw && x0 + xl < W;
+    // the two scan warps: warp 0 slides left to right over tile columns [0, cB), warp 1 right to left over
+    // [cB, tw); each writes its sums in place (left: into the slot of Z(c + u0), right: of Z(c + u1))
+    const int cB = (tw >> 4) << 3;
 
     for (int i = tid; i < depth * NRP; i += blockDim.x) {
         const int b = i / NRP, r = i - b * NRP;
@@ -178,8 +197,14 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
 
     // window sums at the first output row: every row of the span once
     // pixel (minus i_lo) of this thread's column at image row `row`, 0 outside the image
+    // row addresses as one 32 x 32 -> 64-bit multiply-add on this column's base address (the launch keeps row
+    // pitches below 2^32 bytes; rows are loaded only inside [0, H))
+    const char *col_in = reinterpret_cast<const char *>(in + (colv ? xcol : 0));
+    const unsigned in_pb = (unsigned)(in_pitch * sizeof(float));
     auto pixel = [&](int row) -> float {
-        return (colv && row >= 0 && row < H) ? __ldg(in + (size_t)row * in_pitch + xcol) - p.i_lo : 0.f;
+        return (colv && (unsigned)row < (unsigned)H)
+                   ? __ldg(reinterpret_cast<const float *>(col_in + (size_t)(unsigned)row * in_pb)) - p.i_lo
+                   : 0.f;
     };
     if (is_col) {
         float vn = pixel(y0 + p.vlo);  // the next row's pixel is loaded one iteration ahead
@@ -221,7 +246,8 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
     int ys = RING ? pos_mod(y0, D) : 0;  // ring slot of row y (advanced each step)
     const float2 *zq[M];                 // output thread: column of window q's sliding sum
 #pragma unroll
-    for (int q = 0; q < M; ++q) zq[q] = reinterpret_cast<const float2 *>(zb0 + (tid + p.u0[q] + 1) * NRP);
+    for (int q = 0; q < M; ++q)
+        zq[q] = reinterpret_cast<const float2 *>(zb0 + (tid + (xl < cB ? p.u0[q] : p.u1[q]) + 1) * NRP);
     // edge offsets: M entering rows, M leaving rows, the output row
     auto edge_off = [&](int e) -> int { return e < M ? p.v1[e] : (e < 2 * M ? p.v0[e - M] - 1 : 0); };
     // The pixels a step needs from global memory are loaded one step ahead, so their latency overlaps the
@@ -346,38 +372,80 @@ __device__ __forceinline__ void tile_body(const FilterParams &p, const float *__
                 if (is_out) wb[i * tw + xl] = make_float2(aa[i] * ce[2 * M], aa[i] * se[2 * M]);
             }
         } else if (!is_col && j >= 1 && j - 1 < nout) {
-            const int r = tid - ncols;
-            if (r < NROW) {
-                // sliding sum of window q over the row; S(c) replaces Z(c + u0), which the
-                // slide has consumed (index c + u0 + 1 in buffer coordinates)
-                const int q = r / (NK * 4);
+            const int st = tid - ncols;
+            const int seg = st >> 5, l = st & 31;  // scan warp, lane = row pair (rows 2l, 2l + 1)
+            float2 held = make_float2(0.f, 0.f);
+            float2 *hp = nullptr;
+            if (l < NROW / 2) {
+                const int q = (2 * l) / (4 * NK);
                 const int u0 = p.u0[q], u1 = p.u1[q];
-                float *row = zb0 + mod_depth(j - 1, depth) * ZC * NRP + r;
-                float S = 0.f, comp = 0.f;
-                int b = p.rx + u0 + 1;
-                const int bend = p.rx + u1 + 1;
-                for (; b + 7 <= bend; b += 8) {
-                    float v[8];
+                float2 *row = reinterpret_cast<float2 *>(zb0 + mod_depth(j - 1, depth) * ZC * NRP) + l;
+                // tile column c is buffer column c + rx + 1; Z(c) at row[(c + rx + 1) * NP2]
+                float2 S = make_float2(0.f, 0.f), comp = make_float2(0.f, 0.f);
+                if (seg == 0 && cB > 0) {
+                    // left to right: S(c + 1) = S(c) + Z(c + 1 + u1) - Z(c + u0); S(c) replaces Z(c + u0)
+                    int b = p.rx + u0 + 1;
+                    const int bend = p.rx + u1 + 1;
+                    for (; b + 7 <= bend; b += 8) {
+                        float2 v[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) v[u] = row[(b + u) * NRP];
-                    sum_add(S, comp, p.kahan, ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])));
-                }
-                float rest = 0.f;
-                for (; b <= bend; ++b) rest += row[b * NRP];
-                sum_add(S, comp, p.kahan, rest);
-                for (int c0 = p.rx; c0 < p.rx + tw; c0 += 8) {
-                    float d[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) d[u] = row[(c0 + u + u1 + 2) * NRP] - row[(c0 + u + u0 + 1) * NRP];
-                    float pd = -comp;
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        row[(c0 + u + u0 + 1) * NRP] = S + pd;
-                        pd += d[u];
+                        for (int u = 0; u < 8; ++u) v[u] = row[(b + u) * NP2];
+                        sum_add2(S, comp, p.kahan, add2(add2(add2(v[0], v[1]), add2(v[2], v[3])),
+                                                        add2(add2(v[4], v[5]), add2(v[6], v[7]))));
                     }
-                    sum_add(S, comp, p.kahan, pd + comp);
+                    float2 rest = make_float2(0.f, 0.f);
+                    for (; b <= bend; ++b) rest = add2(rest, row[b * NP2]);
+                    sum_add2(S, comp, p.kahan, rest);
+                    for (int c0 = p.rx; c0 < p.rx + cB; c0 += 8) {
+                        float2 d[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) d[u] = sub2(row[(c0 + u + u1 + 2) * NP2], row[(c0 + u + u0 + 1) * NP2]);
+                        float2 pd = make_float2(-comp.x, -comp.y);
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            row[(c0 + u + u0 + 1) * NP2] = add2(S, pd);
+                            pd = add2(pd, d[u]);
+                        }
+                        sum_add2(S, comp, p.kahan, add2(pd, comp));
+                    }
+                } else if (seg == 1) {
+                    // right to left from c = tw - 1: S(c - 1) = S(c) + Z(c - 1 + u0) - Z(c + u1); S(c) replaces
+                    // Z(c + u1).  The last sum, S(cB), goes into the slot of Z(cB + u1), which the left
+                    // warp reads last: it is held until both warps pass the named barrier below.
+                    int b = p.rx + tw - 1 + u0 + 1;
+                    const int bend = p.rx + tw - 1 + u1 + 1;
+                    for (; b + 7 <= bend; b += 8) {
+                        float2 v[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) v[u] = row[(b + u) * NP2];
+                        sum_add2(S, comp, p.kahan, add2(add2(add2(v[0], v[1]), add2(v[2], v[3])),
+                                                        add2(add2(v[4], v[5]), add2(v[6], v[7]))));
+                    }
+                    float2 rest = make_float2(0.f, 0.f);
+                    for (; b <= bend; ++b) rest = add2(rest, row[b * NP2]);
+                    sum_add2(S, comp, p.kahan, rest);
+                    for (int c0 = p.rx + tw - 1; c0 >= p.rx + cB; c0 -= 8) {
+                        float2 d[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) d[u] = sub2(row[(c0 - u + u0) * NP2], row[(c0 - u + u1 + 1) * NP2]);
+                        float2 pd = make_float2(-comp.x, -comp.y);
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const float2 o = add2(S, pd);
+                            if (u == 7 && c0 - 7 == p.rx + cB) {
+                                held = o;
+                                hp = &row[(c0 - u + u1 + 1) * NP2];
+                            } else {
+                                row[(c0 - u + u1 + 1) * NP2] = o;
+                            }
+                            pd = add2(pd, d[u]);
+                        }
+                        sum_add2(S, comp, p.kahan, add2(pd, comp));
+                    }
                 }
             }
+            asm volatile("bar.sync 1, 64;" ::: "memory");  // the two scan warps only
+            if (hp) *hp = held;
         }
         if (depth == 2) __syncthreads();
         if (is_out && j >= lag) {
