@@ -280,14 +280,17 @@ bf_status bf_filter_host(const bf_plan *const *plans, int n, const float *h_in, 
 
 /* Launch geometry bf_filter would use for this plan on a height x width image:
  * info[0] tile width, [1] tile height, [2] threads per CTA, [3] cosine terms per
- * CTA, [4] term groups (grid depth), [5] kernel launches, [6] shared memory
+ * CTA, [4] term groups, [5] kernel launches (pre-pass, filter, finalize), [6] shared memory
  * bytes per CTA, [7] scratch KiB, [8] 1 when the basis inputs are kept in a
  * shared-memory ring per column, [9] exchange buffer depth, [10] columns per
  * CTA (tile width plus the halo of 2 x horizontal reach, in whole warps), [11]
  * kernel family: 1 packed (cosine terms in consecutive pairs on the two-wide
  * fp32 instructions; a gapped selection is covered by groups of consecutive
  * frequencies with zero weights), 0 scalar (any set of terms; offered only for
- * gapped selections), [12] basis inputs: 0 computed in the kernel, 1 / 2 / 3
+ * gapped selections), 2 hybrid (gapped selections: the first group is the
+ * packed family's window of consecutive frequencies from the lowest selected
+ * one, the selected terms above it run in the scalar family, two filter
+ * launches into the partial planes), [12] basis inputs: 0 computed in the kernel, 1 / 2 / 3
  * read from a pre-pass buffer in fp32 / fp16 / bf16 (its 16 or 8 bytes per
  * pixel are part of the scratch).  info must hold 13 ints.  Host only; needs no
  * device for host-only plans (uses 152 SMs as the device size then).

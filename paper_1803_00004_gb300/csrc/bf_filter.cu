@@ -187,10 +187,39 @@ __global__ void __launch_bounds__(256) bf_zlist_kernel(const float *__restrict__
     }
 }
 
-// Term groups of a launch: packed family, greedy windows of NK consecutive frequencies; scalar family,
-// consecutive slices of NK selected terms.
-int family_groups(const FilterParams &p, int nk, bool packed) {
-    return packed ? term_groups(p, nk) : (p.nr + nk - 1) / nk;
+// Selected terms above the first window of NK consecutive frequencies (k >= k[0] + NK).
+int terms_after_first_window(const FilterParams &p, int nk) {
+    int n = 0;
+    for (int i = 0; i < p.nr; ++i) n += p.k[i] >= p.k[0] + nk;
+    return n;
+}
+
+
+// The two launches of a hybrid layout: pk, the packed group (NK slots k[0] .. k[0] + NK - 1, zero-weight
+// where the selection has no term); sc, the selected terms above it (the scalar family's term set).
+bool hybrid_split(const FilterParams &p, int nk, FilterParams &pk, FilterParams &sc) {
+    if (nk > kMaxSlots || p.nr < 1) return false;
+    pk = p;
+    sc = p;
+    const int k0 = p.k[0];
+    int i = 0;
+    for (int s = 0; s < nk; ++s) {
+        pk.k[s] = k0 + s;
+        if (i < p.nr && p.k[i] == k0 + s) {
+            pk.a[s] = p.a[i];
+            ++i;
+        } else {
+            pk.a[s] = 0.f;
+        }
+    }
+    pk.nr = nk;
+    sc.nr = 0;
+    for (; i < p.nr; ++i) {
+        sc.k[sc.nr] = p.k[i];
+        sc.a[sc.nr] = p.a[i];
+        ++sc.nr;
+    }
+    return sc.nr > 0;
 }
 
 // The selection has gaps (the packed family then pads groups with zero-weight frequencies).
@@ -217,6 +246,13 @@ bool groups_need_anchor(const FilterParams &p, int nk, bool packed) {
         while (i < p.nr && p.k[i] < k0 + nk) ++i;
     }
     return false;
+}
+
+// Dynamic shared memory a geometry needs (hybrid: what both of its kernels need).
+size_t tile_smem_bytes(const FilterParams &p, int nk, int ncols, int tw, int depth, int ring, int packed) {
+    const bool pring = ring && packed == 1;
+    return smem_bytes(p.m, nk, ncols, tw, depth, !pring) +
+           (ring ? ring_bytes(p, ncols, packed != 1 || groups_need_anchor(p, nk, true)) : 0);
 }
 
 int device_sms() {
@@ -325,6 +361,14 @@ bf_status cuda_fail(cudaError_t e, const char *what) {
 
 }  // namespace
 
+// Term groups of a launch: packed family (1), greedy windows of NK consecutive frequencies; scalar family (0),
+// consecutive slices of NK selected terms; hybrid (2), the first window of NK consecutive frequencies in the
+// packed family, then the selected terms above it in slices of NK in the scalar family.
+int family_groups(const FilterParams &p, int nk, int packed) {
+    if (packed == 2) return 1 + (terms_after_first_window(p, nk) + nk - 1) / nk;
+    return packed ? term_groups(p, nk) : (p.nr + nk - 1) / nk;
+}
+
 // The input range check of bf_debug_range_checks: pixels outside [lo, hi] (NaN included), counted into one
 // per-device counter.
 __device__ unsigned long long g_out_of_range;
@@ -395,13 +439,19 @@ std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int w
     // the scalar family competes only for gapped selections (otherwise it does the same groups, slower);
     // the 3-D form runs the packed family without the ring
     const bool z3d = p.zbins > 0;
-    for (int packed = 1; packed >= (gapped_terms(p) && !z3d ? 0 : 1); --packed)
-    for (const auto &cls : classes(packed)) {
+    // families: packed (1); for gapped selections also hybrid (2: the first window packed, the rest scalar) and
+    // scalar (0)
+    const bool gapped = gapped_terms(p) && !z3d;
+    for (int packed : {1, 2, 0})
+    for (const auto &cls : classes(packed != 0)) {
+        if (packed != 1 && !gapped) break;
         if (cls.m != p.m) continue;
         if (z3d && !find_zkernel(cls.m, cls.nk, p.zmode)) continue;  // the Haar series runs NK = 2 only
         const int groups = family_groups(p, cls.nk, packed);
-        if (packed && groups * cls.nk > kMaxSlots) continue;
-        const double term_cost = packed ? 40.0 : 60.0;  // per term and window: the scalar family has no pairing
+        if (packed == 1 && groups * cls.nk > kMaxSlots) continue;
+        if (packed == 2 && (groups < 2 || !find_kernel(cls.m, cls.nk, false, false))) continue;
+        const double term_cost = packed == 1 ? 40.0 : 60.0;  // per term and window: the scalar family has no pairing
+                                                              // (hybrid: costed as the scalar family)
         // column threads in whole warps; the tile takes what the halo leaves
         for (int ncols = 32; ncols + kScanThreads <= 512; ncols += 32) {
             int tw = ((ncols - 2 * p.rx) / 8) * 8;
@@ -413,15 +463,14 @@ std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int w
                 const int ring = variant & 1, depth = 2 + ((variant >> 1) & 1);
                 const int pre = variant < 4 ? 0 : precision == BF_PREC_FP16 ? 2 : precision == BF_PREC_BF16 ? 3 : 1;
                 if (!pre_allowed(precision, pre)) continue;
-                if (pre && (ring || z3d || !packed || !find_pre_kernel(cls.m, cls.nk, pre))) continue;
+                if (pre && (ring || z3d || packed != 1 || !find_pre_kernel(cls.m, cls.nk, pre))) continue;
+                if (packed == 2 && !find_kernel(cls.m, cls.nk, ring, false)) continue;
                 if (ring && z3d) continue;
                 // the ring serves the output row too, so it must lie inside the window span
                 if (ring && !(p.vlo <= 0 && p.vhi >= 0)) continue;
                 // the packed ring's output phase reads row y - lag back from the ring: lag <= 1 - vlo
                 if (ring && packed && depth - 1 > 1 - p.vlo) continue;
-                const bool pring = ring && packed;
-                const size_t smem = smem_bytes(p.m, cls.nk, ncols, tw, depth, !pring) +
-                                    (ring ? ring_bytes(p, ncols, groups_need_anchor(p, cls.nk, packed)) : 0);
+                const size_t smem = tile_smem_bytes(p, cls.nk, ncols, tw, depth, ring, packed);
                 // the slice kernel keeps a few bytes of static shared memory besides the tile's
                 if (smem + zweights_bytes(p) > 227 * 1024 - (z3d ? 256 : 0)) continue;
                 const int by_smem = (int)((228 * 1024) / (smem + 1024));
@@ -436,10 +485,16 @@ std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int w
                                     (depth == 3 && !z3d ? 0.9 : 1.0) * (pre == 1 ? 1.02 : 1.0);
                 for (int th : {16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 1024}) {
                     const int the = std::min(th, std::max(height, 1));
-                    const long ctas = (long)((width + tw - 1) / tw) * ((height + the - 1) / the) * groups;
+                    const long tiles = (long)((width + tw - 1) / tw) * ((height + the - 1) / the);
+                    const long ctas = tiles * groups;
                     const double per_cta = (double)ncols * (the + 0.3 * vspan) * (edge + term_cost * cls.nk * p.m);
                     const double waves = std::ceil((double)ctas / (sms * cps));
                     double cost = waves * per_cta * cps + (groups > 1 ? 16.0 * groups * (double)height * width : 0.0);
+                    // hybrid: ranked just behind the scalar family at the same geometry (at 1080p and 4K, N_r = 12
+                    // to 32, sigma_r = 0.1, the first geometry of each family ran from 3 % faster to 6 % slower than
+                    // the scalar family's; the autotuner picked it in 2 of 7 cases), so that the untuned choice
+                    // stays scalar and the autotuners time both
+                    if (packed == 2) cost *= 1.05;
                     if (z3d) {
                         // the 3-D form passes over a tile once per distinct slice among its output pixels; the
                         // count is modelled as 7.5 (tw th)^0.27 (a fit on noisy piecewise-constant images),
@@ -566,7 +621,9 @@ void fill_info(const TileConfig &tc, int height, int width, int *info, int zbins
     info[2] = tc.threads;
     info[3] = tc.nk;
     info[4] = tc.groups;
-    info[5] = tc.groups > 1 ? 2 : 1;
+    // kernel launches: the basis pre-pass, the filter (hybrid: packed and scalar; 3-D form: the slice list and
+    // the slice kernel), the finalize of a grouped launch
+    info[5] = (tc.pre ? 1 : 0) + (tc.packed == 2 || zbins > 0 ? 2 : 1) + (tc.groups > 1 ? 1 : 0);
     info[6] = (int)tc.smem;
     info[7] = (int)(scratch_bytes(tc, height, width, zbins) >> 10);
     info[8] = tc.ring ? 1 : 0;
@@ -677,10 +734,15 @@ bf_status launch_filter(const FilterParams &p, int precision, int kahan, const T
     (void)precision;
     (void)kahan;
     if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");
-    if (tc.pre < 0 || tc.pre > 3 || (tc.pre && (!tc.packed || tc.ring || p.zbins > 0 || cache_mode)))
+    if (tc.pre < 0 || tc.pre > 3 || (tc.pre && (tc.packed != 1 || tc.ring || p.zbins > 0 || cache_mode)))
         return fail(BF_ERR_INVALID_ARG, "malformed launch geometry (pre-pass variant)");
+    if (tc.packed < 0 || tc.packed > 2 || (tc.packed == 2 && (p.zbins > 0 || cache_mode)))
+        return fail(BF_ERR_INVALID_ARG, "malformed launch geometry (family)");
     const void *fn = tc.pre ? find_pre_kernel(p.m, tc.nk, tc.pre) : find_kernel(p.m, tc.nk, tc.ring != 0, tc.packed != 0);
-    if (!fn || tc.ncols <= 0) return fail(BF_ERR_UNSUPPORTED, "no kernel class for this plan and image");
+    // hybrid: the scalar family's kernel for the groups after the first
+    const void *fn_s = tc.packed == 2 ? find_kernel(p.m, tc.nk, tc.ring != 0, false) : nullptr;
+    if (!fn || (tc.packed == 2 && !fn_s) || tc.ncols <= 0)
+        return fail(BF_ERR_UNSUPPORTED, "no kernel class for this plan and image");
     if (tc.threads > 512) return fail(BF_ERR_UNSUPPORTED, "horizontal reach too large for one CTA");
     // the tile body needs whole warps of column threads (its two scan warps meet on a 64-thread named
     // barrier) and tile widths in blocks of 8 columns; geometries from a cache file are checked here
@@ -689,9 +751,11 @@ bf_status launch_filter(const FilterParams &p, int precision, int kahan, const T
         (tc.packed && tc.nk % 2 != 0))
         return fail(BF_ERR_INVALID_ARG, "malformed launch geometry");
     if (tc.smem > 227 * 1024) return fail(BF_ERR_UNSUPPORTED, "tile needs more than 227 KB of shared memory");
+    if (p.zbins == 0 && tc.smem < tile_smem_bytes(p, tc.nk, tc.ncols, tc.tw, tc.depth, tc.ring, tc.packed))
+        return fail(BF_ERR_INVALID_ARG, "malformed launch geometry (shared memory below the tile's)");
     if ((tc.groups > 1 || cache_mode || p.zbins > 0 || tc.pre) && !d_scratch)
         return fail(BF_ERR_INVALID_ARG, "missing scratch for grouped launch");
-    if (cache_mode && !tc.packed) return fail(BF_ERR_INVALID_ARG, "the pre-computation runs the packed family");
+    if (cache_mode && tc.packed != 1) return fail(BF_ERR_INVALID_ARG, "the pre-computation runs the packed family");
     if (p.zbins > 0) {
         if (cache_mode) return fail(BF_ERR_UNSUPPORTED, "the 3-D form has no pre-computation cache");
         return launch_filter_z3d(p, tc, d_in, in_pitch, d_out, out_pitch, d_scratch, height, width, stream);
@@ -703,6 +767,37 @@ bf_status launch_filter(const FilterParams &p, int precision, int kahan, const T
     const float *in = d_in;
     float *out = d_out, *part = d_scratch;
     FilterParams pp = p;  // scalar family: the selection as the plan holds it
+    if (tc.packed == 2) {
+        // hybrid: the first window of NK consecutive frequencies in the packed kernel (group 0, planes 0 and 1),
+        // the selected terms above it in the scalar kernel (groups 1 .., the planes after them), then finalize
+        FilterParams ps;
+        if (tc.groups < 2 || tc.groups != family_groups(p, tc.nk, 2) || !hybrid_split(p, tc.nk, pp, ps))
+            return fail(BF_ERR_INVALID_ARG, "launch geometry does not match the plan's term groups");
+        e = cudaFuncSetAttribute(fn_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc.smem);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+        int mode = kModePartial;
+        const void *pre = nullptr;
+        float *part_s = d_scratch + 2 * (size_t)height * width;
+        void *args_p[] = {(void *)&in,  (void *)&in_pitch, (void *)&out,   (void *)&out_pitch, (void *)&part,
+                          (void *)&H,   (void *)&W,        (void *)&tw,    (void *)&th,        (void *)&ncols,
+                          (void *)&depth, (void *)&mode,   (void *)&pp,    (void *)&pre};
+        void *args_s[] = {(void *)&in,  (void *)&in_pitch, (void *)&out,   (void *)&out_pitch, (void *)&part_s,
+                          (void *)&H,   (void *)&W,        (void *)&tw,    (void *)&th,        (void *)&ncols,
+                          (void *)&depth, (void *)&mode,   (void *)&ps};
+        dim3 grid_p(grid.x, grid.y, 1), grid_s(grid.x, grid.y, tc.groups - 1);
+        e = cudaLaunchKernel(fn, grid_p, dim3(tc.threads), args_p, tc.smem, (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "filter launch (packed group)");
+        if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");
+        e = cudaLaunchKernel(fn_s, grid_s, dim3(tc.threads), args_s, tc.smem, (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "filter launch (scalar groups)");
+        if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");
+        dim3 fg((width + 255) / 256, height);
+        bf_finalize_kernel<<<fg, 256, 0, (cudaStream_t)stream>>>(d_in, in_pitch, d_out, out_pitch, d_scratch, height,
+                                                                 width, tc.groups, p.den_eps, p.i_lo);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "finalize launch");
+        return BF_OK;
+    }
     if (tc.packed ? !term_layout(p, tc.nk, pp) || pp.nr != tc.groups * tc.nk
                   : tc.groups != (p.nr + tc.nk - 1) / tc.nk)
         return fail(BF_ERR_INVALID_ARG, "launch geometry does not match the plan's term groups");

@@ -75,7 +75,8 @@ struct TileConfig {
     int groups;    // term groups (grid.z); > 1 writes partial planes + finalize
     int ring;      // 1: per-column ring of basis inputs in shared memory
     int depth;     // exchange buffers: 2 (two barriers per row) or 3 (one barrier per row)
-    int packed;    // 1: packed-pair family (consecutive term groups); 0: scalar family (any term set)
+    int packed;    // 1: packed-pair family (consecutive term groups); 0: scalar family (any term set); 2: hybrid, the
+                   // first group packed (nk consecutive frequencies from the lowest), the terms above it scalar
     size_t smem;   // dynamic shared memory bytes
     int pre = 0;   // basis inputs: 0 computed in the kernel; 1, 2, 3 read from a pre-pass buffer in fp32, fp16, bf16
 };
@@ -110,6 +111,9 @@ bool kernel_class_supported(int m);
 // at the smallest selected frequency not yet covered), and the launch copy of the parameters laid out in
 // those groups (false if the slots exceed kMaxSlots).
 int term_groups(const FilterParams &p, int nk);
+// Term groups of a launch layout: packed (1), scalar (0) or hybrid (2: the first window of nk consecutive
+// frequencies packed, the selected terms above it scalar).
+int family_groups(const FilterParams &p, int nk, int packed);
 bool term_layout(const FilterParams &p, int nk, FilterParams &out);
 
 // Basis storage (TileConfig::pre) a plan's precision allows: fp32 plans compute the basis in the kernel or read

@@ -139,7 +139,7 @@ bf_status bf_precompute(const bf_plan *plan, const float *d_in, size_t in_pitch,
             break;
         }
     bf_cache *c = nullptr;
-    if (tc.ncols == 0 || !tc.packed) st = fail(BF_ERR_UNSUPPORTED, "no launch geometry for the pre-computation");
+    if (tc.ncols == 0 || tc.packed != 1) st = fail(BF_ERR_UNSUPPORTED, "no launch geometry for the pre-computation");
     if (st == BF_OK) {
         c = new bf_cache;
         c->basis = plan->kp;

@@ -104,7 +104,7 @@ std::vector<TileConfig> timed_candidates(const FilterParams &p, int height, int 
     std::map<std::tuple<int, int, int>, int> per_class;
     for (const auto &c : ranked) {
         const int res = (int)std::min<size_t>(3, (size_t)smem_sm / (c.smem + 1024));  // 1 KiB reserved per CTA
-        if (per_class[std::make_tuple(c.ring * 4 + c.depth + 8 * c.packed + 16 * c.pre, c.nk, res)]++ < 4) out.push_back(c);
+        if (per_class[std::make_tuple(c.ring * 4 + c.depth + 8 * c.packed + 32 * c.pre, c.nk, res)]++ < 4) out.push_back(c);
     }
     return out;
 }
@@ -118,9 +118,10 @@ TileConfig choose_tile(const FilterParams &p, int height, int width, int precisi
         auto it = g_table.find(make_key(p, height, width, precision));
         // an entry stays usable only while its term grouping matches the library's current layout
         if (it != g_table.end() &&
-            it->second.groups == (it->second.packed ? term_groups(p, it->second.nk) : (p.nr + it->second.nk - 1) / it->second.nk) &&
-            (p.zbins == 0 || (it->second.packed && !it->second.ring)) && pre_allowed(precision, it->second.pre) &&
-            (it->second.pre == 0 || (it->second.packed && !it->second.ring && p.zbins == 0)))
+            it->second.packed >= 0 && it->second.packed <= 2 &&
+            it->second.groups == family_groups(p, it->second.nk, it->second.packed) &&
+            (p.zbins == 0 || (it->second.packed == 1 && !it->second.ring)) && pre_allowed(precision, it->second.pre) &&
+            (it->second.pre == 0 || (it->second.packed == 1 && !it->second.ring && p.zbins == 0)))
             return it->second;
     }
     return model_tile(p, height, width, precision);

@@ -327,16 +327,21 @@ def test_term_groups_cover_the_selection(kw):
                 i += 1
         return groups
 
-    # packed family: greedy windows; scalar family (offered only for gapped selections): slices of NK terms
+    # packed family: greedy windows; scalar family (offered only for gapped selections): slices of NK terms;
+    # hybrid (gapped selections): the first window packed, then slices of NK of the terms above it
     consecutive = k == list(range(k[0], k[0] + len(k)))
     seen = set()
     for c in bf.bf_launch_candidates(plan, 300, 500):
-        if c["packed"]:
+        if c["packed"] == 1:
             assert c["groups"] == greedy(c["nk"]) and c["groups"] * c["nk"] <= 128 and c["nk"] % 2 == 0
+        elif c["packed"] == 2:
+            above = sum(1 for x in k if x >= k[0] + c["nk"])
+            assert not consecutive and above > 0 and c["nk"] % 2 == 0
+            assert c["groups"] == 1 + -(-above // c["nk"]) and c["launches"] == 3
         else:
-            assert not consecutive and c["groups"] == -(-len(k) // c["nk"])
+            assert not consecutive and c["packed"] == 0 and c["groups"] == -(-len(k) // c["nk"])
         seen.add((c["packed"], c["nk"]))
-    assert {f for f, _ in seen} == ({1} if consecutive else {0, 1})
+    assert {f for f, _ in seen} == ({1} if consecutive else {0, 1, 2})
     if consecutive:                                    # ceil(N_r / NK) groups
         assert all(greedy(nk) == -(-len(k) // nk) for _, nk in seen)
 
