@@ -287,10 +287,11 @@ bf_status bf_filter_host(const bf_plan *const *plans, int n, const float *h_in, 
  * kernel family: 1 packed (cosine terms in consecutive pairs on the two-wide
  * fp32 instructions; a gapped selection is covered by groups of consecutive
  * frequencies with zero weights), 0 scalar (any set of terms; offered only for
- * gapped selections), 2 hybrid (gapped selections: the first group is the
- * packed family's window of consecutive frequencies from the lowest selected
- * one, the selected terms above it run in the scalar family, two filter
- * launches into the partial planes), [12] basis inputs: 0 computed in the kernel, 1 / 2 / 3
+ * gapped selections), 2 hybrid (gapped selections: windows of consecutive
+ * frequencies in the packed family, the one from the lowest selected
+ * frequency and every later window whose frequencies are all selected, the
+ * other terms in the scalar family; two filter launches into the partial
+ * planes), [12] basis inputs: 0 computed in the kernel, 1 / 2 / 3
  * read from a pre-pass buffer in fp32 / fp16 / bf16 (its 16 or 8 bytes per
  * pixel are part of the scratch).  info must hold 13 ints.  Host only; needs no
  * device for host-only plans (uses 152 SMs as the device size then).

@@ -187,39 +187,42 @@ __global__ void __launch_bounds__(256) bf_zlist_kernel(const float *__restrict__
     }
 }
 
-// Selected terms above the first window of NK consecutive frequencies (k >= k[0] + NK).
-int terms_after_first_window(const FilterParams &p, int nk) {
-    int n = 0;
-    for (int i = 0; i < p.nr; ++i) n += p.k[i] >= p.k[0] + nk;
-    return n;
-}
-
-
-// The two launches of a hybrid layout: pk, the packed group (NK slots k[0] .. k[0] + NK - 1, zero-weight
-// where the selection has no term); sc, the selected terms above it (the scalar family's term set).
-bool hybrid_split(const FilterParams &p, int nk, FilterParams &pk, FilterParams &sc) {
-    if (nk > kMaxSlots || p.nr < 1) return false;
+// The two launches of a hybrid layout: pk, the packed groups (windows of NK consecutive frequencies, slots
+// zero-weight where the selection has no term): the window from the lowest selected frequency, then every later
+// window of NK consecutive selected frequencies, taken greedily in ascending order; sc, the other selected terms
+// (the scalar family's term set).  Returns the number of packed groups (0: no hybrid layout: nothing left for
+// the scalar family, or more than kMaxSlots packed slots).
+int hybrid_split(const FilterParams &p, int nk, FilterParams &pk, FilterParams &sc) {
+    if (nk < 1 || nk > kMaxSlots || p.nr < 1) return 0;
     pk = p;
     sc = p;
-    const int k0 = p.k[0];
-    int i = 0;
-    for (int s = 0; s < nk; ++s) {
-        pk.k[s] = k0 + s;
-        if (i < p.nr && p.k[i] == k0 + s) {
-            pk.a[s] = p.a[i];
-            ++i;
+    pk.nr = 0;
+    sc.nr = 0;
+    int gp = 0;
+    for (int i = 0; i < p.nr;) {
+        const bool dense = i + nk <= p.nr && p.k[i + nk - 1] - p.k[i] == nk - 1;
+        if (i == 0 || dense) {
+            if (pk.nr + nk > kMaxSlots) return 0;
+            const int k0 = p.k[i];
+            for (int s = 0; s < nk; ++s) {
+                pk.k[pk.nr + s] = k0 + s;
+                if (i < p.nr && p.k[i] == k0 + s) {
+                    pk.a[pk.nr + s] = p.a[i];
+                    ++i;
+                } else {
+                    pk.a[pk.nr + s] = 0.f;
+                }
+            }
+            pk.nr += nk;
+            ++gp;
         } else {
-            pk.a[s] = 0.f;
+            sc.k[sc.nr] = p.k[i];
+            sc.a[sc.nr] = p.a[i];
+            ++sc.nr;
+            ++i;
         }
     }
-    pk.nr = nk;
-    sc.nr = 0;
-    for (; i < p.nr; ++i) {
-        sc.k[sc.nr] = p.k[i];
-        sc.a[sc.nr] = p.a[i];
-        ++sc.nr;
-    }
-    return sc.nr > 0;
+    return sc.nr > 0 ? gp : 0;
 }
 
 // The selection has gaps (the packed family then pads groups with zero-weight frequencies).
@@ -365,7 +368,11 @@ bf_status cuda_fail(cudaError_t e, const char *what) {
 // consecutive slices of NK selected terms; hybrid (2), the first window of NK consecutive frequencies in the
 // packed family, then the selected terms above it in slices of NK in the scalar family.
 int family_groups(const FilterParams &p, int nk, int packed) {
-    if (packed == 2) return 1 + (terms_after_first_window(p, nk) + nk - 1) / nk;
+    if (packed == 2) {
+        FilterParams pk, sc;
+        const int gp = hybrid_split(p, nk, pk, sc);
+        return gp > 0 ? gp + (sc.nr + nk - 1) / nk : 0;
+    }
     return packed ? term_groups(p, nk) : (p.nr + nk - 1) / nk;
 }
 
@@ -768,23 +775,25 @@ bf_status launch_filter(const FilterParams &p, int precision, int kahan, const T
     float *out = d_out, *part = d_scratch;
     FilterParams pp = p;  // scalar family: the selection as the plan holds it
     if (tc.packed == 2) {
-        // hybrid: the first window of NK consecutive frequencies in the packed kernel (group 0, planes 0 and 1),
-        // the selected terms above it in the scalar kernel (groups 1 .., the planes after them), then finalize
+        // hybrid: the windows of NK consecutive frequencies in the packed kernel (groups 0 .. gp - 1, their partial
+        // planes first), the other selected terms in the scalar kernel (the groups and planes after them), then
+        // the finalize over all
         FilterParams ps;
-        if (tc.groups < 2 || tc.groups != family_groups(p, tc.nk, 2) || !hybrid_split(p, tc.nk, pp, ps))
+        const int gp = hybrid_split(p, tc.nk, pp, ps);
+        if (gp < 1 || tc.groups < 2 || tc.groups != family_groups(p, tc.nk, 2))
             return fail(BF_ERR_INVALID_ARG, "launch geometry does not match the plan's term groups");
         e = cudaFuncSetAttribute(fn_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc.smem);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
         int mode = kModePartial;
         const void *pre = nullptr;
-        float *part_s = d_scratch + 2 * (size_t)height * width;
+        float *part_s = d_scratch + 2 * (size_t)gp * height * width;
         void *args_p[] = {(void *)&in,  (void *)&in_pitch, (void *)&out,   (void *)&out_pitch, (void *)&part,
                           (void *)&H,   (void *)&W,        (void *)&tw,    (void *)&th,        (void *)&ncols,
                           (void *)&depth, (void *)&mode,   (void *)&pp,    (void *)&pre};
         void *args_s[] = {(void *)&in,  (void *)&in_pitch, (void *)&out,   (void *)&out_pitch, (void *)&part_s,
                           (void *)&H,   (void *)&W,        (void *)&tw,    (void *)&th,        (void *)&ncols,
                           (void *)&depth, (void *)&mode,   (void *)&ps};
-        dim3 grid_p(grid.x, grid.y, 1), grid_s(grid.x, grid.y, tc.groups - 1);
+        dim3 grid_p(grid.x, grid.y, gp), grid_s(grid.x, grid.y, tc.groups - gp);
         e = cudaLaunchKernel(fn, grid_p, dim3(tc.threads), args_p, tc.smem, (cudaStream_t)stream);
         if (e != cudaSuccess) return cuda_fail(e, "filter launch (packed group)");
         if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");
