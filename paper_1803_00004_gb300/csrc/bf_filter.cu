@@ -365,8 +365,8 @@ bf_status cuda_fail(cudaError_t e, const char *what) {
 }  // namespace
 
 // Term groups of a launch: packed family (1), greedy windows of NK consecutive frequencies; scalar family (0),
-// consecutive slices of NK selected terms; hybrid (2), the first window of NK consecutive frequencies in the
-// packed family, then the selected terms above it in slices of NK in the scalar family.
+// consecutive slices of NK selected terms; hybrid (2), the packed windows of hybrid_split, then the other selected
+// terms in slices of NK in the scalar family.
 int family_groups(const FilterParams &p, int nk, int packed) {
     if (packed == 2) {
         FilterParams pk, sc;
@@ -446,8 +446,8 @@ std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int w
     // the scalar family competes only for gapped selections (otherwise it does the same groups, slower);
     // the 3-D form runs the packed family without the ring
     const bool z3d = p.zbins > 0;
-    // families: packed (1); for gapped selections also hybrid (2: the first window packed, the rest scalar) and
-    // scalar (0)
+    // families: packed (1); for gapped selections also hybrid (2: windows of consecutive frequencies packed, the
+    // other terms scalar) and scalar (0)
     const bool gapped = gapped_terms(p) && !z3d;
     for (int packed : {1, 2, 0})
     for (const auto &cls : classes(packed != 0)) {
@@ -497,10 +497,10 @@ std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int w
                     const double per_cta = (double)ncols * (the + 0.3 * vspan) * (edge + term_cost * cls.nk * p.m);
                     const double waves = std::ceil((double)ctas / (sms * cps));
                     double cost = waves * per_cta * cps + (groups > 1 ? 16.0 * groups * (double)height * width : 0.0);
-                    // hybrid: ranked just behind the scalar family at the same geometry (at 1080p and 4K, N_r = 12
-                    // to 32, sigma_r = 0.1, the first geometry of each family ran from 3 % faster to 6 % slower than
-                    // the scalar family's; the autotuner picked it in 2 of 7 cases), so that the untuned choice
-                    // stays scalar and the autotuners time both
+                    // hybrid: ranked just behind the scalar family at the same geometry, where its two launches,
+                    // each over its own groups' tiles, fill the GPU half as well when it runs alone; with smaller
+                    // tiles it can win (at 1080p and 4K, N_r = 12 to 32, sigma_r = 0.1 the autotuner picked it in
+                    // 3 of 7 cases), so the untuned choice stays scalar and the autotuners time both
                     if (packed == 2) cost *= 1.05;
                     if (z3d) {
                         // the 3-D form passes over a tile once per distinct slice among its output pixels; the
@@ -746,7 +746,7 @@ bf_status launch_filter(const FilterParams &p, int precision, int kahan, const T
     if (tc.packed < 0 || tc.packed > 2 || (tc.packed == 2 && (p.zbins > 0 || cache_mode)))
         return fail(BF_ERR_INVALID_ARG, "malformed launch geometry (family)");
     const void *fn = tc.pre ? find_pre_kernel(p.m, tc.nk, tc.pre) : find_kernel(p.m, tc.nk, tc.ring != 0, tc.packed != 0);
-    // hybrid: the scalar family's kernel for the groups after the first
+    // hybrid: the scalar family's kernel for the groups after the packed ones
     const void *fn_s = tc.packed == 2 ? find_kernel(p.m, tc.nk, tc.ring != 0, false) : nullptr;
     if (!fn || (tc.packed == 2 && !fn_s) || tc.ncols <= 0)
         return fail(BF_ERR_UNSUPPORTED, "no kernel class for this plan and image");
@@ -795,7 +795,7 @@ bf_status launch_filter(const FilterParams &p, int precision, int kahan, const T
                           (void *)&depth, (void *)&mode,   (void *)&ps};
         dim3 grid_p(grid.x, grid.y, gp), grid_s(grid.x, grid.y, tc.groups - gp);
         e = cudaLaunchKernel(fn, grid_p, dim3(tc.threads), args_p, tc.smem, (cudaStream_t)stream);
-        if (e != cudaSuccess) return cuda_fail(e, "filter launch (packed group)");
+        if (e != cudaSuccess) return cuda_fail(e, "filter launch (packed groups)");
         if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");
         e = cudaLaunchKernel(fn_s, grid_s, dim3(tc.threads), args_s, tc.smem, (cudaStream_t)stream);
         if (e != cudaSuccess) return cuda_fail(e, "filter launch (scalar groups)");
