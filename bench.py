@@ -234,13 +234,17 @@ def run_ours(args):
             info = {k: 0 for k in bf._binding.INFO_KEYS}
             info.update(dict(zip(keys, r)))
             bf.bf_set_launch(p, H, W, info)
-    elif not args.no_tune:  # launch geometry (untimed): each plan alone, then the nine as the step runs them
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    own_ms = None
+    if not args.tiles and not args.no_tune:  # launch geometry (untimed): each plan alone, then the nine as the step runs them
         for p in plans:
             bf.bf_autotune(p, H, W)
+        # each plan alone in its own tuned geometry (the per-pixel cost by sigma_s without the step's sharing)
+        own_ms = [round(timed_calls(lambda p=p, o=o: bf.bf_filter(p, src, o, stream=stream), flush, 10), 4)
+                  for p, o in zip(plans, outs)]
         bf.bf_autotune_group([plans[j] for j in order], H, W, n_streams=n_streams)
     tiles = [bf.bf_launch_info(p, H, W) for p in plans]
     launches_per_step = sum(t["launches"] for t in tiles)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
 
     def step(ev=None):
         fork = torch.cuda.Event()
@@ -354,6 +358,7 @@ def run_ours(args):
         "psnr_db_vs_exact": [round(x, 2) for x in psnr], "min_psnr_db": round(min(psnr), 2) if psnr else None,
         "plan_build_ms": round(plan_build_ms, 2),
         "per_combo_ms": [round(x, 4) for x in la.mean(0)],
+        "per_combo_ms_own_geometry": own_ms,
         "per_combo_ms_overlapped": [round(x, 4) for x in lm.mean(0)],
         "tiles": [[t["tw"], t["th"], t["threads"], t["nk"], t["groups"], t["ring"], t["depth"], t["ncols"], t["packed"],
                    t["pre"]] for t in tiles],
