@@ -724,7 +724,8 @@ def run_batched(bf, dev, n=512, lo=64, hi=2048, reps=3):
             "sequential_mpix_s": round(px / (t_seq * 1e-3) / 1e6, 1), "sequential_ms": round(t_seq, 3)}
 
 
-def run_serving(bf, dev, n=1000, lo=128, hi=4096, loads=(0.25, 0.5, 0.8, 1.0, 1.2), n_img=64, copies=3):
+def run_serving(bf, dev, n=1000, lo=128, hi=4096, loads=(0.25, 0.5, 0.8, 1.0, 1.2), n_img=64, copies=3,
+                srv_streams=4, srv_batch=8):
     """Config 5: Poisson streams at each `load` x the measured saturation rate through the continuous-batching
     server (pinned host buffers; sides log-uniform 128..4096; every request draws fresh parameters as in
     config 4, sigma_s ~ U[2,32], sigma_r ~ U[0.05,0.3], Gaussian or exponential range kernel, N_r in {8,16},
@@ -738,7 +739,7 @@ def run_serving(bf, dev, n=1000, lo=128, hi=4096, loads=(0.25, 0.5, 0.8, 1.0, 1.
     imgs = [synth.shapes(sz, sz, seed=4321 * 7919 + i, scale=sz / 1080.0) for i, sz in enumerate(sizes)]
     hin = [torch.from_numpy(im).pin_memory() for im in imgs]
     hout = [[torch.empty_like(x).pin_memory() for _ in range(copies)] for x in hin]
-    srv = bf.Server(device=dev.index or 0, max_slots=64, n_streams=4, max_batch=8, plan_threads=6)
+    srv = bf.Server(device=dev.index or 0, max_slots=64, n_streams=srv_streams, max_batch=srv_batch, plan_threads=6)
     rng = np.random.default_rng(7)
 
     def fresh(m):
@@ -814,7 +815,8 @@ def run_serving(bf, dev, n=1000, lo=128, hi=4096, loads=(0.25, 0.5, 0.8, 1.0, 1.
         hout[j][0].copy_(d_out[j], non_blocking=True)
     torch.cuda.synchronize()
     t_plain = time.perf_counter() - t0
-    at = next(r for r in by_load if r["load"] == 0.8)
+    at = next((r for r in by_load if r["load"] == 0.8), by_load[0] if by_load else {"p50_ms": None, "p99_ms": None,
+                                                                                     "mpix_s": None})
     return {"requests_per_load": n, "distinct_images": n_img, "sides": [lo, hi], "megapixels_per_load": round(px_of(n) / 1e6, 1),
             "fresh_parameters": True, "latency_includes": "plan build (host FP64 fit on the server's plan threads), "
             "queueing, H2D, the batched launch and D2H",
