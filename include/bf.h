@@ -290,8 +290,8 @@ bf_status bf_filter_host(const bf_plan *const *plans, int n, const float *h_in, 
  * gapped selections), 2 hybrid (gapped selections: windows of consecutive
  * frequencies in the packed family, the one from the lowest selected
  * frequency and every later window whose frequencies are all selected, the
- * other terms in the scalar family; two filter launches into the partial
- * planes), [12] basis inputs: 0 computed in the kernel, 1 / 2 / 3
+ * other terms in the scalar family, in one launch into the partial planes),
+ * [12] basis inputs: 0 computed in the kernel, 1 / 2 / 3
  * read from a pre-pass buffer in fp32 / fp16 / bf16 (its 16 or 8 bytes per
  * pixel are part of the scratch).  info must hold 13 ints.  Host only; needs no
  * device for host-only plans (uses 152 SMs as the device size then).

@@ -48,6 +48,15 @@ extern const ZKernelClass kZClassesM1M2[];
 extern const ZKernelClass kZClassesM3to6[];
 extern const int kNumZClassesM1M2, kNumZClassesM3to6;
 
+// Hybrid layout (packed groups, then scalar groups, in one launch; bf_tile_hybrid.cuh): kernels_h_*.cu, fn[ring].
+struct HybridKernelClass {
+    int m, nk;
+    const void *fn[2];
+};
+extern const HybridKernelClass kHybridClassesM1[];
+extern const HybridKernelClass kHybridClassesM2[];
+extern const int kNumHybridClassesM1, kNumHybridClassesM2;
+
 // Scalar family (any term set; bf_tile_scalar.cuh): kernels_s_*.cu.
 extern const KernelClass kScalarClassesM1M2[];
 extern const KernelClass kScalarClassesM3to6[];

@@ -100,6 +100,16 @@ const void *find_kernel(int m, int nk, bool ring, bool packed) {
     return nullptr;
 }
 
+// The hybrid layout's kernel of class (m, nk), nullptr where none is built (M = 1 and 2).
+const void *find_hybrid_kernel(int m, int nk, bool ring) {
+    for (const auto *t : {kHybridClassesM1, kHybridClassesM2}) {
+        const int n = t == kHybridClassesM1 ? kNumHybridClassesM1 : kNumHybridClassesM2;
+        for (int i = 0; i < n; ++i)
+            if (t[i].m == m && t[i].nk == nk) return t[i].fn[ring ? 1 : 0];
+    }
+    return nullptr;
+}
+
 // The pre-pass variant `pre` (1 fp32, 2 fp16, 3 bf16) of packed class (m, nk), nullptr where none is built.
 const void *find_pre_kernel(int m, int nk, int pre) {
     if (pre < 1 || pre > 3) return nullptr;
@@ -456,9 +466,14 @@ std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int w
         if (z3d && !find_zkernel(cls.m, cls.nk, p.zmode)) continue;  // the Haar series runs NK = 2 only
         const int groups = family_groups(p, cls.nk, packed);
         if (packed == 1 && groups * cls.nk > kMaxSlots) continue;
-        if (packed == 2 && (groups < 2 || !find_kernel(cls.m, cls.nk, false, false))) continue;
-        const double term_cost = packed == 1 ? 40.0 : 60.0;  // per term and window: the scalar family has no pairing
-                                                              // (hybrid: costed as the scalar family)
+        if (packed == 2 && (groups < 2 || !find_hybrid_kernel(cls.m, cls.nk, false))) continue;
+        // per term and window: the scalar family has no pairing; hybrid: the mean over its packed and scalar groups
+        double term_cost = packed == 1 ? 40.0 : 60.0;
+        if (packed == 2) {
+            FilterParams pk, ps;
+            const int gp = hybrid_split(p, cls.nk, pk, ps);
+            term_cost = (40.0 * gp + 60.0 * (groups - gp)) / groups;
+        }
         // column threads in whole warps; the tile takes what the halo leaves
         for (int ncols = 32; ncols + kScanThreads <= 512; ncols += 32) {
             int tw = ((ncols - 2 * p.rx) / 8) * 8;
@@ -471,7 +486,7 @@ std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int w
                 const int pre = variant < 4 ? 0 : precision == BF_PREC_FP16 ? 2 : precision == BF_PREC_BF16 ? 3 : 1;
                 if (!pre_allowed(precision, pre)) continue;
                 if (pre && (ring || z3d || packed != 1 || !find_pre_kernel(cls.m, cls.nk, pre))) continue;
-                if (packed == 2 && !find_kernel(cls.m, cls.nk, ring, false)) continue;
+                if (packed == 2 && !find_hybrid_kernel(cls.m, cls.nk, ring)) continue;
                 if (ring && z3d) continue;
                 // the ring serves the output row too, so it must lie inside the window span
                 if (ring && !(p.vlo <= 0 && p.vhi >= 0)) continue;
@@ -497,11 +512,6 @@ std::vector<TileConfig> tile_candidates(const FilterParams &p, int height, int w
                     const double per_cta = (double)ncols * (the + 0.3 * vspan) * (edge + term_cost * cls.nk * p.m);
                     const double waves = std::ceil((double)ctas / (sms * cps));
                     double cost = waves * per_cta * cps + (groups > 1 ? 16.0 * groups * (double)height * width : 0.0);
-                    // hybrid: ranked just behind the scalar family at the same geometry, where its two launches,
-                    // each over its own groups' tiles, fill the GPU half as well when it runs alone; with smaller
-                    // tiles it can win (at 1080p and 4K, N_r = 12 to 32, sigma_r = 0.1 the autotuner picked it in
-                    // 3 of 7 cases), so the untuned choice stays scalar and the autotuners time both
-                    if (packed == 2) cost *= 1.05;
                     if (z3d) {
                         // the 3-D form passes over a tile once per distinct slice among its output pixels; the
                         // count is modelled as 7.5 (tw th)^0.27 (a fit on noisy piecewise-constant images),
@@ -628,9 +638,9 @@ void fill_info(const TileConfig &tc, int height, int width, int *info, int zbins
     info[2] = tc.threads;
     info[3] = tc.nk;
     info[4] = tc.groups;
-    // kernel launches: the basis pre-pass, the filter (hybrid: packed and scalar; 3-D form: the slice list and
-    // the slice kernel), the finalize of a grouped launch
-    info[5] = (tc.pre ? 1 : 0) + (tc.packed == 2 || zbins > 0 ? 2 : 1) + (tc.groups > 1 ? 1 : 0);
+    // kernel launches: the basis pre-pass, the filter (3-D form: the slice list and the slice kernel), the
+    // finalize of a grouped launch
+    info[5] = (tc.pre ? 1 : 0) + (zbins > 0 ? 2 : 1) + (tc.groups > 1 ? 1 : 0);
     info[6] = (int)tc.smem;
     info[7] = (int)(scratch_bytes(tc, height, width, zbins) >> 10);
     info[8] = tc.ring ? 1 : 0;
@@ -745,11 +755,10 @@ bf_status launch_filter(const FilterParams &p, int precision, int kahan, const T
         return fail(BF_ERR_INVALID_ARG, "malformed launch geometry (pre-pass variant)");
     if (tc.packed < 0 || tc.packed > 2 || (tc.packed == 2 && (p.zbins > 0 || cache_mode)))
         return fail(BF_ERR_INVALID_ARG, "malformed launch geometry (family)");
-    const void *fn = tc.pre ? find_pre_kernel(p.m, tc.nk, tc.pre) : find_kernel(p.m, tc.nk, tc.ring != 0, tc.packed != 0);
-    // hybrid: the scalar family's kernel for the groups after the packed ones
-    const void *fn_s = tc.packed == 2 ? find_kernel(p.m, tc.nk, tc.ring != 0, false) : nullptr;
-    if (!fn || (tc.packed == 2 && !fn_s) || tc.ncols <= 0)
-        return fail(BF_ERR_UNSUPPORTED, "no kernel class for this plan and image");
+    const void *fn = tc.pre                ? find_pre_kernel(p.m, tc.nk, tc.pre)
+                     : tc.packed == 2      ? find_hybrid_kernel(p.m, tc.nk, tc.ring != 0)
+                                           : find_kernel(p.m, tc.nk, tc.ring != 0, tc.packed != 0);
+    if (!fn || tc.ncols <= 0) return fail(BF_ERR_UNSUPPORTED, "no kernel class for this plan and image");
     if (tc.threads > 512) return fail(BF_ERR_UNSUPPORTED, "horizontal reach too large for one CTA");
     // the tile body needs whole warps of column threads (its two scan warps meet on a 64-thread named
     // barrier) and tile widths in blocks of 8 columns; geometries from a cache file are checked here
@@ -775,30 +784,17 @@ bf_status launch_filter(const FilterParams &p, int precision, int kahan, const T
     float *out = d_out, *part = d_scratch;
     FilterParams pp = p;  // scalar family: the selection as the plan holds it
     if (tc.packed == 2) {
-        // hybrid: the windows of NK consecutive frequencies in the packed kernel (groups 0 .. gp - 1, their partial
-        // planes first), the other selected terms in the scalar kernel (the groups and planes after them), then
-        // the finalize over all
+        // hybrid: one launch over all groups, the packed tile body for groups 0 .. gp - 1 (the windows of NK
+        // consecutive frequencies, their partial planes first), the scalar one for the others, then the finalize
         FilterParams ps;
         const int gp = hybrid_split(p, tc.nk, pp, ps);
         if (gp < 1 || tc.groups < 2 || tc.groups != family_groups(p, tc.nk, 2))
             return fail(BF_ERR_INVALID_ARG, "launch geometry does not match the plan's term groups");
-        e = cudaFuncSetAttribute(fn_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc.smem);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-        int mode = kModePartial;
-        const void *pre = nullptr;
-        float *part_s = d_scratch + 2 * (size_t)gp * height * width;
-        void *args_p[] = {(void *)&in,  (void *)&in_pitch, (void *)&out,   (void *)&out_pitch, (void *)&part,
+        void *args_h[] = {(void *)&in,  (void *)&in_pitch, (void *)&out,   (void *)&out_pitch, (void *)&part,
                           (void *)&H,   (void *)&W,        (void *)&tw,    (void *)&th,        (void *)&ncols,
-                          (void *)&depth, (void *)&mode,   (void *)&pp,    (void *)&pre};
-        void *args_s[] = {(void *)&in,  (void *)&in_pitch, (void *)&out,   (void *)&out_pitch, (void *)&part_s,
-                          (void *)&H,   (void *)&W,        (void *)&tw,    (void *)&th,        (void *)&ncols,
-                          (void *)&depth, (void *)&mode,   (void *)&ps};
-        dim3 grid_p(grid.x, grid.y, gp), grid_s(grid.x, grid.y, tc.groups - gp);
-        e = cudaLaunchKernel(fn, grid_p, dim3(tc.threads), args_p, tc.smem, (cudaStream_t)stream);
-        if (e != cudaSuccess) return cuda_fail(e, "filter launch (packed groups)");
-        if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");
-        e = cudaLaunchKernel(fn_s, grid_s, dim3(tc.threads), args_s, tc.smem, (cudaStream_t)stream);
-        if (e != cudaSuccess) return cuda_fail(e, "filter launch (scalar groups)");
+                          (void *)&depth, (void *)&gp,     (void *)&pp,    (void *)&ps};
+        e = cudaLaunchKernel(fn, grid, dim3(tc.threads), args_h, tc.smem, (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "filter launch (hybrid)");
         if (debug_consume_launch_failure()) return fail(BF_ERR_CUDA, "injected launch failure (test hook)");
         dim3 fg((width + 255) / 256, height);
         bf_finalize_kernel<<<fg, 256, 0, (cudaStream_t)stream>>>(d_in, in_pitch, d_out, out_pitch, d_scratch, height,

@@ -11,7 +11,9 @@
 #include "bf_internal.h"
 
 namespace bfi {
-
+// The scalar family lives in its own namespace, so that a translation unit can hold both families' tile bodies
+// (the hybrid layout's kernel runs either).
+namespace sc {
 
 namespace {
 
@@ -526,9 +528,10 @@ bf_batch_scalar_kernel(const BatchImage *__restrict__ imgs, const FilterParams *
 
 
 }  // namespace
+}  // namespace sc
 
-#define BF_SCALAR_CLASS(M, NK)                                                                          \
-    {M, NK, {(const void *)bf_fused_scalar_kernel<NK, M, false>, (const void *)bf_fused_scalar_kernel<NK, M, true>},  \
-     (const void *)bf_batch_scalar_kernel<NK, M>}
+#define BF_SCALAR_CLASS(M, NK)                                                                                  \
+    {M, NK, {(const void *)sc::bf_fused_scalar_kernel<NK, M, false>, (const void *)sc::bf_fused_scalar_kernel<NK, M, true>}, \
+     (const void *)sc::bf_batch_scalar_kernel<NK, M>}
 
 }  // namespace bfi

@@ -350,7 +350,7 @@ def test_term_groups_cover_the_selection(kw):
             assert c["groups"] == greedy(c["nk"]) and c["groups"] * c["nk"] <= 128 and c["nk"] % 2 == 0
         elif c["packed"] == 2:
             assert not consecutive and c["nk"] % 2 == 0
-            assert c["groups"] == hybrid(c["nk"]) and c["launches"] == 3
+            assert c["groups"] == hybrid(c["nk"]) and c["launches"] == 2
         else:
             assert not consecutive and c["packed"] == 0 and c["groups"] == -(-len(k) // c["nk"])
         seen.add((c["packed"], c["nk"]))
