@@ -116,7 +116,8 @@ typedef enum {
  * roundoff u (2^-11 fp16, 2^-8 bf16) |delta I^| <= 2 u sum_k m_k |a_k| mass
  * (1 + |I^|) / |den| beyond the fp32 path's error (mass = sum |K~_s| over the
  * window).  16-bit plans take the collapsed range policies (not
- * BF_RANGE_PAPER_3D); bf_filter_batch and the server run them one by one.
+ * BF_RANGE_PAPER_3D); bf_filter_batch and the server run them as direct
+ * launches beside the persistent ones.
  * The pre-computation cache of bf_precompute has its own storage precision
  * (same enum): its window sums may be stored as fp16 or bf16, rounded once
  * from the fp32 sums, with |delta I^| <= 2 u sum|a_k| mass (1 + |I^|) / |den|. */
@@ -410,7 +411,8 @@ typedef struct {
  * one persistent launch per kernel class that walks a work list of
  * (image, tile) items across uneven images; images whose plans that kernel
  * does not run (the 3-D form, 16-bit basis storage) follow as one launch
- * sequence each, in their bf_filter geometry.  The whole sequence is captured
+ * sequence each, in their bf_filter geometry, side by side on up to eight
+ * library streams forked from and joined back to `stream`.  The whole sequence is captured
  * once into a CUDA graph per batch shape and replayed.  Each image's result
  * equals bf_filter's for the same plan within fp32 rounding.  All plans must
  * be on the same device.  Errors: as bf_filter. */

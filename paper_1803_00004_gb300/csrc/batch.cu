@@ -58,6 +58,38 @@ int current_device() {
     return d;
 }
 
+// Branch streams of a device for the batch's direct launches (the 3-D form, 16-bit basis storage): they are
+// independent (each image has its own scratch), so they run side by side on up to kDirectStreams streams forked
+// from and joined back to the batch's stream (inside a captured graph: parallel branches).  Created once per
+// device, before any capture; the mutex orders the fork and join of concurrent callers.
+constexpr int kDirectStreams = 8;
+constexpr int kMaxDirectDevices = 64;
+struct DirectStreams {
+    std::mutex mu;
+    bool ready = false;
+    cudaStream_t s[kDirectStreams] = {};
+    cudaEvent_t fork = nullptr, join[kDirectStreams] = {};
+};
+DirectStreams g_direct[kMaxDirectDevices];
+
+DirectStreams *direct_streams(int device) {
+    if (device < 0 || device >= kMaxDirectDevices) return nullptr;
+    DirectStreams &d = g_direct[device];
+    std::lock_guard<std::mutex> lk(d.mu);
+    if (d.ready) return &d;
+    cudaError_t e = cudaEventCreateWithFlags(&d.fork, cudaEventDisableTiming);
+    for (int k = 0; k < kDirectStreams && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&d.s[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d.join[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    d.ready = true;
+    return &d;
+}
+
 }  // namespace
 
 // Host-side layout of one batch; fill() writes the staging bytes for a device base address.
@@ -71,8 +103,9 @@ struct BatchLayout {
     size_t off_params = 0, off_imgs = 0, off_items = 0, off_list = 0, off_cursors = 0, off_scratch = 0, total = 0;
     std::vector<size_t> scratch_off;  // per image, relative to off_scratch (or SIZE_MAX)
     int max_h = 0, max_w = 0;
-    // Images of plans the persistent kernel does not run (the 3-D form; 16-bit basis storage): launched one by
-    // one after the persistent launches, in their own geometry, with their scratch in the buffer's scratch area.
+    // Images of plans the persistent kernel does not run (the 3-D form; 16-bit basis storage): launched after the
+    // persistent launches, side by side on the branch streams, in their own geometry, with their scratch in the
+    // buffer's scratch area.
     struct Direct {
         FilterParams kp;
         int precision, kahan;
@@ -231,11 +264,30 @@ bf_status enqueue_batch(const BatchLayout &L, uint8_t *d_buf, const uint8_t *h_s
     }
     bf_status st = launch_batch_finalize(d_imgs, reinterpret_cast<const int *>(d_buf + L.off_list), (int)L.list.size(),
                                          L.max_h, L.max_w, d_params, s);
+    if (st != BF_OK || L.direct.empty()) return st;
+    // the direct launches, side by side on the device's branch streams (one after another if they cannot be had)
+    DirectStreams *ds = direct_streams(current_device());
+    std::unique_lock<std::mutex> lk;
+    int K = 0;
+    if (ds) {
+        lk = std::unique_lock<std::mutex>(ds->mu);
+        K = (int)std::min<size_t>(kDirectStreams, L.direct.size());
+        e = cudaEventRecord(ds->fork, s);
+        for (int k = 0; k < K && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(ds->s[k], ds->fork, 0);
+        if (e != cudaSuccess) return fail(BF_ERR_CUDA, std::string("batch fork: ") + cudaGetErrorString(e));
+    }
     for (size_t i = 0; i < L.direct.size() && st == BF_OK; ++i) {
         const auto &d = L.direct[i];
         float *scr = d.scratch_bytes ? reinterpret_cast<float *>(d_buf + L.off_scratch + d.scratch_off) : nullptr;
         st = launch_filter(d.kp, d.precision, d.kahan, d.tc, d.im.d_in, d.im.in_pitch_bytes / sizeof(float), d.im.d_out,
-                           d.im.out_pitch_bytes / sizeof(float), scr, d.im.height, d.im.width, s);
+                           d.im.out_pitch_bytes / sizeof(float), scr, d.im.height, d.im.width,
+                           K ? ds->s[i % K] : s);
+    }
+    // join (also after a failure, so that the branch streams end inside the stream's order or the capture)
+    for (int k = 0; k < K; ++k) {
+        e = cudaEventRecord(ds->join[k], ds->s[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ds->join[k], 0);
+        if (e != cudaSuccess && st == BF_OK) st = fail(BF_ERR_CUDA, std::string("batch join: ") + cudaGetErrorString(e));
     }
     return st;
 }
@@ -332,6 +384,7 @@ bf_status make_entry(const bf_plan *const *plans, const bf_image *images, int n,
         return fail(BF_ERR_OOM, "batch buffers");
     }
     L.fill(ent->h_staging, reinterpret_cast<uintptr_t>(ent->d_buf));
+    if (!L.direct.empty()) direct_streams(device);  // the branch streams exist before the capture begins
     cudaStream_t cap;
     if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
