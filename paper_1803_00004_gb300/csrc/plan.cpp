@@ -472,13 +472,14 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
         const int ncand = 20 * d.nr_terms;
         double L = std::min(p.Tr, p.P);
         if (d.range == BF_KERNEL_BOX) L = std::min(L, d.sigma_r);
-        // One composite 20-point Gauss-Legendre node set on [0, L] with at most one period of the highest
-        // candidate frequency per piece (the rule's error there is ~1e-28 relative), 4 + k_max L / (2 P) pieces,
+        // One composite 20-point Gauss-Legendre node set on [0, L] with at most two periods of the highest
+        // candidate frequency per piece (the rule's error on (2 pi m)^40 / 40! for m periods: ~1e-16 relative at
+        // m = 2), 4 + k_max L / (4 P) pieces,
         // serves every candidate: a_k = (2 - [k = 0]) / P sum_i w_i K_r(t_i)
         // cos(pi k t_i / P).  cos(k theta_i) comes from the angle-addition recurrence over k, all nodes at once,
         // re-anchored by a direct cos / sin every 16 frequencies so its rounding stays within ~16 ulp.
         const GaussLegendre &gq = gl20();
-        const int pieces = L > 0 ? 4 + (int)std::ceil(0.5 * (ncand - 1) * L / p.P) : 0;
+        const int pieces = L > 0 ? 4 + (int)std::ceil(0.25 * (ncand - 1) * L / p.P) : 0;
         const int ng = (int)gq.x.size(), nn = pieces * ng;
         std::vector<double> f(nn), th(nn), c1(nn), s1(nn), ck(nn), sk(nn);
         const double hq = pieces > 0 ? L / pieces : 0.0;
@@ -624,15 +625,18 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
     for (auto &e : hw) p.hwin.insert(p.hwin.end(), {e.first, e.second});
     for (int v = 0; v < p.nv; ++v)
         for (int h = 0; h < p.nh; ++h) p.wcoef.push_back(hcoef[v][h]);
-    // verify the compilation reproduces the kernel
+    // verify the compilation reproduces the kernel (hsum[v][dx]: the horizontal windows' weights at dx)
     double maxdiff = 0;
+    std::vector<std::vector<double>> hsum(p.nv, std::vector<double>(w, 0.0));
+    for (int v = 0; v < p.nv; ++v)
+        for (int dx = -R; dx <= R; ++dx)
+            for (int h = 0; h < p.nh; ++h)
+                if (dx >= hw[h].first && dx <= hw[h].second) hsum[v][dx + R] += hcoef[v][h];
     for (int dy = -R; dy <= R; ++dy)
         for (int dx = -R; dx <= R; ++dx) {
             double s = 0;
             for (int v = 0; v < p.nv; ++v)
-                if (dy >= vw[v].first && dy <= vw[v].second)
-                    for (int h = 0; h < p.nh; ++h)
-                        if (dx >= hw[h].first && dx <= hw[h].second) s += hcoef[v][h];
+                if (dy >= vw[v].first && dy <= vw[v].second) s += hsum[v][dx + R];
             maxdiff = std::max(maxdiff, std::fabs(s - Kd(dx, dy)));
         }
     if (maxdiff > 1e-12 * std::max(kmax, 1e-300))
@@ -656,9 +660,10 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
     }
     // the 3-D form keeps the series only inside the range box [-T_r, T_r]
     const double tspan = d.policy == BF_RANGE_PAPER_3D ? std::min(dI, p.Tr) : dI;
-    for (int i = 0; !haar_range && i <= 4000; ++i) {
-        // cos(pi k t / P) for k = 0 .. k_max by the angle-addition recurrence (a report: ~k_max ulp is ample)
-        double t = -tspan + 2.0 * tspan * i / 4000.0, s = 0;
+    for (int i = 0; !haar_range && i <= 2000; ++i) {
+        // cos(pi k t / P) for k = 0 .. k_max by the angle-addition recurrence (a report: ~k_max ulp is ample);
+        // 2001 samples, tens per period of the highest selected frequency
+        double t = -tspan + 2.0 * tspan * i / 2000.0, s = 0;
         const double th = kPi * t / p.P, cth = std::cos(th), sth = std::sin(th);
         double ck = 1.0, sk = 0.0;
         for (int k = 0, j = 0; j < (int)p.k.size(); ++k) {
@@ -670,12 +675,14 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
         p.range_max_err = std::max(p.range_max_err, std::fabs(s - range_value(d.range, d.sigma_r, t)));
     }
     p.spatial_max_err = 0;
+    std::vector<double> g1(w);  // the Gaussian is separable: exp(-dx^2 / 2 s^2) exp(-dy^2 / 2 s^2)
+    for (int dd = -R; dd <= R; ++dd) g1[dd + R] = std::exp(-(double)(dd * dd) / (2.0 * d.sigma_s * d.sigma_s));
     for (int dy = -R; dy <= R; ++dy)
         for (int dx = -R; dx <= R; ++dx) {
             const double r2 = (double)(dx * dx + dy * dy);
             double ks = d.spatial == BF_KERNEL_BOX           ? 1.0
                         : d.spatial == BF_KERNEL_EXPONENTIAL ? std::exp(-std::sqrt(r2) / d.sigma_s)
-                                                             : std::exp(-r2 / (2.0 * d.sigma_s * d.sigma_s));
+                                                             : g1[dx + R] * g1[dy + R];
             p.spatial_max_err = std::max(p.spatial_max_err, std::fabs(ks - p.kernel[(size_t)(dy + R) * w + dx + R]));
         }
 
