@@ -83,6 +83,16 @@ double spatial_profile(int kind, double sigma, double x) {
     return std::exp(-x * x / (2.0 * sigma * sigma));
 }
 
+// int_a^b exp(-x^2 / (2 sigma^2)) dx (a <= b) in closed form, sigma sqrt(pi / 2) (erf(b') - erf(a')) with
+// x' = x / (sigma sqrt 2), written with erfc on a one-signed interval so that a tail interval keeps its
+// relative accuracy (no difference of two numbers near 1).
+double gauss_int(double a, double b, double sigma) {
+    const double s = 1.0 / (sigma * std::sqrt(2.0)), k = sigma * std::sqrt(0.5 * kPi);
+    if (a >= 0) return k * (std::erfc(a * s) - std::erfc(b * s));
+    if (b <= 0) return k * (std::erfc(-b * s) - std::erfc(-a * s));
+    return k * (std::erf(b * s) + std::erf(-a * s));
+}
+
 // ---------------------------------------------------------------- Haar system
 
 // One 1-D Haar function on [-T, T]: +1 on [lo, mid], -1 on [mid, hi]; phi has lev = -1.
@@ -540,6 +550,7 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
     const int n1 = (int)dict.size();
     auto prof_int = [&](double a, double b) {
         if (d.spatial == BF_KERNEL_BOX) return b - a;
+        if (d.spatial == BF_KERNEL_GAUSSIAN) return gauss_int(a, b, d.sigma_s);
         int pieces = std::max(1, (int)std::ceil((b - a) / (0.5 * d.sigma_s)));
         return integrate([&](double x) { return spatial_profile(d.spatial, d.sigma_s, x); }, a, b, pieces);
     };
