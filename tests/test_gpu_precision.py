@@ -43,11 +43,16 @@ def filt(plan, img):
     return dst.cpu().numpy().astype(np.float64)
 
 
-def check_bound(got, img, kw, u, nk, den_eps):
+def oracle_outputs(img, kw):
+    """The FP64 oracle's output, denominator and plan for one image and parameter set."""
+    ref, _, den = O.approx_fast(img.astype(np.float64), O.Desc(**kw), threads=THREADS, return_den=True)
+    return ref, den, O.plan_info(O.Desc(**kw))
+
+
+def check_bound(got, img, kw, u, nk, den_eps, orc=None):
     """Every pixel within the bound above (pixels within 10x of the denominator guard excluded, where the fp32
     and fp64 guard decisions may differ); returns (max-abs error, PSNR) against the oracle."""
-    ref, _, den = O.approx_fast(img.astype(np.float64), O.Desc(**kw), threads=THREADS, return_den=True)
-    p = O.plan_info(O.Desc(**kw))
+    ref, den, p = orc if orc is not None else oracle_outputs(img, kw)
     mass = window_mass(img.shape, p.Ks)
     ks = np.asarray(p.ks)
     ak = np.abs(np.asarray(p.ak))
@@ -120,6 +125,22 @@ def test_16bit_basis_full_size_and_accuracy_against_exact(prec):
         torch.cuda.synchronize()
         mse = float(np.mean((got - ex.cpu().numpy().astype(np.float64)) ** 2))
         assert 10 * np.log10(1.0 / mse) >= 40.0
+
+
+def test_16bit_basis_4k_two_groups_within_its_bound():
+    """The large-image workload at 3840x2160 (objects x2), sigma_s = 16, sigma_r = 0.1, N_r = 16: fp16 and bf16
+    basis storage (the pre-pass variants, three term groups and the finalize pass) in their autotuned geometries,
+    every pixel within the bound against the FP64 oracle, and >= 40 dB against it."""
+    img = synth.shapes(2160, 3840, seed=0, scale=2.0)
+    kw = dict(sigma_s=16.0, sigma_r=0.1, nr_terms=16, ns_terms=5)
+    orc = oracle_outputs(img, kw)
+    for prec in (bf.PREC_FP16, bf.PREC_BF16):
+        plan = bf.Plan(device=0, precision=prec, **kw)
+        info = bf.bf_autotune(plan, 2160, 3840)
+        assert info["pre"] == (2 if prec == bf.PREC_FP16 else 3) and info["groups"] >= 2
+        got = filt(plan, img)
+        _, psnr = check_bound(got, img, kw, U[prec], info["nk"], plan.coeffs()["den_eps"], orc=orc)
+        assert psnr >= 40.0, (prec, psnr)
 
 
 def test_16bit_plans_in_batches_and_rejected_for_the_3d_form():
