@@ -487,7 +487,7 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
         // m = 2), 4 + k_max L / (4 P) pieces,
         // serves every candidate: a_k = (2 - [k = 0]) / P sum_i w_i K_r(t_i)
         // cos(pi k t_i / P).  cos(k theta_i) comes from the angle-addition recurrence over k, all nodes at once,
-        // re-anchored by a direct cos / sin every 16 frequencies so its rounding stays within ~16 ulp.
+        // re-anchored by a direct cos / sin every 64 frequencies so its rounding stays within ~64 ulp (~1e-14).
         const GaussLegendre &gq = gl20();
         const int pieces = L > 0 ? 4 + (int)std::ceil(0.25 * (ncand - 1) * L / p.P) : 0;
         const int ng = (int)gq.x.size(), nn = pieces * ng;
@@ -511,7 +511,7 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
         for (int n0 = 0; n0 < nn; n0 += 256) {
             const int n1 = std::min(nn, n0 + 256);
             for (int k = 0; k < ncand; ++k) {
-                if (k % 16 == 0)
+                if (k % 64 == 0)
                     for (int n = n0; n < n1; ++n) {
                         ck[n] = k == 0 ? 1.0 : std::cos(k * th[n]);
                         sk[n] = k == 0 ? 0.0 : std::sin(k * th[n]);
@@ -671,19 +671,30 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
     }
     // the 3-D form keeps the series only inside the range box [-T_r, T_r]
     const double tspan = d.policy == BF_RANGE_PAPER_3D ? std::min(dI, p.Tr) : dI;
-    for (int i = 0; !haar_range && i <= 2000; ++i) {
-        // cos(pi k t / P) for k = 0 .. k_max by the angle-addition recurrence (a report: ~k_max ulp is ample);
-        // 2001 samples, tens per period of the highest selected frequency
-        double t = -tspan + 2.0 * tspan * i / 2000.0, s = 0;
-        const double th = kPi * t / p.P, cth = std::cos(th), sth = std::sin(th);
-        double ck = 1.0, sk = 0.0;
-        for (int k = 0, j = 0; j < (int)p.k.size(); ++k) {
-            if (p.k[j] == k) s += p.a[j++] * ck;
-            const double cn = ck * cth - sk * sth;
-            sk = sk * cth + ck * sth;
-            ck = cn;
+    if (!haar_range) {
+        // the series at 2001 samples, tens per period of the highest selected frequency: cos(pi k t / P) for
+        // k = 0 .. k_max by the angle-addition recurrence (a report: ~k_max ulp is ample), all samples at once
+        constexpr int ns = 2001;
+        std::vector<double> ts(ns), cth(ns), sth(ns), ck(ns, 1.0), sk(ns, 0.0), sum(ns, 0.0);
+        for (int i = 0; i < ns; ++i) {
+            ts[i] = -tspan + 2.0 * tspan * i / (ns - 1.0);
+            const double th = kPi * ts[i] / p.P;
+            cth[i] = std::cos(th);
+            sth[i] = std::sin(th);
         }
-        p.range_max_err = std::max(p.range_max_err, std::fabs(s - range_value(d.range, d.sigma_r, t)));
+        for (int k = 0, j = 0; j < (int)p.k.size(); ++k) {
+            if (p.k[j] == k) {
+                const double a = p.a[j++];
+                for (int i = 0; i < ns; ++i) sum[i] += a * ck[i];
+            }
+            for (int i = 0; i < ns; ++i) {
+                const double cn = ck[i] * cth[i] - sk[i] * sth[i];
+                sk[i] = sk[i] * cth[i] + ck[i] * sth[i];
+                ck[i] = cn;
+            }
+        }
+        for (int i = 0; i < ns; ++i)
+            p.range_max_err = std::max(p.range_max_err, std::fabs(sum[i] - range_value(d.range, d.sigma_r, ts[i])));
     }
     p.spatial_max_err = 0;
     std::vector<double> g1(w);  // the Gaussian is separable: exp(-dx^2 / 2 s^2) exp(-dy^2 / 2 s^2)
