@@ -516,9 +516,13 @@ bf_status build(const bf_plan_desc &d, bf_plan &p) {
                         ck[n] = k == 0 ? 1.0 : std::cos(k * th[n]);
                         sk[n] = k == 0 ? 0.0 : std::sin(k * th[n]);
                     }
-                double a = 0.0;
-                for (int n = n0; n < n1; ++n) a += f[n] * ck[n];
-                acc[k] += a;
+                // eight partial sums: independent chains the compiler can keep in vector registers
+                double part[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                int n = n0;
+                for (; n + 8 <= n1; n += 8)
+                    for (int u = 0; u < 8; ++u) part[u] += f[n + u] * ck[n + u];
+                for (; n < n1; ++n) part[0] += f[n] * ck[n];
+                acc[k] += ((part[0] + part[1]) + (part[2] + part[3])) + ((part[4] + part[5]) + (part[6] + part[7]));
                 for (int n = n0; n < n1; ++n) {
                     const double cn = ck[n] * c1[n] - sk[n] * s1[n];
                     sk[n] = sk[n] * c1[n] + ck[n] * s1[n];
